@@ -1,0 +1,260 @@
+"""Seeded synthetic inputs for the column radiative-transfer solver.
+
+This module only draws inputs.  It holds none of the solver's arithmetic and
+is the one piece of code that the oracle side and the CUDA side share.
+
+The paper's WASP-43b opacities (HELIOS-K k-tables, Sec. 2.1.3) and PHOENIX
+stellar template (Sec. 2.1.5) are not available, so seeded random inputs with
+the paper's shapes stand in for them:
+
+* 2562 columns (icosahedral g_level = 4, Sec. 2.1.1), 40 layers, 30 bins
+  uniform in wavenumber over 0.3-200 um, 20 Gauss points per bin (Sec. 2.1.3);
+* pressure log-spaced from 1e-6 to 100 bar (layer 0 at the top);
+* T linear in log p from 800 K (top) to 2000 K (bottom) plus N(0, 50 K) per
+  layer centre; interface T linear in log p between centres, extrapolated at
+  the ends (Sec. 2.2.1);
+* cos(theta*) uniform in [0.1, 1] per column;
+* g = 47 m s^-2, c_P = 12436 J kg^-1 K^-1, eps2 = 2/3, T_int = 100 K
+  (Table 3, Sec. 3.1);
+* stellar flux per bin: a 4798 K blackbody (Table 3) evaluated at the bin
+  centre times the bin width, times pi (R*/a)^2 -- a crude stand-in for the
+  bin-averaged PHOENIX template.
+
+Layout: cubes are float32 ``[column][layer][bin][g]`` with g fastest, columns
+packed back to back; per-column arrays are float64.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+WN_MIN = 50.0            # cm^-1  (200 um)
+WN_MAX = 1.0e4 / 0.3     # cm^-1  (0.3 um)
+GRAV = 47.0
+CP = 12436.0
+EPS2 = 2.0 / 3.0
+T_INT = 100.0
+T_STAR = 4798.0
+R_STAR = 4.64e8
+A_ORBIT = 2.28e9
+P_TOP_BAR = 1e-6
+P_BOT_BAR = 100.0
+
+_H, _C, _KB = 6.62607015e-34, 299792458.0, 1.380649e-23
+
+
+@dataclass
+class Columns:
+    """A packed batch of atmospheric columns (host arrays)."""
+    n_layers: np.ndarray        # int32 [C]
+    n_bins: np.ndarray          # int32 [C]
+    n_g: int
+    g_weights: np.ndarray       # float64 [n_g], sum = 1
+    dtau: np.ndarray            # float32 [sum L_c*NB_c*n_g]
+    w0: np.ndarray              # float32, same layout
+    g0: np.ndarray              # float32, same layout
+    T_center: np.ndarray        # float64 [sum L_c]
+    T_iface: np.ndarray         # float64 [sum (L_c+1)]
+    p_iface: np.ndarray         # float64 [sum (L_c+1)], Pa
+    mu_star: np.ndarray         # float64 [C]
+    F_star: np.ndarray          # float64 [sum NB_c], W m^-2 normal to the beam
+    consts: dict = field(default_factory=dict)
+    name: str = ""
+
+    @property
+    def n_cols(self) -> int:
+        return int(self.n_layers.size)
+
+    @property
+    def n_systems(self) -> int:
+        return int((self.n_bins.astype(np.int64) * self.n_g).sum())
+
+    def offsets(self):
+        L = self.n_layers.astype(np.int64)
+        NB = self.n_bins.astype(np.int64)
+        z = lambda a: np.concatenate([[0], np.cumsum(a)])
+        return dict(cube=z(L * NB * self.n_g), lay=z(L), iface=z(L + 1), bins=z(NB))
+
+    def subset(self, idx) -> "Columns":
+        """The columns ``idx`` (in that order) as a new packed batch."""
+        idx = np.asarray(idx, dtype=np.int64)
+        o = self.offsets()
+        cat = lambda a, key: np.concatenate([a[o[key][i]:o[key][i + 1]] for i in idx]) \
+            if idx.size else a[:0]
+        return replace(self, n_layers=self.n_layers[idx].copy(), n_bins=self.n_bins[idx].copy(),
+                       dtau=cat(self.dtau, "cube"), w0=cat(self.w0, "cube"),
+                       g0=cat(self.g0, "cube"), T_center=cat(self.T_center, "lay"),
+                       T_iface=cat(self.T_iface, "iface"), p_iface=cat(self.p_iface, "iface"),
+                       mu_star=self.mu_star[idx].copy(), F_star=cat(self.F_star, "bins"),
+                       name=self.name + f"[{idx.size} cols]")
+
+    @property
+    def nbytes_inputs(self) -> int:
+        return sum(a.nbytes for a in (self.dtau, self.w0, self.g0, self.T_center,
+                                      self.T_iface, self.p_iface, self.mu_star, self.F_star))
+
+
+def gauss_legendre_01(n: int):
+    """Gauss-Legendre nodes and weights on [0, 1]; weights sum to 1."""
+    if n == 1:
+        return np.array([0.5]), np.array([1.0])
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def stellar_flux_bins(n_bins: int, wn_min: float = WN_MIN, wn_max: float = WN_MAX):
+    """Stand-in stellar spectrum per bin, W m^-2 normal to the beam."""
+    edges = np.linspace(wn_min, wn_max, n_bins + 1) * 100.0    # m^-1
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    width = np.diff(edges)
+    x = _H * _C * mid / (_KB * T_STAR)
+    b_mid = 2.0 * _H * _C ** 2 * mid ** 3 / np.expm1(x)
+    return np.pi * b_mid * width * (R_STAR / A_ORBIT) ** 2
+
+
+def _profile(rng, L: int):
+    """Pressure grid (Pa) and temperatures of one column, layer 0 at the top."""
+    lp = np.linspace(np.log(P_TOP_BAR), np.log(P_BOT_BAR), L + 1)
+    p_if = np.exp(lp) * 1.0e5
+    lpc = 0.5 * (lp[1:] + lp[:-1])
+    frac = (lpc - lp[0]) / (lp[-1] - lp[0])
+    Tc = 800.0 + 1200.0 * frac + rng.normal(0.0, 50.0, L)
+    Ti = np.empty(L + 1)
+    if L == 1:
+        Ti[:] = Tc[0]
+    else:
+        Ti[1:L] = Tc[:-1] + (Tc[1:] - Tc[:-1]) * (lp[1:L] - lpc[:-1]) / (lpc[1:] - lpc[:-1])
+        Ti[0] = Tc[0] + (Tc[1] - Tc[0]) * (lp[0] - lpc[0]) / (lpc[1] - lpc[0])
+        Ti[L] = Tc[-2] + (Tc[-1] - Tc[-2]) * (lp[L] - lpc[-2]) / (lpc[-1] - lpc[-2])
+    Ti = np.maximum(Ti, 10.0)
+    Tc = np.maximum(Tc, 10.0)
+    return p_if, Tc, Ti
+
+
+def _consts():
+    return dict(T_int=T_INT, grav=GRAV, cp=CP, eps2=EPS2, wn_min=WN_MIN, wn_max=WN_MAX)
+
+
+def generate(n_layers, n_bins, n_g: int, seed: int, optics: str = "uniform",
+             name: str = "", mu_range=(0.1, 1.0)) -> Columns:
+    """Draw a packed batch.
+
+    optics:
+      "uniform"  dtau ~ logU[1e-6, 10], w0 ~ U[0, 0.95], g0 ~ U[0, 0.8]
+      "ktable"   k ~ logU[1e-8, 1] m^2/kg sorted ascending over g within each
+                 (column, layer, bin); dtau = k dp / g; w0, g0 as "uniform"
+      "stress"   dtau ~ logU[1e-8, 1e4], w0 ~ U[0.99, 1-1e-6], g0 ~ U[0.5, 0.95]
+    """
+    rng = np.random.default_rng(seed)
+    n_layers = np.asarray(n_layers, dtype=np.int32)
+    n_bins = np.asarray(n_bins, dtype=np.int32)
+    C = n_layers.size
+    gx, gw = gauss_legendre_01(n_g)
+    Tc_all, Ti_all, p_all, Fs_all = [], [], [], []
+    cubes = {k: [] for k in ("dtau", "w0", "g0")}
+    mu = rng.uniform(mu_range[0], mu_range[1], C)
+    fs_cache = {}
+    for c in range(C):
+        L, NB = int(n_layers[c]), int(n_bins[c])
+        p_if, Tc, Ti = _profile(rng, L)
+        shape = (L, NB, n_g)
+        if optics == "uniform":
+            dtau = np.exp(rng.uniform(np.log(1e-6), np.log(10.0), shape))
+            w0 = rng.uniform(0.0, 0.95, shape)
+            g0 = rng.uniform(0.0, 0.8, shape)
+        elif optics == "ktable":
+            k = np.sort(rng.uniform(np.log(1e-8), np.log(1.0), shape), axis=-1)
+            dp = np.diff(p_if)[:, None, None]
+            dtau = np.exp(k) * dp / GRAV
+            w0 = rng.uniform(0.0, 0.95, shape)
+            g0 = rng.uniform(0.0, 0.8, shape)
+        elif optics == "stress":
+            dtau = np.exp(rng.uniform(np.log(1e-8), np.log(1e4), shape))
+            w0 = rng.uniform(0.99, 1.0 - 1e-6, shape)
+            g0 = rng.uniform(0.5, 0.95, shape)
+        else:
+            raise ValueError(optics)
+        cubes["dtau"].append(dtau.astype(np.float32).ravel())
+        cubes["w0"].append(w0.astype(np.float32).ravel())
+        cubes["g0"].append(g0.astype(np.float32).ravel())
+        Tc_all.append(Tc); Ti_all.append(Ti); p_all.append(p_if)
+        if NB not in fs_cache:
+            fs_cache[NB] = stellar_flux_bins(NB)
+        Fs_all.append(fs_cache[NB])
+    cat = lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt)
+    return Columns(n_layers=n_layers, n_bins=n_bins, n_g=n_g, g_weights=gw,
+                   dtau=cat(cubes["dtau"], np.float32), w0=cat(cubes["w0"], np.float32),
+                   g0=cat(cubes["g0"], np.float32), T_center=cat(Tc_all, np.float64),
+                   T_iface=cat(Ti_all, np.float64), p_iface=cat(p_all, np.float64),
+                   mu_star=mu, F_star=cat(Fs_all, np.float64), consts=_consts(), name=name)
+
+
+def generate_fast(n_cols: int, L: int, NB: int, n_g: int, seed: int, optics: str,
+                  name: str = "") -> Columns:
+    """Uniform-shape batch drawn with whole-array numpy calls (large configs)."""
+    rng = np.random.default_rng(seed)
+    gx, gw = gauss_legendre_01(n_g)
+    prof = [_profile(rng, L) for _ in range(n_cols)]
+    p_if = np.stack([p[0] for p in prof])
+    Tc = np.stack([p[1] for p in prof])
+    Ti = np.stack([p[2] for p in prof])
+    mu = rng.uniform(0.1, 1.0, n_cols)
+    shape = (n_cols, L, NB, n_g)
+    if optics == "ktable":
+        k = rng.uniform(np.log(1e-8), np.log(1.0), shape).astype(np.float32)
+        k.sort(axis=-1)
+        dp = (np.diff(p_if, axis=1) / GRAV).astype(np.float32)[:, :, None, None]
+        dtau = (np.exp(k) * dp).astype(np.float32)
+        del k
+        w0 = rng.uniform(0.0, 0.95, shape).astype(np.float32)
+        g0 = rng.uniform(0.0, 0.8, shape).astype(np.float32)
+    elif optics == "stress":
+        dtau = np.exp(rng.uniform(np.log(1e-8), np.log(1e4), shape)).astype(np.float32)
+        w0 = rng.uniform(0.99, 1.0 - 1e-6, shape).astype(np.float32)
+        g0 = rng.uniform(0.5, 0.95, shape).astype(np.float32)
+    elif optics == "uniform":
+        dtau = np.exp(rng.uniform(np.log(1e-6), np.log(10.0), shape)).astype(np.float32)
+        w0 = rng.uniform(0.0, 0.95, shape).astype(np.float32)
+        g0 = rng.uniform(0.0, 0.8, shape).astype(np.float32)
+    else:
+        raise ValueError(optics)
+    return Columns(n_layers=np.full(n_cols, L, np.int32), n_bins=np.full(n_cols, NB, np.int32),
+                   n_g=n_g, g_weights=gw, dtau=dtau.ravel(), w0=w0.ravel(), g0=g0.ravel(),
+                   T_center=Tc.ravel(), T_iface=Ti.ravel(), p_iface=p_if.ravel(),
+                   mu_star=mu, F_star=np.tile(stellar_flux_bins(NB), n_cols),
+                   consts=_consts(), name=name)
+
+
+# ----------------------------------------------------------------------
+# The five workloads.
+# ----------------------------------------------------------------------
+
+def config0(seed: int = 0) -> Columns:
+    """Plain FP64 case: 64 x 40 layers x 30 bins x 1 g-point, seed 0."""
+    return generate([40] * 64, [30] * 64, 1, seed, "uniform", name="config0 64x40x30x1")
+
+
+def config1(n_cols: int = 2562, seed: int = 1) -> Columns:
+    """GCM-shaped: 2562 x 40 x 30 x 20 Gauss points, k-table optical depths."""
+    return generate_fast(n_cols, 40, 30, 20, seed, "ktable",
+                         name=f"config1 {n_cols}x40x30x20")
+
+
+def config2(n_cols: int = 2562, seed: int = 2) -> Columns:
+    """Precision stress: w0 in [0.99, 1-1e-6], dtau in [1e-8, 1e4], g0 in [0.5, 0.95]."""
+    return generate_fast(n_cols, 40, 30, 20, seed, "stress",
+                         name=f"config2 {n_cols}x40x30x20")
+
+
+def uneven_shapes(n_cols: int, seed: int, L_range=(20, 200), NB_range=(30, 300)):
+    rng = np.random.default_rng(seed + 1000)
+    L = rng.integers(L_range[0], L_range[1] + 1, n_cols).astype(np.int32)
+    NB = rng.integers(NB_range[0], NB_range[1] + 1, n_cols).astype(np.int32)
+    return L, NB
+
+
+def config3(n_cols: int = 4096, seed: int = 3) -> Columns:
+    """Uneven batch: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g-points, optics as config 0."""
+    L, NB = uneven_shapes(n_cols, seed)
+    return generate(L, NB, 20, seed, "uniform", name=f"config3 {n_cols} uneven")

@@ -1,0 +1,400 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's closed forms.  The references are:
+the two-stream ODE solved with matrix exponentials (tests/twostream_ode.py),
+a dense LU of the assembled block system, scipy quadrature of the Planck
+function, sigma T^4 / pi, Beer's law, the conservative two-stream layer
+t = 1/(1 + (1 - g0) dtau), flux conservation, layer-splitting invariance, the
+O(m^-2) convergence of thin isothermal layers to a non-isothermal layer, and
+the telescoping of the heating rate.
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+import rt_synth
+import twostream_ode as ode
+
+H, C, KB = 6.62607015e-34, 299792458.0, 1.380649e-23
+SIGMA = 2 * np.pi ** 5 * KB ** 4 / (15 * H ** 3 * C ** 2)   # exact in SI
+WN_MIN, WN_MAX = 50.0, 1e4 / 0.3
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def planck_quad(T, lo, hi):
+    """Bin integral of the Planck function by adaptive quadrature (scipy)."""
+    f = lambda nu: 2 * H * C ** 2 * (nu * 100) ** 3 / np.expm1(H * C * nu * 100 / (KB * T)) * 100
+    v, _ = integrate.quad(f, lo, hi, epsabs=0, epsrel=1e-13, limit=200)
+    return v
+
+
+def random_column(rng, L, tau_lo=2e-3, tau_hi=2.0, w_hi=0.95):
+    dtau = f32(np.exp(rng.uniform(np.log(tau_lo), np.log(tau_hi), L)))
+    w0 = f32(rng.uniform(0.0, w_hi, L))
+    g0 = f32(rng.uniform(0.0, 0.8, L))
+    Bc = rng.uniform(1e3, 5e4, L)
+    Bi = rng.uniform(1e3, 5e4, L + 1)
+    return dtau, w0, g0, Bc, Bi
+
+
+def rel_err(a, b):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return np.max(np.abs(a - b)) / scale
+
+
+# ----------------------------------------------------------------------
+# Planck per bin (reading R13)
+# ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("T", [100.0, 800.0, 2000.0, 4798.0])
+def test_planck_bins_sum_to_sigma_T4_over_pi(orc, T):
+    wn_top = 60.0 * KB * T / (H * C) / 100.0      # x = 60: tail below 1e-20
+    edges = np.linspace(1e-9, wn_top, 301)
+    tot = sum(orc.planck_bin(T, a, b) for a, b in zip(edges[:-1], edges[1:]))
+    assert abs(tot - SIGMA * T ** 4 / np.pi) <= 1e-11 * SIGMA * T ** 4 / np.pi
+
+
+@pytest.mark.parametrize("T,nb,b", [(100.0, 30, 0), (100.0, 30, 5), (800.0, 30, 0), (800.0, 30, 29),
+                                     (2000.0, 30, 3), (2000.0, 300, 150), (1500.0, 7, 6)])
+def test_planck_bin_vs_scipy_quad(orc, T, nb, b):
+    d = (WN_MAX - WN_MIN) / nb
+    lo, hi = WN_MIN + b * d, WN_MIN + (b + 1) * d
+    ref = planck_quad(T, lo, hi)
+    assert abs(orc.planck_bin(T, lo, hi) - ref) <= 1e-10 * abs(ref)
+
+
+def test_planck_zero_temperature(orc):
+    assert orc.planck_bin(0.0, 50.0, 100.0) == 0.0
+
+
+# ----------------------------------------------------------------------
+# Block Thomas (Eqs. 13-15) against a dense LU of the same system
+# ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("iso", [False, True])
+@pytest.mark.parametrize("L", [1, 2, 3, 6])
+def test_block_thomas_matches_dense_lu(orc, iso, L):
+    rng = np.random.default_rng(100 + L + 10 * iso)
+    for trial in range(5):
+        dtau, w0, g0, Bc, Bi = random_column(rng, L, 1e-5, 30.0)
+        mu = rng.uniform(0.05, 1.0) if trial % 2 == 0 else -0.3
+        cfg = oracle.OracleConfig(isothermal=iso, F_toa=rng.uniform(0, 10))
+        A, B, Cm, D, Fb = orc.assemble(cfg, dtau, w0, g0, Bc, Bi, mu, 1e5, 5.0)
+        n = A.shape[0] - 1
+        M = np.zeros((2 * (n + 1), 2 * (n + 1)))
+        for i in range(n + 1):
+            M[2 * i:2 * i + 2, 2 * i:2 * i + 2] = B[i]
+            if i > 0:
+                M[2 * i:2 * i + 2, 2 * i - 2:2 * i] = A[i]
+            if i < n:
+                M[2 * i:2 * i + 2, 2 * i + 2:2 * i + 4] = Cm[i]
+        x_lu = np.linalg.solve(M, D.ravel())
+        x_th = orc.block_thomas(A, B, Cm, D).ravel()
+        assert rel_err(x_th, x_lu) < 1e-12
+
+
+# ----------------------------------------------------------------------
+# Whole column against the two-stream ODE boundary-value problem
+# ----------------------------------------------------------------------
+
+ZENITH = [0.0, 30.0, 60.0, 89.0]   # the 1-D benchmark angles of Sec. 3
+
+
+@pytest.mark.parametrize("iso", [False, True])
+@pytest.mark.parametrize("improved", [True, False])
+@pytest.mark.parametrize("zenith", ZENITH + [None])
+def test_column_matches_two_stream_ode(orc, iso, improved, zenith):
+    rng = np.random.default_rng(7 + 3 * iso + 5 * improved + int(zenith or 123))
+    for L in (1, 3, 5):
+        dtau, w0, g0, Bc, Bi = random_column(rng, L)
+        mu = np.cos(np.radians(zenith)) if zenith is not None else -1.0
+        F_TOA = 3.0 if L == 3 else 0.0
+        for eps2 in (2 / 3, 0.5):
+            cfg = oracle.OracleConfig(isothermal=iso, improved=improved, eps2=eps2, F_toa=F_TOA)
+            up, dn, fb = orc.solve_system(cfg, dtau, w0, g0, Bc, Bi, mu, 2e5, 5.0)
+            u2, d2, fb2 = ode.solve_column(dtau, w0, g0, Bc, Bi, mu, 2e5, 5.0, isothermal=iso,
+                                           improved=improved, eps2=eps2, F_TOA=F_TOA)
+            scale = max(np.abs(u2).max(), np.abs(d2).max())
+            assert np.max(np.abs(up - u2)) <= 1e-9 * scale
+            assert np.max(np.abs(dn - d2)) <= 1e-9 * scale
+            np.testing.assert_allclose(fb, fb2, rtol=1e-13, atol=0)
+
+
+def test_column_matches_ode_with_thin_sublayers(orc):
+    """Sub-layers below e_tau take the isothermal fallback on both sides."""
+    rng = np.random.default_rng(31)
+    dtau, w0, g0, Bc, Bi = random_column(rng, 6, 1e-5, 1.0)
+    dtau[1] = f32(1.5e-4)   # dtau/2 = 7.5e-5 < e_tau
+    dtau[3] = f32(2.5e-4)   # dtau/2 > e_tau
+    cfg = oracle.OracleConfig()
+    up, dn, _ = orc.solve_system(cfg, dtau, w0, g0, Bc, Bi, 0.6, 1e5, 5.0)
+    u2, d2, _ = ode.solve_column(dtau, w0, g0, Bc, Bi, 0.6, 1e5, 5.0)
+    scale = max(np.abs(u2).max(), np.abs(d2).max())
+    assert np.max(np.abs(up - u2)) <= 1e-9 * scale
+    assert np.max(np.abs(dn - d2)) <= 1e-9 * scale
+
+
+def test_raw_e_fit_matches_ode_where_defined(orc):
+    """With the clamp off (raw Eq. 19) the oracle still solves the ODE where E > w0."""
+    rng = np.random.default_rng(5)
+    dtau, w0, g0, Bc, Bi = random_column(rng, 4)
+    w0[:] = f32([0.97, 0.5, 0.99, 0.3])
+    g0[:] = f32([0.05, 0.3, 0.92, 0.1])
+    cfg = oracle.OracleConfig(e_clamp=False)
+    up, dn, _ = orc.solve_system(cfg, dtau, w0, g0, Bc, Bi, 0.7, 1e5, 5.0)
+    u2, d2, _ = ode.solve_column(dtau, w0, g0, Bc, Bi, 0.7, 1e5, 5.0, clamp=False)
+    scale = max(np.abs(u2).max(), np.abs(d2).max())
+    assert np.max(np.abs(up - u2)) <= 1e-9 * scale
+
+
+# ----------------------------------------------------------------------
+# Limits with closed forms
+# ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_pure_absorption_beam_is_beer_law(orc, iso):
+    rng = np.random.default_rng(11)
+    dtau, _, g0, Bc, Bi = random_column(rng, 8, 1e-3, 3.0)
+    w0 = np.zeros(8)
+    mu, Fs = 0.37, 1.3e5
+    cfg = oracle.OracleConfig(isothermal=iso)
+    _, _, fb = orc.solve_system(cfg, dtau, w0, g0, Bc, Bi, mu, Fs, 0.0)
+    sub = dtau if iso else np.repeat(dtau / 2, 2)
+    tau_top = np.concatenate([[0.0], np.cumsum(sub)])      # TOA first
+    np.testing.assert_allclose(fb[::-1], mu * Fs * np.exp(-tau_top / mu), rtol=1e-14)
+
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_pure_absorption_no_emission(orc, iso):
+    """w0 = 0, B = 0, no beam, F_TOA = 0: F_dn = 0 and F_up decays as exp(-2 dtau)."""
+    rng = np.random.default_rng(12)
+    dtau, _, g0, _, _ = random_column(rng, 7, 1e-3, 2.0)
+    L = 7
+    cfg = oracle.OracleConfig(isothermal=iso)
+    up, dn, _ = orc.solve_system(cfg, dtau, np.zeros(L), g0, np.zeros(L), np.zeros(L + 1),
+                                 -1.0, 0.0, 4.2)
+    sub = (dtau if iso else np.repeat(dtau / 2, 2))[::-1]  # BOA first
+    depth = np.concatenate([[0.0], np.cumsum(sub)])        # optical depth above the BOA
+    np.testing.assert_allclose(up, 4.2 * np.exp(-2 * depth), rtol=1e-13)
+    assert np.max(np.abs(dn)) <= 1e-14 * 4.2
+
+
+def test_opaque_absorbing_isothermal_layer_emits_pi_B(orc):
+    """w0 = 0 isothermal layers: F_up,top = T F_up,bot + pi B (1 - T), T = exp(-2 dtau)."""
+    rng = np.random.default_rng(13)
+    dtau, _, g0, Bc, _ = random_column(rng, 5, 1e-2, 40.0)
+    cfg = oracle.OracleConfig(isothermal=True)
+    up, dn, _ = orc.solve_system(cfg, dtau, np.zeros(5), g0, Bc, np.zeros(6), -1.0, 0.0, 7.0)
+    Bb = Bc[::-1]
+    d = dtau[::-1]
+    for j in range(5):
+        T = np.exp(-2 * d[j])
+        assert abs(up[j + 1] - (T * up[j] + np.pi * Bb[j] * (1 - T))) <= 1e-12 * up.max()
+
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_pure_scattering_conserves_net_flux(orc, iso):
+    """w0 = 1, regular two-stream, no emission, reflecting BOA: F_up - F_dn - F_beam = 0."""
+    rng = np.random.default_rng(14)
+    L = 9
+    dtau, _, g0, _, _ = random_column(rng, L, 1e-3, 5.0)
+    cfg = oracle.OracleConfig(isothermal=iso, improved=False, T_int=0.0)
+    mu, Fs = 0.55, 1e5
+    up, dn, fb = orc.solve_system(cfg, dtau, np.ones(L), g0, np.zeros(L), np.zeros(L + 1),
+                                  mu, Fs, 0.0)
+    assert np.max(np.abs(up - dn - fb)) <= 1e-11 * mu * Fs
+    # same for w0 just below 1 (literal branch, k > 0): conservation to O(1 - w0)
+    w0 = np.full(L, np.float32(1 - 6e-8), dtype=np.float64)
+    up, dn, fb = orc.solve_system(cfg, dtau, w0, g0, np.zeros(L), np.zeros(L + 1), mu, Fs, 0.0)
+    assert np.max(np.abs(up - dn - fb)) <= 1e-5 * mu * Fs
+
+
+@pytest.mark.parametrize("g0v", [0.0, 0.3, 0.85])
+@pytest.mark.parametrize("dt", [1e-3, 0.5, 7.0])
+def test_conservative_layer_transmission(orc, g0v, dt):
+    """A conservative (w0 = 1, E = 1) layer over a black absorber: the textbook
+    two-stream transmissivity t = 1/(1 + (1 - g0) dtau) and r = 1 - t."""
+    cfg = oracle.OracleConfig(isothermal=True, improved=False, T_int=0.0, F_toa=1.0)
+    dtau = np.array([dt, 60.0])         # API order: TOA layer first
+    w0 = np.array([1.0, 0.0])
+    g0 = np.float32(g0v)
+    up, dn, _ = orc.solve_system(cfg, dtau, w0, np.array([g0, 0.0]), np.zeros(2), np.zeros(3),
+                                 -1.0, 0.0, 0.0)
+    t = 1.0 / (1.0 + (1.0 - float(g0)) * float(np.float32(dt)))
+    # levels BOA first: 0 BOA, 1 interface, 2 TOA
+    assert abs(dn[1] - t) <= 1e-12
+    assert abs(up[2] - (1.0 - t)) <= 1e-12
+
+
+# ----------------------------------------------------------------------
+# Invariances
+# ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_layer_splitting_invariance(orc, iso):
+    rng = np.random.default_rng(15)
+    L = 6
+    dtau, w0, g0, Bc, Bi = random_column(rng, L, 1e-3, 3.0)
+    dtau = f32(np.round(dtau * 2 ** 12) / 2 ** 12 + 2 ** -10)   # exactly halvable
+    cfg = oracle.OracleConfig(isothermal=iso)
+    mu, Fs = 0.66, 1e5
+    up, dn, fb = orc.solve_system(cfg, dtau, w0, g0, Bc, Bi, mu, Fs, 5.0)
+    d2 = np.repeat(dtau / 2, 2)
+    w2, g2 = np.repeat(w0, 2), np.repeat(g0, 2)
+    if iso:
+        Bc2, Bi2 = np.repeat(Bc, 2), np.zeros(2 * L + 1)
+    else:
+        Bc2 = np.empty(2 * L)
+        Bi2 = np.empty(2 * L + 1)
+        for l in range(L):
+            Bc2[2 * l] = 0.5 * (Bi[l] + Bc[l])
+            Bc2[2 * l + 1] = 0.5 * (Bc[l] + Bi[l + 1])
+            Bi2[2 * l] = Bi[l]
+            Bi2[2 * l + 1] = Bc[l]
+        Bi2[2 * L] = Bi[L]
+    u2, dn2, fb2 = orc.solve_system(cfg, d2, w2, g2, Bc2, Bi2, mu, Fs, 5.0)
+    step = 1 if iso else 2
+    idx = np.arange(0, up.size) * 2 if iso else np.arange(0, up.size, step) * 2
+    ifc = np.arange(L + 1) * step             # interfaces in the coarse column
+    scale = max(np.abs(up).max(), np.abs(dn).max())
+    assert np.max(np.abs(up[ifc] - u2[2 * ifc])) <= 1e-10 * scale
+    assert np.max(np.abs(dn[ifc] - dn2[2 * ifc])) <= 1e-10 * scale
+
+
+def test_isothermal_sublayers_converge_to_nonisothermal(orc):
+    """m thin isothermal layers per sub-layer, B sampled at their centres from
+    the piecewise-linear B(tau) of the non-isothermal column: error ~ m^-2."""
+    rng = np.random.default_rng(16)
+    L = 4
+    dtau, w0, g0, Bc, Bi = random_column(rng, L, 0.05, 1.5)
+    mu, Fs = 0.8, 1e5
+    ref_up, ref_dn, _ = orc.solve_system(oracle.OracleConfig(), dtau, w0, g0, Bc, Bi, mu, Fs, 5.0)
+    errs = []
+    for m in (4, 8, 16):
+        d, a, g, B = [], [], [], []
+        for l in range(L):
+            for (Bt, Bb) in ((Bi[l], Bc[l]), (Bc[l], Bi[l + 1])):
+                for s in range(m):
+                    x = (s + 0.5) / m
+                    d.append(dtau[l] / (2 * m)); a.append(w0[l]); g.append(g0[l])
+                    B.append(Bt + (Bb - Bt) * x)
+        up, dn, _ = orc.solve_system(oracle.OracleConfig(isothermal=True), np.array(d, np.float64),
+                                     np.array(a), np.array(g), np.array(B),
+                                     np.zeros(len(d) + 1), mu, Fs, 5.0)
+        # interfaces: iso level 2 m k  <->  non-iso level 2 k
+        ifc = np.arange(L + 1)
+        e = max(np.max(np.abs(up[2 * m * ifc] - ref_up[2 * ifc])),
+                np.max(np.abs(dn[2 * m * ifc] - ref_dn[2 * ifc])))
+        errs.append(e)
+    assert errs[0] > errs[1] > errs[2] > 0
+    for e1, e2 in zip(errs[:-1], errs[1:]):
+        assert 3.5 < e1 / e2 < 4.5
+
+
+# ----------------------------------------------------------------------
+# Batch driver: spectral sum, net flux, heating, boundary flux
+# ----------------------------------------------------------------------
+
+def tiny_batch(seed=0, iso=False):
+    return rt_synth.generate([3, 2], [2, 3], 2, seed, "uniform", name="tiny")
+
+
+@pytest.mark.parametrize("iso", [False, True])
+def test_batch_matches_ode_and_quadrature(orc, iso):
+    """The full batch path (Planck by the oracle, spectral sum, beam added to
+    F_down) against the ODE per system with Planck by scipy quadrature."""
+    cols = tiny_batch(3)
+    cols.dtau = np.maximum(cols.dtau, np.float32(3e-4))   # keep the ODE well-posed
+    cfg = oracle.OracleConfig(isothermal=iso)
+    out = orc.solve_columns(cfg, cols)
+    o = cols.offsets()
+    for c in range(cols.n_cols):
+        L, NB = int(cols.n_layers[c]), int(cols.n_bins[c])
+        Tc = cols.T_center[o["lay"][c]:o["lay"][c + 1]]
+        Ti = cols.T_iface[o["iface"][c]:o["iface"][c + 1]]
+        cube = lambda a: a[o["cube"][c]:o["cube"][c + 1]].reshape(L, NB, cols.n_g)
+        up_ref = np.zeros(L + 1); dn_ref = np.zeros(L + 1)
+        d = (WN_MAX - WN_MIN) / NB
+        for b in range(NB):
+            lo, hi = WN_MIN + b * d, WN_MIN + (b + 1) * d
+            Bc = np.array([planck_quad(T, lo, hi) for T in Tc])
+            Bi = np.array([planck_quad(T, lo, hi) for T in Ti])
+            FB = np.pi * planck_quad(100.0, lo, hi)
+            for g in range(cols.n_g):
+                u, dn, fb = ode.solve_column(f32(cube(cols.dtau)[:, b, g]), f32(cube(cols.w0)[:, b, g]),
+                                             f32(cube(cols.g0)[:, b, g]), Bc, Bi, cols.mu_star[c],
+                                             cols.F_star[o["bins"][c] + b], FB, isothermal=iso)
+                lev = (L - np.arange(L + 1)) * (1 if iso else 2)
+                up_ref += cols.g_weights[g] * u[lev]
+                dn_ref += cols.g_weights[g] * (dn[lev] + fb[lev])
+        sl = slice(o["iface"][c], o["iface"][c + 1])
+        scale = max(up_ref.max(), dn_ref.max())
+        assert np.max(np.abs(out["F_up"][sl] - up_ref)) <= 1e-9 * scale
+        assert np.max(np.abs(out["F_down"][sl] - dn_ref)) <= 1e-9 * scale
+        np.testing.assert_allclose(out["F_net"][sl], out["F_up"][sl] - out["F_down"][sl], rtol=0,
+                                   atol=1e-12 * scale)
+
+
+def test_heating_telescopes_to_boundary_net_fluxes(orc):
+    cols = rt_synth.generate([40, 12, 25], [30, 4, 7], 3, 9, "ktable")
+    out = orc.solve_columns(oracle.OracleConfig(), cols)
+    o = cols.offsets()
+    for c in range(cols.n_cols):
+        L = int(cols.n_layers[c])
+        p = cols.p_iface[o["iface"][c]:o["iface"][c + 1]]
+        net = out["F_net"][o["iface"][c]:o["iface"][c + 1]]
+        Q = out["Q"][o["lay"][c]:o["lay"][c + 1]]
+        lhs = np.sum(Q * np.diff(p)) * 12436.0 / 47.0
+        assert abs(lhs - (net[-1] - net[0])) <= 1e-9 * np.abs(net).max()
+
+
+def test_boa_net_flux_is_interior_flux(orc):
+    """Eq. 10: at the BOA F_net = F_BOA = sum_b pi B_b(T_int), beam or not."""
+    cols = rt_synth.generate([10, 10], [30, 30], 4, 4, "uniform")
+    out = orc.solve_columns(oracle.OracleConfig(), cols)
+    d = (WN_MAX - WN_MIN) / 30
+    fboa = sum(np.pi * planck_quad(100.0, WN_MIN + b * d, WN_MIN + (b + 1) * d) for b in range(30))
+    o = cols.offsets()
+    for c in range(2):
+        assert abs(out["F_net"][o["iface"][c + 1] - 1] - fboa) <= 1e-9 * out["F_up"].max()
+
+
+def test_resonance_rule_and_limit_mode(orc):
+    """Near mu alpha = 1 the paper switches D to 2 mu* when |D| < 1e-5 (its
+    value there is a reading and stays unpinned); the limit mode is pinned by
+    the ODE, which is regular at resonance."""
+    w0v, g0v = np.float32(0.6), np.float32(0.3)
+    w0d, g0d = float(w0v), float(g0v)
+    E = ode.e_fit(w0d, g0d)
+    alpha = 2 * np.sqrt(E * (E - w0d) * (1 - w0d * g0d))
+    mu = (1.0 + 2e-6) / alpha          # D = (mu alpha)^2 - 1 ~ 4e-6
+    assert 0 < mu <= 1
+    dtau = np.array([0.4, 0.8, 0.3], np.float32).astype(np.float64)
+    w0 = np.full(3, w0d); g0 = np.full(3, g0d)
+    Bc = np.array([1e4, 2e4, 3e4]); Bi = np.array([0.5e4, 1.5e4, 2.5e4, 3.5e4])
+    cols_cfg = oracle.OracleConfig(resonance="limit")
+    up, dn, _ = orc.solve_system(cols_cfg, dtau, w0, g0, Bc, Bi, mu, 1e5, 5.0)
+    u2, d2, _ = ode.solve_column(dtau, w0, g0, Bc, Bi, mu, 1e5, 5.0)
+    scale = max(np.abs(u2).max(), np.abs(d2).max())
+    assert np.max(np.abs(up - u2)) <= 1e-9 * scale
+    assert np.max(np.abs(dn - d2)) <= 1e-9 * scale
+    # right at the singularity (|D| < 1e-7) limit mode averages across it
+    mu0 = (1.0 + 1e-10) / alpha
+    up0, dn0, _ = orc.solve_system(cols_cfg, dtau, w0, g0, Bc, Bi, mu0, 1e5, 5.0)
+    u3, d3, _ = ode.solve_column(dtau, w0, g0, Bc, Bi, mu0, 1e5, 5.0)
+    assert np.max(np.abs(up0 - u3)) <= 1e-8 * scale
+    assert np.max(np.abs(dn0 - d3)) <= 1e-8 * scale
+    up_p, dn_p, _ = orc.solve_system(oracle.OracleConfig(), dtau, w0, g0, Bc, Bi, mu, 1e5, 5.0)
+    assert np.all(np.isfinite(up_p)) and np.all(np.isfinite(dn_p))
+    # the paper rule changes the answer materially at resonance
+    assert np.max(np.abs(up_p - u2)) > 1e-4 * scale
+    # and its trigger is counted once per layer
+    cols = rt_synth.generate([3], [1], 1, 0, "uniform")
+    cols.dtau[:] = dtau.astype(np.float32); cols.w0[:] = w0v; cols.g0[:] = g0v
+    cols.mu_star[:] = mu
+    st = orc.solve_columns(oracle.OracleConfig(), cols)["stats"]
+    assert st["resonance_hits"] == 3
