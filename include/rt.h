@@ -1,0 +1,166 @@
+/*
+ * rt.h -- C ABI of the B300 column radiative-transfer library.
+ *
+ * The library solves, for every atmospheric column, every k-table bin and
+ * every Gauss point (one "system"), the improved two-stream equations with
+ * multiple scattering of Deitrick et al., "The THOR+HELIOS general
+ * circulation model" (arXiv 2203.02293), Sec. 2.2 and App. B, by a
+ * tridiagonal (Thomas) elimination over the layer interfaces (Sec. 2.2.2,
+ * Eqs. 12-15), then sums the systems over Gauss points and bins (Sec. 2.2.6)
+ * into interface fluxes, net flux (stellar beam added to the downward flux,
+ * Sec. 2.2.1) and a heating rate per layer (App. A: Q depends on the
+ * vertical gradient of the net flux).
+ *
+ * Conventions
+ *   - Every call returns an rt_status (0 = RT_OK); rt_last_error() gives a
+ *     one-line reason for the last failure on that handle.
+ *   - Layer 0 and interface 0 are at the top of the atmosphere (TOA);
+ *     interface L is the bottom (BOA).  Optical depth grows with the index.
+ *   - Device pointers are CUDA device memory owned by the caller and must
+ *     stay valid until the work enqueued on the stream has finished.  Host
+ *     pointers are read before the call returns.
+ *   - Work is asynchronous on the caller's CUDA stream (cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  rt_stats() is the only
+ *     call that synchronises.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Nothing in the library calls back into the host or waits on the
+ *     device inside a kernel; no kernel spins.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_handle rt_handle;
+
+typedef enum {
+    RT_OK = 0,
+    RT_EINVAL = -1,       /* malformed argument: shape, pointer, range */
+    RT_ENOMEM = -2,       /* device or pinned-host allocation failed */
+    RT_ECUDA = -3,        /* a CUDA call failed (message in rt_last_error) */
+    RT_ENOTSOLVED = -4,   /* rt_fluxes / rt_heating before a successful solve */
+    RT_EBUDGET = -5,      /* workspace would exceed hbm_budget_bytes */
+    RT_ETIMEOUT = -6      /* reserved for bounded device waits (none today) */
+} rt_status;
+
+/* Two-stream closure (Sec. 2.2.4, Eq. 19): improved = E from the fit for
+ * w0 > 0.1 and E = 1 otherwise; regular = E = 1 everywhere. */
+enum { RT_IMPROVED = 0, RT_REGULAR = 1 };
+/* Layer model (Sec. 2.2.1): non-isothermal layers are split into two
+ * sub-layers with a linear Planck function in optical depth; isothermal
+ * layers carry one Planck value at the layer centre. */
+enum { RT_NONISOTHERMAL = 0, RT_ISOTHERMAL = 1 };
+/* Arithmetic of the solve: FP32 cancellation-free form (FP64 only for the
+ * resonance test near |D| = 1e-5), or FP64 with the paper's literal
+ * formulas. */
+enum { RT_FP32_FORM = 0, RT_FP64_PLAIN = 1 };
+/* Beam singularity of Eq. B8 at D = 4 E mu*^2 (E - w0)(1 - w0 g0) - 1 = 0
+ * (Eq. 11): PAPER switches D to 2 mu* when |D| < 1e-5 (text after Eq. 11);
+ * LIMIT uses the exact (finite) solution at every mu*. */
+enum { RT_RESONANCE_PAPER = 0, RT_RESONANCE_LIMIT = 1 };
+
+typedef struct {
+    int32_t n_g;                 /* Gauss points per bin, 1..64 */
+    const double *g_weights;     /* HOST [n_g], copied by rt_create; should sum to 1 */
+    double wn_min, wn_max;       /* bin range in cm^-1; a column with NB bins uses NB
+                                    bins of equal width in wavenumber (Sec. 2.1.3) */
+    int32_t two_stream;          /* RT_IMPROVED | RT_REGULAR */
+    int32_t layers;              /* RT_NONISOTHERMAL | RT_ISOTHERMAL */
+    int32_t precision;           /* RT_FP32_FORM | RT_FP64_PLAIN */
+    int32_t resonance;           /* RT_RESONANCE_PAPER | RT_RESONANCE_LIMIT */
+    int32_t e_clamp;             /* 1: E := max(E_fit, 1); 0: raw fit (may give NaN) */
+    double eps2;                 /* second Eddington coefficient, Table 3: 2/3 (App. B) */
+    double grav, cp;             /* m s^-2 and J kg^-1 K^-1 for the heating rate (Table 3) */
+    double T_int;                /* K; F_BOA = pi B(T_int) per bin (Eq. 10); 0 gives 0 */
+    double F_toa_diffuse;        /* W m^-2 diffuse downward flux imposed at the TOA of
+                                    every (bin, g) system (caption of the matrix-form
+                                    figure of Sec. 2.2); normally 0 */
+    int32_t max_layers;          /* largest L of any column, 1..1024 */
+    int32_t max_bins;            /* largest NB of any column, >= 1 */
+    size_t hbm_budget_bytes;     /* workspace cap; 0 = no cap */
+    int32_t block_threads;       /* threads per CTA (multiple of 32, 64..1024); 0 = default */
+} rt_config;
+
+/* A packed batch of columns.  Column c has L_c layers, NB_c bins and
+ * S_c = NB_c * n_g systems.  Data of consecutive columns follow each other
+ * with no gaps:
+ *   dtau, w0, g0   DEVICE float  [sum_c L_c*NB_c*n_g], per column
+ *                  [layer][bin][g] with g fastest (layer 0 = TOA):
+ *                  layer optical depth (>= 0), single-scattering albedo
+ *                  ([0, 1]), asymmetry parameter ((-1, 1)).  In
+ *                  non-isothermal mode each sub-layer gets half the optical
+ *                  depth and the layer's w0, g0 (Sec. 2.2.1).
+ *   T_center       DEVICE double [sum_c L_c]      K, layer centres
+ *   T_iface        DEVICE double [sum_c (L_c+1)]  K, interfaces
+ *   p_iface        DEVICE double [sum_c (L_c+1)]  Pa, interfaces, increasing
+ *   mu_star        DEVICE double [n_cols]         cos(zenith angle); <= 0: no beam
+ *   F_star         DEVICE double [sum_c NB_c]     W m^-2 stellar flux per bin,
+ *                                                  normal to the beam, at the TOA
+ * Shapes are HOST arrays (or NULL with the uniform L, NB given). */
+typedef struct {
+    int32_t n_cols;
+    const int32_t *n_layers;     /* HOST [n_cols] or NULL -> every column has L layers */
+    const int32_t *n_bins;       /* HOST [n_cols] or NULL -> every column has NB bins */
+    int32_t L, NB;
+    const float *dtau, *w0, *g0;
+    const double *T_center, *T_iface, *p_iface;
+    const double *mu_star, *F_star;
+} rt_columns;
+
+typedef struct {
+    int64_t systems;             /* (column, bin, g) systems in the last solve */
+    int64_t resonance_hits;      /* layer-systems with |D| < 1e-5 (Eq. 11) */
+    int64_t etau_hits;           /* sub-layer-systems below e_tau = 1e-4 (Sec. 2.2.1) */
+    int64_t eclamp_hits;         /* layer-systems where the E fit fell below 1 */
+    int64_t invalid_inputs;      /* layer-systems with dtau < 0, w0 outside [0,1], |g0| >= 1, NaN */
+    int64_t nonfinite_outputs;   /* systems whose fluxes came out non-finite */
+    int64_t fp64_evals;          /* FP32 form: layer-systems whose resonance test ran in FP64 */
+} rt_stats_t;
+
+/* Create a handle.  Copies cfg (and g_weights).  RT_EINVAL on a bad field,
+ * RT_ECUDA if no device is usable.  The handle holds device workspace that
+ * grows on demand and is freed by rt_destroy. */
+int rt_create(const rt_config *cfg, rt_handle **out);
+
+/* Device workspace (bytes) that a solve of cols needs, outputs included. */
+int rt_query_bytes(const rt_handle *h, const rt_columns *cols, size_t *bytes);
+
+/* Enqueue the whole path for cols on stream: Planck per bin (R13), layer
+ * coefficients (App. B), beam (Eq. B6), sources, Thomas elimination,
+ * spectral sum, net flux and heating.  Results stay in the handle until the
+ * next solve.  Validates shapes and pointers synchronously (RT_EINVAL);
+ * RT_EBUDGET if the workspace would pass hbm_budget_bytes.  May grow the
+ * workspace (cudaMalloc) when cols is larger than anything seen before; a
+ * solve inside CUDA-graph capture must therefore follow one of the same
+ * shape outside it. */
+int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream);
+
+/* Copy the last solve's interface fluxes, W m^-2, [sum_c (L_c+1)] each,
+ * interface 0 = TOA, to F_up, F_down (diffuse + beam), F_net (= F_up -
+ * F_down).  Pointers may be host or device memory, or NULL to skip.
+ * RT_ENOTSOLVED before a solve. */
+int rt_fluxes(rt_handle *h, double *F_up, double *F_down, double *F_net, void *stream);
+
+/* Copy the last solve's heating rates, K s^-1, [sum_c L_c], layer 0 = TOA:
+ * Q_l = (g / c_P) (F_net[l+1] - F_net[l]) / (p[l+1] - p[l]). */
+int rt_heating(rt_handle *h, double *Q, void *stream);
+
+/* Branch and error counters of the last solve (synchronises the stream of
+ * that solve). */
+int rt_stats(rt_handle *h, rt_stats_t *out);
+
+/* Last error message of this handle ("" if none).  Valid until the next call. */
+const char *rt_last_error(const rt_handle *h);
+
+/* Free the handle and its workspace (synchronises the device). */
+void rt_destroy(rt_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

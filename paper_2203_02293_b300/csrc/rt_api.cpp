@@ -1,0 +1,458 @@
+// rt_api.cpp -- host side of the C ABI declared in include/rt.h.
+//
+// A handle owns: a copy of the configuration, the Gauss weights on the
+// device, a per-batch plan (column shapes, offsets and processing order),
+// the output arrays, the per-thread-slot elimination scratch, a work counter
+// and the branch counters.  Device buffers grow on demand and are reused.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "rt.h"
+#include "rt_internal.h"
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct rt_handle {
+    rt_config cfg{};
+    std::vector<double> gw;
+    int device = 0;
+    int sm_count = 0;
+    double *d_gw = nullptr;
+    // plan
+    DevBuf plan;                  // n_layers, n_bins, order (int32) + offsets (int64)
+    std::vector<int32_t> plan_nl, plan_nb;
+    bool plan_valid = false;
+    void *h_stage = nullptr;      // pinned staging for plan uploads
+    size_t stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;
+    bool stage_pending = false;
+    // outputs and scratch
+    DevBuf out, scr;
+    int32_t *d_counter = nullptr;
+    unsigned long long *d_stats = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool solved = false;
+    int64_t n_cols = 0, n_if = 0, n_lay = 0, n_sys = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(rt_handle *h, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return code;
+}
+
+int cuda_fail(rt_handle *h, cudaError_t e, const char *what) {
+    return fail(h, RT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Sizes derived from one batch.
+struct Plan {
+    std::vector<int32_t> nl, nb, order;
+    std::vector<int64_t> cube_off, lay_off, bin_off;
+    int64_t n_if = 0, n_lay = 0, n_sys = 0, n_cube = 0, n_bins = 0;
+    int Lmax = 0, NBmax = 0;
+    // launch
+    int block = 0, grid = 0, nb_chunk = 0;
+    size_t smem = 0;
+    int64_t n_slots = 0;
+    // workspace layout (bytes)
+    size_t plan_bytes = 0, out_bytes = 0, scr_bytes = 0;
+};
+
+int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
+    const rt_config &cfg = h->cfg;
+    const int n = c->n_cols;
+    P.nl.resize(n);
+    P.nb.resize(n);
+    for (int i = 0; i < n; ++i) {
+        P.nl[i] = c->n_layers ? c->n_layers[i] : c->L;
+        P.nb[i] = c->n_bins ? c->n_bins[i] : c->NB;
+        if (P.nl[i] < 1 || P.nl[i] > cfg.max_layers)
+            return fail(h, RT_EINVAL, "column %d: n_layers %d outside [1, %d]", i, P.nl[i], cfg.max_layers);
+        if (P.nb[i] < 1 || P.nb[i] > cfg.max_bins)
+            return fail(h, RT_EINVAL, "column %d: n_bins %d outside [1, %d]", i, P.nb[i], cfg.max_bins);
+    }
+    P.cube_off.resize(n);
+    P.lay_off.resize(n);
+    P.bin_off.resize(n);
+    int64_t cube = 0, lay = 0, bins = 0;
+    for (int i = 0; i < n; ++i) {
+        P.cube_off[i] = cube;
+        P.lay_off[i] = lay;
+        P.bin_off[i] = bins;
+        cube += (int64_t)P.nl[i] * P.nb[i] * cfg.n_g;
+        lay += P.nl[i];
+        bins += P.nb[i];
+        P.Lmax = std::max(P.Lmax, (int)P.nl[i]);
+        P.NBmax = std::max(P.NBmax, (int)P.nb[i]);
+    }
+    P.n_cube = cube;
+    P.n_lay = lay;
+    P.n_if = lay + n;
+    P.n_bins = bins;
+    P.n_sys = bins * cfg.n_g;
+    // largest work first (longest-processing-time order), ties by index
+    P.order.resize(n);
+    std::iota(P.order.begin(), P.order.end(), 0);
+    std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) {
+        return (int64_t)P.nl[a] * P.nb[a] > (int64_t)P.nl[b] * P.nb[b];
+    });
+    // launch shape
+    const bool fp64 = cfg.precision == RT_FP64_PLAIN;
+    P.block = cfg.block_threads;
+    if (n > 0) {
+        for (;;) {
+            P.nb_chunk = rt::bins_per_chunk(P.block, cfg.n_g, P.NBmax);
+            P.smem = fp64 ? rt::fp64_smem_bytes(P.block, P.Lmax, P.nb_chunk)
+                          : rt::fp32_smem_bytes(P.block, P.Lmax, P.nb_chunk);
+            const int occ = rt::occupancy(fp64, P.block, P.smem);
+            if (occ > 0) {
+                P.grid = std::min<int64_t>(n, (int64_t)occ * h->sm_count);
+                break;
+            }
+            if (P.block <= 64)
+                return fail(h, RT_EINVAL, "no launch shape fits shared memory (L=%d, NB=%d)", P.Lmax, P.NBmax);
+            P.block -= 32;
+        }
+        P.n_slots = (int64_t)P.grid * P.block;
+    }
+    P.plan_bytes = align_up(sizeof(int32_t) * 3 * (size_t)n, 256) + align_up(sizeof(int64_t) * 3 * (size_t)n, 256);
+    P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256);
+    P.scr_bytes = (size_t)P.n_slots *
+                  (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
+                        : rt::fp32_scratch_per_slot(P.Lmax));
+    return RT_OK;
+}
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+int grow(rt_handle *h, DevBuf &b, size_t need, bool capturing, const char *what) {
+    if (b.cap >= need) return RT_OK;
+    if (capturing)
+        return fail(h, RT_EINVAL, "%s workspace must grow (%zu bytes) during stream capture; "
+                    "run one solve of this shape outside capture first", what, need);
+    if (b.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, RT_ENOMEM, "cudaMalloc(%zu) for %s: %s", need, what, cudaGetErrorString(e));
+    }
+    b.cap = need;
+    return RT_OK;
+}
+
+int check_columns(rt_handle *h, const rt_columns *c) {
+    if (!c) return fail(h, RT_EINVAL, "columns descriptor is NULL");
+    if (c->n_cols < 0) return fail(h, RT_EINVAL, "n_cols %d < 0", c->n_cols);
+    if (c->n_cols == 0) return RT_OK;
+    if (!c->n_layers && c->L < 1) return fail(h, RT_EINVAL, "uniform L %d < 1", c->L);
+    if (!c->n_bins && c->NB < 1) return fail(h, RT_EINVAL, "uniform NB %d < 1", c->NB);
+    const void *ptrs[] = {c->dtau, c->w0, c->g0, c->T_center, c->T_iface, c->p_iface, c->mu_star, c->F_star};
+    const char *names[] = {"dtau", "w0", "g0", "T_center", "T_iface", "p_iface", "mu_star", "F_star"};
+    for (int i = 0; i < 8; ++i)
+        if (!ptrs[i]) return fail(h, RT_EINVAL, "%s is NULL", names[i]);
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_create(const rt_config *cfg, rt_handle **out) {
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    if (!cfg) return RT_EINVAL;
+    if (cfg->n_g < 1 || cfg->n_g > 64 || !cfg->g_weights) return RT_EINVAL;
+    if (!(cfg->wn_max > cfg->wn_min) || !(cfg->wn_min >= 0.0)) return RT_EINVAL;
+    if (cfg->two_stream != RT_IMPROVED && cfg->two_stream != RT_REGULAR) return RT_EINVAL;
+    if (cfg->layers != RT_NONISOTHERMAL && cfg->layers != RT_ISOTHERMAL) return RT_EINVAL;
+    if (cfg->precision != RT_FP32_FORM && cfg->precision != RT_FP64_PLAIN) return RT_EINVAL;
+    if (cfg->resonance != RT_RESONANCE_PAPER && cfg->resonance != RT_RESONANCE_LIMIT) return RT_EINVAL;
+    if (!(cfg->eps2 > 0.0) || !(cfg->cp > 0.0) || !(cfg->T_int >= 0.0)) return RT_EINVAL;
+    if (cfg->max_layers < 1 || cfg->max_layers > rt::kMaxLayers || cfg->max_bins < 1) return RT_EINVAL;
+    if (cfg->block_threads != 0 &&
+        (cfg->block_threads % 32 || cfg->block_threads < 64 || cfg->block_threads > rt::kMaxBlock))
+        return RT_EINVAL;
+    for (int i = 0; i < cfg->n_g; ++i)
+        if (!(cfg->g_weights[i] >= 0.0)) return RT_EINVAL;
+
+    rt_handle *h = new rt_handle();
+    h->cfg = *cfg;
+    if (h->cfg.block_threads == 0) h->cfg.block_threads = 256;
+    h->gw.assign(cfg->g_weights, cfg->g_weights + cfg->n_g);
+    h->cfg.g_weights = h->gw.data();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = rt::init_kernels();
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_gw, sizeof(double) * cfg->n_g);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_gw, h->gw.data(), sizeof(double) * cfg->n_g, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_counter, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_stats, sizeof(unsigned long long) * rt::ST_COUNT);
+    if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rt_destroy(h);
+        return RT_ECUDA;
+    }
+    *out = h;
+    return RT_OK;
+}
+
+int rt_query_bytes(const rt_handle *hc, const rt_columns *cols, size_t *bytes) {
+    rt_handle *h = const_cast<rt_handle *>(hc);
+    if (!h || !bytes) return RT_EINVAL;
+    int rc = check_columns(h, cols);
+    if (rc) return rc;
+    Plan P;
+    rc = build_plan(h, cols, P);
+    if (rc) return rc;
+    *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes;
+    return RT_OK;
+}
+
+int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
+    if (!h) return RT_EINVAL;
+    h->err.clear();
+    int rc = check_columns(h, cols);
+    if (rc) return rc;
+    Plan P;
+    rc = build_plan(h, cols, P);
+    if (rc) return rc;
+    const rt_config &cfg = h->cfg;
+    if (cfg.hbm_budget_bytes && P.plan_bytes + P.out_bytes + P.scr_bytes > cfg.hbm_budget_bytes)
+        return fail(h, RT_EBUDGET, "workspace %zu bytes exceeds budget %zu",
+                    P.plan_bytes + P.out_bytes + P.scr_bytes, cfg.hbm_budget_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool cap = stream_capturing(s);
+    // order after the previous solve of this handle when it ran on another stream
+    if (h->solved && s != h->last_stream && !cap) {
+        cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
+    }
+    const int n = cols->n_cols;
+    void *old_plan = h->plan.p;
+    if ((rc = grow(h, h->plan, std::max<size_t>(P.plan_bytes, 256), cap, "plan"))) return rc;
+    if (h->plan.p != old_plan) h->plan_valid = false;
+    if ((rc = grow(h, h->out, std::max<size_t>(P.out_bytes, 256), cap, "output"))) return rc;
+    if ((rc = grow(h, h->scr, std::max<size_t>(P.scr_bytes, 256), cap, "scratch"))) return rc;
+
+    char *pb = (char *)h->plan.p;
+    int32_t *d_nl = (int32_t *)pb;
+    int32_t *d_nb = d_nl + n;
+    int32_t *d_order = d_nb + n;
+    int64_t *d_cube = (int64_t *)(pb + align_up(sizeof(int32_t) * 3 * (size_t)n, 256));
+    int64_t *d_lay = d_cube + n;
+    int64_t *d_bin = d_lay + n;
+
+    const bool same_plan = h->plan_valid && h->plan_nl == P.nl && h->plan_nb == P.nb;
+    if (n > 0 && !same_plan) {
+        if (cap) return fail(h, RT_EINVAL, "a new batch shape cannot be planned during stream capture");
+        const size_t need = P.plan_bytes;
+        if (h->stage_pending) {
+            cudaError_t e = cudaEventSynchronize(h->stage_ev);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+            h->stage_pending = false;
+        }
+        if (h->stage_cap < need) {
+            if (h->h_stage) cudaFreeHost(h->h_stage);
+            h->h_stage = nullptr;
+            h->stage_cap = 0;
+            cudaError_t e = cudaMallocHost(&h->h_stage, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, RT_ENOMEM, "cudaMallocHost(%zu): %s", need, cudaGetErrorString(e));
+            }
+            h->stage_cap = need;
+        }
+        char *hs = (char *)h->h_stage;
+        memcpy(hs, P.nl.data(), sizeof(int32_t) * n);
+        memcpy(hs + sizeof(int32_t) * n, P.nb.data(), sizeof(int32_t) * n);
+        memcpy(hs + sizeof(int32_t) * 2 * n, P.order.data(), sizeof(int32_t) * n);
+        char *hs64 = hs + align_up(sizeof(int32_t) * 3 * (size_t)n, 256);
+        memcpy(hs64, P.cube_off.data(), sizeof(int64_t) * n);
+        memcpy(hs64 + sizeof(int64_t) * n, P.lay_off.data(), sizeof(int64_t) * n);
+        memcpy(hs64 + sizeof(int64_t) * 2 * n, P.bin_off.data(), sizeof(int64_t) * n);
+        cudaError_t e = cudaMemcpyAsync(h->plan.p, h->h_stage, need, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "plan upload");
+        h->stage_pending = true;
+        h->plan_nl = P.nl;
+        h->plan_nb = P.nb;
+        h->plan_valid = true;
+    }
+
+    char *ob = (char *)h->out.p;
+    double *F_up = (double *)ob;
+    double *F_dn = F_up + P.n_if;
+    double *F_net = F_dn + P.n_if;
+    double *Q = (double *)(ob + align_up(sizeof(double) * 3 * (size_t)P.n_if, 256));
+
+    cudaError_t e = cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+
+    if (n > 0) {
+        rt::KParams kp{};
+        kp.dtau = cols->dtau;
+        kp.w0 = cols->w0;
+        kp.g0 = cols->g0;
+        kp.T_center = cols->T_center;
+        kp.T_iface = cols->T_iface;
+        kp.p_iface = cols->p_iface;
+        kp.mu_star = cols->mu_star;
+        kp.F_star = cols->F_star;
+        kp.n_layers = d_nl;
+        kp.n_bins = d_nb;
+        kp.cube_off = d_cube;
+        kp.lay_off = d_lay;
+        kp.bin_off = d_bin;
+        kp.order = d_order;
+        kp.n_cols = n;
+        kp.n_g = cfg.n_g;
+        kp.g_w = h->d_gw;
+        kp.F_up = F_up;
+        kp.F_dn = F_dn;
+        kp.F_net = F_net;
+        kp.Q = Q;
+        kp.scr32 = (float4 *)h->scr.p;
+        kp.scr64 = (double2 *)h->scr.p;
+        kp.n_slots = P.n_slots;
+        kp.counter = h->d_counter;
+        kp.stats = h->d_stats;
+        kp.improved = cfg.two_stream == RT_IMPROVED;
+        kp.isothermal = cfg.layers == RT_ISOTHERMAL;
+        kp.resonance_paper = cfg.resonance == RT_RESONANCE_PAPER;
+        kp.e_clamp = cfg.e_clamp;
+        kp.eps2 = cfg.eps2;
+        kp.inv_eps2 = (float)(1.0 / cfg.eps2);
+        kp.grav = cfg.grav;
+        kp.cp = cfg.cp;
+        kp.T_int = cfg.T_int;
+        kp.F_toa = cfg.F_toa_diffuse;
+        kp.wn_min = cfg.wn_min;
+        kp.wn_max = cfg.wn_max;
+        kp.Lmax = P.Lmax;
+        kp.nb_chunk = P.nb_chunk;
+        e = cfg.precision == RT_FP64_PLAIN ? rt::launch_fp64(kp, P.grid, P.block, P.smem, s)
+                                           : rt::launch_fp32(kp, P.grid, P.block, P.smem, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    }
+    e = cudaEventRecord(h->done_ev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    h->last_stream = s;
+    h->solved = true;
+    h->n_cols = n;
+    h->n_if = P.n_if;
+    h->n_lay = P.n_lay;
+    h->n_sys = P.n_sys;
+    return RT_OK;
+}
+
+static int copy_out(rt_handle *h, void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (!dst || bytes == 0) return RT_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync");
+    return RT_OK;
+}
+
+int rt_fluxes(rt_handle *h, double *F_up, double *F_down, double *F_net, void *stream) {
+    if (!h) return RT_EINVAL;
+    if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_fluxes before rt_solve_columns");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s != h->last_stream && !stream_capturing(s)) {
+        cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
+    }
+    const double *base = (const double *)h->out.p;
+    const size_t b = sizeof(double) * (size_t)h->n_if;
+    int rc = copy_out(h, F_up, base, b, s);
+    if (!rc) rc = copy_out(h, F_down, base + h->n_if, b, s);
+    if (!rc) rc = copy_out(h, F_net, base + 2 * h->n_if, b, s);
+    return rc;
+}
+
+int rt_heating(rt_handle *h, double *Q, void *stream) {
+    if (!h) return RT_EINVAL;
+    if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_heating before rt_solve_columns");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s != h->last_stream && !stream_capturing(s)) {
+        cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
+    }
+    const char *ob = (const char *)h->out.p;
+    const double *q = (const double *)(ob + align_up(sizeof(double) * 3 * (size_t)h->n_if, 256));
+    return copy_out(h, Q, q, sizeof(double) * (size_t)h->n_lay, s);
+}
+
+int rt_stats(rt_handle *h, rt_stats_t *out) {
+    if (!h || !out) return RT_EINVAL;
+    if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_stats before rt_solve_columns");
+    cudaError_t e = cudaEventSynchronize(h->done_ev);
+    unsigned long long v[rt::ST_COUNT] = {0};
+    if (e == cudaSuccess) e = cudaMemcpy(v, h->d_stats, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rt_stats");
+    out->systems = h->n_sys;
+    out->resonance_hits = (int64_t)v[rt::ST_RESONANCE];
+    out->etau_hits = (int64_t)v[rt::ST_ETAU];
+    out->eclamp_hits = (int64_t)v[rt::ST_ECLAMP];
+    out->invalid_inputs = (int64_t)v[rt::ST_INVALID];
+    out->nonfinite_outputs = (int64_t)v[rt::ST_NONFINITE];
+    out->fp64_evals = (int64_t)v[rt::ST_FP64];
+    return RT_OK;
+}
+
+const char *rt_last_error(const rt_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+void rt_destroy(rt_handle *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_gw);
+    cudaFree(h->plan.p);
+    cudaFree(h->out.p);
+    cudaFree(h->scr.p);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_stats);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    if (h->done_ev) cudaEventDestroy(h->done_ev);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// rt_internal.h -- kernel parameter block shared by the API and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rt {
+
+// Device counters, in this order (see rt_stats_t).
+enum StatIdx {
+    ST_RESONANCE = 0,
+    ST_ETAU = 1,
+    ST_ECLAMP = 2,
+    ST_INVALID = 3,
+    ST_NONFINITE = 4,
+    ST_FP64 = 5,
+    ST_COUNT = 8
+};
+
+struct KParams {
+    // inputs (caller-owned device memory)
+    const float *dtau, *w0, *g0;
+    const double *T_center, *T_iface, *p_iface, *mu_star, *F_star;
+    // per-column layout (handle workspace)
+    const int32_t *n_layers, *n_bins;
+    const int64_t *cube_off;     // element offset of the column's cube block
+    const int64_t *lay_off;      // offset into T_center / Q (sum of L)
+    const int64_t *bin_off;      // offset into F_star (sum of NB)
+    const int32_t *order;        // columns in processing order (largest first)
+    int32_t n_cols;
+    // Gauss points
+    int32_t n_g;
+    const double *g_w;           // [n_g]
+    // outputs (handle workspace); interface arrays use lay_off[c] + c
+    double *F_up, *F_dn, *F_net, *Q;
+    // per-level elimination scratch, layout [level][slot]; one slot per
+    // resident thread of the persistent grid (slot = global thread index)
+    float4 *scr32;               // FP32 form: (P, Q, alpha', e) per interface
+    double2 *scr64;              // FP64 path: 2 x double2 = (P, Q), (a, e) per level
+    int64_t n_slots;
+    // scheduling and counters
+    int32_t *counter;
+    unsigned long long *stats;
+    // method switches and constants
+    int32_t improved, isothermal, resonance_paper, e_clamp;
+    double eps2, grav, cp, T_int, F_toa, wn_min, wn_max;
+    float inv_eps2;
+    int32_t Lmax;                // largest L in this batch
+    int32_t nb_chunk;            // bins covered by one chunk of systems (smem sizing)
+};
+
+// Shared memory needed per CTA for a given block size (bytes).
+size_t fp32_smem_bytes(int block, int Lmax, int nb_chunk);
+size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
+// Scratch bytes per thread slot.
+size_t fp32_scratch_per_slot(int Lmax);
+size_t fp64_scratch_per_slot(int Lmax, int isothermal);
+// Bins that one chunk of `block` consecutive systems can touch.
+int bins_per_chunk(int block, int n_g, int max_bins);
+
+// One-time per-device set-up (dynamic shared-memory limits).
+cudaError_t init_kernels();
+// Resident CTAs per SM for a launch shape (0 if it does not fit).
+int occupancy(int precision_fp64, int block, size_t smem);
+// Launch the fused column kernels.  Return cudaGetLastError().
+cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
+
+// Largest L the kernels support.
+constexpr int kMaxLayers = 1024;
+// Largest CTA size (launch bounds of both kernels).
+constexpr int kMaxBlock = 512;
+
+}  // namespace rt

@@ -1,0 +1,857 @@
+// rt_kernels.cu -- fused column kernels for sm_103a.
+//
+// One persistent CTA handles one column at a time (columns are taken from a
+// largest-first list through an atomic counter).  Inside a column the CTA
+// walks the column's (bin, g) systems in chunks of blockDim, one thread per
+// system, g fastest, so that a warp reads 32 consecutive floats of each
+// optical-property cube per layer.  For each chunk the CTA:
+//   1. evaluates the Planck function per bin at every interface and layer
+//      centre of the column into shared memory (bin-integrated B, Sec. 2.2.1);
+//   2. per thread: walks the layers from the TOA down, forming the layer
+//      coefficients (App. B), the stellar beam (Eq. B6) and its source terms
+//      (Eq. B7-B8), the thermal source terms (Eqs. 2-9), and eliminates
+//      towards the BOA (Thomas forward sweep, Sec. 2.2.2), keeping per
+//      interface what the back-substitution needs in a global scratch laid
+//      out [level][thread slot];
+//   3. closes the system at the BOA (Eq. 10) and substitutes back to the TOA,
+//      reducing the Gauss-weighted fluxes of the 32 systems of each warp with
+//      a fixed butterfly, then across warps in a fixed order.
+// After the last chunk it writes the column's interface fluxes, net flux and
+// heating rate.  Every reduction runs in a fixed order, so a column gives the
+// same bits whatever else is in the batch (for a fixed block size).
+//
+// Two arithmetic variants:
+//   fp32_columns  -- the FP32 "chosen form": cancellation-free transmission,
+//                    reflection and absorption forms, a beam source with the
+//                    removable singularity at mu* alpha = 1 divided out, and
+//                    departure variables u = F - pi B at every level.  FP64 is
+//                    used only to decide the paper's resonance switch when the
+//                    FP32 estimate of D lies within 2e-5 of zero.
+//   fp64_columns  -- FP64 with the paper's literal formulas, scalar Thomas on
+//                    every level (sub-layers not merged).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "rt_internal.h"
+
+namespace rt {
+
+// ---------------------------------------------------------------------
+// Physical constants (SI defining constants, exact) and Planck series.
+// ---------------------------------------------------------------------
+constexpr double kH = 6.62607015e-34;
+constexpr double kC = 299792458.0;
+constexpr double kKB = 1.380649e-23;
+constexpr double kC2 = kH * kC / kKB;                       // m K
+constexpr double kPlanckK = 2.0 * kKB * kKB * kKB * kKB / (kH * kH * kH * kC * kC);
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kPi4Over15 = 6.4939394022668291491;      // integral_0^inf x^3/(e^x-1)
+constexpr float kPiF = 3.14159265358979323846f;
+
+// Bernoulli numbers B_k give t/(e^t - 1) = sum_k B_k t^k / k!, hence
+//   S(x) = integral_0^x t^3/(e^t-1) dt = sum_k B_k x^(k+3) / (k! (k+3)),
+// convergent for |x| < 2 pi.  Coefficients c_k = B_k / (k! (k+3)).
+#define BC(num, den, kfact, k) ((double)(num) / (double)(den) / ((double)(kfact) * ((k) + 3.0)))
+__device__ constexpr double kS0 = 1.0 / 3.0;
+__device__ constexpr double kS1 = -1.0 / 8.0;
+__device__ constexpr double kS2 = BC(1, 6, 2.0, 2);
+__device__ constexpr double kS4 = BC(-1, 30, 24.0, 4);
+__device__ constexpr double kS6 = BC(1, 42, 720.0, 6);
+__device__ constexpr double kS8 = BC(-1, 30, 40320.0, 8);
+__device__ constexpr double kS10 = BC(5, 66, 3628800.0, 10);
+__device__ constexpr double kS12 = BC(-691, 2730, 479001600.0, 12);
+__device__ constexpr double kS14 = BC(7, 6, 87178291200.0, 14);
+__device__ constexpr double kS16 = BC(-3617, 510, 20922789888000.0, 16);
+__device__ constexpr double kS18 = BC(43867, 798, 6402373705728000.0, 18);
+__device__ constexpr double kS20 = BC(-174611, 330, 2432902008176640000.0, 20);
+__device__ constexpr double kS22 = BC(854513, 138, 1.1240007277776077e21, 22);
+__device__ constexpr double kS24 = BC(-236364091, 2730, 6.2044840173323941e23, 24);
+__device__ constexpr double kS26 = BC(8553103, 6, 4.0329146112660565e26, 26);
+__device__ constexpr double kS28 = BC(-23749461029.0, 870, 3.0488834461171386e29, 28);
+__device__ constexpr double kS30 = BC(8615841276005.0, 14322, 2.6525285981219105e32, 30);
+#undef BC
+
+// FP32: S(x) for x <= 2 (terms to k = 14, relative error < 1e-7).
+__device__ __forceinline__ float planck_lower_f(float x) {
+    const float x2 = x * x;
+    float s = (float)kS14;
+    s = fmaf(s, x2, (float)kS12);
+    s = fmaf(s, x2, (float)kS10);
+    s = fmaf(s, x2, (float)kS8);
+    s = fmaf(s, x2, (float)kS6);
+    s = fmaf(s, x2, (float)kS4);
+    const float head = fmaf(x, fmaf(x, (float)kS2, (float)kS1), (float)kS0);
+    return fmaf(x2 * x2, s, head) * x2 * x;
+}
+
+// FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
+//   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms.
+__device__ __forceinline__ float planck_upper_f(float x) {
+    const float e = expf(-x);
+    const float x2 = x * x, x3 = x2 * x;
+    float en = e, s = 0.f;
+#pragma unroll
+    for (int n = 1; n <= 8; ++n) {
+        const float y = 1.0f / (float)n;
+        const float poly = y * fmaf(y, fmaf(y, fmaf(6.f, y, 6.f * x), 3.f * x2), x3);
+        s = fmaf(en, poly, s);
+        en *= e;
+    }
+    return s;
+}
+
+// Bin-integrated Planck function (W m^-2 sr^-1) between two wavenumbers
+// (cm^-1), FP32.  The difference is taken in the form without cancellation.
+__device__ float planck_bin_f(float T, float wlo, float whi) {
+    if (!(T > 0.f)) return 0.f;
+    const float a = (float)(kC2 * 100.0) / T;
+    const float xlo = a * wlo, xhi = a * whi;
+    float d;
+    if (xlo >= 2.f) {
+        d = planck_upper_f(xlo) - planck_upper_f(xhi);
+    } else if (xhi <= 2.f) {
+        d = planck_lower_f(xhi) - planck_lower_f(xlo);
+    } else {
+        d = ((float)kPi4Over15 - planck_lower_f(xlo)) - planck_upper_f(xhi);
+    }
+    const float T2 = T * T;
+    return (float)kPlanckK * (T2 * T2) * d;
+}
+
+// FP64 versions (terms to k = 30 below x = 2, 20 exponential terms above).
+__device__ __forceinline__ double planck_lower_d(double x) {
+    const double x2 = x * x;
+    double s = kS30;
+    s = fma(s, x2, kS28); s = fma(s, x2, kS26); s = fma(s, x2, kS24);
+    s = fma(s, x2, kS22); s = fma(s, x2, kS20); s = fma(s, x2, kS18);
+    s = fma(s, x2, kS16); s = fma(s, x2, kS14); s = fma(s, x2, kS12);
+    s = fma(s, x2, kS10); s = fma(s, x2, kS8); s = fma(s, x2, kS6);
+    s = fma(s, x2, kS4);
+    const double head = fma(x, fma(x, kS2, kS1), kS0);
+    return fma(x2 * x2, s, head) * x2 * x;
+}
+
+__device__ __forceinline__ double planck_upper_d(double x) {
+    const double e = exp(-x);
+    const double x2 = x * x, x3 = x2 * x;
+    double en = e, s = 0.0;
+#pragma unroll
+    for (int n = 1; n <= 20; ++n) {
+        const double y = 1.0 / (double)n;
+        const double poly = y * fma(y, fma(y, fma(6.0, y, 6.0 * x), 3.0 * x2), x3);
+        s = fma(en, poly, s);
+        en *= e;
+    }
+    return s;
+}
+
+__device__ double planck_bin_d(double T, double wlo, double whi) {
+    if (!(T > 0.0)) return 0.0;
+    const double a = kC2 * 100.0 / T;
+    const double xlo = a * wlo, xhi = a * whi;
+    double d;
+    if (xlo >= 2.0) {
+        d = planck_upper_d(xlo) - planck_upper_d(xhi);
+    } else if (xhi <= 2.0) {
+        d = planck_lower_d(xhi) - planck_lower_d(xlo);
+    } else {
+        d = (kPi4Over15 - planck_lower_d(xlo)) - planck_upper_d(xhi);
+    }
+    const double T2 = T * T;
+    return kPlanckK * (T2 * T2) * d;
+}
+
+// ---------------------------------------------------------------------
+// Counters kept in registers and flushed once per CTA.
+// ---------------------------------------------------------------------
+struct Counters {
+    unsigned res, etau, eclamp, inv, nonfinite, fp64;
+    unsigned on;   // 1 while the thread works on a real system, 0 on padding lanes
+};
+
+__device__ __forceinline__ void flush_counters(const Counters &cn, unsigned long long *stats) {
+    unsigned v[6] = {cn.res, cn.etau, cn.eclamp, cn.inv, cn.nonfinite, cn.fp64};
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        unsigned x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) atomicAdd(stats + i, (unsigned long long)x);
+    }
+}
+
+// The paper's resonance test (Eq. 11 and the text after it) evaluated in
+// FP64 with the same operation order as a plain C evaluation, so the branch
+// matches an FP64 reference bit for bit.
+__device__ double resonance_D_fp64(float w0f, float g0f, double mu, int improved, int e_clamp) {
+    const double w0 = (double)w0f, g0 = (double)g0f;
+    double E = 1.0;
+    if (improved && w0 > (double)0.1f) {
+        double t = __dsub_rn(1.225, __dmul_rn(0.1582, g0));
+        t = __dsub_rn(t, __dmul_rn(0.1777, w0));
+        t = __dsub_rn(t, __dmul_rn(__dmul_rn(0.07465, g0), g0));
+        t = __dadd_rn(t, __dmul_rn(__dmul_rn(0.2351, w0), g0));
+        t = __dsub_rn(t, __dmul_rn(__dmul_rn(0.05582, w0), w0));
+        E = (e_clamp && t < 1.0) ? 1.0 : t;
+    }
+    const double mus = -mu;
+    double v = __dmul_rn(4.0, E);
+    v = __dmul_rn(v, mus);
+    v = __dmul_rn(v, mus);
+    v = __dmul_rn(v, __dsub_rn(E, w0));
+    v = __dmul_rn(v, __dsub_rn(1.0, __dmul_rn(w0, g0)));
+    return __dsub_rn(v, 1.0);
+}
+
+// ---------------------------------------------------------------------
+// FP32 chosen form: one layer.
+//
+// Notation: q = E (1 - w0 g0), k = sqrt((E - w0)/q) so that the transmission
+// exponent of Eq. B2 is 2 q k dtau and zeta_-/zeta_+ = eps = (1-k)/(1+k).
+// With x = 2 q k dtau, T = exp(-x), u = (1 - T)/x, h = 2 q dtau u + 2T/(1+k),
+// p = 1 + eps T, the relations of Eqs. B1-B3 divided by chi give
+//   t = psi/chi = 4T / ((1+k)^2 h p),  r = -xi/chi = eps 2 q dtau u (1+T)/(h p),
+//   1-t-r = 4 q k^2 dtau u / ((1+k) p),  1-t+r = 4 q dtau u / ((1+k) h),
+// free of cancellation as k -> 0 (w0 -> 1) and dtau -> 0.
+// Thermal sources are written for departures u = F - pi B at both ends of
+// the sub-layer; with Pi - pi = -pi (E-1)/(E-w0) they carry no difference of
+// large terms, and the Planck-gradient term c B' (1-t+r) becomes
+// Pi (B_bot - B_top) 2u/((1+k) h) with no division by dtau.
+// The beam source (Eqs. B7-B8) per unit beam at the sub-layer top is
+// rewritten with rho = mu 2 q k, delta = dtau/mu, m = exp(-delta) and
+// Lambda = (T - m)/(1 - rho) (evaluated as m delta expm1(z)/z, z =
+// (1-rho) delta, near rho = 1): the factor 1/D of G+- cancels analytically,
+// so the source is finite and accurate through mu* alpha = 1.
+// Two identical sub-layers (half the optical depth each) are merged into one
+// layer with T_L = t^2/(1-r^2), R_L = r (1 + T_L) and combined sources.
+// ---------------------------------------------------------------------
+struct Layer32 {
+    float T, R, Su, Sd, omtr, opr, mlay;
+};
+
+__device__ __forceinline__ void thermal_sub(float dPi, float Pi, float t, float r, float omtr,
+                                            float gs, bool fallback, float B1, float B2,
+                                            float &su, float &sd) {
+    if (!fallback) {
+        const float omr = omtr + t;            // 1 - r
+        const float grad = Pi * (B2 - B1) * gs;
+        su = dPi * (omr * B1 - t * B2) + grad;
+        sd = dPi * (omr * B2 - t * B1) - grad;
+    } else {
+        // optical depth below e_tau: isothermal at the mean B (Sec. 2.2.1)
+        const float Bm = 0.5f * (B1 + B2), hdB = 0.5f * (B2 - B1);
+        const float side = kPiF * hdB * (omtr + 2.f * t);   // pi dB/2 (1 - r + t)
+        su = dPi * Bm * omtr + side;
+        sd = dPi * Bm * omtr - side;
+    }
+}
+
+__device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float Bt, float Bc, float Bb,
+                                           float mu, double mu_d, bool beam, float Fb,
+                                           const KParams &kp, Counters &cn) {
+    if (!(dt >= 0.f) || !(w0 >= 0.f && w0 <= 1.f) || !(g0 > -1.f && g0 < 1.f)) cn.inv += cn.on;
+    // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
+    float em1 = 0.f;
+    if (kp.improved && w0 > 0.1f) {
+        em1 = 0.225f - 0.1582f * g0 - 0.1777f * w0 - 0.07465f * g0 * g0 + 0.2351f * w0 * g0
+              - 0.05582f * w0 * w0;
+        if (kp.e_clamp && em1 < 0.f) {
+            em1 = 0.f;
+            cn.eclamp += cn.on;
+        }
+    }
+    const float E = 1.f + em1;
+    const float omw = 1.f - w0;
+    const float ewm = em1 + omw;                 // E - w0
+    const float q = E * (1.f - w0 * g0);
+    const float k = sqrtf(ewm / q);
+    float Pi = kPiF, dPi = 0.f;                  // E = w0 = 1: Pi := pi
+    if (ewm > 0.f) {
+        const float iw = 1.f / ewm;
+        Pi = kPiF * omw * iw;
+        dPi = -kPiF * em1 * iw;                  // Pi - pi
+    }
+    const float ip = 1.f / (1.f + k);
+    const float eps = (1.f - k) * ip;
+    const bool iso = kp.isothermal;
+    const float dts = iso ? dt : 0.5f * dt;
+
+    const float x = 2.f * q * k * dts;
+    const float Tm = expf(-x);
+    const float u = (x > 0.f) ? -expm1f(-x) / x : 1.f;
+    const float qd = 2.f * q * dts * u;          // (1 - T)/k
+    const float h = fmaf(2.f * Tm, ip, qd);
+    const float p = fmaf(eps, Tm, 1.f);
+    const float ihp = 1.f / (h * p);
+    const float t = 4.f * Tm * ip * ip * ihp;
+    const float r = eps * qd * (1.f + Tm) * ihp;
+    const float omtr = 2.f * k * k * qd * ip * h * ihp;   // 1 - t - r
+    const float gs = 2.f * u * ip * p * ihp;              // 2u / ((1+k) h)
+
+    float suU, sdU, suL = 0.f, sdL = 0.f;
+    if (!iso) {
+        const bool fb = dts < 1e-4f;
+        if (fb) cn.etau += 2 * cn.on;
+        thermal_sub(dPi, Pi, t, r, omtr, gs, fb, Bt, Bc, suU, sdU);
+        thermal_sub(dPi, Pi, t, r, omtr, gs, fb, Bc, Bb, suL, sdL);
+    } else {
+        const float omr = omtr + t;
+        const float base = dPi * Bc * omtr;
+        suU = base + kPiF * (omr * (Bc - Bt) - t * (Bc - Bb));
+        sdU = base + kPiF * (omr * (Bc - Bb) - t * (Bc - Bt));
+    }
+
+    float m = 1.f;
+    if (beam) {
+        const float dl = dts / mu;
+        m = expf(-dl);
+        const float omm = -expm1f(-dl);          // 1 - m
+        const float rho = mu * 2.f * q * k;
+        const float ie2 = kp.inv_eps2;
+        const float A = w0 * fmaf(g0, ie2, 2.f * q);
+        const float G0h = w0 * g0 * ie2 / (4.f * q);   // G0/2 of Eq. B8
+        // resonance test of Eq. 11: decide in FP64 only when FP32 cannot
+        const float D32 = fmaf(rho, rho, -1.f);
+        bool sw = false;
+        if (fabsf(D32) < 2e-5f) {
+            cn.fp64 += cn.on;
+            const double D = resonance_D_fp64(w0, g0, mu_d, kp.improved, kp.e_clamp);
+            if (fabs(D) < 1e-5) {
+                cn.res += cn.on;
+                sw = kp.resonance_paper != 0;
+            }
+        }
+        float bu, bd;
+        if (sw) {
+            // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
+            const float c1 = 1.f / (2.f * q);
+            const float lead = A / (-2.f * mu);
+            const float Gp = 0.5f * lead * (c1 - mu) + G0h;
+            const float Gm = -0.5f * lead * (c1 + mu) - G0h;
+            bu = -Gp * (omtr + r + t * omm) + r * Gm;         // Gp (t m - 1) + r Gm
+            bd = Gm * (omm - omtr - r) + r * Gp * m;          // Gm (t - m) + r Gp m
+        } else {
+            const float z = (1.f - rho) * dl;
+            float Lam;
+            if (fabsf(z) < 0.5f) {
+                Lam = m * dl * ((z != 0.f) ? expm1f(z) / z : 1.f);
+            } else {
+                Lam = (Tm - m) / (1.f - rho);
+            }
+            const float Y = qd * (1.f + Tm);                   // (1 - T^2)/k
+            const float SA = A * ip * ip * ihp / (4.f * q * (1.f + rho));
+            const float tq = 2.f * q * mu;
+            const float k2 = k * k;
+            const float tm1r = -(omtr + 2.f * r + t * omm);    // (t m - 1) - r
+            const float rmtm = (omtr + r) - omm + r * m;       // r m - (t - m)
+            bu = SA * (2.f * (1.f + k) * Y + 4.f * Tm * (1.f - tq) * Lam) + G0h * tm1r;
+            bd = SA * (-2.f * Tm * (1.f - k) * Y
+                       + Lam * ((1.f + tq) * (Y * (1.f + k2) + 2.f * (1.f + Tm * Tm))
+                                + (1.f - tq) * (1.f - k2) * Y))
+                 + G0h * rmtm;
+        }
+        suU += Fb * bu;
+        sdU += Fb * bd;
+        if (!iso) {
+            const float Fc = Fb * m;
+            suL += Fc * bu;
+            sdL += Fc * bd;
+        }
+    }
+
+    Layer32 o;
+    if (iso) {
+        o.T = t;
+        o.R = r;
+        o.Su = suU;
+        o.Sd = sdU;
+        o.omtr = omtr;
+        o.opr = omtr + 2.f * t;
+        o.mlay = m;
+    } else {
+        // merge upper (top -> centre) and lower (centre -> bottom) sub-layers
+        const float omr = omtr + t;              // 1 - r
+        const float Dr = 1.f / (omr * (1.f + r));
+        const float tD = t * Dr;
+        o.T = t * tD;
+        o.R = r * (1.f + o.T);
+        o.Su = suU + tD * (suL + r * sdU);
+        o.Sd = sdL + tD * (sdU + r * suL);
+        o.omtr = omtr * (omtr + 2.f * t) / omr;
+        o.opr = omr * (1.f + o.T);
+        o.mlay = m * m;
+    }
+    return o;
+}
+
+// ---------------------------------------------------------------------
+// Shared-memory layout (both kernels):
+//   acc   double [2 (Lmax+1)]                  column sums (F_up, F_net)
+//   wpart R      [2 (Lmax+1) nwarps]            warp partial sums
+//   sB    R      [(2 Lmax + 1) nb_chunk]        Planck at levels (2i iface, 2i+1 centre)
+//   sFs   R      [nb_chunk]                     stellar flux per bin
+//   sFB   R      [nb_chunk]                     F_BOA per bin
+// ---------------------------------------------------------------------
+template <typename R>
+__host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk) {
+    const int nw = block / 32;
+    size_t b = sizeof(double) * 2 * (size_t)(Lmax + 1);
+    b += sizeof(R) * 2 * (size_t)(Lmax + 1) * nw;
+    b += sizeof(R) * (size_t)(2 * Lmax + 1) * nb_chunk;
+    b += sizeof(R) * 2 * (size_t)nb_chunk;
+    return b;
+}
+
+size_t fp32_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<float>(block, Lmax, nb_chunk); }
+size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
+size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
+size_t fp64_scratch_per_slot(int Lmax, int isothermal) {
+    const int nlev = isothermal ? Lmax : 2 * Lmax;
+    return 2 * sizeof(double2) * (size_t)nlev;
+}
+int bins_per_chunk(int block, int n_g, int max_bins) {
+    int nb = (block - 1) / n_g + 2;
+    return nb < max_bins ? nb : max_bins;
+}
+
+template <typename R>
+struct Smem {
+    double *acc;
+    R *wpart, *sB, *sFs, *sFB;
+    __device__ Smem(unsigned char *raw, int Lmax, int nb_chunk, int nwarps) {
+        acc = reinterpret_cast<double *>(raw);
+        wpart = reinterpret_cast<R *>(acc + 2 * (Lmax + 1));
+        sB = wpart + 2 * (Lmax + 1) * nwarps;
+        sFs = sB + (2 * Lmax + 1) * nb_chunk;
+        sFB = sFs + nb_chunk;
+    }
+};
+
+// Column bookkeeping common to both kernels.
+struct ColInfo {
+    int c, L, NB, S;
+    long long cube0, lay0, if0, bin0;
+    double mu;
+};
+
+__device__ __forceinline__ bool next_column(const KParams &kp, int *s_unit, ColInfo &ci) {
+    if (threadIdx.x == 0) *s_unit = atomicAdd(kp.counter, 1);
+    __syncthreads();
+    const int unit = *s_unit;
+    __syncthreads();
+    if (unit >= kp.n_cols) return false;
+    ci.c = kp.order[unit];
+    ci.L = kp.n_layers[ci.c];
+    ci.NB = kp.n_bins[ci.c];
+    ci.S = ci.NB * kp.n_g;
+    ci.cube0 = kp.cube_off[ci.c];
+    ci.lay0 = kp.lay_off[ci.c];
+    ci.if0 = ci.lay0 + ci.c;
+    ci.bin0 = kp.bin_off[ci.c];
+    ci.mu = kp.mu_star[ci.c];
+    return true;
+}
+
+// Planck at the 2L+1 levels of the column for bins [b_lo, b_lo + nbc).
+template <typename R>
+__device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &ci, int b_lo, int nbc,
+                                             Smem<R> &sm) {
+    const int nlev = 2 * ci.L + 1;
+    const double dwn = (kp.wn_max - kp.wn_min) / ci.NB;
+    for (int i = threadIdx.x; i < nlev * nbc; i += blockDim.x) {
+        const int lev = i / nbc, bb = i - lev * nbc, b = b_lo + bb;
+        const double T = (lev & 1) ? kp.T_center[ci.lay0 + (lev >> 1)] : kp.T_iface[ci.if0 + (lev >> 1)];
+        const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
+        if constexpr (sizeof(R) == 4)
+            sm.sB[i] = planck_bin_f((float)T, (float)wlo, (float)whi);
+        else
+            sm.sB[i] = planck_bin_d(T, wlo, whi);
+    }
+    for (int bb = threadIdx.x; bb < nbc; bb += blockDim.x) {
+        const int b = b_lo + bb;
+        const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
+        sm.sFs[bb] = (R)kp.F_star[ci.bin0 + b];
+        if constexpr (sizeof(R) == 4)
+            sm.sFB[bb] = kPiF * planck_bin_f((float)kp.T_int, (float)wlo, (float)whi);
+        else
+            sm.sFB[bb] = kPi * planck_bin_d(kp.T_int, wlo, whi);
+    }
+}
+
+// Butterfly sum of two values over the warp; lane 0 stores the warp partial.
+template <typename R>
+__device__ __forceinline__ void warp_store(R a, R n, int level, int nwarps, R *wpart) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        wpart[2 * (level * nwarps + w)] = a;
+        wpart[2 * (level * nwarps + w) + 1] = n;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void fold_warps(int L, int nwarps, Smem<R> &sm) {
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) {
+        double sa = 0.0, sn = 0.0;
+        for (int w = 0; w < nwarps; ++w) {
+            sa += (double)sm.wpart[2 * (i * nwarps + w)];
+            sn += (double)sm.wpart[2 * (i * nwarps + w) + 1];
+        }
+        sm.acc[2 * i] += sa;
+        sm.acc[2 * i + 1] += sn;
+    }
+}
+
+__device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &ci, const double *acc) {
+    for (int i = threadIdx.x; i <= ci.L; i += blockDim.x) {
+        const double up = acc[2 * i], net = acc[2 * i + 1];
+        kp.F_up[ci.if0 + i] = up;
+        kp.F_net[ci.if0 + i] = net;
+        kp.F_dn[ci.if0 + i] = up - net;
+    }
+    const double gc = kp.grav / kp.cp;
+    for (int l = threadIdx.x; l < ci.L; l += blockDim.x) {
+        const double dF = acc[2 * (l + 1) + 1] - acc[2 * l + 1];
+        const double dp = kp.p_iface[ci.if0 + l + 1] - kp.p_iface[ci.if0 + l];
+        kp.Q[ci.lay0 + l] = gc * dF / dp;
+    }
+}
+
+// ---------------------------------------------------------------------
+// FP32 chosen form.
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(kMaxBlock) fp32_columns(KParams kp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_unit;
+    const int tid = threadIdx.x;
+    const int nwarps = blockDim.x >> 5;
+    Smem<float> sm(smem_raw, kp.Lmax, kp.nb_chunk, nwarps);
+    const int NG = kp.n_g;
+    const long long slot = (long long)blockIdx.x * blockDim.x + tid;
+    float4 *scr = kp.scr32 + slot;
+    const long long sstride = kp.n_slots;
+    Counters cn = {0, 0, 0, 0, 0, 0, 0};
+    ColInfo ci;
+
+    while (next_column(kp, &s_unit, ci)) {
+        for (int i = tid; i < 2 * (ci.L + 1); i += blockDim.x) sm.acc[i] = 0.0;
+        const float mu = (float)ci.mu;
+        const bool beam = ci.mu > 0.0;
+        for (int s0 = 0; s0 < ci.S; s0 += blockDim.x) {
+            const int b_lo = s0 / NG;
+            const int b_hi = min(ci.NB - 1, (s0 + (int)blockDim.x - 1) / NG);
+            const int nbc = b_hi - b_lo + 1;
+            stage_planck<float>(kp, ci, b_lo, nbc, sm);
+            __syncthreads();
+
+            const int s = s0 + tid;
+            const bool active = s < ci.S;
+            cn.on = active ? 1u : 0u;
+            const int b = active ? s / NG : b_lo;
+            const int bb = b - b_lo;
+            const float wg = active ? (float)kp.g_w[s - b * NG] : 0.f;
+            const float *Bcol = sm.sB + bb;        // level stride nbc
+
+            // forward elimination, TOA -> BOA, departure variables
+            float al = 1.f;                                      // alpha' = 1 - a'
+            float bl = (float)kp.F_toa - kPiF * Bcol[0];         // b' at the TOA
+            float Fb = beam ? mu * sm.sFs[bb] : 0.f;
+            const long long base = ci.cube0 + s;
+            for (int l = 0; l < ci.L; ++l) {
+                float dt = 0.f, w0 = 0.f, g0 = 0.f;
+                if (active) {
+                    const long long idx = base + (long long)l * ci.S;
+                    dt = __ldg(kp.dtau + idx);
+                    w0 = __ldg(kp.w0 + idx);
+                    g0 = __ldg(kp.g0 + idx);
+                }
+                const float Bt = Bcol[(2 * l) * nbc], Bc = Bcol[(2 * l + 1) * nbc],
+                            Bb = Bcol[(2 * l + 2) * nbc];
+                const Layer32 ly = layer32(dt, w0, g0, Bt, Bc, Bb, mu, ci.mu, beam, Fb, kp, cn);
+                const float omr = ly.omtr + ly.T;                // 1 - R
+                const float ipv = 1.f / fmaf(ly.R, al, omr);     // 1 / (1 - R a')
+                float4 st;
+                st.x = ly.T * ipv;                               // P
+                st.y = fmaf(ly.R, bl, ly.Su) * ipv;              // Q
+                st.z = al;                                       // alpha' at interface l
+                st.w = bl + Fb;                                  // e = b' + F_beam
+                scr[(long long)l * sstride] = st;
+                const float al_n = fmaf(al, fmaf(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
+                const float bl_n = ly.Sd + ly.T * fmaf(1.f - al, ly.Su, bl) * ipv;
+                al = al_n;
+                bl = bl_n;
+                Fb *= ly.mlay;
+            }
+            // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b'
+            const float FBOA = sm.sFB[bb];
+            float uu = active ? (FBOA + Fb + bl) / al : 0.f;
+            warp_store<float>(wg * (kPiF * Bcol[(2 * ci.L) * nbc] + uu), wg * FBOA, ci.L, nwarps,
+                              sm.wpart);
+            bool bad = !isfinite(uu);
+            for (int l = ci.L - 1; l >= 0; --l) {
+                float fup = 0.f, fnet = 0.f;
+                if (active) {
+                    const float4 st = scr[(long long)l * sstride];
+                    uu = fmaf(st.x, uu, st.y);
+                    fup = kPiF * Bcol[(2 * l) * nbc] + uu;
+                    fnet = st.z * uu - st.w;
+                    bad |= !isfinite(uu);
+                }
+                warp_store<float>(wg * fup, wg * fnet, l, nwarps, sm.wpart);
+            }
+            if (active && bad) cn.nonfinite++;
+            __syncthreads();
+            fold_warps<float>(ci.L, nwarps, sm);
+            __syncthreads();
+        }
+        write_column(kp, ci, sm.acc);
+        __syncthreads();
+    }
+    flush_counters(cn, kp.stats);
+}
+
+// ---------------------------------------------------------------------
+// FP64 plain path: the paper's formulas as written (App. B), scalar
+// elimination over every level.
+// ---------------------------------------------------------------------
+struct Sub64 {
+    double t, r, su, sd;
+};
+
+__device__ __forceinline__ void g_factors64(double w0, double g0, double E, double mus, double eps2,
+                                            double D, double &Gp, double &Gm) {
+    const double omwg = 1.0 - w0 * g0;
+    const double lead = w0 * (2.0 * E * omwg + g0 / eps2) / D;
+    const double tail = w0 * g0 / (2.0 * eps2 * E * omwg);
+    Gp = 0.5 * (lead * (mus + 1.0 / (2.0 * E * omwg)) + tail);
+    Gm = 0.5 * (lead * (mus - 1.0 / (2.0 * E * omwg)) - tail);
+}
+
+__device__ __forceinline__ Sub64 sub64(double dts, double w0, double g0, double E, double B1,
+                                       double Biso, double B2, double mu, double Fb1, double Fb2,
+                                       const KParams &kp, Counters &cn, bool count_layer) {
+    const double omwg = 1.0 - w0 * g0;
+    const double k = sqrt((E - w0) / (E * omwg));
+    const double zp = 0.5 * (1.0 + k), zm = 0.5 * (1.0 - k);
+    const double Pi = (E == w0) ? kPi : kPi * (1.0 - w0) / (E - w0);
+    double chi, xi, psi;
+    if (k > 0.0) {
+        const double T = exp(-2.0 * sqrt(E * (E - w0) * omwg) * dts);
+        chi = zm * zm * T * T - zp * zp;
+        xi = zp * zm * (1.0 - T * T);
+        psi = (zm * zm - zp * zp) * T;
+    } else {
+        const double q = E * omwg;
+        chi = -(1.0 + q * dts);
+        xi = q * dts;
+        psi = -1.0;
+    }
+    double Su, Sd;
+    if (kp.isothermal) {
+        Su = Pi * Biso * (chi + xi - psi);
+        Sd = Su;
+    } else {
+        double Bt = B1, Bb = B2, Bp;
+        if (dts < (double)1e-4f) {
+            Bt = Bb = 0.5 * (B1 + B2);
+            Bp = 0.0;
+            cn.etau += cn.on;
+        } else {
+            Bp = (B2 - B1) / dts;
+        }
+        const double Theta = (chi - psi - xi) / (2.0 * E * omwg);
+        Su = Pi * (Bt * (chi + xi) - psi * Bb + Bp * Theta);
+        Sd = Pi * (Bb * (chi + xi) - psi * Bt - Bp * Theta);
+    }
+    if (mu > 0.0) {
+        const double mus = -mu;
+        const double D = 4.0 * E * mus * mus * (E - w0) * omwg - 1.0;
+        double bu, bd;
+        bool avg = false;
+        double Dx = D;
+        if (fabs(D) < 1e-5) {
+            if (count_layer) cn.res += cn.on;
+            if (kp.resonance_paper) Dx = 2.0 * mus;
+            else if (fabs(D) < 1e-7) avg = true;
+        }
+        if (!avg) {
+            double Gp, Gm;
+            g_factors64(w0, g0, E, mus, kp.eps2, Dx, Gp, Gm);
+            bu = psi * Gp * Fb2 - (xi * Gm + chi * Gp) * Fb1;
+            bd = psi * Gm * Fb1 - (xi * Gp + chi * Gm) * Fb2;
+        } else {
+            // exact limit: mean of the per-unit-beam source at mu (1 -+ 5e-6)
+            bu = bd = 0.0;
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double mu2 = mu * (1.0 + sg * 5e-6);
+                const double D2 = 4.0 * E * mu2 * mu2 * (E - w0) * omwg - 1.0;
+                double Gp, Gm;
+                g_factors64(w0, g0, E, -mu2, kp.eps2, D2, Gp, Gm);
+                const double m2 = exp(-dts / mu2);
+                bu += 0.5 * Fb1 * (psi * Gp * m2 - (xi * Gm + chi * Gp));
+                bd += 0.5 * Fb1 * (psi * Gm - (xi * Gp + chi * Gm) * m2);
+            }
+        }
+        Su += bu;
+        Sd += bd;
+    }
+    Sub64 o;
+    o.t = psi / chi;
+    o.r = -xi / chi;
+    o.su = Su / chi;
+    o.sd = Sd / chi;
+    return o;
+}
+
+__global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_unit;
+    const int tid = threadIdx.x;
+    const int nwarps = blockDim.x >> 5;
+    Smem<double> sm(smem_raw, kp.Lmax, kp.nb_chunk, nwarps);
+    const int NG = kp.n_g;
+    const long long slot = (long long)blockIdx.x * blockDim.x + tid;
+    double2 *scr = kp.scr64 + slot;           // element (2 lev + j) n_slots + slot
+    Counters cn = {0, 0, 0, 0, 0, 0, 0};
+    ColInfo ci;
+    const bool iso = kp.isothermal;
+
+    while (next_column(kp, &s_unit, ci)) {
+        for (int i = tid; i < 2 * (ci.L + 1); i += blockDim.x) sm.acc[i] = 0.0;
+        const double mu = ci.mu;
+        const bool beam = mu > 0.0;
+        const int nsub = iso ? ci.L : 2 * ci.L;
+        for (int s0 = 0; s0 < ci.S; s0 += blockDim.x) {
+            const int b_lo = s0 / NG;
+            const int b_hi = min(ci.NB - 1, (s0 + (int)blockDim.x - 1) / NG);
+            const int nbc = b_hi - b_lo + 1;
+            stage_planck<double>(kp, ci, b_lo, nbc, sm);
+            __syncthreads();
+
+            const int s = s0 + tid;
+            const bool active = s < ci.S;
+            cn.on = active ? 1u : 0u;
+            const int b = active ? s / NG : b_lo;
+            const int bb = b - b_lo;
+            const double wg = active ? kp.g_w[s - b * NG] : 0.0;
+            const double *Bcol = sm.sB + bb;
+            const double Fs = sm.sFs[bb];
+
+            double a = 0.0, bv = kp.F_toa;       // F_dn = a F_up + b at the TOA
+            double tau = 0.0;
+            double Fb = beam ? mu * Fs : 0.0;
+            const long long base = ci.cube0 + s;
+            for (int l = 0; l < ci.L; ++l) {
+                double dt = 0.0, w0 = 0.0, g0 = 0.0;
+                float w0f = 0.f, g0f = 0.f;
+                if (active) {
+                    const long long idx = base + (long long)l * ci.S;
+                    dt = (double)__ldg(kp.dtau + idx);
+                    w0f = __ldg(kp.w0 + idx);
+                    g0f = __ldg(kp.g0 + idx);
+                    w0 = (double)w0f;
+                    g0 = (double)g0f;
+                }
+                if (!(dt >= 0.0) || !(w0 >= 0.0 && w0 <= 1.0) || !(g0 > -1.0 && g0 < 1.0)) cn.inv += cn.on;
+                double E = 1.0;
+                if (kp.improved && w0 > (double)0.1f) {
+                    E = 1.225 - 0.1582 * g0 - 0.1777 * w0 - 0.07465 * g0 * g0 + 0.2351 * w0 * g0
+                        - 0.05582 * w0 * w0;
+                    if (kp.e_clamp && E < 1.0) {
+                        E = 1.0;
+                        cn.eclamp += cn.on;
+                    }
+                }
+                const int nh = iso ? 1 : 2;
+                for (int hsub = 0; hsub < nh; ++hsub) {
+                    const double dts = iso ? dt : 0.5 * dt;
+                    const int lev = iso ? l : 2 * l + hsub;        // top level of the sub-layer
+                    const double B1 = iso ? 0.0 : Bcol[lev * nbc];
+                    const double B2 = iso ? 0.0 : Bcol[(lev + 1) * nbc];
+                    const double Biso = iso ? Bcol[(2 * l + 1) * nbc] : 0.0;
+                    const double tau2 = tau + dts;
+                    const double Fb2 = beam ? mu * Fs * exp(-tau2 / mu) : 0.0;
+                    const Sub64 sb = sub64(dts, w0, g0, E, B1, Biso, B2, mu, Fb, Fb2, kp, cn, hsub == 0);
+                    const double piv = 1.0 - sb.r * a;
+                    double2 st0, st1;
+                    st0.x = sb.t / piv;                            // P
+                    st0.y = (sb.r * bv + sb.su) / piv;             // Q
+                    st1.x = a;
+                    st1.y = bv + Fb;                               // b + F_beam at the top level
+                    scr[(long long)(2 * lev) * kp.n_slots] = st0;
+                    scr[(long long)(2 * lev + 1) * kp.n_slots] = st1;
+                    const double a_n = sb.r + sb.t * sb.t * a / piv;
+                    const double b_n = sb.sd + sb.t * (bv + a * sb.su) / piv;
+                    a = a_n;
+                    bv = b_n;
+                    tau = tau2;
+                    Fb = Fb2;
+                }
+            }
+            // BOA (Eq. 10): F_up - F_dn = F_BOA + F_beam, F_dn = a F_up + b
+            const double FBOA = sm.sFB[bb];
+            double fu = active ? (FBOA + Fb + bv) / (1.0 - a) : 0.0;
+            double fnet = active ? (1.0 - a) * fu - (bv + Fb) : 0.0;
+            warp_store<double>(wg * fu, wg * fnet, ci.L, nwarps, sm.wpart);
+            bool bad = !isfinite(fu);
+            for (int lev = nsub - 1; lev >= 0; --lev) {
+                if (active) {
+                    const double2 st0 = scr[(long long)(2 * lev) * kp.n_slots];
+                    const double2 st1 = scr[(long long)(2 * lev + 1) * kp.n_slots];
+                    fu = st0.x * fu + st0.y;
+                    fnet = (1.0 - st1.x) * fu - st1.y;
+                    bad |= !isfinite(fu);
+                }
+                const bool is_iface = iso || ((lev & 1) == 0);
+                if (is_iface) {
+                    const int i = iso ? lev : (lev >> 1);
+                    warp_store<double>(active ? wg * fu : 0.0, active ? wg * fnet : 0.0, i, nwarps,
+                                       sm.wpart);
+                }
+            }
+            if (active && bad) cn.nonfinite++;
+            __syncthreads();
+            fold_warps<double>(ci.L, nwarps, sm);
+            __syncthreads();
+        }
+        write_column(kp, ci, sm.acc);
+        __syncthreads();
+    }
+    flush_counters(cn, kp.stats);
+}
+
+constexpr int kMaxDynSmem = 200 * 1024;
+
+cudaError_t init_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(fp32_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fp64_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+}
+
+int occupancy(int precision_fp64, int block, size_t smem) {
+    if (smem > (size_t)kMaxDynSmem) return 0;
+    int n = 0;
+    cudaError_t e = precision_fp64
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_columns, block, smem);
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
+    fp32_columns<<<grid, block, smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
+    fp64_columns<<<grid, block, smem, s>>>(kp);
+    return cudaGetLastError();
+}
+
+}  // namespace rt

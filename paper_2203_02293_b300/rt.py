@@ -1,0 +1,201 @@
+"""ctypes binding of the C ABI in include/rt.h.
+
+Argument marshalling only: every step of the radiative-transfer path runs in
+the CUDA library.  If librt.so is missing the import fails; there is no
+fallback.  Device arrays are passed as torch CUDA tensors (PyTorch provides
+device memory and streams and nothing else).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librt.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENOTSOLVED, RT_EBUDGET, RT_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+RT_IMPROVED, RT_REGULAR = 0, 1
+RT_NONISOTHERMAL, RT_ISOTHERMAL = 0, 1
+RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
+RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
+
+_STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
+           -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}
+
+
+class rt_config(ctypes.Structure):
+    _fields_ = [
+        ("n_g", ctypes.c_int32), ("g_weights", ctypes.POINTER(ctypes.c_double)),
+        ("wn_min", ctypes.c_double), ("wn_max", ctypes.c_double),
+        ("two_stream", ctypes.c_int32), ("layers", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("resonance", ctypes.c_int32),
+        ("e_clamp", ctypes.c_int32),
+        ("eps2", ctypes.c_double), ("grav", ctypes.c_double), ("cp", ctypes.c_double),
+        ("T_int", ctypes.c_double), ("F_toa_diffuse", ctypes.c_double),
+        ("max_layers", ctypes.c_int32), ("max_bins", ctypes.c_int32),
+        ("hbm_budget_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
+    ]
+
+
+class rt_columns(ctypes.Structure):
+    _fields_ = [
+        ("n_cols", ctypes.c_int32),
+        ("n_layers", ctypes.POINTER(ctypes.c_int32)), ("n_bins", ctypes.POINTER(ctypes.c_int32)),
+        ("L", ctypes.c_int32), ("NB", ctypes.c_int32),
+        ("dtau", ctypes.c_void_p), ("w0", ctypes.c_void_p), ("g0", ctypes.c_void_p),
+        ("T_center", ctypes.c_void_p), ("T_iface", ctypes.c_void_p), ("p_iface", ctypes.c_void_p),
+        ("mu_star", ctypes.c_void_p), ("F_star", ctypes.c_void_p),
+    ]
+
+
+class rt_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "systems", "resonance_hits", "etau_hits", "eclamp_hits", "invalid_inputs",
+        "nonfinite_outputs", "fp64_evals")]
+
+
+def _load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                           "`python -m paper_2203_02293_b300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    lib.rt_create.argtypes = [ctypes.POINTER(rt_config), ctypes.POINTER(H)]
+    lib.rt_query_bytes.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.POINTER(ctypes.c_size_t)]
+    lib.rt_solve_columns.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p]
+    lib.rt_fluxes.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_heating.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_stats.argtypes = [H, ctypes.POINTER(rt_stats_t)]
+    lib.rt_last_error.argtypes = [H]
+    lib.rt_last_error.restype = ctypes.c_char_p
+    lib.rt_destroy.argtypes = [H]
+    lib.rt_destroy.restype = None
+    for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
+              "rt_stats"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_lib: ctypes.CDLL | None = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+class RTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int, handle=None):
+    if code != RT_OK:
+        msg = lib().rt_last_error(handle).decode() if handle else ""
+        raise RTError(code, msg)
+
+
+def _ptr(t) -> int | None:
+    """Raw address of a torch tensor / numpy array (None passes NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+@dataclass
+class Config:
+    """Python mirror of rt_config with the paper's defaults (Table 3)."""
+    g_weights: np.ndarray
+    wn_min: float = 50.0
+    wn_max: float = 1.0e4 / 0.3
+    two_stream: int = RT_IMPROVED
+    layers: int = RT_NONISOTHERMAL
+    precision: int = RT_FP32_FORM
+    resonance: int = RT_RESONANCE_PAPER
+    e_clamp: int = 1
+    eps2: float = 2.0 / 3.0
+    grav: float = 47.0
+    cp: float = 12436.0
+    T_int: float = 100.0
+    F_toa_diffuse: float = 0.0
+    max_layers: int = 1024
+    max_bins: int = 4096
+    hbm_budget_bytes: int = 0
+    block_threads: int = 0
+
+
+def rt_create(cfg: Config):
+    """Create a handle (returns an opaque ctypes pointer)."""
+    gw = np.ascontiguousarray(cfg.g_weights, dtype=np.float64)
+    c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
+                  cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
+                  cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
+                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads)
+    h = ctypes.c_void_p()
+    _check(lib().rt_create(ctypes.byref(c), ctypes.byref(h)))
+    return h
+
+
+def make_columns(n_cols: int, n_layers, n_bins, dtau, w0, g0, T_center, T_iface, p_iface,
+                 mu_star, F_star, L: int = 0, NB: int = 0):
+    """Build an rt_columns descriptor.  n_layers / n_bins are host int32 arrays
+    (or None with uniform L, NB); the rest are device tensors.  The returned
+    object keeps the host shape arrays alive."""
+    nl = None if n_layers is None else np.ascontiguousarray(n_layers, dtype=np.int32)
+    nb = None if n_bins is None else np.ascontiguousarray(n_bins, dtype=np.int32)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    c = rt_columns(n_cols, nl.ctypes.data_as(P32) if nl is not None else None,
+                   nb.ctypes.data_as(P32) if nb is not None else None, L, NB,
+                   _ptr(dtau), _ptr(w0), _ptr(g0), _ptr(T_center), _ptr(T_iface), _ptr(p_iface),
+                   _ptr(mu_star), _ptr(F_star))
+    c._keep = (nl, nb)
+    return c
+
+
+def rt_query_bytes(h, cols) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().rt_query_bytes(h, ctypes.byref(cols), ctypes.byref(n)), h)
+    return n.value
+
+
+def rt_solve_columns(h, cols, stream=None):
+    _check(lib().rt_solve_columns(h, ctypes.byref(cols), _stream_ptr(stream)), h)
+
+
+def rt_fluxes(h, F_up=None, F_down=None, F_net=None, stream=None):
+    _check(lib().rt_fluxes(h, _ptr(F_up), _ptr(F_down), _ptr(F_net), _stream_ptr(stream)), h)
+
+
+def rt_heating(h, Q, stream=None):
+    _check(lib().rt_heating(h, _ptr(Q), _stream_ptr(stream)), h)
+
+
+def rt_stats(h) -> dict:
+    s = rt_stats_t()
+    _check(lib().rt_stats(h, ctypes.byref(s)), h)
+    return {n: getattr(s, n) for n, _ in rt_stats_t._fields_}
+
+
+def rt_last_error(h) -> str:
+    return lib().rt_last_error(h).decode()
+
+
+def rt_destroy(h):
+    if h:
+        lib().rt_destroy(h)

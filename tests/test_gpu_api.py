@@ -1,0 +1,124 @@
+"""C-ABI behaviour on the GPU: validation, error codes, budgets, streams."""
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import assert_parity, gpu_solver, method_opts, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_02293_b300 import rt  # noqa: E402
+from paper_2203_02293_b300.solver import DeviceBatch, Solver  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def small():
+    cols = rt_synth.generate([5, 9, 3], [4, 2, 6], 3, seed=61, optics="uniform")
+    return cols, DeviceBatch(cols)
+
+
+def test_fluxes_before_solve(small):
+    s = Solver(small[0].g_weights)
+    with pytest.raises(rt.RTError) as e:
+        s.outputs(small[1])
+    assert e.value.code == rt.RT_ENOTSOLVED
+    s.close()
+
+
+def test_malformed_descriptors(small):
+    cols, b = small
+    s = Solver(cols.g_weights, max_layers=8)
+    with pytest.raises(rt.RTError) as e:      # 9 layers > max_layers
+        s.solve(b)
+    assert e.value.code == rt.RT_EINVAL and "n_layers" in str(e.value)
+    s.close()
+    s = Solver(cols.g_weights)
+    bad = rt.make_columns(3, b.n_layers, b.n_bins, b.dtau, b.w0, None, b.T_center, b.T_iface,
+                          b.p_iface, b.mu_star, b.F_star)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_solve_columns(s.h, bad)
+    assert e.value.code == rt.RT_EINVAL and "g0" in str(e.value)
+    neg = rt.make_columns(-1, None, None, b.dtau, b.w0, b.g0, b.T_center, b.T_iface, b.p_iface,
+                          b.mu_star, b.F_star, L=5, NB=4)
+    with pytest.raises(rt.RTError):
+        rt.rt_solve_columns(s.h, neg)
+    zero_nb = rt.make_columns(3, b.n_layers, np.array([4, 0, 6], np.int32), b.dtau, b.w0, b.g0,
+                              b.T_center, b.T_iface, b.p_iface, b.mu_star, b.F_star)
+    with pytest.raises(rt.RTError):
+        rt.rt_solve_columns(s.h, zero_nb)
+    s.close()
+
+
+def test_empty_batch_is_a_no_op(small):
+    cols, b = small
+    s = Solver(cols.g_weights)
+    empty = rt.make_columns(0, None, None, None, None, None, None, None, None, None, None, L=1, NB=1)
+    rt.rt_solve_columns(s.h, empty)
+    rt.rt_fluxes(s.h, None, None, None)
+    assert s.stats()["systems"] == 0
+    s.close()
+
+
+def test_budget_refusal(small):
+    cols, b = small
+    s = Solver(cols.g_weights, hbm_budget_bytes=1024)
+    need = s.query_bytes(b)
+    assert need > 1024
+    with pytest.raises(rt.RTError) as e:
+        s.solve(b)
+    assert e.value.code == rt.RT_EBUDGET
+    s.close()
+    s = Solver(cols.g_weights, hbm_budget_bytes=need)
+    s.solve(b)
+    s.close()
+
+
+def test_uniform_shape_descriptor_and_side_stream(small):
+    cols = rt_synth.generate([12] * 5, [7] * 5, 4, seed=62, optics="ktable")
+    b = DeviceBatch(cols)
+    ref = oracle_solve(cols, method_opts())
+    s = gpu_solver(cols, method_opts(), "fp32")
+    desc = rt.make_columns(5, None, None, b.dtau, b.w0, b.g0, b.T_center, b.T_iface, b.p_iface,
+                           b.mu_star, b.F_star, L=12, NB=7)
+    st = torch.cuda.Stream()
+    rt.rt_solve_columns(s.h, desc, st)
+    o = s.outputs(b, stream=st)
+    st.synchronize()
+    got = {k: v.cpu().numpy() for k, v in o.items()}
+    assert_parity(cols, got, ref, "fp32", "uniform+stream")
+    # outputs read on another stream after the solve are ordered after it
+    o2 = s.outputs(b, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(o2["F_up"].cpu().numpy(), got["F_up"])
+    s.close()
+
+
+def test_outputs_to_host_memory(small):
+    cols, b = small
+    s = Solver(cols.g_weights)
+    s.solve(b)
+    up = np.zeros(b.n_if)
+    q = np.zeros(b.n_lay)
+    rt.rt_fluxes(s.h, up, None, None)
+    rt.rt_heating(s.h, q)
+    torch.cuda.synchronize()
+    o = s.outputs(b)
+    torch.cuda.synchronize()
+    assert np.array_equal(up, o["F_up"].cpu().numpy())
+    assert np.array_equal(q, o["Q"].cpu().numpy())
+    s.close()
+
+
+def test_repeated_solves_reuse_workspace_and_change_shape():
+    a = rt_synth.generate([30, 4], [10, 3], 5, seed=63, optics="uniform")
+    c = rt_synth.generate([7, 50, 2, 9], [2, 12, 20, 1], 5, seed=64, optics="uniform")
+    s = gpu_solver(a, method_opts(), "fp32")
+    for cols in (a, c, a, c):
+        b = DeviceBatch(cols)
+        got = s.solve_numpy(b)
+        assert_parity(cols, got, oracle_solve(cols, method_opts()), "fp32", "reuse")
+    s.close()

@@ -1,0 +1,178 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element.
+
+Every test here calls the C-ABI library on the GPU and the oracle on the CPU
+with the same seeded inputs.  Sizes span several CTAs, partial warps and
+partial bins; the full GCM-shaped and precision-stress workloads are checked
+over every column.
+"""
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import assert_parity, gpu_solve, method_opts, oracle_solve, strict_errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    return rt_synth.config0()
+
+
+@pytest.fixture(scope="module")
+def cfg0_ref(cfg0):
+    return oracle_solve(cfg0, method_opts())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_config0_parity(cfg0, cfg0_ref, precision):
+    got = gpu_solve(cfg0, method_opts(), precision)
+    e = assert_parity(cfg0, got, cfg0_ref, precision, "config0")
+    print(precision, "config0 error/tol", e)
+    st, rs = got["stats"], cfg0_ref["stats"]
+    assert st["systems"] == 64 * 30
+    assert st["etau_hits"] == rs["etau_hits"]
+    assert st["resonance_hits"] == rs["resonance_hits"]
+    assert st["eclamp_hits"] == rs["eclamp_hits"]
+    assert st["invalid_inputs"] == 0 and st["nonfinite_outputs"] == 0
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return rt_synth.config1()
+
+
+@pytest.fixture(scope="module")
+def cfg1_ref(cfg1):
+    return oracle_solve(cfg1, method_opts())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_config1_gcm_shaped_full(cfg1, cfg1_ref, precision):
+    got = gpu_solve(cfg1, method_opts(), precision)
+    e = assert_parity(cfg1, got, cfg1_ref, precision, "config1")
+    print(precision, "config1 error/tol", e)
+    if precision == "fp32":
+        print("config1 fp32 strict-reading error/tol", strict_errors(cfg1, got, cfg1_ref))
+    st, rs = got["stats"], cfg1_ref["stats"]
+    assert st["systems"] == 2562 * 600
+    assert st["etau_hits"] == rs["etau_hits"]
+    assert st["resonance_hits"] == rs["resonance_hits"]
+
+
+def test_config2_precision_stress_full():
+    cols = rt_synth.config2()
+    ref = oracle_solve(cols, method_opts())
+    got = gpu_solve(cols, method_opts(), "fp32")
+    e = assert_parity(cols, got, ref, "fp32", "config2")
+    print("config2 fp32 error/tol", e, "strict", strict_errors(cols, got, ref))
+    print("config2 stats gpu", got["stats"], "oracle", ref["stats"])
+    assert got["stats"]["eclamp_hits"] > 0
+
+
+MODES = {
+    "isothermal": dict(isothermal=True),
+    "regular": dict(improved=False),
+    "limit": dict(resonance="limit"),
+    "no_interior_flux": dict(T_int=0.0),
+    "toa_diffuse": dict(F_toa=25.0),
+    "eps2_half": dict(eps2=0.5),
+    "iso_regular_limit": dict(isothermal=True, improved=False, resonance="limit"),
+}
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_method_switches_on_ragged_batch(mode, precision):
+    L, NB = rt_synth.uneven_shapes(37, seed=5, L_range=(1, 60), NB_range=(1, 41))
+    cols = rt_synth.generate(L, NB, 7, seed=11, optics="uniform")
+    opts = method_opts(**MODES[mode])
+    ref = oracle_solve(cols, opts)
+    got = gpu_solve(cols, opts, precision)
+    assert_parity(cols, got, ref, precision, mode)
+    assert got["stats"]["etau_hits"] == ref["stats"]["etau_hits"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ktable_ragged_many_bins(precision):
+    """Columns up to 200 layers and 300 bins with k-table optical depths."""
+    cols = rt_synth.generate([200, 20, 113, 57], [300, 30, 7, 171], 20, seed=23, optics="ktable")
+    ref = oracle_solve(cols, method_opts())
+    got = gpu_solve(cols, method_opts(), precision)
+    assert_parity(cols, got, ref, precision, "ragged-ktable")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_edge_cases(precision):
+    # one layer, one bin, one g-point; night side; sun at zenith; opaque and
+    # transparent layers; w0 = 0 and w0 = 1 exactly; zero optical depth
+    cols = rt_synth.generate([1, 1, 5, 3, 4, 2], [1, 2, 1, 3, 2, 1], 1, seed=3, optics="uniform")
+    cols.mu_star[:] = [1.0, -0.5, 0.0, 1e-3, 0.999, 0.5]
+    o = cols.offsets()
+    c3 = slice(o["cube"][3], o["cube"][4])
+    cols.dtau[c3] = np.array([0.0, 1e4, 1e-7, 3.0, 0.0, 2.0, 1e-3, 50.0, 1e-9], np.float32)
+    cols.w0[c3] = np.array([0.0, 1.0, 1.0, 0.0, 0.5, 1.0, 0.999, 0.2, 1.0], np.float32)
+    c4 = slice(o["cube"][4], o["cube"][5])
+    cols.w0[c4] = 1.0
+    cols.g0[c4] = 0.0
+    for opts in (method_opts(), method_opts(improved=False), method_opts(isothermal=True)):
+        ref = oracle_solve(cols, opts)
+        got = gpu_solve(cols, opts, precision)
+        assert_parity(cols, got, ref, precision, f"edge {opts}")
+
+
+@pytest.mark.parametrize("block", [64, 96, 160, 512])
+def test_block_sizes_and_partial_chunks(block):
+    L, NB = rt_synth.uneven_shapes(19, seed=8, L_range=(2, 50), NB_range=(3, 33))
+    cols = rt_synth.generate(L, NB, 20, seed=9, optics="ktable")
+    ref = oracle_solve(cols, method_opts())
+    for precision in ("fp32", "fp64"):
+        got = gpu_solve(cols, method_opts(), precision, block_threads=block)
+        assert_parity(cols, got, ref, precision, f"block {block}")
+
+
+def test_fp32_column_alone_equals_column_in_batch():
+    """Fixed reduction order: a column's bits do not depend on the batch."""
+    L, NB = rt_synth.uneven_shapes(24, seed=31, L_range=(5, 80), NB_range=(3, 40))
+    cols = rt_synth.generate(L, NB, 20, seed=32, optics="uniform")
+    full = gpu_solve(cols, method_opts(), "fp32")
+    o = cols.offsets()
+    for c in (0, 7, 23):
+        alone = gpu_solve(cols.subset([c]), method_opts(), "fp32")
+        sl = slice(o["iface"][c], o["iface"][c + 1])
+        for k in ("F_up", "F_down", "F_net"):
+            assert np.array_equal(alone[k], full[k][sl]), (c, k)
+        assert np.array_equal(alone["Q"], full["Q"][o["lay"][c]:o["lay"][c + 1]])
+
+
+def test_resonance_counts_and_limit_mode():
+    """Layers placed right on mu* alpha = 1: both sides count the same hits;
+    limit mode agrees with the oracle's limit mode."""
+    cols = rt_synth.generate([6] * 4, [2] * 4, 3, seed=41, optics="uniform")
+    w0 = np.float32(0.6); g0 = np.float32(0.3)
+    E = 1.225 - 0.1582 * float(g0) - 0.1777 * float(w0) - 0.07465 * float(g0) ** 2 \
+        + 0.2351 * float(w0) * float(g0) - 0.05582 * float(w0) ** 2
+    alpha = 2 * np.sqrt(E * (E - float(w0)) * (1 - float(w0) * float(g0)))
+    cols.w0[:] = w0
+    cols.g0[:] = g0
+    cols.mu_star[:] = (1.0 + np.array([2e-6, -3e-6, 1e-9, 0.2])) / alpha
+    for res in ("paper", "limit"):
+        opts = method_opts(resonance=res)
+        ref = oracle_solve(cols, opts)
+        for precision in ("fp32", "fp64"):
+            got = gpu_solve(cols, opts, precision)
+            assert got["stats"]["resonance_hits"] == ref["stats"]["resonance_hits"] == 3 * 6 * 6
+            assert_parity(cols, got, ref, precision, f"resonance {res}")
+
+
+def test_invalid_inputs_are_counted_not_hidden():
+    cols = rt_synth.generate([4, 4], [2, 2], 2, seed=51, optics="uniform")
+    cols.w0[3] = np.float32(1.5)
+    cols.dtau[9] = np.float32("nan")
+    got = gpu_solve(cols, method_opts(), "fp32")
+    assert got["stats"]["invalid_inputs"] == 2
+    assert got["stats"]["nonfinite_outputs"] >= 1
