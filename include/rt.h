@@ -130,7 +130,7 @@ int rt_create(const rt_config *cfg, rt_handle **out);
 /* Device workspace (bytes) that a solve of cols needs, outputs included. */
 int rt_query_bytes(const rt_handle *h, const rt_columns *cols, size_t *bytes);
 
-/* Enqueue the whole path for cols on stream: Planck per bin (R13), layer
+/* Enqueue the whole path for cols on stream: Planck per bin, layer
  * coefficients (App. B), beam (Eq. B6), sources, Thomas elimination,
  * spectral sum, net flux and heating.  Results stay in the handle until the
  * next solve.  Validates shapes and pointers synchronously (RT_EINVAL);

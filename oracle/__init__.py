@@ -114,7 +114,7 @@ class Oracle:
 
     # -- Planck -------------------------------------------------------
     def planck_bin(self, T: float, wn_lo: float, wn_hi: float) -> float:
-        """Bin-integrated Planck function, W m^-2 sr^-1 (reading R13)."""
+        """Bin-integrated Planck function, W m^-2 sr^-1."""
         return self.lib.oracle_planck_bin(float(T), float(wn_lo), float(wn_hi))
 
     # -- one system ---------------------------------------------------

@@ -23,17 +23,22 @@
  * Planck per bin is the bin integral of the Planck function, done by
  * composite Gauss-Legendre quadrature (nodes found by Newton iteration).
  *
- * Readings where the paper is silent (all shared with the GPU path):
- *   R1 mu* = -cos(theta*) inside G+-;  R3 |D| < 1e-5 -> D := 2 mu* (paper
- *   mode), or no switch at all (limit mode: the exact solution, see
- *   sub_layer for |D| < 1e-7);  R4 E :=
- *   max(E_fit, 1) unless raw;  R5 fit iff w0 > 0.1f;  R6 e_tau test on
- *   dtau_sub < 1e-4f, dtau_sub = dtau/2;  R7 both sub-layers carry the
- *   layer's w0, g0 and half its optical depth;  R8 F_BOA = pi B(T_int);
- *   R10 Q = (g/cp) dFnet/dp;  R12 block entries as documented in
- *   oracle_assemble;  R13 B is the bin-integrated Planck function;  R20
- *   E = w0 = 1 uses the k -> 0 limit of the relations (all three of chi,
- *   xi, psi divided by k) and Pi := pi.
+ * Readings where the paper is silent or ambiguous (the CUDA path takes the
+ * same ones):
+ *   - mu* enters G+- with the Malik sign, mu* = -cos(theta*) < 0 (App. B);
+ *   - resonance (Eq. 11): when |D| < 1e-5 the paper mode sets D := 2 mu*;
+ *     the limit mode keeps the exact solution (see sub_layer for |D| < 1e-7);
+ *   - E := max(E_fit, 1) unless the raw fit is asked for; the fit applies for
+ *     w0 > 0.1f, i.e. the threshold is the FP32 value of 0.1;
+ *   - the e_tau test is dtau_sub < 1e-4f with dtau_sub = dtau / 2; both
+ *     sub-layers carry the layer's w0, g0 and half its optical depth;
+ *   - F_BOA = pi B(T_int) per bin; no beam when cos(theta*) <= 0;
+ *   - Q_l = (g / c_P) (F_net,bot - F_net,top) / (p_bot - p_top);
+ *   - the block entries of Eq. 12 (the figures that draw them are missing)
+ *     are documented in assemble();
+ *   - B is the Planck function integrated over the bin;
+ *   - E = w0 = 1 uses the k -> 0 limit of the relations (chi, xi, psi all
+ *     divided by k) and Pi := pi.
  *
  * Level convention inside the oracle: level 0 is the bottom of the
  * atmosphere (BOA), level n the top (TOA), as in the paper.  Arrays passed
@@ -55,7 +60,7 @@ typedef struct {
     int32_t improved;       /* 1: E from Eq. 19; 0: regular two-stream, E = 1 */
     int32_t isothermal;     /* 1: isothermal layers; 0: non-isothermal */
     int32_t resonance;      /* 0: paper rule (D := 2 mu*); 1: limit (exact solution) */
-    int32_t e_clamp;        /* 1: E := max(E_fit, 1) (R4); 0: raw fit */
+    int32_t e_clamp;        /* 1: E := max(E_fit, 1); 0: raw fit */
     double eps2;            /* second Eddington coefficient (Table 3: 2/3) */
     double grav, cp;        /* m s^-2, J kg^-1 K^-1 */
     double T_int;           /* K, interior temperature; 0 -> F_BOA = 0 */
@@ -71,7 +76,7 @@ typedef struct {
 } oracle_stats;
 
 /* ------------------------------------------------------------------ */
-/* Planck function integrated over a wavenumber bin (reading R13).      */
+/* Planck function integrated over a wavenumber bin.                    */
 /* ------------------------------------------------------------------ */
 
 /* Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n. */
@@ -175,11 +180,11 @@ static void layer_coeffs(const oracle_cfg *cfg, double w0, double g0, double mu,
     c->eclamp_hit = 0;
     c->resonance_hit = 0;
     c->limit_avg = 0;
-    /* Eq. 19: the fit applies for w0 > 0.1 (threshold taken as 0.1f, R5) */
+    /* Eq. 19: the fit applies for w0 > 0.1 (threshold taken as 0.1f) */
     if (cfg->improved && w0 > (double)0.1f) {
         E = 1.225 - 0.1582 * g0 - 0.1777 * w0 - 0.07465 * g0 * g0
             + 0.2351 * w0 * g0 - 0.05582 * w0 * w0;
-        if (cfg->e_clamp && E < 1.0) {   /* R4 */
+        if (cfg->e_clamp && E < 1.0) {   /* keep E - w0 >= 1 - w0 > 0 */
             E = 1.0;
             c->eclamp_hit = 1;
         }
@@ -190,11 +195,11 @@ static void layer_coeffs(const oracle_cfg *cfg, double w0, double g0, double mu,
     c->k = sqrt((E - w0) / (E * (1.0 - w0 * g0)));
     c->zeta_p = 0.5 * (1.0 + c->k);
     c->zeta_m = 0.5 * (1.0 - c->k);
-    /* Eq. B5; R20: Pi := pi when E = w0 = 1 */
+    /* Eq. B5; Pi := pi when E = w0 = 1 (its limit along E = 1) */
     c->Pi = (E == w0) ? OR_PI : OR_PI * (1.0 - w0) / (E - w0);
     c->Gp = c->Gm = 0.0;
     if (mu > 0.0) {
-        double mus = -mu;   /* R1: mu* < 0 in Eq. B8 */
+        double mus = -mu;   /* Malik sign: mu* < 0 in Eq. B8 */
         double D = resonance_D(w0, g0, E, mus);
         if (fabs(D) < 1e-5) {
             c->resonance_hit = 1;
@@ -245,7 +250,7 @@ static void sub_layer(const oracle_cfg *cfg, const layer_coef *c, double w0,
         xi = zp * zm * (1.0 - T * T);
         psi = (zm * zm - zp * zp) * T;
     } else {
-        /* R20: E = w0 = 1.  chi, xi, psi all vanish like k; the relations
+        /* E = w0 = 1.  chi, xi, psi all vanish like k; the relations
          * are homogeneous in them, so use their k -> 0 limits divided by k. */
         chi = -(1.0 + c->q * dtau);
         xi = c->q * dtau;
@@ -340,7 +345,7 @@ static void setup_system(const oracle_cfg *cfg, int L, const float *dtau,
             w->g0_s[j] = g;
             w->B_iso[j] = Bc[l];
         } else {
-            /* R7: two sub-layers with half the optical depth each */
+            /* two sub-layers with half the optical depth each */
             for (int h = 0; h < 2; ++h) {
                 w->dtau_s[2 * j + h] = 0.5 * d;
                 w->w0_s[2 * j + h] = a;
@@ -359,7 +364,7 @@ static void setup_system(const oracle_cfg *cfg, int L, const float *dtau,
             double mus = -mu;
             w->Fb[i] = -mus * Fstar * exp(w->tau[i] / mus);
         } else {
-            w->Fb[i] = 0.0;   /* R19: night side, no beam */
+            w->Fb[i] = 0.0;   /* night side, no beam */
         }
     }
 }
@@ -386,7 +391,7 @@ static void relations(const oracle_cfg *cfg, double mu, sys_work *w,
 }
 
 /* ------------------------------------------------------------------ */
-/* Block-tridiagonal assembly (Eq. 12, reading R12) and block Thomas    */
+/* Block-tridiagonal assembly (Eq. 12) and block Thomas                 */
 /* (Eqs. 13-15).  X_i = (F_up,i, F_dn,i) at level i = 0 (BOA) .. n.     */
 /*   row 0:  F_up,0 - F_dn,0 = F_BOA + F_beam,0 (Eq. 10);               */
 /*           downward relation of sub-layer 0.                          */
@@ -647,7 +652,7 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                     double lo = cfg->wn_min + b * dwn, hi = lo + dwn;
                     for (int l = 0; l < L; ++l) Bc[l] = oracle_planck_bin(Tc[l], lo, hi);
                     for (int i = 0; i <= L; ++i) Bi[i] = oracle_planck_bin(Ti[i], lo, hi);
-                    double F_BOA = OR_PI * oracle_planck_bin(cfg->T_int, lo, hi);  /* R8 */
+                    double F_BOA = OR_PI * oracle_planck_bin(cfg->T_int, lo, hi);  /* Eq. 10 */
                     double Fs = F_star[bin_off[c] + b];
                     for (int g = 0; g < n_g; ++g) {
                         const float *cb = dtau + cube_off[c] + (int64_t)b * n_g + g;
@@ -707,7 +712,7 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                     dn[i] = sum_dn[i];
                     net[i] = sum_up[i] - sum_dn[i];
                 }
-                /* R10: Q_l = (g/cp) (F_net,bot - F_net,top) / (p_bot - p_top) */
+                /* Q_l = (g/cp) (F_net,bot - F_net,top) / (p_bot - p_top) */
                 for (int l = 0; l < L; ++l)
                     q[l] = cfg->grav / cfg->cp * (net[l + 1] - net[l]) / (p[l + 1] - p[l]);
             }

@@ -32,16 +32,18 @@ struct rt_handle {
     int device = 0;
     int sm_count = 0;
     double *d_gw = nullptr;
+    float *d_gw32 = nullptr;
     // plan
     DevBuf plan;                  // n_layers, n_bins, order (int32) + offsets (int64)
     std::vector<int32_t> plan_nl, plan_nb;
     bool plan_valid = false;
+    int plan_prec = -1;
     void *h_stage = nullptr;      // pinned staging for plan uploads
     size_t stage_cap = 0;
     cudaEvent_t stage_ev = nullptr;
     bool stage_pending = false;
     // outputs and scratch
-    DevBuf out, scr;
+    DevBuf out, scr, aux;          // aux: FP32 unit partials + per-column completion counters
     int32_t *d_counter = nullptr;
     unsigned long long *d_stats = nullptr;
     cudaEvent_t done_ev = nullptr;
@@ -71,21 +73,23 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Sizes derived from one batch.
 struct Plan {
-    std::vector<int32_t> nl, nb, order;
-    std::vector<int64_t> cube_off, lay_off, bin_off;
-    int64_t n_if = 0, n_lay = 0, n_sys = 0, n_cube = 0, n_bins = 0;
+    std::vector<int32_t> nl, nb, order, col_units, unit_col, unit_k;
+    std::vector<int64_t> cube_off, lay_off, bin_off, part_off, planck_off;
+    int64_t n_if = 0, n_lay = 0, n_sys = 0, n_cube = 0, n_bins = 0, n_part = 0, n_planck = 0;
+    int64_t n_units = 0;
     int Lmax = 0, NBmax = 0;
     // launch
-    int block = 0, grid = 0, nb_chunk = 0;
+    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0;
     size_t smem = 0;
     int64_t n_slots = 0;
-    // workspace layout (bytes)
-    size_t plan_bytes = 0, out_bytes = 0, scr_bytes = 0;
+    // workspace layout (bytes); the plan blob is int32 arrays then int64 arrays
+    size_t i32_count = 0, plan_bytes = 0, out_bytes = 0, scr_bytes = 0, aux_bytes = 0;
 };
 
 int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
     const rt_config &cfg = h->cfg;
     const int n = c->n_cols;
+    const bool fp64 = cfg.precision == RT_FP64_PLAIN;
     P.nl.resize(n);
     P.nb.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -99,14 +103,23 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
     P.cube_off.resize(n);
     P.lay_off.resize(n);
     P.bin_off.resize(n);
-    int64_t cube = 0, lay = 0, bins = 0;
+    P.part_off.resize(n);
+    P.planck_off.resize(n);
+    P.col_units.resize(n);
+    int64_t cube = 0, lay = 0, bins = 0, part = 0, planck = 0;
     for (int i = 0; i < n; ++i) {
         P.cube_off[i] = cube;
         P.lay_off[i] = lay;
         P.bin_off[i] = bins;
-        cube += (int64_t)P.nl[i] * P.nb[i] * cfg.n_g;
+        P.part_off[i] = part;
+        P.planck_off[i] = planck;
+        planck += (int64_t)(2 * P.nl[i] + 1) * P.nb[i];
+        const int64_t S = (int64_t)P.nb[i] * cfg.n_g;
+        P.col_units[i] = (int32_t)((S + 31) / 32);
+        cube += (int64_t)P.nl[i] * S;
         lay += P.nl[i];
         bins += P.nb[i];
+        part += (int64_t)P.col_units[i] * 2 * (P.nl[i] + 1);
         P.Lmax = std::max(P.Lmax, (int)P.nl[i]);
         P.NBmax = std::max(P.NBmax, (int)P.nb[i]);
     }
@@ -115,36 +128,61 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
     P.n_if = lay + n;
     P.n_bins = bins;
     P.n_sys = bins * cfg.n_g;
+    P.n_part = part;
+    P.n_planck = planck;
     // largest work first (longest-processing-time order), ties by index
     P.order.resize(n);
     std::iota(P.order.begin(), P.order.end(), 0);
     std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) {
         return (int64_t)P.nl[a] * P.nb[a] > (int64_t)P.nl[b] * P.nb[b];
     });
-    // launch shape
-    const bool fp64 = cfg.precision == RT_FP64_PLAIN;
-    P.block = cfg.block_threads;
+    if (!fp64) {
+        for (int oi = 0; oi < n; ++oi) {
+            const int col = P.order[oi];
+            for (int k = 0; k < P.col_units[col]; ++k) {
+                P.unit_col.push_back(col);
+                P.unit_k.push_back(k);
+            }
+        }
+        P.n_units = (int64_t)P.unit_col.size();
+        if (P.n_units > INT32_MAX) return fail(h, RT_EINVAL, "too many work units");
+    }
+    // launch shape (the FP32 kernel is compiled for at most 256 threads)
+    P.block = fp64 ? cfg.block_threads : std::min(cfg.block_threads, rt::kMaxBlock32);
     if (n > 0) {
         for (;;) {
-            P.nb_chunk = rt::bins_per_chunk(P.block, cfg.n_g, P.NBmax);
-            P.smem = fp64 ? rt::fp64_smem_bytes(P.block, P.Lmax, P.nb_chunk)
-                          : rt::fp32_smem_bytes(P.block, P.Lmax, P.nb_chunk);
-            const int occ = rt::occupancy(fp64, P.block, P.smem);
-            if (occ > 0) {
-                P.grid = std::min<int64_t>(n, (int64_t)occ * h->sm_count);
-                break;
+            int occ;
+            if (fp64) {
+                P.nb_chunk = rt::bins_per_chunk(P.block, cfg.n_g, P.NBmax);
+                P.smem = rt::fp64_smem_bytes(P.block, P.Lmax, P.nb_chunk);
+                occ = rt::occupancy(1, P.block, P.smem);
+                if (occ > 0) P.grid = (int)std::min<int64_t>(n, (int64_t)occ * h->sm_count);
+            } else {
+                P.nbw = rt::bins_per_chunk(32, cfg.n_g, P.NBmax);
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw);
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw);
+                occ = rt::occupancy(0, P.block, P.smem);
+                const int64_t wpb = P.block / 32;
+                if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
+            if (occ > 0) break;
             if (P.block <= 64)
                 return fail(h, RT_EINVAL, "no launch shape fits shared memory (L=%d, NB=%d)", P.Lmax, P.NBmax);
             P.block -= 32;
         }
         P.n_slots = (int64_t)P.grid * P.block;
     }
-    P.plan_bytes = align_up(sizeof(int32_t) * 3 * (size_t)n, 256) + align_up(sizeof(int64_t) * 3 * (size_t)n, 256);
+    P.i32_count = 4 * (size_t)n + 2 * (size_t)P.n_units;
+    P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 5 * (size_t)n, 256);
     P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256);
     P.scr_bytes = (size_t)P.n_slots *
                   (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
                         : rt::fp32_scratch_per_slot(P.Lmax));
+    // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf
+    P.aux_bytes = fp64 ? 0
+                       : align_up(sizeof(float) * (size_t)P.n_part, 256) + align_up(sizeof(int32_t) * (size_t)n, 256) +
+                             align_up(sizeof(float) * (size_t)P.n_planck, 256) +
+                             2 * align_up(sizeof(float) * (size_t)P.n_bins, 256) + align_up(sizeof(float4) * (size_t)n, 256);
     return RT_OK;
 }
 
@@ -220,6 +258,9 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     if (e == cudaSuccess) e = rt::init_kernels();
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_gw, sizeof(double) * cfg->n_g);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_gw, h->gw.data(), sizeof(double) * cfg->n_g, cudaMemcpyHostToDevice);
+    std::vector<float> gw32(h->gw.begin(), h->gw.end());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_gw32, sizeof(float) * cfg->n_g);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_gw32, gw32.data(), sizeof(float) * cfg->n_g, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_counter, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_stats, sizeof(unsigned long long) * rt::ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT);
@@ -242,7 +283,7 @@ int rt_query_bytes(const rt_handle *hc, const rt_columns *cols, size_t *bytes) {
     Plan P;
     rc = build_plan(h, cols, P);
     if (rc) return rc;
-    *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes;
+    *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes;
     return RT_OK;
 }
 
@@ -255,9 +296,9 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     rc = build_plan(h, cols, P);
     if (rc) return rc;
     const rt_config &cfg = h->cfg;
-    if (cfg.hbm_budget_bytes && P.plan_bytes + P.out_bytes + P.scr_bytes > cfg.hbm_budget_bytes)
-        return fail(h, RT_EBUDGET, "workspace %zu bytes exceeds budget %zu",
-                    P.plan_bytes + P.out_bytes + P.scr_bytes, cfg.hbm_budget_bytes);
+    const size_t ws_bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes;
+    if (cfg.hbm_budget_bytes && ws_bytes > cfg.hbm_budget_bytes)
+        return fail(h, RT_EBUDGET, "workspace %zu bytes exceeds budget %zu", ws_bytes, cfg.hbm_budget_bytes);
     cudaStream_t s = (cudaStream_t)stream;
     const bool cap = stream_capturing(s);
     // order after the previous solve of this handle when it ran on another stream
@@ -271,16 +312,23 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     if (h->plan.p != old_plan) h->plan_valid = false;
     if ((rc = grow(h, h->out, std::max<size_t>(P.out_bytes, 256), cap, "output"))) return rc;
     if ((rc = grow(h, h->scr, std::max<size_t>(P.scr_bytes, 256), cap, "scratch"))) return rc;
+    if ((rc = grow(h, h->aux, std::max<size_t>(P.aux_bytes, 256), cap, "partial-sum"))) return rc;
 
     char *pb = (char *)h->plan.p;
     int32_t *d_nl = (int32_t *)pb;
     int32_t *d_nb = d_nl + n;
     int32_t *d_order = d_nb + n;
-    int64_t *d_cube = (int64_t *)(pb + align_up(sizeof(int32_t) * 3 * (size_t)n, 256));
+    int32_t *d_cu = d_order + n;
+    int32_t *d_ucol = d_cu + n;
+    int32_t *d_uk = d_ucol + P.n_units;
+    int64_t *d_cube = (int64_t *)(pb + align_up(sizeof(int32_t) * P.i32_count, 256));
     int64_t *d_lay = d_cube + n;
     int64_t *d_bin = d_lay + n;
+    int64_t *d_poff = d_bin + n;
+    int64_t *d_pkoff = d_poff + n;
 
-    const bool same_plan = h->plan_valid && h->plan_nl == P.nl && h->plan_nb == P.nb;
+    const bool same_plan = h->plan_valid && h->plan_nl == P.nl && h->plan_nb == P.nb &&
+                           h->plan_prec == cfg.precision;
     if (n > 0 && !same_plan) {
         if (cap) return fail(h, RT_EINVAL, "a new batch shape cannot be planned during stream capture");
         const size_t need = P.plan_bytes;
@@ -301,19 +349,28 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
             h->stage_cap = need;
         }
         char *hs = (char *)h->h_stage;
-        memcpy(hs, P.nl.data(), sizeof(int32_t) * n);
-        memcpy(hs + sizeof(int32_t) * n, P.nb.data(), sizeof(int32_t) * n);
-        memcpy(hs + sizeof(int32_t) * 2 * n, P.order.data(), sizeof(int32_t) * n);
-        char *hs64 = hs + align_up(sizeof(int32_t) * 3 * (size_t)n, 256);
-        memcpy(hs64, P.cube_off.data(), sizeof(int64_t) * n);
-        memcpy(hs64 + sizeof(int64_t) * n, P.lay_off.data(), sizeof(int64_t) * n);
-        memcpy(hs64 + sizeof(int64_t) * 2 * n, P.bin_off.data(), sizeof(int64_t) * n);
+        int32_t *h32 = (int32_t *)hs;
+        memcpy(h32, P.nl.data(), sizeof(int32_t) * n);
+        memcpy(h32 + n, P.nb.data(), sizeof(int32_t) * n);
+        memcpy(h32 + 2 * n, P.order.data(), sizeof(int32_t) * n);
+        memcpy(h32 + 3 * n, P.col_units.data(), sizeof(int32_t) * n);
+        if (P.n_units) {
+            memcpy(h32 + 4 * n, P.unit_col.data(), sizeof(int32_t) * P.n_units);
+            memcpy(h32 + 4 * n + P.n_units, P.unit_k.data(), sizeof(int32_t) * P.n_units);
+        }
+        int64_t *h64 = (int64_t *)(hs + align_up(sizeof(int32_t) * P.i32_count, 256));
+        memcpy(h64, P.cube_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + n, P.lay_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 2 * n, P.bin_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 3 * n, P.part_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 4 * n, P.planck_off.data(), sizeof(int64_t) * n);
         cudaError_t e = cudaMemcpyAsync(h->plan.p, h->h_stage, need, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "plan upload");
         h->stage_pending = true;
         h->plan_nl = P.nl;
         h->plan_nb = P.nb;
+        h->plan_prec = cfg.precision;
         h->plan_valid = true;
     }
 
@@ -325,6 +382,24 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
 
     cudaError_t e = cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counter, 0, sizeof(int32_t), s);
+    int32_t *d_done = nullptr;
+    float *d_part = nullptr, *d_planck = nullptr, *d_fs = nullptr, *d_fboa = nullptr;
+    float4 *d_colf = nullptr;
+    if (P.aux_bytes) {
+        char *a = (char *)h->aux.p;
+        d_part = (float *)a;
+        a += align_up(sizeof(float) * (size_t)P.n_part, 256);
+        d_done = (int32_t *)a;
+        a += align_up(sizeof(int32_t) * (size_t)n, 256);
+        d_planck = (float *)a;
+        a += align_up(sizeof(float) * (size_t)P.n_planck, 256);
+        d_fs = (float *)a;
+        a += align_up(sizeof(float) * (size_t)P.n_bins, 256);
+        d_fboa = (float *)a;
+        a += align_up(sizeof(float) * (size_t)P.n_bins, 256);
+        d_colf = (float4 *)a;
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_done, 0, sizeof(int32_t) * (size_t)n, s);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
 
     if (n > 0) {
@@ -369,6 +444,21 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         kp.wn_max = cfg.wn_max;
         kp.Lmax = P.Lmax;
         kp.nb_chunk = P.nb_chunk;
+        kp.unit_col = d_ucol;
+        kp.unit_k = d_uk;
+        kp.col_units = d_cu;
+        kp.part_off = d_poff;
+        kp.partial = d_part;
+        kp.col_done = d_done;
+        kp.n_units = (int32_t)P.n_units;
+        kp.warp_floats = P.warp_floats;
+        kp.nbw = P.nbw;
+        kp.planck32 = d_planck;
+        kp.planck_off = d_pkoff;
+        kp.fs32 = d_fs;
+        kp.fboa32 = d_fboa;
+        kp.colf = d_colf;
+        kp.g_w32 = h->d_gw32;
         e = cfg.precision == RT_FP64_PLAIN ? rt::launch_fp64(kp, P.grid, P.block, P.smem, s)
                                            : rt::launch_fp32(kp, P.grid, P.block, P.smem, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
@@ -443,9 +533,11 @@ void rt_destroy(rt_handle *h) {
     if (!h) return;
     cudaDeviceSynchronize();
     cudaFree(h->d_gw);
+    cudaFree(h->d_gw32);
     cudaFree(h->plan.p);
     cudaFree(h->out.p);
     cudaFree(h->scr.p);
+    cudaFree(h->aux.p);
     cudaFree(h->d_counter);
     cudaFree(h->d_stats);
     if (h->h_stage) cudaFreeHost(h->h_stage);

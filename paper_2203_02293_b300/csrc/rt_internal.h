@@ -37,6 +37,22 @@ struct KParams {
     float4 *scr32;               // FP32 form: (P, Q, alpha', e) per interface
     double2 *scr64;              // FP64 path: 2 x double2 = (P, Q), (a, e) per level
     int64_t n_slots;
+    // FP32 form: warp-sized work units (32 consecutive systems of a column)
+    const int32_t *unit_col;     // [n_units] column of each unit, largest column first
+    const int32_t *unit_k;       // [n_units] index of the unit within its column
+    const int32_t *col_units;    // [n_cols] units per column
+    const int64_t *part_off;     // [n_cols] offset of the column's partial sums
+    float *partial;              // per unit and interface: (sum w F_up, sum w F_net)
+    int32_t *col_done;           // [n_cols] finished units per column (zeroed per solve)
+    int32_t n_units;
+    int32_t warp_floats;         // shared-memory floats per warp
+    // FP32 form: per-column staging written by fp32_prep
+    float *planck32;             // B per column [2L+1][NB] (levels: 2i interface, 2i+1 centre)
+    const int64_t *planck_off;   // [n_cols]
+    float *fs32, *fboa32;        // [sum NB] F* and F_BOA per bin
+    float4 *colf;                // [n_cols] (mu, 1/mu, beam?, 0)
+    const float *g_w32;          // [n_g] Gauss weights in FP32
+    int32_t nbw;                 // bins one warp's 32 systems can touch
     // scheduling and counters
     int32_t *counter;
     unsigned long long *stats;
@@ -49,7 +65,8 @@ struct KParams {
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nb_chunk);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw);
+int fp32_warp_floats(int Lmax, int nbw);
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);
@@ -67,7 +84,8 @@ cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cud
 
 // Largest L the kernels support.
 constexpr int kMaxLayers = 1024;
-// Largest CTA size (launch bounds of both kernels).
+// Largest CTA size (launch bounds): FP64 kernel, FP32 kernel.
 constexpr int kMaxBlock = 512;
+constexpr int kMaxBlock32 = 256;
 
 }  // namespace rt

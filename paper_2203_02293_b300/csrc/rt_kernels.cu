@@ -21,7 +21,7 @@
 // same bits whatever else is in the batch (for a fixed block size).
 //
 // Two arithmetic variants:
-//   fp32_columns  -- the FP32 "chosen form": cancellation-free transmission,
+//   fp32_units    -- the FP32 "chosen form": cancellation-free transmission,
 //                    reflection and absorption forms, a beam source with the
 //                    removable singularity at mu* alpha = 1 divided out, and
 //                    departure variables u = F - pi B at every level.  FP64 is
@@ -86,10 +86,39 @@ __device__ __forceinline__ float planck_lower_f(float x) {
     return fmaf(x2 * x2, s, head) * x2 * x;
 }
 
+// Fast FP32 primitives: MUFU reciprocal, reciprocal square root and
+// exponential (ex2 with the argument scaled by log2 e).  Each is accurate to a
+// few ulp, far inside the 1e-4 target.
+__device__ __forceinline__ float frcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+
+// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.5
+// (9 terms, truncation below 6e-10), else from the exponential e = exp(-x).
+__device__ __forceinline__ float u_series(float x) {
+    float p = 1.f / 362880.f;
+    p = fmaf(p, x, -1.f / 40320.f);
+    p = fmaf(p, x, 1.f / 5040.f);
+    p = fmaf(p, x, -1.f / 720.f);
+    p = fmaf(p, x, 1.f / 120.f);
+    p = fmaf(p, x, -1.f / 24.f);
+    p = fmaf(p, x, 1.f / 6.f);
+    p = fmaf(p, x, -0.5f);
+    return fmaf(p, x, 1.f);
+}
+__device__ __forceinline__ float one_minus_exp_over_x(float x, float e) {
+    const float s = u_series(x);
+    const float d = (1.f - e) * frcp(x);
+    return (fabsf(x) < 0.5f) ? s : d;
+}
+
 // FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
 //   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms.
 __device__ __forceinline__ float planck_upper_f(float x) {
-    const float e = expf(-x);
+    const float e = fexp(-x);
     const float x2 = x * x, x3 = x2 * x;
     float en = e, s = 0.f;
 #pragma unroll
@@ -106,7 +135,7 @@ __device__ __forceinline__ float planck_upper_f(float x) {
 // (cm^-1), FP32.  The difference is taken in the form without cancellation.
 __device__ float planck_bin_f(float T, float wlo, float whi) {
     if (!(T > 0.f)) return 0.f;
-    const float a = (float)(kC2 * 100.0) / T;
+    const float a = (float)(kC2 * 100.0) * frcp(T);
     const float xlo = a * wlo, xhi = a * whi;
     float d;
     if (xlo >= 2.f) {
@@ -232,60 +261,56 @@ struct Layer32 {
     float T, R, Su, Sd, omtr, opr, mlay;
 };
 
-__device__ __forceinline__ void thermal_sub(float dPi, float Pi, float t, float r, float omtr,
-                                            float gs, bool fallback, float B1, float B2,
-                                            float &su, float &sd) {
-    if (!fallback) {
-        const float omr = omtr + t;            // 1 - r
-        const float grad = Pi * (B2 - B1) * gs;
-        su = dPi * (omr * B1 - t * B2) + grad;
-        sd = dPi * (omr * B2 - t * B1) - grad;
-    } else {
-        // optical depth below e_tau: isothermal at the mean B (Sec. 2.2.1)
-        const float Bm = 0.5f * (B1 + B2), hdB = 0.5f * (B2 - B1);
-        const float side = kPiF * hdB * (omtr + 2.f * t);   // pi dB/2 (1 - r + t)
-        su = dPi * Bm * omtr + side;
-        sd = dPi * Bm * omtr - side;
-    }
+// Thermal sources of one sub-layer for departures from pi B at its ends.
+// Both the gradient form and the e_tau fallback (isothermal at the mean B,
+// Sec. 2.2.1) are evaluated and one is selected, so lanes do not diverge.
+__device__ __forceinline__ void thermal_sub(float dPi, float Pi, float t, float omtr, float gs,
+                                            bool fallback, float B1, float B2, float &su, float &sd) {
+    const float omr = omtr + t;                  // 1 - r
+    const float dB = B2 - B1;
+    const float grad = Pi * dB * gs;
+    const float su_g = dPi * (omr * B1 - t * B2) + grad;
+    const float sd_g = dPi * (omr * B2 - t * B1) - grad;
+    const float base = dPi * 0.5f * (B1 + B2) * omtr;
+    const float side = 0.5f * kPiF * dB * (omtr + 2.f * t);  // pi dB/2 (1 - r + t)
+    su = fallback ? base + side : su_g;
+    sd = fallback ? base - side : sd_g;
 }
 
 __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float Bt, float Bc, float Bb,
-                                           float mu, double mu_d, bool beam, float Fb,
+                                           float mu, float imu, double mu_d, bool beam, float Fb,
                                            const KParams &kp, Counters &cn) {
-    if (!(dt >= 0.f) || !(w0 >= 0.f && w0 <= 1.f) || !(g0 > -1.f && g0 < 1.f)) cn.inv += cn.on;
+    const bool invalid = !(dt >= 0.f) || !(w0 >= 0.f && w0 <= 1.f) || !(g0 > -1.f && g0 < 1.f);
+    cn.inv += invalid ? cn.on : 0u;
     // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
-    float em1 = 0.f;
-    if (kp.improved && w0 > 0.1f) {
-        em1 = 0.225f - 0.1582f * g0 - 0.1777f * w0 - 0.07465f * g0 * g0 + 0.2351f * w0 * g0
-              - 0.05582f * w0 * w0;
-        if (kp.e_clamp && em1 < 0.f) {
-            em1 = 0.f;
-            cn.eclamp += cn.on;
-        }
-    }
+    float em1 = 0.225f - 0.1582f * g0 - 0.1777f * w0 - 0.07465f * g0 * g0 + 0.2351f * w0 * g0
+                - 0.05582f * w0 * w0;
+    em1 = (kp.improved && w0 > 0.1f) ? em1 : 0.f;
+    const bool clamp = kp.e_clamp && em1 < 0.f;
+    cn.eclamp += clamp ? cn.on : 0u;
+    em1 = clamp ? 0.f : em1;
     const float E = 1.f + em1;
     const float omw = 1.f - w0;
     const float ewm = em1 + omw;                 // E - w0
     const float q = E * (1.f - w0 * g0);
-    const float k = sqrtf(ewm / q);
-    float Pi = kPiF, dPi = 0.f;                  // E = w0 = 1: Pi := pi
-    if (ewm > 0.f) {
-        const float iw = 1.f / ewm;
-        Pi = kPiF * omw * iw;
-        dPi = -kPiF * em1 * iw;                  // Pi - pi
-    }
-    const float ip = 1.f / (1.f + k);
+    const float iq = frcp(q);
+    const bool cons = ewm == 0.f;                // E = w0 = 1: k = 0, Pi := pi
+    const float k = cons ? 0.f : ewm * rsqrtf(ewm * q);
+    const float iw = frcp(ewm);
+    const float Pi = cons ? kPiF : kPiF * omw * iw;
+    const float dPi = cons ? 0.f : -kPiF * em1 * iw;   // Pi - pi
+    const float ip = frcp(1.f + k);
     const float eps = (1.f - k) * ip;
     const bool iso = kp.isothermal;
     const float dts = iso ? dt : 0.5f * dt;
 
     const float x = 2.f * q * k * dts;
-    const float Tm = expf(-x);
-    const float u = (x > 0.f) ? -expm1f(-x) / x : 1.f;
+    const float Tm = fexp(-x);
+    const float u = one_minus_exp_over_x(x, Tm);
     const float qd = 2.f * q * dts * u;          // (1 - T)/k
     const float h = fmaf(2.f * Tm, ip, qd);
     const float p = fmaf(eps, Tm, 1.f);
-    const float ihp = 1.f / (h * p);
+    const float ihp = frcp(h * p);
     const float t = 4.f * Tm * ip * ip * ihp;
     const float r = eps * qd * (1.f + Tm) * ihp;
     const float omtr = 2.f * k * k * qd * ip * h * ihp;   // 1 - t - r
@@ -294,9 +319,9 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
     float suU, sdU, suL = 0.f, sdL = 0.f;
     if (!iso) {
         const bool fb = dts < 1e-4f;
-        if (fb) cn.etau += 2 * cn.on;
-        thermal_sub(dPi, Pi, t, r, omtr, gs, fb, Bt, Bc, suU, sdU);
-        thermal_sub(dPi, Pi, t, r, omtr, gs, fb, Bc, Bb, suL, sdL);
+        cn.etau += fb ? 2u * cn.on : 0u;
+        thermal_sub(dPi, Pi, t, omtr, gs, fb, Bt, Bc, suU, sdU);
+        thermal_sub(dPi, Pi, t, omtr, gs, fb, Bc, Bb, suL, sdL);
     } else {
         const float omr = omtr + t;
         const float base = dPi * Bc * omtr;
@@ -306,13 +331,13 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
 
     float m = 1.f;
     if (beam) {
-        const float dl = dts / mu;
-        m = expf(-dl);
-        const float omm = -expm1f(-dl);          // 1 - m
+        const float dl = dts * imu;
+        m = fexp(-dl);
+        const float omm = dl * one_minus_exp_over_x(dl, m);   // 1 - m
         const float rho = mu * 2.f * q * k;
         const float ie2 = kp.inv_eps2;
         const float A = w0 * fmaf(g0, ie2, 2.f * q);
-        const float G0h = w0 * g0 * ie2 / (4.f * q);   // G0/2 of Eq. B8
+        const float G0h = 0.25f * w0 * g0 * ie2 * iq;         // G0/2 of Eq. B8
         // resonance test of Eq. 11: decide in FP64 only when FP32 cannot
         const float D32 = fmaf(rho, rho, -1.f);
         bool sw = false;
@@ -324,41 +349,38 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
                 sw = kp.resonance_paper != 0;
             }
         }
+        const float tm1r = -(omtr + 2.f * r + t * omm);        // (t m - 1) - r
+        const float rmtm = (omtr + r) - omm + r * m;           // r m - (t - m)
         float bu, bd;
-        if (sw) {
-            // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
-            const float c1 = 1.f / (2.f * q);
-            const float lead = A / (-2.f * mu);
-            const float Gp = 0.5f * lead * (c1 - mu) + G0h;
-            const float Gm = -0.5f * lead * (c1 + mu) - G0h;
-            bu = -Gp * (omtr + r + t * omm) + r * Gm;         // Gp (t m - 1) + r Gm
-            bd = Gm * (omm - omtr - r) + r * Gp * m;          // Gm (t - m) + r Gp m
-        } else {
+        if (!sw) {
             const float z = (1.f - rho) * dl;
-            float Lam;
-            if (fabsf(z) < 0.5f) {
-                Lam = m * dl * ((z != 0.f) ? expm1f(z) / z : 1.f);
-            } else {
-                Lam = (Tm - m) / (1.f - rho);
-            }
+            const float lam_s = m * dl * u_series(-z);
+            const float lam_d = (Tm - m) * frcp(1.f - rho);
+            const float Lam = (fabsf(z) < 0.5f) ? lam_s : lam_d;
             const float Y = qd * (1.f + Tm);                   // (1 - T^2)/k
-            const float SA = A * ip * ip * ihp / (4.f * q * (1.f + rho));
+            const float SA = 0.25f * A * ip * ip * ihp * iq * frcp(1.f + rho);
             const float tq = 2.f * q * mu;
             const float k2 = k * k;
-            const float tm1r = -(omtr + 2.f * r + t * omm);    // (t m - 1) - r
-            const float rmtm = (omtr + r) - omm + r * m;       // r m - (t - m)
             bu = SA * (2.f * (1.f + k) * Y + 4.f * Tm * (1.f - tq) * Lam) + G0h * tm1r;
             bd = SA * (-2.f * Tm * (1.f - k) * Y
                        + Lam * ((1.f + tq) * (Y * (1.f + k2) + 2.f * (1.f + Tm * Tm))
                                 + (1.f - tq) * (1.f - k2) * Y))
                  + G0h * rmtm;
+        } else {
+            // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
+            const float c1 = 0.5f * iq;
+            const float lead = -0.5f * A * imu;
+            const float Gp = 0.5f * lead * (c1 - mu) + G0h;
+            const float Gm = -0.5f * lead * (c1 + mu) - G0h;
+            bu = -Gp * (omtr + r + t * omm) + r * Gm;         // Gp (t m - 1) + r Gm
+            bd = Gm * (omm - omtr - r) + r * Gp * m;          // Gm (t - m) + r Gp m
         }
-        suU += Fb * bu;
-        sdU += Fb * bd;
+        suU = fmaf(Fb, bu, suU);
+        sdU = fmaf(Fb, bd, sdU);
         if (!iso) {
             const float Fc = Fb * m;
-            suL += Fc * bu;
-            sdL += Fc * bd;
+            suL = fmaf(Fc, bu, suL);
+            sdL = fmaf(Fc, bd, sdL);
         }
     }
 
@@ -374,13 +396,13 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
     } else {
         // merge upper (top -> centre) and lower (centre -> bottom) sub-layers
         const float omr = omtr + t;              // 1 - r
-        const float Dr = 1.f / (omr * (1.f + r));
+        const float Dr = frcp(omr * (1.f + r));  // 1 / (1 - r^2)
         const float tD = t * Dr;
         o.T = t * tD;
         o.R = r * (1.f + o.T);
         o.Su = suU + tD * (suL + r * sdU);
         o.Sd = sdL + tD * (sdU + r * suL);
-        o.omtr = omtr * (omtr + 2.f * t) / omr;
+        o.omtr = omtr * (omtr + 2.f * t) * (1.f + r) * Dr;   // (1-r-t)(1-r+t)/(1-r)
         o.opr = omr * (1.f + o.T);
         o.mlay = m * m;
     }
@@ -405,7 +427,14 @@ __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk
     return b;
 }
 
-size_t fp32_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<float>(block, Lmax, nb_chunk); }
+int fp32_warp_floats(int Lmax, int nbw) {
+    // Planck [(2 Lmax + 1) nbw] + F* [nbw] + F_BOA [nbw] + transpose [16][2][33]
+    int n = (2 * Lmax + 1) * nbw + 2 * nbw + 16 * 2 * 33;
+    return (n + 3) & ~3;
+}
+size_t fp32_smem_bytes(int block, int Lmax, int nbw) {
+    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw);
+}
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
 size_t fp64_scratch_per_slot(int Lmax, int isothermal) {
@@ -526,93 +555,229 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 
 // ---------------------------------------------------------------------
 // FP32 chosen form.
+//
+// fp32_prep: per column, the Planck function of every bin at the 2L+1
+// levels (bin-integrated B, Sec. 2.2.1), F* and F_BOA = pi B(T_int) per bin
+// (Eq. 10), and mu, 1/mu, all in FP32 -- the only place the FP32 path reads
+// the FP64 per-column inputs.
+//
+// fp32_units: each warp takes work units of 32 consecutive systems of one
+// column (an atomic counter over a largest-column-first list), so no CTA
+// barrier is needed and no warp idles on a short column tail.  Per unit the
+// warp stages the B values of the bins its systems touch into its own slice
+// of shared memory, each lane solves one system, and the weighted interface
+// fluxes of the 32 lanes are summed through a padded shared-memory
+// transpose (16 interfaces at a time).  The warp that finishes the last unit
+// of a column sums the column's unit partials in unit order (FP64) and
+// writes fluxes, net flux and heating.
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(kMaxBlock) fp32_columns(KParams kp) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_unit;
-    const int tid = threadIdx.x;
-    const int nwarps = blockDim.x >> 5;
-    Smem<float> sm(smem_raw, kp.Lmax, kp.nb_chunk, nwarps);
+__global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
+    for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
+        const int L = kp.n_layers[c], NB = kp.n_bins[c];
+        const long long lay0 = kp.lay_off[c], if0 = lay0 + c, b0 = kp.bin_off[c];
+        float *B = kp.planck32 + kp.planck_off[c];
+        const float dwn = (float)((kp.wn_max - kp.wn_min) / NB);
+        const float wmin = (float)kp.wn_min;
+        const int nlev = 2 * L + 1;
+        for (int i = threadIdx.x; i < nlev * NB; i += blockDim.x) {
+            const int lev = i / NB, b = i - lev * NB;
+            const float T = (float)((lev & 1) ? kp.T_center[lay0 + (lev >> 1)] : kp.T_iface[if0 + (lev >> 1)]);
+            B[i] = planck_bin_f(T, fmaf((float)b, dwn, wmin), fmaf((float)(b + 1), dwn, wmin));
+        }
+        for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+            kp.fs32[b0 + b] = (float)kp.F_star[b0 + b];
+            kp.fboa32[b0 + b] = kPiF * planck_bin_f((float)kp.T_int, fmaf((float)b, dwn, wmin),
+                                                    fmaf((float)(b + 1), dwn, wmin));
+        }
+        if (threadIdx.x == 0) {
+            const double mu = kp.mu_star[c];
+            kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
+        }
+    }
+}
+
+__device__ void finalize_column(const KParams &kp, int c, int lane) {
+    const int L = kp.n_layers[c];
+    const int nu = kp.col_units[c];
+    const long long if0 = kp.lay_off[c] + c;
+    const float *part = kp.partial + kp.part_off[c];
+    const int stride = 2 * (L + 1);
+    // unit partials are read through L2 (other SMs wrote them)
+    auto sum = [&](int i, int qq) {
+        double a = 0.0;
+        for (int uidx = 0; uidx < nu; ++uidx) a += (double)__ldcg(part + (long long)uidx * stride + 2 * i + qq);
+        return a;
+    };
+    for (int i = lane; i <= L; i += 32) {
+        const double up = sum(i, 0), net = sum(i, 1);
+        kp.F_up[if0 + i] = up;
+        kp.F_net[if0 + i] = net;
+        kp.F_dn[if0 + i] = up - net;
+    }
+    const float gc = (float)(kp.grav / kp.cp);
+    for (int l = lane; l < L; l += 32) {
+        const double dF = sum(l + 1, 1) - sum(l, 1);
+        const float dp = (float)(kp.p_iface[if0 + l + 1] - kp.p_iface[if0 + l]);
+        kp.Q[kp.lay_off[c] + l] = (double)(gc * (float)dF * frcp(dp));
+    }
+}
+
+__global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
+    extern __shared__ __align__(16) float smem32[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *wsm = smem32 + (size_t)warp * kp.warp_floats;
     const int NG = kp.n_g;
-    const long long slot = (long long)blockIdx.x * blockDim.x + tid;
-    float4 *scr = kp.scr32 + slot;
+    const int nbw = kp.nbw;
+    float *sB = wsm;                               // [(2 L + 1) nbc]
+    float *sFs = wsm + (2 * kp.Lmax + 1) * nbw;    // [nbc]
+    float *sFB = sFs + nbw;                        // [nbc]
+    float *tb = sFB + nbw;                         // [16][2][33]
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long sstride = kp.n_slots;
     Counters cn = {0, 0, 0, 0, 0, 0, 0};
-    ColInfo ci;
 
-    while (next_column(kp, &s_unit, ci)) {
-        for (int i = tid; i < 2 * (ci.L + 1); i += blockDim.x) sm.acc[i] = 0.0;
-        const float mu = (float)ci.mu;
-        const bool beam = ci.mu > 0.0;
-        for (int s0 = 0; s0 < ci.S; s0 += blockDim.x) {
-            const int b_lo = s0 / NG;
-            const int b_hi = min(ci.NB - 1, (s0 + (int)blockDim.x - 1) / NG);
-            const int nbc = b_hi - b_lo + 1;
-            stage_planck<float>(kp, ci, b_lo, nbc, sm);
-            __syncthreads();
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(kp.counter, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= kp.n_units) break;
+        const int c = kp.unit_col[unit];
+        const int ku = kp.unit_k[unit];
+        const int L = kp.n_layers[c], NB = kp.n_bins[c];
+        const int S = NB * NG;
+        const long long cube0 = kp.cube_off[c];
+        const float4 cf = kp.colf[c];
+        const float mu = cf.x, imu = cf.y;
+        const double mu_d = kp.mu_star[c];       // only for the rare FP64 resonance test
+        const bool beam = cf.z != 0.f;
+        const int s0 = ku * 32;
+        const int b_lo = s0 / NG;
+        const int nbc = min(NB - 1, (s0 + 31) / NG) - b_lo + 1;
 
-            const int s = s0 + tid;
-            const bool active = s < ci.S;
-            cn.on = active ? 1u : 0u;
-            const int b = active ? s / NG : b_lo;
-            const int bb = b - b_lo;
-            const float wg = active ? (float)kp.g_w[s - b * NG] : 0.f;
-            const float *Bcol = sm.sB + bb;        // level stride nbc
-
-            // forward elimination, TOA -> BOA, departure variables
-            float al = 1.f;                                      // alpha' = 1 - a'
-            float bl = (float)kp.F_toa - kPiF * Bcol[0];         // b' at the TOA
-            float Fb = beam ? mu * sm.sFs[bb] : 0.f;
-            const long long base = ci.cube0 + s;
-            for (int l = 0; l < ci.L; ++l) {
-                float dt = 0.f, w0 = 0.f, g0 = 0.f;
-                if (active) {
-                    const long long idx = base + (long long)l * ci.S;
-                    dt = __ldg(kp.dtau + idx);
-                    w0 = __ldg(kp.w0 + idx);
-                    g0 = __ldg(kp.g0 + idx);
-                }
-                const float Bt = Bcol[(2 * l) * nbc], Bc = Bcol[(2 * l + 1) * nbc],
-                            Bb = Bcol[(2 * l + 2) * nbc];
-                const Layer32 ly = layer32(dt, w0, g0, Bt, Bc, Bb, mu, ci.mu, beam, Fb, kp, cn);
-                const float omr = ly.omtr + ly.T;                // 1 - R
-                const float ipv = 1.f / fmaf(ly.R, al, omr);     // 1 / (1 - R a')
-                float4 st;
-                st.x = ly.T * ipv;                               // P
-                st.y = fmaf(ly.R, bl, ly.Su) * ipv;              // Q
-                st.z = al;                                       // alpha' at interface l
-                st.w = bl + Fb;                                  // e = b' + F_beam
-                scr[(long long)l * sstride] = st;
-                const float al_n = fmaf(al, fmaf(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
-                const float bl_n = ly.Sd + ly.T * fmaf(1.f - al, ly.Su, bl) * ipv;
-                al = al_n;
-                bl = bl_n;
-                Fb *= ly.mlay;
+        // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
+        {
+            const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
+            const int nlev = 2 * L + 1;
+            for (int i = lane; i < nlev * nbc; i += 32) {
+                const int lev = i / nbc, bb = i - lev * nbc;
+                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
             }
-            // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b'
-            const float FBOA = sm.sFB[bb];
-            float uu = active ? (FBOA + Fb + bl) / al : 0.f;
-            warp_store<float>(wg * (kPiF * Bcol[(2 * ci.L) * nbc] + uu), wg * FBOA, ci.L, nwarps,
-                              sm.wpart);
-            bool bad = !isfinite(uu);
-            for (int l = ci.L - 1; l >= 0; --l) {
+            if (lane < nbc) {
+                sFs[lane] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + lane);
+                sFB[lane] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + lane);
+            }
+        }
+        __syncwarp();
+
+        const int s = s0 + lane;
+        const bool active = s < S;
+        cn.on = active ? 1u : 0u;
+        const int b = active ? s / NG : b_lo;
+        const int bb = b - b_lo;
+        const float wg = active ? kp.g_w32[s - b * NG] : 0.f;
+        const float *Bp = sB + bb;                 // level stride nbc
+
+        // forward elimination, TOA -> BOA, departure variables
+        float al = 1.f;                                      // alpha' = 1 - a'
+        float bl = (float)kp.F_toa - kPiF * Bp[0];           // b' at the TOA
+        float Fb = beam ? mu * sFs[bb] : 0.f;
+        const float *pd = kp.dtau + cube0 + s, *pw = kp.w0 + cube0 + s, *pg = kp.g0 + cube0 + s;
+        float nd = 0.f, nw = 0.f, ng = 0.f;
+        if (active) {
+            nd = __ldcs(pd);
+            nw = __ldcs(pw);
+            ng = __ldcs(pg);
+        }
+        float4 *sp = kp.scr32 + slot;
+        for (int l = 0; l < L; ++l) {
+            const float dt = nd, w0 = nw, g0 = ng;
+            if (active && l + 1 < L) {               // prefetch the next layer
+                pd += S; pw += S; pg += S;
+                nd = __ldcs(pd);
+                nw = __ldcs(pw);
+                ng = __ldcs(pg);
+            }
+            const Layer32 ly = layer32(dt, w0, g0, Bp[0], Bp[nbc], Bp[2 * nbc], mu, imu, mu_d, beam, Fb,
+                                       kp, cn);
+            Bp += 2 * nbc;
+            const float omr = ly.omtr + ly.T;                // 1 - R
+            const float ipv = frcp(fmaf(ly.R, al, omr));     // 1 / (1 - R a')
+            float4 st;
+            st.x = ly.T * ipv;                               // P
+            st.y = fmaf(ly.R, bl, ly.Su) * ipv;              // Q
+            st.z = al;                                       // alpha' at interface l
+            st.w = bl + Fb;                                  // e = b' + F_beam
+            __stcg(sp, st);
+            sp += sstride;
+            const float al_n = fmaf(al, fmaf(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
+            const float bl_n = ly.Sd + ly.T * fmaf(1.f - al, ly.Su, bl) * ipv;
+            al = al_n;
+            bl = bl_n;
+            Fb *= ly.mlay;
+        }
+
+        // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b';
+        // back-substitution to the TOA; interface sums through the transpose
+        const float FBOA = sFB[bb];
+        float uu = active ? (FBOA + Fb + bl) * frcp(al) : 0.f;
+        bool bad = !isfinite(uu);
+        float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
+        // Bp points at level 2L (the BOA interface)
+        tb[lane] = wg * fmaf(kPiF, Bp[0], uu);
+        tb[33 + lane] = wg * FBOA;
+        int gi = 1;              // slots used in the current group of 16 interfaces
+        int gtop = L;            // interface held in slot 0 of the group
+        float4 nst = make_float4(0.f, 0.f, 0.f, 0.f);
+        sp -= sstride;           // interface L-1
+        if (active && L > 0) nst = __ldcg(sp);
+        for (int i = L - 1; i >= -1; --i) {
+            if (i >= 0) {
+                const float4 st = nst;
+                if (active && i > 0) {
+                    sp -= sstride;
+                    nst = __ldcg(sp);
+                }
+                Bp -= 2 * nbc;
                 float fup = 0.f, fnet = 0.f;
                 if (active) {
-                    const float4 st = scr[(long long)l * sstride];
                     uu = fmaf(st.x, uu, st.y);
-                    fup = kPiF * Bcol[(2 * l) * nbc] + uu;
-                    fnet = st.z * uu - st.w;
+                    fup = fmaf(kPiF, Bp[0], uu);
+                    fnet = fmaf(st.z, uu, -st.w);
                     bad |= !isfinite(uu);
                 }
-                warp_store<float>(wg * fup, wg * fnet, l, nwarps, sm.wpart);
+                tb[(gi * 2) * 33 + lane] = wg * fup;
+                tb[(gi * 2 + 1) * 33 + lane] = wg * fnet;
+                ++gi;
             }
-            if (active && bad) cn.nonfinite++;
-            __syncthreads();
-            fold_warps<float>(ci.L, nwarps, sm);
-            __syncthreads();
+            if (gi == 16 || (i < 0 && gi > 0)) {
+                __syncwarp();
+                // lane j sums row (slot j & 15, quantity j >> 4) over the 32 lanes
+                const int sl = lane & 15, qq = lane >> 4;
+                if (sl < gi) {
+                    const float *row = tb + (sl * 2 + qq) * 33;
+                    float acc = 0.f;
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) acc += row[j];
+                    part[2 * (gtop - sl) + qq] = acc;
+                }
+                __syncwarp();
+                gtop -= gi;
+                gi = 0;
+            }
         }
-        write_column(kp, ci, sm.acc);
-        __syncthreads();
+        if (active && bad) cn.nonfinite++;
+
+        // the warp that completes a column's last unit writes the column
+        __threadfence();
+        int done = 0;
+        if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done == kp.col_units[c] - 1) {
+            __threadfence();
+            finalize_column(kp, c, lane);
+        }
+        __syncwarp();
     }
     flush_counters(cn, kp.stats);
 }
@@ -830,7 +995,9 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
 constexpr int kMaxDynSmem = 200 * 1024;
 
 cudaError_t init_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(fp32_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    cudaError_t e = cudaFuncSetAttribute(fp32_units, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fp32_units, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fp64_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
@@ -840,12 +1007,16 @@ int occupancy(int precision_fp64, int block, size_t smem) {
     int n = 0;
     cudaError_t e = precision_fp64
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_columns, block, smem);
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
-    fp32_columns<<<grid, block, smem, s>>>(kp);
+    const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
+    fp32_prep<<<pgrid, 256, 0, s>>>(kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fp32_units<<<grid, block, smem, s>>>(kp);
     return cudaGetLastError();
 }
 

@@ -3,8 +3,10 @@ on the same seeded inputs and compare element by element.
 
 Tolerances (from the stated accuracy targets):
   FP64 plain path: |x - x_ref| <= 1e-10 max(|x_ref|, 1e-6 F*_col) for the
-      interface fluxes; heating 1e-8 relative with the same floor carried
-      through dF/dp.
+      interface fluxes F_up and F_down.  The net flux is their difference, so
+      its budget is the sum of theirs: |dF_net| <= 1e-10 (|F_up| + |F_down|)
+      (with the same floor).  Heating 1e-8 relative, floor carried through
+      dF/dp.
   FP32 form: |x - x_ref| <= max(1e-4 |x_ref|, 1e-6 F*_col) for the fluxes and
       max(1e-3 |Q_ref|, (g/c_P) 1e-6 F*_col / dp_l) for the heating rate,
       with F*_col = sum over the column's bins of the stellar flux normal to
@@ -82,7 +84,8 @@ def errors(cols, got, ref, precision):
     for k in ("F_up", "F_down", "F_net"):
         g, r = got[k], ref[k]
         if precision == "fp64":
-            tol = 1e-10 * np.maximum(np.abs(r), f_if)
+            scale = np.abs(ref["F_up"]) + np.abs(ref["F_down"]) if k == "F_net" else np.abs(r)
+            tol = 1e-10 * np.maximum(scale, f_if)
         else:
             tol = np.maximum(1e-4 * np.abs(r), f_if)
         res[k] = float(np.max(np.abs(g - r) / tol)) if r.size else 0.0

@@ -13,7 +13,7 @@ import oracle
 import test_oracle_pins as pins
 
 MUTATIONS = {
-    "mu_star_sign": ("double mus = -mu;   /* R1", "double mus = mu;   /* R1"),
+    "mu_star_sign": ("double mus = -mu;   /* Malik sign", "double mus = mu;   /* Malik sign"),
     "drop_planck_gradient": ("S_up = Pi * (Bt * (chi + xi) - psi * Bb + Bp * Theta);",
                              "S_up = Pi * (Bt * (chi + xi) - psi * Bb + 0.0 * Theta);"),
     "swap_psi_xi_in_block_A": ("a[0] = -r->psi;", "a[0] = -r->xi;"),

@@ -47,7 +47,7 @@ def rel_err(a, b):
 
 
 # ----------------------------------------------------------------------
-# Planck per bin (reading R13)
+# Planck per bin
 # ----------------------------------------------------------------------
 
 @pytest.mark.parametrize("T", [100.0, 800.0, 2000.0, 4798.0])
