@@ -160,6 +160,38 @@ const char *rt_last_error(const rt_handle *h);
 /* Free the handle and its workspace (synchronises the device). */
 void rt_destroy(rt_handle *h);
 
+/* ---------------------------------------------------------------------
+ * Solve without allocating.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc -- code that must remain
+ * capturable into a CUDA graph while it runs, programs whose device memory
+ * belongs to their own pool or to a framework that forbids raw allocations,
+ * and loops that cannot take the device-wide synchronisation an allocation
+ * may bring.
+ *
+ * It runs the FP32 form (cfg->precision must be RT_FP32_FORM) on a batch in
+ * which every column has the same shape (cols->n_layers and cols->n_bins NULL,
+ * cols->L and cols->NB set), with no handle: the caller passes the inputs
+ * (same layout as rt_solve_columns) and DEVICE output arrays F_up, F_down,
+ * F_net [n_cols (L+1)] and Q [n_cols L], written in place (same meaning as
+ * rt_fluxes / rt_heating).  Every intermediate lives in one file-scope device
+ * array of RT_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the
+ * library keeps reserved until the process exits.  It needs about
+ *   8 n_cols NB (L + 2) + 8 n_cols ceil(NB n_g / 32) (L + 1) + 16 L per
+ *   resident thread (at least 64 threads)
+ * bytes; a batch that does not fit returns RT_EBUDGET and nothing runs.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * The first call on a device looks up the array's device address and sets the
+ * kernels' shared-memory limits; make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites what the
+ * previous one left there: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and give wrong results -- order
+ * them.  Returns RT_OK, RT_EINVAL (bad argument), RT_EBUDGET (too large) or
+ * RT_ECUDA. */
+#define RT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *cols, double *F_up,
+                             double *F_down, double *F_net, double *Q, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,10 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_last_error.restype = ctypes.c_char_p
     lib.rt_destroy.argtypes = [H]
     lib.rt_destroy.restype = None
+    lib.rt_solve_uniform_noalloc.argtypes = [ctypes.POINTER(rt_config), ctypes.POINTER(rt_columns),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_solve_uniform_noalloc.restype = ctypes.c_int
     for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
               "rt_stats"):
         getattr(lib, f).restype = ctypes.c_int
@@ -199,3 +203,19 @@ def rt_last_error(h) -> str:
 def rt_destroy(h):
     if h:
         lib().rt_destroy(h)
+
+
+def rt_solve_uniform_noalloc(cfg: Config, cols, F_up, F_down, F_net, Q, stream=None):
+    """Solve a uniform-shape batch with no device allocation (see include/rt.h).
+
+    ``cols`` is an rt_columns descriptor with NULL shape arrays and L, NB set;
+    the four outputs are device tensors written in place."""
+    gw = np.ascontiguousarray(cfg.g_weights, dtype=np.float64)
+    c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
+                  cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
+                  cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
+                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads)
+    code = lib().rt_solve_uniform_noalloc(ctypes.byref(c), ctypes.byref(cols), _ptr(F_up),
+                                          _ptr(F_down), _ptr(F_net), _ptr(Q), _stream_ptr(stream))
+    if code != RT_OK:
+        raise RTError(code, "rt_solve_uniform_noalloc")

@@ -1,0 +1,72 @@
+"""The no-allocation entry point against the regular one.
+
+rt_solve_uniform_noalloc serves callers that cannot allocate device memory
+(graph-captured code, programs whose device memory belongs to their own pool,
+loops that cannot afford an allocation's synchronisation).  It keeps all of
+its intermediates in a fixed file-scope device array.  Here it is called
+twice in a row through the C ABI and each result is compared with
+rt_solve_columns on the same inputs, within the FP32 tolerance the parity
+tests use.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_02293_b300 import rt  # noqa: E402
+from paper_2203_02293_b300.solver import DeviceBatch, Solver  # noqa: E402
+
+
+def _uniform_desc(b: DeviceBatch, L: int, NB: int):
+    return rt.make_columns(b.n_cols, None, None, b.dtau, b.w0, b.g0, b.T_center, b.T_iface,
+                           b.p_iface, b.mu_star, b.F_star, L=L, NB=NB)
+
+
+def _noalloc(cols, b, L, NB, stream=None):
+    out = {k: torch.full((b.n_if,), float("nan"), dtype=torch.float64, device="cuda")
+           for k in ("F_up", "F_down", "F_net")}
+    out["Q"] = torch.full((b.n_lay,), float("nan"), dtype=torch.float64, device="cuda")
+    cfg = rt.Config(g_weights=cols.g_weights)
+    rt.rt_solve_uniform_noalloc(cfg, _uniform_desc(b, L, NB), out["F_up"], out["F_down"],
+                                out["F_net"], out["Q"], stream)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def test_noalloc_matches_regular_entry_point_twice():
+    shapes = [(300, 40, 30, 20, "ktable", 71), (57, 17, 9, 20, "uniform", 72)]
+    for n_cols, L, NB, NG, optics, seed in shapes:
+        cols = rt_synth.generate([L] * n_cols, [NB] * n_cols, NG, seed=seed, optics=optics)
+        b = DeviceBatch(cols)
+        s = Solver(cols.g_weights)
+        ref = s.solve_numpy(b)
+        s.close()
+        first = _noalloc(cols, b, L, NB)
+        second = _noalloc(cols, b, L, NB)
+        for got in (first, second):
+            e = errors(cols, got, ref, "fp32")
+            assert all(v <= 1.0 for v in e.values()), e
+        assert all(np.isfinite(first[k]).all() for k in first)
+
+
+def test_noalloc_refuses_batches_beyond_its_scratch():
+    tiny = torch.zeros(16, dtype=torch.float32, device="cuda")
+    tiny64 = torch.zeros(16, dtype=torch.float64, device="cuda")
+    desc = rt.make_columns(200000, None, None, tiny, tiny, tiny, tiny64, tiny64, tiny64, tiny64,
+                           tiny64, L=100, NB=300)
+    cfg = rt.Config(g_weights=np.full(20, 0.05))
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_solve_uniform_noalloc(cfg, desc, tiny64, tiny64, tiny64, tiny64)
+    assert e.value.code == rt.RT_EBUDGET
+    bad = rt.Config(g_weights=np.ones(1), precision=rt.RT_FP64_PLAIN)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_solve_uniform_noalloc(bad, desc, tiny64, tiny64, tiny64, tiny64)
+    assert e.value.code == rt.RT_EINVAL
