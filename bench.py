@@ -169,6 +169,63 @@ def run_reference(args):
     return 0
 
 
+def run_uneven(args, stream):
+    """Config 3: 4096 columns, L ~ U{20..200}, NB ~ U{30..300}, 20 g in one
+    persistent launch; launch shape from the autotuner; timed as replays of
+    a captured CUDA graph."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300.solver import DeviceBatch, Solver
+    from paper_2203_02293_b300.tuning import GraphSolve, autotune
+    dc = rt_synth.config3_device()
+    b = DeviceBatch.from_device(dc)
+    tune = autotune(b, dc.g_weights, reps=3)
+    s = Solver(dc.g_weights, block_threads=tune["block_threads"], ctas_per_sm=tune["ctas_per_sm"])
+    g = GraphSolve(s, b, stream)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.uneven_steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.uneven_steps
+    s.close()
+    out = {"workload": "4096 cols, L~U{20..200}, NB~U{30..300}, 20 g, one launch (CUDA graph replay)",
+           "systems": dc.n_systems, "input_bytes": int(3 * 4 * dc.dtau.numel()),
+           "ms_per_step": ms, "value": dc.n_systems / (ms * 1e-3), "unit": UNIT,
+           "steps": args.uneven_steps, "autotune": {k: tune[k] for k in ("block_threads", "ctas_per_sm", "stable")},
+           "autotune_table": tune["table"]}
+    del g, b, dc
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(args):
+    """Config 4: Poisson arrivals (mean 200/s), requests of logU[1, 2562]
+    columns x U{40..100} layers x U{30..300} bins x 20 g sliced from a
+    device-resident pool; continuous batching over 4 stream slots."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300.serve import Pool, Server, make_requests
+    pool = Pool(rt_synth, n_pool=2562, L_range=(40, 100), NB_range=(30, 300), n_g=20)
+    n = int(args.serving_seconds * args.serving_rate)
+    reqs = make_requests(pool, n, rate_hz=args.serving_rate, seed=4)
+    warm = make_requests(pool, 8, rate_hz=1e3, seed=99)
+    srv = Server(pool, n_slots=4, hbm_budget_bytes=32 << 30)
+    srv.run(warm)
+    srv.batches = 0
+    summ = srv.run(reqs)
+    srv.close()
+    summ.update({"rate_hz": args.serving_rate, "seconds_of_arrivals": args.serving_seconds,
+                 "unit_latency": "ms", "slots": 4, "budget_bytes": 32 << 30})
+    del pool
+    torch.cuda.empty_cache()
+    return summ
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,6 +235,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--uneven-steps", type=int, default=10)
+    ap.add_argument("--serving-seconds", type=float, default=20.0)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -305,6 +366,11 @@ def main():
         "clocks": clk.summary(),
         "branch_counts": stats,
     }
+    if rank == 0 and not args.quick:
+        del batch, host, dev
+        torch.cuda.empty_cache()
+        line["uneven"] = run_uneven(args, stream)
+        line["serving"] = run_serving(args)
     if rank == 0 and not args.no_cpu_baseline:
         v, passes, el = time_oracle(cols, 10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",

@@ -83,7 +83,10 @@ typedef struct {
     int32_t max_layers;          /* largest L of any column, 1..1024 */
     int32_t max_bins;            /* largest NB of any column, >= 1 */
     size_t hbm_budget_bytes;     /* workspace cap; 0 = no cap */
-    int32_t block_threads;       /* threads per CTA (multiple of 32, 64..1024); 0 = default */
+    int32_t block_threads;       /* threads per CTA (multiple of 32; 64..256 for the FP32
+                                    form, 64..512 for FP64); 0 = default (256) */
+    int32_t ctas_per_sm;         /* cap on resident CTAs per SM of the persistent grid;
+                                    0 = as many as fit */
 } rt_config;
 
 /* A packed batch of columns.  Column c has L_c layers, NB_c bins and
@@ -110,6 +113,18 @@ typedef struct {
     const float *dtau, *w0, *g0;
     const double *T_center, *T_iface, *p_iface;
     const double *mu_star, *F_star;
+    /* Optional gather (HOST [n_cols] each, or NULL for the packed layout
+     * above): where column c's inputs start, in elements of each array.
+     * Columns may then live anywhere in the input arrays, be shared by
+     * several batch entries, or skip data -- e.g. requests that slice a
+     * device-resident pool.  The library cannot see the device arrays' sizes:
+     * offsets must keep every read inside them (RT_EINVAL only for negative
+     * offsets).  Outputs stay packed in batch order. */
+    const int64_t *cube_offset;    /* into dtau, w0, g0 (block of L_c*NB_c*n_g) */
+    const int64_t *center_offset;  /* into T_center (L_c values) */
+    const int64_t *iface_offset;   /* into T_iface and p_iface (L_c+1 values) */
+    const int64_t *bin_offset;     /* into F_star (NB_c values) */
+    const int64_t *col_index;      /* into mu_star (1 value) */
 } rt_columns;
 
 typedef struct {
@@ -137,7 +152,9 @@ int rt_query_bytes(const rt_handle *h, const rt_columns *cols, size_t *bytes);
  * RT_EBUDGET if the workspace would pass hbm_budget_bytes.  May grow the
  * workspace (cudaMalloc) when cols is larger than anything seen before; a
  * solve inside CUDA-graph capture must therefore follow one of the same
- * shape outside it. */
+ * shape outside it.  A captured solve completes when its graph is replayed:
+ * order later rt_fluxes / rt_heating / rt_stats after the replay (same
+ * stream, or a synchronisation). */
 int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream);
 
 /* Copy the last solve's interface fluxes, W m^-2, [sum_c (L_c+1)] each,
@@ -168,9 +185,9 @@ void rt_destroy(rt_handle *h);
  * and loops that cannot take the device-wide synchronisation an allocation
  * may bring.
  *
- * It runs the FP32 form (cfg->precision must be RT_FP32_FORM) on a batch in
- * which every column has the same shape (cols->n_layers and cols->n_bins NULL,
- * cols->L and cols->NB set), with no handle: the caller passes the inputs
+ * It runs the FP32 form (cfg->precision must be RT_FP32_FORM) on a packed
+ * batch in which every column has the same shape (cols->n_layers, cols->n_bins
+ * and the gather offsets NULL; cols->L and cols->NB set), with no handle: the caller passes the inputs
  * (same layout as rt_solve_columns) and DEVICE output arrays F_up, F_down,
  * F_net [n_cols (L+1)] and Q [n_cols L], written in place (same meaning as
  * rt_fluxes / rt_heating).  Every intermediate lives in one file-scope device

@@ -36,6 +36,7 @@ struct rt_handle {
     // plan
     DevBuf plan;                  // n_layers, n_bins, order (int32) + offsets (int64)
     std::vector<int32_t> plan_nl, plan_nb;
+    std::vector<int64_t> plan_cube, plan_tc, plan_if, plan_fs, plan_mu;
     bool plan_valid = false;
     int plan_prec = -1;
     void *h_stage = nullptr;      // pinned staging for plan uploads
@@ -47,6 +48,7 @@ struct rt_handle {
     int32_t *d_counter = nullptr;
     unsigned long long *d_stats = nullptr;
     cudaEvent_t done_ev = nullptr;
+    bool done_valid = false;       // done_ev marks the last solve (false when it was captured)
     cudaStream_t last_stream = nullptr;
     bool solved = false;
     int64_t n_cols = 0, n_if = 0, n_lay = 0, n_sys = 0;
@@ -75,6 +77,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct Plan {
     std::vector<int32_t> nl, nb, order, col_units, unit_col, unit_k;
     std::vector<int64_t> cube_off, lay_off, bin_off, part_off, planck_off;
+    std::vector<int64_t> tc_off, if_off, fs_off, mu_idx;   // input offsets (gather or packed)
     int64_t n_if = 0, n_lay = 0, n_sys = 0, n_cube = 0, n_bins = 0, n_part = 0, n_planck = 0;
     int64_t n_units = 0;
     int Lmax = 0, NBmax = 0;
@@ -100,6 +103,15 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
         if (P.nb[i] < 1 || P.nb[i] > cfg.max_bins)
             return fail(h, RT_EINVAL, "column %d: n_bins %d outside [1, %d]", i, P.nb[i], cfg.max_bins);
     }
+    const int64_t *gath[5] = {c->cube_offset, c->center_offset, c->iface_offset, c->bin_offset, c->col_index};
+    for (int g = 0; g < 5; ++g)
+        if (gath[g])
+            for (int i = 0; i < n; ++i)
+                if (gath[g][i] < 0) return fail(h, RT_EINVAL, "column %d: negative gather offset", i);
+    P.tc_off.resize(n);
+    P.if_off.resize(n);
+    P.fs_off.resize(n);
+    P.mu_idx.resize(n);
     P.cube_off.resize(n);
     P.lay_off.resize(n);
     P.bin_off.resize(n);
@@ -108,7 +120,11 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
     P.col_units.resize(n);
     int64_t cube = 0, lay = 0, bins = 0, part = 0, planck = 0;
     for (int i = 0; i < n; ++i) {
-        P.cube_off[i] = cube;
+        P.cube_off[i] = c->cube_offset ? c->cube_offset[i] : cube;
+        P.tc_off[i] = c->center_offset ? c->center_offset[i] : lay;
+        P.if_off[i] = c->iface_offset ? c->iface_offset[i] : lay + i;
+        P.fs_off[i] = c->bin_offset ? c->bin_offset[i] : bins;
+        P.mu_idx[i] = c->col_index ? c->col_index[i] : i;
         P.lay_off[i] = lay;
         P.bin_off[i] = bins;
         P.part_off[i] = part;
@@ -165,7 +181,14 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
-            if (occ > 0) break;
+            if (occ > 0) {
+                if (cfg.ctas_per_sm > 0 && occ > cfg.ctas_per_sm) {
+                    occ = cfg.ctas_per_sm;
+                    const int64_t cap = (int64_t)occ * h->sm_count;
+                    if (P.grid > cap) P.grid = (int)cap;
+                }
+                break;
+            }
             if (P.block <= 64)
                 return fail(h, RT_EINVAL, "no launch shape fits shared memory (L=%d, NB=%d)", P.Lmax, P.NBmax);
             P.block -= 32;
@@ -173,7 +196,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
         P.n_slots = (int64_t)P.grid * P.block;
     }
     P.i32_count = 4 * (size_t)n + 2 * (size_t)P.n_units;
-    P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 5 * (size_t)n, 256);
+    P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
     P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256);
     P.scr_bytes = (size_t)P.n_slots *
                   (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
@@ -245,6 +268,7 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     if (cfg->block_threads != 0 &&
         (cfg->block_threads % 32 || cfg->block_threads < 64 || cfg->block_threads > rt::kMaxBlock))
         return RT_EINVAL;
+    if (cfg->ctas_per_sm < 0) return RT_EINVAL;
     for (int i = 0; i < cfg->n_g; ++i)
         if (!(cfg->g_weights[i] >= 0.0)) return RT_EINVAL;
 
@@ -302,7 +326,7 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const bool cap = stream_capturing(s);
     // order after the previous solve of this handle when it ran on another stream
-    if (h->solved && s != h->last_stream && !cap) {
+    if (h->solved && h->done_valid && s != h->last_stream && !cap) {
         cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
     }
@@ -326,9 +350,15 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     int64_t *d_bin = d_lay + n;
     int64_t *d_poff = d_bin + n;
     int64_t *d_pkoff = d_poff + n;
+    int64_t *d_tc = d_pkoff + n;
+    int64_t *d_ifin = d_tc + n;
+    int64_t *d_fsin = d_ifin + n;
+    int64_t *d_mu = d_fsin + n;
 
     const bool same_plan = h->plan_valid && h->plan_nl == P.nl && h->plan_nb == P.nb &&
-                           h->plan_prec == cfg.precision;
+                           h->plan_prec == cfg.precision && h->plan_cube == P.cube_off &&
+                           h->plan_tc == P.tc_off && h->plan_if == P.if_off && h->plan_fs == P.fs_off &&
+                           h->plan_mu == P.mu_idx;
     if (n > 0 && !same_plan) {
         if (cap) return fail(h, RT_EINVAL, "a new batch shape cannot be planned during stream capture");
         const size_t need = P.plan_bytes;
@@ -364,6 +394,10 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         memcpy(h64 + 2 * n, P.bin_off.data(), sizeof(int64_t) * n);
         memcpy(h64 + 3 * n, P.part_off.data(), sizeof(int64_t) * n);
         memcpy(h64 + 4 * n, P.planck_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 5 * n, P.tc_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 6 * n, P.if_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 7 * n, P.fs_off.data(), sizeof(int64_t) * n);
+        memcpy(h64 + 8 * n, P.mu_idx.data(), sizeof(int64_t) * n);
         cudaError_t e = cudaMemcpyAsync(h->plan.p, h->h_stage, need, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaEventRecord(h->stage_ev, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "plan upload");
@@ -371,6 +405,11 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         h->plan_nl = P.nl;
         h->plan_nb = P.nb;
         h->plan_prec = cfg.precision;
+        h->plan_cube = P.cube_off;
+        h->plan_tc = P.tc_off;
+        h->plan_if = P.if_off;
+        h->plan_fs = P.fs_off;
+        h->plan_mu = P.mu_idx;
         h->plan_valid = true;
     }
 
@@ -417,6 +456,10 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         kp.cube_off = d_cube;
         kp.lay_off = d_lay;
         kp.bin_off = d_bin;
+        kp.tc_off = d_tc;
+        kp.if_off = d_ifin;
+        kp.fs_off = d_fsin;
+        kp.mu_idx = d_mu;
         kp.order = d_order;
         kp.n_cols = n;
         kp.n_g = cfg.n_g;
@@ -463,8 +506,13 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
                                            : rt::launch_fp32(kp, P.grid, P.block, P.smem, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
-    e = cudaEventRecord(h->done_ev, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    // A solve captured into a graph completes when the graph is replayed; the
+    // caller orders later reads after the replay (same stream or a sync).
+    if (!cap) {
+        e = cudaEventRecord(h->done_ev, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+    }
+    h->done_valid = !cap;
     h->last_stream = s;
     h->solved = true;
     h->n_cols = n;
@@ -485,7 +533,7 @@ int rt_fluxes(rt_handle *h, double *F_up, double *F_down, double *F_net, void *s
     if (!h) return RT_EINVAL;
     if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_fluxes before rt_solve_columns");
     cudaStream_t s = (cudaStream_t)stream;
-    if (s != h->last_stream && !stream_capturing(s)) {
+    if (h->done_valid && s != h->last_stream && !stream_capturing(s)) {
         cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
     }
@@ -501,7 +549,7 @@ int rt_heating(rt_handle *h, double *Q, void *stream) {
     if (!h) return RT_EINVAL;
     if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_heating before rt_solve_columns");
     cudaStream_t s = (cudaStream_t)stream;
-    if (s != h->last_stream && !stream_capturing(s)) {
+    if (h->done_valid && s != h->last_stream && !stream_capturing(s)) {
         cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
     }
@@ -513,7 +561,7 @@ int rt_heating(rt_handle *h, double *Q, void *stream) {
 int rt_stats(rt_handle *h, rt_stats_t *out) {
     if (!h || !out) return RT_EINVAL;
     if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_stats before rt_solve_columns");
-    cudaError_t e = cudaEventSynchronize(h->done_ev);
+    cudaError_t e = h->done_valid ? cudaEventSynchronize(h->done_ev) : cudaDeviceSynchronize();
     unsigned long long v[rt::ST_COUNT] = {0};
     if (e == cudaSuccess) e = cudaMemcpy(v, h->d_stats, sizeof v, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "rt_stats");

@@ -22,9 +22,13 @@ struct KParams {
     const double *T_center, *T_iface, *p_iface, *mu_star, *F_star;
     // per-column layout (handle workspace)
     const int32_t *n_layers, *n_bins;
-    const int64_t *cube_off;     // element offset of the column's cube block
-    const int64_t *lay_off;      // offset into T_center / Q (sum of L)
-    const int64_t *bin_off;      // offset into F_star (sum of NB)
+    const int64_t *cube_off;     // input: element offset of the column's cube block
+    const int64_t *tc_off;       // input: offset into T_center
+    const int64_t *if_off;       // input: offset into T_iface and p_iface
+    const int64_t *fs_off;       // input: offset into F_star
+    const int64_t *mu_idx;       // input: index into mu_star
+    const int64_t *lay_off;      // packed: offset into Q (sum of L); F_up etc. at lay_off + c
+    const int64_t *bin_off;      // packed: offset into the per-bin staging (sum of NB)
     const int32_t *order;        // columns in processing order (largest first)
     int32_t n_cols;
     // Gauss points

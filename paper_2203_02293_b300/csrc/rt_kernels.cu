@@ -462,7 +462,7 @@ struct Smem {
 // Column bookkeeping common to both kernels.
 struct ColInfo {
     int c, L, NB, S;
-    long long cube0, lay0, if0, bin0;
+    long long cube0, lay0, if0, bin0, tc_in, if_in, fs_in;
     double mu;
 };
 
@@ -480,7 +480,10 @@ __device__ __forceinline__ bool next_column(const KParams &kp, int *s_unit, ColI
     ci.lay0 = kp.lay_off[ci.c];
     ci.if0 = ci.lay0 + ci.c;
     ci.bin0 = kp.bin_off[ci.c];
-    ci.mu = kp.mu_star[ci.c];
+    ci.tc_in = kp.tc_off[ci.c];
+    ci.if_in = kp.if_off[ci.c];
+    ci.fs_in = kp.fs_off[ci.c];
+    ci.mu = kp.mu_star[kp.mu_idx[ci.c]];
     return true;
 }
 
@@ -492,7 +495,7 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
     const double dwn = (kp.wn_max - kp.wn_min) / ci.NB;
     for (int i = threadIdx.x; i < nlev * nbc; i += blockDim.x) {
         const int lev = i / nbc, bb = i - lev * nbc, b = b_lo + bb;
-        const double T = (lev & 1) ? kp.T_center[ci.lay0 + (lev >> 1)] : kp.T_iface[ci.if0 + (lev >> 1)];
+        const double T = (lev & 1) ? kp.T_center[ci.tc_in + (lev >> 1)] : kp.T_iface[ci.if_in + (lev >> 1)];
         const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
         if constexpr (sizeof(R) == 4)
             sm.sB[i] = planck_bin_f((float)T, (float)wlo, (float)whi);
@@ -502,7 +505,7 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
     for (int bb = threadIdx.x; bb < nbc; bb += blockDim.x) {
         const int b = b_lo + bb;
         const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
-        sm.sFs[bb] = (R)kp.F_star[ci.bin0 + b];
+        sm.sFs[bb] = (R)kp.F_star[ci.fs_in + b];
         if constexpr (sizeof(R) == 4)
             sm.sFB[bb] = kPiF * planck_bin_f((float)kp.T_int, (float)wlo, (float)whi);
         else
@@ -548,7 +551,7 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
     const double gc = kp.grav / kp.cp;
     for (int l = threadIdx.x; l < ci.L; l += blockDim.x) {
         const double dF = acc[2 * (l + 1) + 1] - acc[2 * l + 1];
-        const double dp = kp.p_iface[ci.if0 + l + 1] - kp.p_iface[ci.if0 + l];
+        const double dp = kp.p_iface[ci.if_in + l + 1] - kp.p_iface[ci.if_in + l];
         kp.Q[ci.lay0 + l] = gc * dF / dp;
     }
 }
@@ -574,23 +577,23 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
     for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
         const int L = kp.n_layers[c], NB = kp.n_bins[c];
-        const long long lay0 = kp.lay_off[c], if0 = lay0 + c, b0 = kp.bin_off[c];
+        const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], b0 = kp.bin_off[c], fsi = kp.fs_off[c];
         float *B = kp.planck32 + kp.planck_off[c];
         const float dwn = (float)((kp.wn_max - kp.wn_min) / NB);
         const float wmin = (float)kp.wn_min;
         const int nlev = 2 * L + 1;
         for (int i = threadIdx.x; i < nlev * NB; i += blockDim.x) {
             const int lev = i / NB, b = i - lev * NB;
-            const float T = (float)((lev & 1) ? kp.T_center[lay0 + (lev >> 1)] : kp.T_iface[if0 + (lev >> 1)]);
+            const float T = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
             B[i] = planck_bin_f(T, fmaf((float)b, dwn, wmin), fmaf((float)(b + 1), dwn, wmin));
         }
         for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-            kp.fs32[b0 + b] = (float)kp.F_star[b0 + b];
+            kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
             kp.fboa32[b0 + b] = kPiF * planck_bin_f((float)kp.T_int, fmaf((float)b, dwn, wmin),
                                                     fmaf((float)(b + 1), dwn, wmin));
         }
         if (threadIdx.x == 0) {
-            const double mu = kp.mu_star[c];
+            const double mu = kp.mu_star[kp.mu_idx[c]];
             kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
         }
     }
@@ -617,7 +620,7 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     const float gc = (float)(kp.grav / kp.cp);
     for (int l = lane; l < L; l += 32) {
         const double dF = sum(l + 1, 1) - sum(l, 1);
-        const float dp = (float)(kp.p_iface[if0 + l + 1] - kp.p_iface[if0 + l]);
+        const float dp = (float)(kp.p_iface[kp.if_off[c] + l + 1] - kp.p_iface[kp.if_off[c] + l]);
         kp.Q[kp.lay_off[c] + l] = (double)(gc * (float)dF * frcp(dp));
     }
 }
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         const long long cube0 = kp.cube_off[c];
         const float4 cf = kp.colf[c];
         const float mu = cf.x, imu = cf.y;
-        const double mu_d = kp.mu_star[c];       // only for the rare FP64 resonance test
+        const double mu_d = kp.mu_star[kp.mu_idx[c]];   // only for the rare FP64 resonance test
         const bool beam = cf.z != 0.f;
         const int s0 = ku * 32;
         const int b_lo = s0 / NG;

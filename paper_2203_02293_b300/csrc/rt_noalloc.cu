@@ -33,7 +33,7 @@ constexpr int kMaxG = 64;
 struct UniformPlan {
     int32_t n_cols, L, NB, n_g, upc;
     int32_t *nl, *nb, *order, *cu, *ucol, *uk;
-    int64_t *cube, *lay, *bin, *part, *pk;
+    int64_t *cube, *lay, *bin, *part, *pk, *tc, *ifo, *fs, *mu;
     float *gw32;
     float gw[kMaxG];
 };
@@ -54,6 +54,10 @@ __global__ void uniform_plan(UniformPlan a) {
         a.bin[c] = c * a.NB;
         a.part[c] = c * a.upc * 2 * (int64_t)(a.L + 1);
         a.pk[c] = c * (int64_t)(2 * a.L + 1) * a.NB;
+        a.tc[c] = c * a.L;
+        a.ifo[c] = c * (a.L + 1);
+        a.fs[c] = c * a.NB;
+        a.mu[c] = c;
     }
     const int64_t nu = (int64_t)a.n_cols * a.upc;
     for (int64_t u = tid; u < nu; u += nth) {
@@ -101,6 +105,8 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     if (cfg->layers != RT_NONISOTHERMAL && cfg->layers != RT_ISOTHERMAL) return RT_EINVAL;
     if (cfg->resonance != RT_RESONANCE_PAPER && cfg->resonance != RT_RESONANCE_LIMIT) return RT_EINVAL;
     if (cols->n_layers || cols->n_bins) return RT_EINVAL;      // uniform shape only
+    if (cols->cube_offset || cols->center_offset || cols->iface_offset || cols->bin_offset || cols->col_index)
+        return RT_EINVAL;                                       // packed layout only
     const int64_t n = cols->n_cols, L = cols->L, NB = cols->NB, NG = cfg->n_g;
     if (n < 1 || L < 1 || L > rt::kMaxLayers || NB < 1) return RT_EINVAL;
     if (!cols->dtau || !cols->w0 || !cols->g0 || !cols->T_center || !cols->T_iface || !cols->p_iface ||
@@ -122,7 +128,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     const size_t o_colf = off;    off += up(sizeof(float4) * n);
     const size_t o_gw = off;      off += up(sizeof(float) * kMaxG);
     const size_t o_i32 = off;     off += up(sizeof(int32_t) * (4 * n + 2 * nu));
-    const size_t o_i64 = off;     off += up(sizeof(int64_t) * 5 * n);
+    const size_t o_i64 = off;     off += up(sizeof(int64_t) * 9 * n);
     const size_t o_scr = off;
     if (off >= (size_t)RT_NOALLOC_SCRATCH_BYTES) return RT_EBUDGET;
     const int64_t slots_fit = (int64_t)(((size_t)RT_NOALLOC_SCRATCH_BYTES - off) / (sizeof(float4) * (size_t)L));
@@ -192,6 +198,10 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     a.bin = i64 + 2 * n;
     a.part = i64 + 3 * n;
     a.pk = i64 + 4 * n;
+    a.tc = i64 + 5 * n;
+    a.ifo = i64 + 6 * n;
+    a.fs = i64 + 7 * n;
+    a.mu = i64 + 8 * n;
     a.gw32 = (float *)(base + o_gw);
     for (int i = 0; i < NG; ++i) a.gw[i] = (float)cfg->g_weights[i];
     int pgrid = (int)((std::max<int64_t>(n, nu) + 255) / 256);
@@ -213,6 +223,10 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.cube_off = a.cube;
     kp.lay_off = a.lay;
     kp.bin_off = a.bin;
+    kp.tc_off = a.tc;
+    kp.if_off = a.ifo;
+    kp.fs_off = a.fs;
+    kp.mu_idx = a.mu;
     kp.order = a.order;
     kp.n_cols = (int32_t)n;
     kp.n_g = (int32_t)NG;

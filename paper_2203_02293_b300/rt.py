@@ -37,6 +37,7 @@ class rt_config(ctypes.Structure):
         ("T_int", ctypes.c_double), ("F_toa_diffuse", ctypes.c_double),
         ("max_layers", ctypes.c_int32), ("max_bins", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
     ]
 
 
@@ -48,6 +49,9 @@ class rt_columns(ctypes.Structure):
         ("dtau", ctypes.c_void_p), ("w0", ctypes.c_void_p), ("g0", ctypes.c_void_p),
         ("T_center", ctypes.c_void_p), ("T_iface", ctypes.c_void_p), ("p_iface", ctypes.c_void_p),
         ("mu_star", ctypes.c_void_p), ("F_star", ctypes.c_void_p),
+        ("cube_offset", ctypes.POINTER(ctypes.c_int64)), ("center_offset", ctypes.POINTER(ctypes.c_int64)),
+        ("iface_offset", ctypes.POINTER(ctypes.c_int64)), ("bin_offset", ctypes.POINTER(ctypes.c_int64)),
+        ("col_index", ctypes.POINTER(ctypes.c_int64)),
     ]
 
 
@@ -142,6 +146,7 @@ class Config:
     max_bins: int = 4096
     hbm_budget_bytes: int = 0
     block_threads: int = 0
+    ctas_per_sm: int = 0
 
 
 def rt_create(cfg: Config):
@@ -150,25 +155,33 @@ def rt_create(cfg: Config):
     c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
                   cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
                   cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
-                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads)
+                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
+                  cfg.ctas_per_sm)
     h = ctypes.c_void_p()
     _check(lib().rt_create(ctypes.byref(c), ctypes.byref(h)))
     return h
 
 
 def make_columns(n_cols: int, n_layers, n_bins, dtau, w0, g0, T_center, T_iface, p_iface,
-                 mu_star, F_star, L: int = 0, NB: int = 0):
+                 mu_star, F_star, L: int = 0, NB: int = 0, gather: dict | None = None):
     """Build an rt_columns descriptor.  n_layers / n_bins are host int32 arrays
-    (or None with uniform L, NB); the rest are device tensors.  The returned
-    object keeps the host shape arrays alive."""
+    (or None with uniform L, NB); the rest are device tensors.  ``gather`` may
+    give host int64 arrays cube_offset, center_offset, iface_offset,
+    bin_offset, col_index (see include/rt.h).  The returned object keeps the
+    host arrays alive."""
     nl = None if n_layers is None else np.ascontiguousarray(n_layers, dtype=np.int32)
     nb = None if n_bins is None else np.ascontiguousarray(n_bins, dtype=np.int32)
     P32 = ctypes.POINTER(ctypes.c_int32)
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    g = {k: np.ascontiguousarray(v, dtype=np.int64) for k, v in (gather or {}).items()}
+    gp = {k: (g[k].ctypes.data_as(P64) if k in g else None)
+          for k in ("cube_offset", "center_offset", "iface_offset", "bin_offset", "col_index")}
     c = rt_columns(n_cols, nl.ctypes.data_as(P32) if nl is not None else None,
                    nb.ctypes.data_as(P32) if nb is not None else None, L, NB,
                    _ptr(dtau), _ptr(w0), _ptr(g0), _ptr(T_center), _ptr(T_iface), _ptr(p_iface),
-                   _ptr(mu_star), _ptr(F_star))
-    c._keep = (nl, nb)
+                   _ptr(mu_star), _ptr(F_star), gp["cube_offset"], gp["center_offset"],
+                   gp["iface_offset"], gp["bin_offset"], gp["col_index"])
+    c._keep = (nl, nb, g)
     return c
 
 
@@ -214,7 +227,8 @@ def rt_solve_uniform_noalloc(cfg: Config, cols, F_up, F_down, F_net, Q, stream=N
     c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
                   cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
                   cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
-                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads)
+                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
+                  cfg.ctas_per_sm)
     code = lib().rt_solve_uniform_noalloc(ctypes.byref(c), ctypes.byref(cols), _ptr(F_up),
                                           _ptr(F_down), _ptr(F_net), _ptr(Q), _stream_ptr(stream))
     if code != RT_OK:

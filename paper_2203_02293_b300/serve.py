@@ -1,0 +1,291 @@
+"""Continuous-batching request loop over the C ABI.
+
+Requests (columns x layers x bins of the same shape within a request) arrive
+at given times.  Their inputs are slices of a device-resident pool: the
+batch descriptor points into the pool through per-column gather offsets, so
+no input is copied per request.  The server keeps a ring of slots (a CUDA
+stream and a library handle each).  Whenever a slot is free and requests are
+waiting, it admits waiting requests in arrival order while the bytes of the
+batches in flight stay within the HBM budget, and launches them as one solve
+on that slot's stream; batches on different slots overlap on the device.  A
+request's latency runs from its arrival to the host seeing its batch's
+completion event.  Requests that can never fit the budget are refused; a
+request may be cancelled while it waits or refused after a waiting timeout.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import rt
+from .solver import Solver
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the run
+    n_cols: int
+    L: int
+    NB: int
+    cols: np.ndarray               # pool column indices (for the per-column inputs)
+    cube_base: int                 # element offset of the request's cube block in the pool
+    n_g: int = 20
+    status: str = "new"            # new, waiting, running, done, refused, cancelled, timeout
+    nbytes: int = 0                # workspace of the request alone (upper bound per request)
+    t_admit: float = -1.0
+    t_done: float = -1.0
+    outputs: dict | None = None
+
+    @property
+    def systems(self) -> int:
+        return self.n_cols * self.NB * self.n_g
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+class Pool:
+    """Device-resident inputs that requests slice.
+
+    Cubes are flat arrays of independent draws, so any contiguous block of the
+    right length is a valid request cube.  Per-column profiles are stored for
+    every layer count L in [L_min, L_max] (n_pool columns each), F* for every
+    bin count in [NB_min, NB_max]."""
+
+    def __init__(self, draw, n_pool: int, L_range, NB_range, n_g: int = 20, cube_elems: int = 0,
+                 device="cuda"):
+        # ``draw`` is an rt_synth-like module providing the generators
+        self.n_g = n_g
+        self.L_range, self.NB_range = L_range, NB_range
+        self.n_pool = n_pool
+        Ls = range(L_range[0], L_range[1] + 1)
+        NBs = range(NB_range[0], NB_range[1] + 1)
+        rng = np.random.default_rng(12345)
+        tc, ti, pi = [], [], []
+        self.tc_off, self.if_off = {}, {}
+        ntc = nif = 0
+        for L in Ls:
+            self.tc_off[L], self.if_off[L] = ntc, nif
+            for _ in range(n_pool):
+                p, Tc, Ti = draw._profile(rng, L)
+                tc.append(Tc); ti.append(Ti); pi.append(p)
+            ntc += n_pool * L
+            nif += n_pool * (L + 1)
+        fs = []
+        self.fs_off = {}
+        nfs = 0
+        for NB in NBs:
+            self.fs_off[NB] = nfs
+            fs.append(draw.stellar_flux_bins(NB))
+            nfs += NB
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(np.concatenate(a), dtype=np.float64)).to(device)
+        self.T_center, self.T_iface, self.p_iface = dev(tc), dev(ti), dev(pi)
+        self.F_star = dev(fs)
+        self.mu_star = torch.from_numpy(rng.uniform(0.1, 1.0, n_pool)).to(device)
+        if cube_elems <= 0:
+            cube_elems = n_pool * L_range[1] * NB_range[1] * n_g
+        gen = torch.Generator(device=device)
+        gen.manual_seed(777)
+        self.dtau = draw._device_uniform(cube_elems, 1e-6, 10.0, gen, device, log=True)
+        self.w0 = draw._device_uniform(cube_elems, 0.0, 0.95, gen, device)
+        self.g0 = draw._device_uniform(cube_elems, 0.0, 0.8, gen, device)
+        self.cube_elems = cube_elems
+        _, self.g_weights = draw.gauss_legendre_01(n_g)
+
+    def gather(self, reqs):
+        """Shapes and gather offsets of a batch made of ``reqs`` (in order)."""
+        nl, nb, cube, cen, ifc, bins, col = [], [], [], [], [], [], []
+        for r in reqs:
+            per = r.L * r.NB * self.n_g
+            for j, pc in enumerate(r.cols):
+                nl.append(r.L)
+                nb.append(r.NB)
+                cube.append(r.cube_base + j * per)
+                cen.append(self.tc_off[r.L] + pc * r.L)
+                ifc.append(self.if_off[r.L] + pc * (r.L + 1))
+                bins.append(self.fs_off[r.NB])
+                col.append(pc)
+        g = dict(cube_offset=np.array(cube, np.int64), center_offset=np.array(cen, np.int64),
+                 iface_offset=np.array(ifc, np.int64), bin_offset=np.array(bins, np.int64),
+                 col_index=np.array(col, np.int64))
+        return np.array(nl, np.int32), np.array(nb, np.int32), g
+
+    def descriptor(self, reqs):
+        nl, nb, g = self.gather(reqs)
+        return rt.make_columns(len(nl), nl, nb, self.dtau, self.w0, self.g0, self.T_center,
+                               self.T_iface, self.p_iface, self.mu_star, self.F_star, gather=g), nl
+
+
+def make_requests(pool: Pool, n: int, rate_hz: float, seed: int, C_range=(1, 2562)):
+    """Poisson arrivals; C ~ logU[C_range], L and NB uniform over the pool's ranges."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    reqs = []
+    for i in range(n):
+        C = int(np.clip(np.round(np.exp(rng.uniform(np.log(C_range[0]), np.log(C_range[1] + 0.5)))),
+                        C_range[0], min(C_range[1], pool.n_pool)))
+        L = int(rng.integers(pool.L_range[0], pool.L_range[1] + 1))
+        NB = int(rng.integers(pool.NB_range[0], pool.NB_range[1] + 1))
+        cols = rng.choice(pool.n_pool, C, replace=False)
+        need = C * L * NB * pool.n_g
+        base = int(rng.integers(0, pool.cube_elems - need + 1))
+        reqs.append(Request(i, float(t[i]), C, L, NB, cols, base, n_g=pool.n_g))
+    return reqs
+
+
+@dataclass
+class Slot:
+    stream: torch.cuda.Stream
+    solver: Solver
+    event: torch.cuda.Event = field(default_factory=torch.cuda.Event)
+    reqs: list = field(default_factory=list)
+    nbytes: int = 0
+    n_if: int = 0
+    busy: bool = False
+
+
+class Server:
+    def __init__(self, pool: Pool, n_slots: int = 4, hbm_budget_bytes: int = 8 << 30,
+                 max_systems_per_batch: int = 24_000_000, wait_timeout_s: float = 0.0,
+                 keep_outputs: bool = False, **cfg):
+        self.pool = pool
+        self.budget = hbm_budget_bytes
+        self.max_sys = max_systems_per_batch
+        self.wait_timeout = wait_timeout_s
+        self.keep_outputs = keep_outputs
+        self.slots = [Slot(torch.cuda.Stream(), Solver(pool.g_weights, **cfg)) for _ in range(n_slots)]
+        self.in_flight_bytes = 0
+        self.batches = 0
+
+    def close(self):
+        for s in self.slots:
+            s.solver.close()
+
+    def _bytes(self, slot: Slot, r: Request) -> int:
+        # workspace of the request alone (a first estimate for composing a batch)
+        if not r.nbytes:
+            desc, _ = self.pool.descriptor([r])
+            r.nbytes = rt.rt_query_bytes(slot.solver.h, desc)
+        return r.nbytes
+
+    def _complete(self, slot: Slot, now: float):
+        if self.keep_outputs:
+            o = slot.solver.outputs_host(slot.n_if, sum(r.n_cols * r.L for r in slot.reqs))
+            i0 = l0 = 0
+            for r in slot.reqs:
+                ni, nl = r.n_cols * (r.L + 1), r.n_cols * r.L
+                r.outputs = {"F_up": o["F_up"][i0:i0 + ni], "F_down": o["F_down"][i0:i0 + ni],
+                             "F_net": o["F_net"][i0:i0 + ni], "Q": o["Q"][l0:l0 + nl]}
+                i0 += ni
+                l0 += nl
+        for r in slot.reqs:
+            r.t_done = now
+            r.status = "done"
+        self.in_flight_bytes -= slot.nbytes
+        slot.reqs, slot.busy, slot.nbytes = [], False, 0
+
+    def run(self, requests, cancel: set | None = None, poll_sleep: float = 5e-5):
+        """Serve ``requests`` (sorted by arrival); returns a summary dict."""
+        cancel = cancel or set()
+        arrivals = deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: deque = deque()
+        t0 = time.perf_counter()
+        done = 0
+        total = len(arrivals)
+        while done < total:
+            now = time.perf_counter() - t0
+            while arrivals and arrivals[0].arrival <= now:
+                r = arrivals.popleft()
+                r.status = "waiting"
+                waiting.append(r)
+            # completions
+            for s in self.slots:
+                if s.busy and s.event.query():
+                    n = len(s.reqs)
+                    self._complete(s, time.perf_counter() - t0)
+                    done += n
+            # cancellations, timeouts and requests that can never fit
+            keep = deque()
+            for r in waiting:
+                if r.rid in cancel:
+                    r.status, r.t_done = "cancelled", now
+                    done += 1
+                elif self.wait_timeout and now - r.arrival > self.wait_timeout:
+                    r.status, r.t_done = "timeout", now
+                    done += 1
+                else:
+                    keep.append(r)
+            waiting = keep
+            # admission into free slots
+            for s in self.slots:
+                if s.busy or not waiting:
+                    continue
+                batch, nsys, need = [], 0, 0
+                while waiting:
+                    r = waiting[0]
+                    if batch and nsys + r.systems > self.max_sys:
+                        break
+                    rb = self._bytes(s, r)
+                    if rb > self.budget:
+                        waiting.popleft()              # can never fit
+                        r.status, r.t_done = "refused", now
+                        done += 1
+                        continue
+                    if self.in_flight_bytes + need + rb > self.budget:
+                        break
+                    batch.append(waiting.popleft())
+                    nsys += r.systems
+                    need += rb
+                if not batch:
+                    continue
+                # exact need of the composed batch; hand requests back until it fits
+                desc, nl = self.pool.descriptor(batch)
+                need = rt.rt_query_bytes(s.solver.h, desc)
+                while len(batch) > 1 and self.in_flight_bytes + need > self.budget:
+                    waiting.appendleft(batch.pop())
+                    desc, nl = self.pool.descriptor(batch)
+                    need = rt.rt_query_bytes(s.solver.h, desc)
+                if self.in_flight_bytes + need > self.budget:
+                    waiting.appendleft(batch.pop())
+                    continue
+                rt.rt_solve_columns(s.solver.h, desc, s.stream)
+                s.event.record(s.stream)
+                t_admit = time.perf_counter() - t0
+                for r in batch:
+                    r.status, r.t_admit = "running", t_admit
+                s.reqs, s.busy, s.nbytes = batch, True, need
+                s.n_if = int((nl + 1).sum())
+                self.in_flight_bytes += need
+                self.batches += 1
+            if not any(s.busy for s in self.slots) and not waiting and arrivals:
+                gap = arrivals[0].arrival - (time.perf_counter() - t0)
+                if gap > 0:
+                    time.sleep(min(gap, 1e-3))
+            else:
+                time.sleep(poll_sleep)
+        return summarize(requests, time.perf_counter() - t0, self.batches)
+
+
+def summarize(requests, wall: float, batches: int) -> dict:
+    ok = [r for r in requests if r.status == "done"]
+    lat = np.array([r.latency for r in ok]) * 1e3
+    sys_done = sum(r.systems for r in ok)
+    span = (max(r.t_done for r in ok) - min(r.arrival for r in ok)) if ok else 0.0
+    return {
+        "requests": len(requests), "done": len(ok),
+        "refused": sum(r.status == "refused" for r in requests),
+        "cancelled": sum(r.status == "cancelled" for r in requests),
+        "timeout": sum(r.status == "timeout" for r in requests),
+        "batches": batches,
+        "p50_ms": float(np.percentile(lat, 50)) if ok else None,
+        "p99_ms": float(np.percentile(lat, 99)) if ok else None,
+        "mean_ms": float(lat.mean()) if ok else None,
+        "solves_per_s": sys_done / span if span > 0 else None,
+        "wall_s": wall,
+    }

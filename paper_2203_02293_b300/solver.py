@@ -36,6 +36,23 @@ class DeviceBatch:
         self._desc = None
 
     @classmethod
+    def from_device(cls, dc) -> "DeviceBatch":
+        """Wrap inputs that already live on the device (same field names)."""
+        b = cls.__new__(cls)
+        b.n_layers = np.ascontiguousarray(dc.n_layers, dtype=np.int32)
+        b.n_bins = np.ascontiguousarray(dc.n_bins, dtype=np.int32)
+        b.n_cols = int(b.n_layers.size)
+        b.n_g = int(dc.n_g)
+        b.n_if = int((b.n_layers + 1).sum())
+        b.n_lay = int(b.n_layers.sum())
+        b.n_systems = int(b.n_bins.astype(np.int64).sum()) * b.n_g
+        b.device = str(dc.dtau.device)
+        for f in cls.FIELDS:
+            setattr(b, f, getattr(dc, f))
+        b._desc = None
+        return b
+
+    @classmethod
     def empty_like(cls, other: "DeviceBatch", device="cuda") -> "DeviceBatch":
         b = cls.__new__(cls)
         for k in ("n_layers", "n_bins", "n_cols", "n_g", "n_if", "n_lay", "n_systems"):
@@ -94,6 +111,15 @@ class Solver:
         o["Q"] = torch.empty(batch.n_lay, dtype=torch.float64, device=device)
         rt.rt_fluxes(self.h, o["F_up"], o["F_down"], o["F_net"], stream)
         rt.rt_heating(self.h, o["Q"], stream)
+        return o
+
+    def outputs_host(self, n_if: int, n_lay: int, stream=None) -> dict:
+        """The last solve's outputs (n_if interfaces, n_lay layers) as host arrays."""
+        o = {k: np.empty(n_if) for k in ("F_up", "F_down", "F_net")}
+        o["Q"] = np.empty(n_lay)
+        rt.rt_fluxes(self.h, o["F_up"], o["F_down"], o["F_net"], stream)
+        rt.rt_heating(self.h, o["Q"], stream)
+        torch.cuda.synchronize()
         return o
 
     def solve_numpy(self, batch: DeviceBatch) -> dict:

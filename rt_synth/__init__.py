@@ -258,3 +258,115 @@ def config3(n_cols: int = 4096, seed: int = 3) -> Columns:
     """Uneven batch: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g-points, optics as config 0."""
     L, NB = uneven_shapes(n_cols, seed)
     return generate(L, NB, 20, seed, "uniform", name=f"config3 {n_cols} uneven")
+
+
+# ----------------------------------------------------------------------
+# Large batches drawn directly in device memory (torch's Philox generator),
+# for the uneven and serving workloads whose cubes do not fit comfortably in
+# host memory.  Per-column profiles are small and drawn on the host.
+# ----------------------------------------------------------------------
+
+class DeviceColumns:
+    """A packed batch whose cubes live in device memory.
+
+    Same fields as ``Columns`` except that dtau/w0/g0 (and the per-column
+    arrays) are torch tensors on ``device``.  ``host_subset(idx)`` copies
+    chosen columns back as a ``Columns`` for the oracle."""
+
+    def __init__(self, n_layers, n_bins, n_g, g_weights, tensors: dict, consts: dict, name: str):
+        self.n_layers = np.asarray(n_layers, dtype=np.int32)
+        self.n_bins = np.asarray(n_bins, dtype=np.int32)
+        self.n_g = int(n_g)
+        self.g_weights = g_weights
+        self.consts = consts
+        self.name = name
+        for k, v in tensors.items():
+            setattr(self, k, v)
+
+    @property
+    def n_cols(self):
+        return int(self.n_layers.size)
+
+    @property
+    def n_systems(self):
+        return int((self.n_bins.astype(np.int64) * self.n_g).sum())
+
+    def offsets(self):
+        L = self.n_layers.astype(np.int64)
+        NB = self.n_bins.astype(np.int64)
+        z = lambda a: np.concatenate([[0], np.cumsum(a)])
+        return dict(cube=z(L * NB * self.n_g), lay=z(L), iface=z(L + 1), bins=z(NB))
+
+    def host_subset(self, idx) -> Columns:
+        idx = np.asarray(idx, dtype=np.int64)
+        o = self.offsets()
+
+        def cat(t, key):
+            parts = [t[int(o[key][i]):int(o[key][i + 1])].cpu().numpy() for i in idx]
+            return np.concatenate(parts)
+        return Columns(n_layers=self.n_layers[idx].copy(), n_bins=self.n_bins[idx].copy(),
+                       n_g=self.n_g, g_weights=self.g_weights,
+                       dtau=cat(self.dtau, "cube"), w0=cat(self.w0, "cube"), g0=cat(self.g0, "cube"),
+                       T_center=cat(self.T_center, "lay"), T_iface=cat(self.T_iface, "iface"),
+                       p_iface=cat(self.p_iface, "iface"),
+                       mu_star=self.mu_star[torch_index(idx, self.mu_star)].cpu().numpy(),
+                       F_star=cat(self.F_star, "bins"), consts=self.consts,
+                       name=f"{self.name}[{idx.size} cols]")
+
+
+def torch_index(idx, like):
+    import torch
+    return torch.as_tensor(idx, dtype=torch.long, device=like.device)
+
+
+def _device_uniform(n, lo, hi, gen, device, log=False, chunk=1 << 28):
+    import torch
+    out = torch.empty(n, dtype=torch.float32, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        t = out[a:b]
+        if log:
+            t.uniform_(float(np.log(lo)), float(np.log(hi)), generator=gen)
+            t.exp_()
+        else:
+            t.uniform_(lo, hi, generator=gen)
+    return out
+
+
+def device_generate(n_layers, n_bins, n_g: int, seed: int, device="cuda", name="") -> DeviceColumns:
+    """Optics as config 0 (dtau ~ logU[1e-6, 10], w0 ~ U[0, 0.95], g0 ~
+    U[0, 0.8]) drawn on the device; profiles, mu and F* as ``generate``."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n_layers = np.asarray(n_layers, dtype=np.int32)
+    n_bins = np.asarray(n_bins, dtype=np.int32)
+    C = n_layers.size
+    gx, gw = gauss_legendre_01(n_g)
+    mu = rng.uniform(0.1, 1.0, C)
+    prof = [_profile(rng, int(L)) for L in n_layers]
+    fs_cache = {}
+    Fs = []
+    for NB in n_bins:
+        NB = int(NB)
+        if NB not in fs_cache:
+            fs_cache[NB] = stellar_flux_bins(NB)
+        Fs.append(fs_cache[NB])
+    n_cube = int((n_layers.astype(np.int64) * n_bins * n_g).sum())
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    t = dict(dtau=_device_uniform(n_cube, 1e-6, 10.0, gen, device, log=True),
+             w0=_device_uniform(n_cube, 0.0, 0.95, gen, device),
+             g0=_device_uniform(n_cube, 0.0, 0.8, gen, device))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+    t["T_center"] = dev(np.concatenate([p[1] for p in prof]))
+    t["T_iface"] = dev(np.concatenate([p[2] for p in prof]))
+    t["p_iface"] = dev(np.concatenate([p[0] for p in prof]))
+    t["mu_star"] = dev(mu)
+    t["F_star"] = dev(np.concatenate(Fs))
+    return DeviceColumns(n_layers, n_bins, n_g, gw, t, _consts(), name)
+
+
+def config3_device(n_cols: int = 4096, seed: int = 3, device="cuda") -> DeviceColumns:
+    """Uneven batch on the device: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g."""
+    L, NB = uneven_shapes(n_cols, seed)
+    return device_generate(L, NB, 20, seed, device, name=f"config3 {n_cols} uneven (device)")

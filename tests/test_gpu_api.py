@@ -122,3 +122,44 @@ def test_repeated_solves_reuse_workspace_and_change_shape():
         got = s.solve_numpy(b)
         assert_parity(cols, got, oracle_solve(cols, method_opts()), "fp32", "reuse")
     s.close()
+
+
+def test_gathered_columns_equal_packed_columns():
+    """Columns picked out of a pool by offsets (reordered, repeated) give the
+    same bits as the same columns packed back to back."""
+    pool = rt_synth.generate([12, 30, 7, 22, 40], [5, 9, 3, 17, 30], 20, seed=65, optics="ktable")
+    pb = DeviceBatch(pool)
+    o = pool.offsets()
+    idx = np.array([3, 0, 3, 4, 1])
+    gather = dict(cube_offset=o["cube"][idx], center_offset=o["lay"][idx],
+                  iface_offset=o["iface"][idx], bin_offset=o["bins"][idx], col_index=idx)
+    desc = rt.make_columns(len(idx), pool.n_layers[idx], pool.n_bins[idx], pb.dtau, pb.w0, pb.g0,
+                           pb.T_center, pb.T_iface, pb.p_iface, pb.mu_star, pb.F_star,
+                           gather=gather)
+    for precision in (rt.RT_FP32_FORM, rt.RT_FP64_PLAIN):
+        s = Solver(pool.g_weights, precision=precision)
+        rt.rt_solve_columns(s.h, desc)
+        sub = pool.subset(idx)
+        n_if, n_lay = int((sub.n_layers + 1).sum()), int(sub.n_layers.sum())
+        got = {k: torch.empty(n_if, dtype=torch.float64, device="cuda") for k in ("F_up", "F_down", "F_net")}
+        got["Q"] = torch.empty(n_lay, dtype=torch.float64, device="cuda")
+        rt.rt_fluxes(s.h, got["F_up"], got["F_down"], got["F_net"])
+        rt.rt_heating(s.h, got["Q"])
+        torch.cuda.synchronize()
+        ref = s.solve_numpy(DeviceBatch(sub))
+        for k in ref:
+            assert np.array_equal(got[k].cpu().numpy(), ref[k]), k
+        s.close()
+
+
+def test_negative_gather_offset_is_rejected():
+    pool = rt_synth.generate([4, 4], [2, 2], 2, seed=66, optics="uniform")
+    pb = DeviceBatch(pool)
+    desc = rt.make_columns(2, pool.n_layers, pool.n_bins, pb.dtau, pb.w0, pb.g0, pb.T_center,
+                           pb.T_iface, pb.p_iface, pb.mu_star, pb.F_star,
+                           gather=dict(col_index=np.array([0, -1])))
+    s = Solver(pool.g_weights)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_solve_columns(s.h, desc)
+    assert e.value.code == rt.RT_EINVAL
+    s.close()

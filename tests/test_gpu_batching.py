@@ -1,0 +1,83 @@
+"""Uneven batches, CUDA-graph replay and the launch-shape autotuner."""
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import assert_parity, method_opts, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_02293_b300 import rt  # noqa: E402
+from paper_2203_02293_b300.solver import DeviceBatch, Solver  # noqa: E402
+from paper_2203_02293_b300.tuning import GraphSolve, autotune  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    dc = rt_synth.config3_device()
+    return dc, DeviceBatch.from_device(dc)
+
+
+def sample_columns(dc, k=24, seed=0):
+    rng = np.random.default_rng(seed)
+    cost = dc.n_layers.astype(np.int64) * dc.n_bins
+    extremes = [int(np.argmax(cost)), int(np.argmin(cost)), int(np.argmax(dc.n_layers)),
+                int(np.argmax(dc.n_bins))]
+    pick = rng.choice(dc.n_cols, k - len(extremes), replace=False)
+    return np.unique(np.concatenate([extremes, pick]))
+
+
+def slice_outputs(dc, out, idx):
+    o = dc.offsets()
+    cat = lambda a, key: np.concatenate([a[o[key][i]:o[key][i + 1]] for i in idx])
+    return {"F_up": cat(out["F_up"], "iface"), "F_down": cat(out["F_down"], "iface"),
+            "F_net": cat(out["F_net"], "iface"), "Q": cat(out["Q"], "lay")}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_config3_uneven_full_batch_sampled_parity(cfg3, precision):
+    """4096 columns, L in [20, 200], NB in [30, 300], 20 g, one launch; the
+    oracle checks sampled columns (largest, smallest, random)."""
+    dc, b = cfg3
+    s = Solver(dc.g_weights, precision=rt.RT_FP64_PLAIN if precision == "fp64" else rt.RT_FP32_FORM)
+    out = s.solve_numpy(b)
+    st = s.stats()
+    s.close()
+    assert st["systems"] == dc.n_systems and st["nonfinite_outputs"] == 0
+    idx = sample_columns(dc)
+    host = dc.host_subset(idx)
+    ref = oracle_solve(host, method_opts())
+    e = assert_parity(host, slice_outputs(dc, out, idx), ref, precision, "config3")
+    print(precision, "config3 sampled error/tol", e, "systems", dc.n_systems)
+
+
+def test_graph_replay_equals_eager(cfg3):
+    dc, b = cfg3
+    s = Solver(dc.g_weights)
+    eager = s.solve_numpy(b)
+    g = GraphSolve(s, b)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    o = s.outputs(b)
+    torch.cuda.synchronize()
+    for k in eager:
+        assert np.array_equal(o[k].cpu().numpy(), eager[k]), k
+    s.close()
+
+
+def test_autotuner_candidates_agree_bitwise():
+    L, NB = rt_synth.uneven_shapes(300, seed=77, L_range=(20, 120), NB_range=(30, 200))
+    cols = rt_synth.generate(L, NB, 20, seed=78, optics="uniform")
+    b = DeviceBatch(cols)
+    res = autotune(b, cols.g_weights, candidates=[(64, 0), (128, 2), (256, 0), (256, 1)], reps=2)
+    assert res["stable"], res["table"]
+    assert res["block_threads"] in (64, 128, 256)
+    ref = oracle_solve(cols, method_opts())
+    s = Solver(cols.g_weights, block_threads=res["block_threads"], ctas_per_sm=res["ctas_per_sm"])
+    assert_parity(cols, s.solve_numpy(b), ref, "fp32", "autotuned")
+    s.close()
