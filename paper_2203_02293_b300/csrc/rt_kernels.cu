@@ -96,11 +96,11 @@ __device__ __forceinline__ float frcp(float x) {
 }
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 
-// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.5
-// (9 terms, truncation below 6e-10), else from the exponential e = exp(-x).
+// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.25
+// (7 terms, truncation below 2e-9), else from the exponential e = exp(-x)
+// (relative error of 1 - e below 5e-7 there).
 __device__ __forceinline__ float u_series(float x) {
-    float p = 1.f / 362880.f;
-    p = fmaf(p, x, -1.f / 40320.f);
+    float p = -1.f / 40320.f;
     p = fmaf(p, x, 1.f / 5040.f);
     p = fmaf(p, x, -1.f / 720.f);
     p = fmaf(p, x, 1.f / 120.f);
@@ -112,7 +112,7 @@ __device__ __forceinline__ float u_series(float x) {
 __device__ __forceinline__ float one_minus_exp_over_x(float x, float e) {
     const float s = u_series(x);
     const float d = (1.f - e) * frcp(x);
-    return (fabsf(x) < 0.5f) ? s : d;
+    return (fabsf(x) < 0.25f) ? s : d;
 }
 
 // FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
@@ -261,69 +261,74 @@ struct Layer32 {
     float T, R, Su, Sd, omtr, opr, mlay;
 };
 
-// Thermal sources of one sub-layer for departures from pi B at its ends.
-// Both the gradient form and the e_tau fallback (isothermal at the mean B,
-// Sec. 2.2.1) are evaluated and one is selected, so lanes do not diverge.
-__device__ __forceinline__ void thermal_sub(float dPi, float Pi, float t, float omtr, float gs,
-                                            bool fallback, float B1, float B2, float &su, float &sd) {
-    const float omr = omtr + t;                  // 1 - r
-    const float dB = B2 - B1;
-    const float grad = Pi * dB * gs;
-    const float su_g = dPi * (omr * B1 - t * B2) + grad;
-    const float sd_g = dPi * (omr * B2 - t * B1) - grad;
-    const float base = dPi * 0.5f * (B1 + B2) * omtr;
-    const float side = 0.5f * kPiF * dB * (omtr + 2.f * t);  // pi dB/2 (1 - r + t)
-    su = fallback ? base + side : su_g;
-    sd = fallback ? base - side : sd_g;
-}
-
+// Products are grouped by hand: float multiplication is not reassociated by
+// the compiler, and shared factors (1/h and 1/p from one reciprocal of h p,
+// 2q, w0 g0, ...) are formed once per layer.
+template <bool ISO>
 __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float Bt, float Bc, float Bb,
                                            float mu, float imu, double mu_d, bool beam, float Fb,
                                            const KParams &kp, Counters &cn) {
-    const bool invalid = !(dt >= 0.f) || !(w0 >= 0.f && w0 <= 1.f) || !(g0 > -1.f && g0 < 1.f);
-    cn.inv += invalid ? cn.on : 0u;
+    const bool valid = (dt >= 0.f) && (w0 >= 0.f) && (w0 <= 1.f) && (fabsf(g0) < 1.f);
+    cn.inv += valid ? 0u : cn.on;
     // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
-    float em1 = 0.225f - 0.1582f * g0 - 0.1777f * w0 - 0.07465f * g0 * g0 + 0.2351f * w0 * g0
-                - 0.05582f * w0 * w0;
+    const float wg = w0 * g0;
+    float em1 = fmaf(g0, fmaf(-0.07465f, g0, -0.1582f), fmaf(w0, fmaf(-0.05582f, w0, -0.1777f), 0.225f));
+    em1 = fmaf(0.2351f, wg, em1);
     em1 = (kp.improved && w0 > 0.1f) ? em1 : 0.f;
     const bool clamp = kp.e_clamp && em1 < 0.f;
     cn.eclamp += clamp ? cn.on : 0u;
     em1 = clamp ? 0.f : em1;
-    const float E = 1.f + em1;
     const float omw = 1.f - w0;
     const float ewm = em1 + omw;                 // E - w0
-    const float q = E * (1.f - w0 * g0);
+    const float q = (1.f + em1) * (1.f - wg);    // E (1 - w0 g0)
     const float iq = frcp(q);
     const bool cons = ewm == 0.f;                // E = w0 = 1: k = 0, Pi := pi
     const float k = cons ? 0.f : ewm * rsqrtf(ewm * q);
-    const float iw = frcp(ewm);
-    const float Pi = cons ? kPiF : kPiF * omw * iw;
-    const float dPi = cons ? 0.f : -kPiF * em1 * iw;   // Pi - pi
+    const float piw = kPiF * frcp(ewm);
+    const float Pi = cons ? kPiF : omw * piw;
+    const float dPi = cons ? 0.f : -em1 * piw;  // Pi - pi
     const float ip = frcp(1.f + k);
     const float eps = (1.f - k) * ip;
-    const bool iso = kp.isothermal;
-    const float dts = iso ? dt : 0.5f * dt;
+    const float dts = ISO ? dt : 0.5f * dt;
 
-    const float x = 2.f * q * k * dts;
+    const float q2 = q + q;
+    const float q2d = q2 * dts;
+    const float x = q2d * k;
     const float Tm = fexp(-x);
     const float u = one_minus_exp_over_x(x, Tm);
-    const float qd = 2.f * q * dts * u;          // (1 - T)/k
-    const float h = fmaf(2.f * Tm, ip, qd);
+    const float qd = q2d * u;                    // (1 - T)/k
+    const float h = fmaf(Tm + Tm, ip, qd);
     const float p = fmaf(eps, Tm, 1.f);
     const float ihp = frcp(h * p);
-    const float t = 4.f * Tm * ip * ip * ihp;
-    const float r = eps * qd * (1.f + Tm) * ihp;
-    const float omtr = 2.f * k * k * qd * ip * h * ihp;   // 1 - t - r
-    const float gs = 2.f * u * ip * p * ihp;              // 2u / ((1+k) h)
+    const float ih = p * ihp, ipp = h * ihp;     // 1/h, 1/p
+    const float ipihp = ip * ihp;
+    const float t = (4.f * Tm) * (ip * ipihp);
+    const float Y = fmaf(qd, Tm, qd);            // (1 - T^2)/k = qd (1 + T)
+    const float r = (eps * ihp) * Y;
+    const float k2 = k * k;
+    const float omtr = (k2 + k2) * (qd * ip) * ipp;      // 1 - t - r
+    const float omr = omtr + t;                          // 1 - r
 
     float suU, sdU, suL = 0.f, sdL = 0.f;
-    if (!iso) {
+    if (!ISO) {
         const bool fb = dts < 1e-4f;
         cn.etau += fb ? 2u * cn.on : 0u;
-        thermal_sub(dPi, Pi, t, omtr, gs, fb, Bt, Bc, suU, sdU);
-        thermal_sub(dPi, Pi, t, omtr, gs, fb, Bc, Bb, suL, sdL);
+        // gradient form and e_tau fallback (isothermal at the mean B), selected
+        const float pig = Pi * (2.f * u) * (ip * ih);    // Pi 2u/((1+k) h)
+        const float hb = 0.5f * dPi * omtr;
+        const float side = (0.5f * kPiF) * (omtr + 2.f * t);
+        const float d1 = Bc - Bt, d2 = Bb - Bc;
+        const float gU = pig * d1, gL = pig * d2;
+        const float suUg = fmaf(dPi, fmaf(omr, Bt, -t * Bc), gU);
+        const float sdUg = fmaf(dPi, fmaf(omr, Bc, -t * Bt), -gU);
+        const float suLg = fmaf(dPi, fmaf(omr, Bc, -t * Bb), gL);
+        const float sdLg = fmaf(dPi, fmaf(omr, Bb, -t * Bc), -gL);
+        const float bU = hb * (Bt + Bc), bL = hb * (Bc + Bb);
+        suU = fb ? fmaf(side, d1, bU) : suUg;
+        sdU = fb ? fmaf(-side, d1, bU) : sdUg;
+        suL = fb ? fmaf(side, d2, bL) : suLg;
+        sdL = fb ? fmaf(-side, d2, bL) : sdLg;
     } else {
-        const float omr = omtr + t;
         const float base = dPi * Bc * omtr;
         suU = base + kPiF * (omr * (Bc - Bt) - t * (Bc - Bb));
         sdU = base + kPiF * (omr * (Bc - Bb) - t * (Bc - Bt));
@@ -334,10 +339,11 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
         const float dl = dts * imu;
         m = fexp(-dl);
         const float omm = dl * one_minus_exp_over_x(dl, m);   // 1 - m
-        const float rho = mu * 2.f * q * k;
+        const float q2k = q2 * k;
+        const float rho = mu * q2k;
         const float ie2 = kp.inv_eps2;
-        const float A = w0 * fmaf(g0, ie2, 2.f * q);
-        const float G0h = 0.25f * w0 * g0 * ie2 * iq;         // G0/2 of Eq. B8
+        const float A = w0 * fmaf(g0, ie2, q2);
+        const float G0h = wg * (0.25f * ie2) * iq;            // G0/2 of Eq. B8
         // resonance test of Eq. 11: decide in FP64 only when FP32 cannot
         const float D32 = fmaf(rho, rho, -1.f);
         bool sw = false;
@@ -349,23 +355,22 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
                 sw = kp.resonance_paper != 0;
             }
         }
-        const float tm1r = -(omtr + 2.f * r + t * omm);        // (t m - 1) - r
-        const float rmtm = (omtr + r) - omm + r * m;           // r m - (t - m)
+        const float r2 = r + r;
+        const float tm1r = -fmaf(t, omm, omtr + r2);           // (t m - 1) - r
+        const float rmtm = fmaf(r, m, (omtr + r) - omm);      // r m - (t - m)
         float bu, bd;
         if (!sw) {
-            const float z = (1.f - rho) * dl;
-            const float lam_s = m * dl * u_series(-z);
-            const float lam_d = (Tm - m) * frcp(1.f - rho);
-            const float Lam = (fabsf(z) < 0.5f) ? lam_s : lam_d;
-            const float Y = qd * (1.f + Tm);                   // (1 - T^2)/k
-            const float SA = 0.25f * A * ip * ip * ihp * iq * frcp(1.f + rho);
-            const float tq = 2.f * q * mu;
-            const float k2 = k * k;
-            bu = SA * (2.f * (1.f + k) * Y + 4.f * Tm * (1.f - tq) * Lam) + G0h * tm1r;
-            bd = SA * (-2.f * Tm * (1.f - k) * Y
-                       + Lam * ((1.f + tq) * (Y * (1.f + k2) + 2.f * (1.f + Tm * Tm))
-                                + (1.f - tq) * (1.f - k2) * Y))
-                 + G0h * rmtm;
+            const float omrho = 1.f - rho;
+            const float z = omrho * dl;
+            const float lam_s = (m * dl) * u_series(-z);
+            const float lam_d = (Tm - m) * frcp(omrho);
+            const float Lam = (fabsf(z) < 0.25f) ? lam_s : lam_d;
+            const float SA2 = (0.5f * A) * (ip * ipihp) * (iq * frcp(1.f + rho));   // 2 SA
+            const float tq = mu * q2;
+            const float TL = Tm * Lam;
+            bu = fmaf(SA2, fmaf((1.f + k) * Y, 1.f, (TL + TL) * (1.f - tq)), G0h * tm1r);
+            const float cl = fmaf(Y, fmaf(tq, k2, 1.f), (1.f + tq) * fmaf(Tm, Tm, 1.f));
+            bd = fmaf(SA2, fmaf(Lam, cl, -(Tm * (1.f - k)) * Y), G0h * rmtm);
         } else {
             // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
             const float c1 = 0.5f * iq;
@@ -377,7 +382,7 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
         }
         suU = fmaf(Fb, bu, suU);
         sdU = fmaf(Fb, bd, sdU);
-        if (!iso) {
+        if (!ISO) {
             const float Fc = Fb * m;
             suL = fmaf(Fc, bu, suL);
             sdL = fmaf(Fc, bd, sdL);
@@ -385,7 +390,7 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
     }
 
     Layer32 o;
-    if (iso) {
+    if (ISO) {
         o.T = t;
         o.R = r;
         o.Su = suU;
@@ -395,15 +400,15 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
         o.mlay = m;
     } else {
         // merge upper (top -> centre) and lower (centre -> bottom) sub-layers
-        const float omr = omtr + t;              // 1 - r
-        const float Dr = frcp(omr * (1.f + r));  // 1 / (1 - r^2)
+        const float opr1 = 1.f + r;
+        const float Dr = frcp(omr * opr1);      // 1 / (1 - r^2)
         const float tD = t * Dr;
         o.T = t * tD;
-        o.R = r * (1.f + o.T);
-        o.Su = suU + tD * (suL + r * sdU);
-        o.Sd = sdL + tD * (sdU + r * suL);
-        o.omtr = omtr * (omtr + 2.f * t) * (1.f + r) * Dr;   // (1-r-t)(1-r+t)/(1-r)
-        o.opr = omr * (1.f + o.T);
+        o.R = fmaf(r, o.T, r);
+        o.Su = fmaf(tD, fmaf(r, sdU, suL), suU);
+        o.Sd = fmaf(tD, fmaf(r, suL, sdU), sdL);
+        o.omtr = (omtr * (omtr + 2.f * t)) * (opr1 * Dr);   // (1-r-t)(1-r+t)/(1-r)
+        o.opr = fmaf(omr, o.T, omr);
         o.mlay = m * m;
     }
     return o;
@@ -574,7 +579,33 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 // of a column sums the column's unit partials in unit order (FP64) and
 // writes fluxes, net flux and heating.
 // ---------------------------------------------------------------------
+// One (column, level) per warp: lane e evaluates the Planck integral at bin
+// edge e (whichever of S(x) or P(x) that edge needs), and bin b takes edges b
+// and b+1 from its lane and the next (shuffle).  31 bins per pass.
+__device__ __forceinline__ void planck_level_warp(float T, int NB, float dwn, float wmin, float scale,
+                                                  float *dst, int lane) {
+    const float a = (T > 0.f) ? (float)(kC2 * 100.0) * frcp(T) : 0.f;
+    const float T2 = T * T;
+    const float pref = (float)kPlanckK * (T2 * T2) * scale;
+    for (int b0 = 0; b0 < NB; b0 += 31) {
+        const int e = b0 + lane;
+        const float x = a * fmaf((float)e, dwn, wmin);
+        const float v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
+        const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
+        const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
+        const int bin = e;
+        if (lane < 31 && bin < NB) {
+            float d;
+            if (x >= 2.f) d = v - v1;
+            else if (x1 <= 2.f) d = v1 - v;
+            else d = ((float)kPi4Over15 - v) - v1;
+            dst[bin] = (T > 0.f) ? pref * d : 0.f;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
         const int L = kp.n_layers[c], NB = kp.n_bins[c];
         const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], b0 = kp.bin_off[c], fsi = kp.fs_off[c];
@@ -582,19 +613,23 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         const float dwn = (float)((kp.wn_max - kp.wn_min) / NB);
         const float wmin = (float)kp.wn_min;
         const int nlev = 2 * L + 1;
-        for (int i = threadIdx.x; i < nlev * NB; i += blockDim.x) {
-            const int lev = i / NB, b = i - lev * NB;
-            const float T = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
-            B[i] = planck_bin_f(T, fmaf((float)b, dwn, wmin), fmaf((float)(b + 1), dwn, wmin));
-        }
-        for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-            kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
-            kp.fboa32[b0 + b] = kPiF * planck_bin_f((float)kp.T_int, fmaf((float)b, dwn, wmin),
-                                                    fmaf((float)(b + 1), dwn, wmin));
-        }
-        if (threadIdx.x == 0) {
-            const double mu = kp.mu_star[kp.mu_idx[c]];
-            kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
+        // levels 0..2L, then one extra task for the per-bin and per-column data
+        for (int lev = warp; lev <= nlev; lev += nw) {
+            if (lev < nlev) {
+                float T = 0.f;
+                if (lane == 0)
+                    T = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
+                T = __shfl_sync(0xffffffffu, T, 0);
+                planck_level_warp(T, NB, dwn, wmin, 1.f, B + (long long)lev * NB, lane);
+            } else {
+                planck_level_warp((float)kp.T_int, NB, dwn, wmin, kPiF, kp.fboa32 + b0, lane);
+                for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
+                if (lane == 0) {
+                    const double mu = kp.mu_star[kp.mu_idx[c]];
+                    kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f,
+                                             mu > 0.0 ? 1.f : 0.f, 0.f);
+                }
+            }
         }
     }
 }
@@ -625,6 +660,7 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     }
 }
 
+template <bool ISO>
 __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
     extern __shared__ __align__(16) float smem32[];
     const int lane = threadIdx.x & 31;
@@ -701,8 +737,8 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
                 nw = __ldcs(pw);
                 ng = __ldcs(pg);
             }
-            const Layer32 ly = layer32(dt, w0, g0, Bp[0], Bp[nbc], Bp[2 * nbc], mu, imu, mu_d, beam, Fb,
-                                       kp, cn);
+            const Layer32 ly = layer32<ISO>(dt, w0, g0, Bp[0], Bp[nbc], Bp[2 * nbc], mu, imu, mu_d, beam,
+                                            Fb, kp, cn);
             Bp += 2 * nbc;
             const float omr = ly.omtr + ly.T;                // 1 - R
             const float ipv = frcp(fmaf(ly.R, al, omr));     // 1 / (1 - R a')
@@ -998,9 +1034,13 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
 constexpr int kMaxDynSmem = 200 * 1024;
 
 cudaError_t init_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(fp32_units, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fp32_units, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = cudaSuccess;
+    for (auto f : {fp32_units<false>, fp32_units<true>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fp64_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
@@ -1010,7 +1050,7 @@ int occupancy(int precision_fp64, int block, size_t smem) {
     int n = 0;
     cudaError_t e = precision_fp64
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units, block, smem);
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false>, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -1019,7 +1059,10 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     fp32_prep<<<pgrid, 256, 0, s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    fp32_units<<<grid, block, smem, s>>>(kp);
+    if (kp.isothermal)
+        fp32_units<true><<<grid, block, smem, s>>>(kp);
+    else
+        fp32_units<false><<<grid, block, smem, s>>>(kp);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,9 @@ class GraphSolve:
             solver.solve(batch, self.stream)
 
     def replay(self):
-        self.graph.replay()
+        # replay() launches on the current stream; keep it on the capture stream
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
 
 
 def signature(batch: DeviceBatch, cfg: dict) -> str:
