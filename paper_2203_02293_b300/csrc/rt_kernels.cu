@@ -198,6 +198,8 @@ __device__ double planck_bin_d(double T, double wlo, double whi) {
 struct Counters {
     unsigned res, etau, eclamp, inv, nonfinite, fp64;
     unsigned on;   // 1 while the thread works on a real system, 0 on padding lanes
+    // FP32 form: raw per-system counts, added (masked by `on`) once per system
+    unsigned s_inv, s_ecl, s_etau;
 };
 
 __device__ __forceinline__ void flush_counters(const Counters &cn, unsigned long long *stats) {
@@ -215,7 +217,7 @@ __device__ __forceinline__ void flush_counters(const Counters &cn, unsigned long
 // The paper's resonance test (Eq. 11 and the text after it) evaluated in
 // FP64 with the same operation order as a plain C evaluation, so the branch
 // matches an FP64 reference bit for bit.
-__device__ double resonance_D_fp64(float w0f, float g0f, double mu, int improved, int e_clamp) {
+__device__ __noinline__ double resonance_D_fp64(float w0f, float g0f, double mu, int improved, int e_clamp) {
     const double w0 = (double)w0f, g0 = (double)g0f;
     double E = 1.0;
     if (improved && w0 > (double)0.1f) {
@@ -269,14 +271,14 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
                                            float mu, float imu, double mu_d, bool beam, float Fb,
                                            const KParams &kp, Counters &cn) {
     const bool valid = (dt >= 0.f) && (w0 >= 0.f) && (w0 <= 1.f) && (fabsf(g0) < 1.f);
-    cn.inv += valid ? 0u : cn.on;
+    cn.s_inv += valid ? 0u : 1u;
     // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
     const float wg = w0 * g0;
     float em1 = fmaf(g0, fmaf(-0.07465f, g0, -0.1582f), fmaf(w0, fmaf(-0.05582f, w0, -0.1777f), 0.225f));
     em1 = fmaf(0.2351f, wg, em1);
     em1 = (kp.improved && w0 > 0.1f) ? em1 : 0.f;
     const bool clamp = kp.e_clamp && em1 < 0.f;
-    cn.eclamp += clamp ? cn.on : 0u;
+    cn.s_ecl += clamp ? 1u : 0u;
     em1 = clamp ? 0.f : em1;
     const float omw = 1.f - w0;
     const float ewm = em1 + omw;                 // E - w0
@@ -312,22 +314,23 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
     float suU, sdU, suL = 0.f, sdL = 0.f;
     if (!ISO) {
         const bool fb = dts < 1e-4f;
-        cn.etau += fb ? 2u * cn.on : 0u;
-        // gradient form and e_tau fallback (isothermal at the mean B), selected
-        const float pig = Pi * (2.f * u) * (ip * ih);    // Pi 2u/((1+k) h)
-        const float hb = 0.5f * dPi * omtr;
+        cn.s_etau += fb ? 1u : 0u;
+        // Gradient form  su = dPi ((1-r) B1 - t B2) + G (B2 - B1),
+        //                sd = dPi ((1-r) B2 - t B1) - G (B2 - B1),
+        // with G = Pi 2u/((1+k) h).  The e_tau fallback (isothermal at the mean
+        // B, Sec. 2.2.1) is the same expression with B1 = B2 = mean B and
+        // G = pi (1 - r + t)/2, so only the inputs are selected.
+        const float pig = Pi * (2.f * u) * (ip * ih);
         const float side = (0.5f * kPiF) * (omtr + 2.f * t);
-        const float d1 = Bc - Bt, d2 = Bb - Bc;
-        const float gU = pig * d1, gL = pig * d2;
-        const float suUg = fmaf(dPi, fmaf(omr, Bt, -t * Bc), gU);
-        const float sdUg = fmaf(dPi, fmaf(omr, Bc, -t * Bt), -gU);
-        const float suLg = fmaf(dPi, fmaf(omr, Bc, -t * Bb), gL);
-        const float sdLg = fmaf(dPi, fmaf(omr, Bb, -t * Bc), -gL);
-        const float bU = hb * (Bt + Bc), bL = hb * (Bc + Bb);
-        suU = fb ? fmaf(side, d1, bU) : suUg;
-        sdU = fb ? fmaf(-side, d1, bU) : sdUg;
-        suL = fb ? fmaf(side, d2, bL) : suLg;
-        sdL = fb ? fmaf(-side, d2, bL) : sdLg;
+        const float G = fb ? side : pig;
+        const float mU = 0.5f * (Bt + Bc), mL = 0.5f * (Bc + Bb);
+        const float tU = fb ? mU : Bt, cU = fb ? mU : Bc;    // upper sub-layer ends
+        const float cL = fb ? mL : Bc, bL = fb ? mL : Bb;    // lower sub-layer ends
+        const float gU = G * (Bc - Bt), gL = G * (Bb - Bc);
+        suU = fmaf(dPi, fmaf(omr, tU, -t * cU), gU);
+        sdU = fmaf(dPi, fmaf(omr, cU, -t * tU), -gU);
+        suL = fmaf(dPi, fmaf(omr, cL, -t * bL), gL);
+        sdL = fmaf(dPi, fmaf(omr, bL, -t * cL), -gL);
     } else {
         const float base = dPi * Bc * omtr;
         suU = base + kPiF * (omr * (Bc - Bt) - t * (Bc - Bb));
@@ -338,47 +341,50 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
     if (beam) {
         const float dl = dts * imu;
         m = fexp(-dl);
-        const float omm = dl * one_minus_exp_over_x(dl, m);   // 1 - m
+        const float omm = (dl < 0.25f) ? dl * u_series(dl) : 1.f - m;   // 1 - m
         const float q2k = q2 * k;
         const float rho = mu * q2k;
         const float ie2 = kp.inv_eps2;
         const float A = w0 * fmaf(g0, ie2, q2);
         const float G0h = wg * (0.25f * ie2) * iq;            // G0/2 of Eq. B8
-        // resonance test of Eq. 11: decide in FP64 only when FP32 cannot
-        const float D32 = fmaf(rho, rho, -1.f);
-        bool sw = false;
-        if (fabsf(D32) < 2e-5f) {
-            cn.fp64 += cn.on;
-            const double D = resonance_D_fp64(w0, g0, mu_d, kp.improved, kp.e_clamp);
-            if (fabs(D) < 1e-5) {
-                cn.res += cn.on;
-                sw = kp.resonance_paper != 0;
-            }
-        }
         const float r2 = r + r;
         const float tm1r = -fmaf(t, omm, omtr + r2);           // (t m - 1) - r
         const float rmtm = fmaf(r, m, (omtr + r) - omm);      // r m - (t - m)
-        float bu, bd;
-        if (!sw) {
-            const float omrho = 1.f - rho;
-            const float z = omrho * dl;
-            const float lam_s = (m * dl) * u_series(-z);
-            const float lam_d = (Tm - m) * frcp(omrho);
-            const float Lam = (fabsf(z) < 0.25f) ? lam_s : lam_d;
-            const float SA2 = (0.5f * A) * (ip * ipihp) * (iq * frcp(1.f + rho));   // 2 SA
-            const float tq = mu * q2;
-            const float TL = Tm * Lam;
-            bu = fmaf(SA2, fmaf((1.f + k) * Y, 1.f, (TL + TL) * (1.f - tq)), G0h * tm1r);
-            const float cl = fmaf(Y, fmaf(tq, k2, 1.f), (1.f + tq) * fmaf(Tm, Tm, 1.f));
-            bd = fmaf(SA2, fmaf(Lam, cl, -(Tm * (1.f - k)) * Y), G0h * rmtm);
-        } else {
-            // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
-            const float c1 = 0.5f * iq;
-            const float lead = -0.5f * A * imu;
-            const float Gp = 0.5f * lead * (c1 - mu) + G0h;
-            const float Gm = -0.5f * lead * (c1 + mu) - G0h;
-            bu = -Gp * (omtr + r + t * omm) + r * Gm;         // Gp (t m - 1) + r Gm
-            bd = Gm * (omm - omtr - r) + r * Gp * m;          // Gm (t - m) + r Gp m
+        // stable form: the 1/D of G+- divided out (see the block comment)
+        const float omrho = 1.f - rho;
+        const float z = omrho * dl;
+        const float lam_s = (m * dl) * u_series(-z);
+        const float lam_d = (Tm - m) * frcp(omrho);
+        const float Lam = (fabsf(z) < 0.25f) ? lam_s : lam_d;
+        const float SA2 = (0.5f * A) * (ip * ipihp) * (iq * frcp(1.f + rho));   // 2 SA
+        const float tq = mu * q2;
+        const float TL = Tm * Lam;
+        float bu = fmaf(SA2, fmaf((1.f + k) * Y, 1.f, (TL + TL) * (1.f - tq)), G0h * tm1r);
+        const float cl = fmaf(Y, fmaf(tq, k2, 1.f), (1.f + tq) * fmaf(Tm, Tm, 1.f));
+        float bd = fmaf(SA2, fmaf(Lam, cl, -(Tm * (1.f - k)) * Y), G0h * rmtm);
+        // resonance test of Eq. 11 (rare): the FP64 decision, and the paper's
+        // switch to D := 2 mu* when |D| < 1e-5, run only if a lane needs them
+        const float D32 = fmaf(rho, rho, -1.f);
+        const bool near = fabsf(D32) < 2e-5f;
+        if (__any_sync(0xffffffffu, near)) {
+            bool sw = false;
+            if (near) {
+                cn.fp64 += cn.on;
+                const double D = resonance_D_fp64(w0, g0, mu_d, kp.improved, kp.e_clamp);
+                if (fabs(D) < 1e-5) {
+                    cn.res += cn.on;
+                    sw = kp.resonance_paper != 0;
+                }
+            }
+            if (sw) {
+                // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
+                const float c1 = 0.5f * iq;
+                const float lead = -0.5f * A * imu;
+                const float Gp = 0.5f * lead * (c1 - mu) + G0h;
+                const float Gm = -0.5f * lead * (c1 + mu) - G0h;
+                bu = -Gp * (omtr + r + t * omm) + r * Gm;     // Gp (t m - 1) + r Gm
+                bd = Gm * (omm - omtr - r) + r * Gp * m;      // Gm (t - m) + r Gp m
+            }
         }
         suU = fmaf(Fb, bu, suU);
         sdU = fmaf(Fb, bd, sdU);
@@ -605,6 +611,7 @@ __device__ __forceinline__ void planck_level_warp(float T, int NB, float dwn, fl
 }
 
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
+    extern __shared__ float sT[];                 // [2 Lmax + 1] temperatures of one column
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
         const int L = kp.n_layers[c], NB = kp.n_bins[c];
@@ -613,14 +620,14 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         const float dwn = (float)((kp.wn_max - kp.wn_min) / NB);
         const float wmin = (float)kp.wn_min;
         const int nlev = 2 * L + 1;
+        __syncthreads();                          // previous column done with sT
+        for (int lev = threadIdx.x; lev < nlev; lev += blockDim.x)
+            sT[lev] = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
+        __syncthreads();
         // levels 0..2L, then one extra task for the per-bin and per-column data
         for (int lev = warp; lev <= nlev; lev += nw) {
             if (lev < nlev) {
-                float T = 0.f;
-                if (lane == 0)
-                    T = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
-                T = __shfl_sync(0xffffffffu, T, 0);
-                planck_level_warp(T, NB, dwn, wmin, 1.f, B + (long long)lev * NB, lane);
+                planck_level_warp(sT[lev], NB, dwn, wmin, 1.f, B + (long long)lev * NB, lane);
             } else {
                 planck_level_warp((float)kp.T_int, NB, dwn, wmin, kPiF, kp.fboa32 + b0, lane);
                 for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
@@ -674,7 +681,7 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
     float *tb = sFB + nbw;                         // [16][2][33]
     const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long sstride = kp.n_slots;
-    Counters cn = {0, 0, 0, 0, 0, 0, 0};
+    Counters cn = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     for (;;) {
         int unit = 0;
@@ -709,10 +716,13 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         }
         __syncwarp();
 
-        const int s = s0 + lane;
-        const bool active = s < S;
+        // padding lanes of a column's last unit repeat system s0 with zero
+        // weight, so the loops below need no per-lane predicates
+        const bool active = s0 + lane < S;
+        const int s = active ? s0 + lane : s0;
         cn.on = active ? 1u : 0u;
-        const int b = active ? s / NG : b_lo;
+        cn.s_inv = cn.s_ecl = cn.s_etau = 0u;
+        const int b = s / NG;
         const int bb = b - b_lo;
         const float wg = active ? kp.g_w32[s - b * NG] : 0.f;
         const float *Bp = sB + bb;                 // level stride nbc
@@ -722,16 +732,11 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         float bl = (float)kp.F_toa - kPiF * Bp[0];           // b' at the TOA
         float Fb = beam ? mu * sFs[bb] : 0.f;
         const float *pd = kp.dtau + cube0 + s, *pw = kp.w0 + cube0 + s, *pg = kp.g0 + cube0 + s;
-        float nd = 0.f, nw = 0.f, ng = 0.f;
-        if (active) {
-            nd = __ldcs(pd);
-            nw = __ldcs(pw);
-            ng = __ldcs(pg);
-        }
+        float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);
         float4 *sp = kp.scr32 + slot;
         for (int l = 0; l < L; ++l) {
             const float dt = nd, w0 = nw, g0 = ng;
-            if (active && l + 1 < L) {               // prefetch the next layer
+            if (l + 1 < L) {                         // prefetch the next layer
                 pd += S; pw += S; pg += S;
                 nd = __ldcs(pd);
                 nw = __ldcs(pw);
@@ -756,35 +761,35 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
             Fb *= ly.mlay;
         }
 
+        if (active) {
+            cn.inv += cn.s_inv;
+            cn.eclamp += cn.s_ecl;
+            cn.etau += (ISO ? 1u : 2u) * cn.s_etau;
+        }
         // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b';
         // back-substitution to the TOA; interface sums through the transpose
         const float FBOA = sFB[bb];
-        float uu = active ? (FBOA + Fb + bl) * frcp(al) : 0.f;
-        bool bad = !isfinite(uu);
+        float uu = (FBOA + Fb + bl) * frcp(al);
+        bool bad = !isfinite(uu);   // NaN and Inf propagate up the substitution
         float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
         // Bp points at level 2L (the BOA interface)
         tb[lane] = wg * fmaf(kPiF, Bp[0], uu);
         tb[33 + lane] = wg * FBOA;
         int gi = 1;              // slots used in the current group of 16 interfaces
         int gtop = L;            // interface held in slot 0 of the group
-        float4 nst = make_float4(0.f, 0.f, 0.f, 0.f);
         sp -= sstride;           // interface L-1
-        if (active && L > 0) nst = __ldcg(sp);
+        float4 nst = __ldcg(sp);
         for (int i = L - 1; i >= -1; --i) {
             if (i >= 0) {
                 const float4 st = nst;
-                if (active && i > 0) {
+                if (i > 0) {
                     sp -= sstride;
                     nst = __ldcg(sp);
                 }
                 Bp -= 2 * nbc;
-                float fup = 0.f, fnet = 0.f;
-                if (active) {
-                    uu = fmaf(st.x, uu, st.y);
-                    fup = fmaf(kPiF, Bp[0], uu);
-                    fnet = fmaf(st.z, uu, -st.w);
-                    bad |= !isfinite(uu);
-                }
+                uu = fmaf(st.x, uu, st.y);
+                const float fup = fmaf(kPiF, Bp[0], uu);
+                const float fnet = fmaf(st.z, uu, -st.w);
                 tb[(gi * 2) * 33 + lane] = wg * fup;
                 tb[(gi * 2 + 1) * 33 + lane] = wg * fnet;
                 ++gi;
@@ -805,6 +810,7 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
                 gi = 0;
             }
         }
+        bad |= !isfinite(uu);
         if (active && bad) cn.nonfinite++;
 
         // the warp that completes a column's last unit writes the column
@@ -923,7 +929,7 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
     const int NG = kp.n_g;
     const long long slot = (long long)blockIdx.x * blockDim.x + tid;
     double2 *scr = kp.scr64 + slot;           // element (2 lev + j) n_slots + slot
-    Counters cn = {0, 0, 0, 0, 0, 0, 0};
+    Counters cn = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     ColInfo ci;
     const bool iso = kp.isothermal;
 
@@ -1056,7 +1062,7 @@ int occupancy(int precision_fp64, int block, size_t smem) {
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
     const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
-    fp32_prep<<<pgrid, 256, 0, s>>>(kp);
+    fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 1), s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (kp.isothermal)
