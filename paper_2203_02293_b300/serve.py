@@ -153,7 +153,10 @@ class Slot:
 class Server:
     def __init__(self, pool: Pool, n_slots: int = 4, hbm_budget_bytes: int = 8 << 30,
                  max_systems_per_batch: int = 24_000_000, wait_timeout_s: float = 0.0,
-                 keep_outputs: bool = False, **cfg):
+                 keep_outputs: bool = False, policy: str = "fifo", **cfg):
+        # policy: "fifo" admits in arrival order; "sjf" admits the smallest
+        # waiting requests first (shorter latency for small requests)
+        self.policy = policy
         self.pool = pool
         self.budget = hbm_budget_bytes
         self.max_sys = max_systems_per_batch
@@ -222,6 +225,8 @@ class Server:
                 else:
                     keep.append(r)
             waiting = keep
+            if self.policy == "sjf" and len(waiting) > 1:
+                waiting = deque(sorted(waiting, key=lambda r: r.systems * r.L))
             # admission into free slots
             for s in self.slots:
                 if s.busy or not waiting:
