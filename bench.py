@@ -237,6 +237,92 @@ def run_uneven(args, stream):
     return out
 
 
+def run_postproc(args, stream):
+    """Post-processing shape (Sec. 2.1.3): 2562 columns extended to 1 ubar
+    (40-52 layers), 3255 bins log-spaced at R = 500, one g-point; the
+    per-bin TOA spectrum is written with the fluxes.  Inputs ~4.6 GB, above L2."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300.solver import DeviceBatch, Solver
+    dc = rt_synth.postproc_device(2562, seed=5)
+    b = DeviceBatch.from_device(dc)
+    s = Solver(dc.g_weights, wn_edges=dc.consts["wn_edges"])
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            s.solve(b, stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.postproc_steps):
+            s.solve(b, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.postproc_steps
+    st = s.stats()
+    s.close()
+    out = {"workload": "2562 cols extended to 1 ubar (L 40-52), 3255 bins (R=500), 1 g, per-bin TOA spectrum",
+           "systems": dc.n_systems, "layer_systems": int((dc.n_layers.astype(np.int64) * dc.n_bins).sum()),
+           "input_bytes": int(3 * 4 * dc.dtau.numel()), "ms_per_step": ms,
+           "value": dc.n_systems / (ms * 1e-3), "unit": UNIT,
+           "spectra_per_s": dc.n_cols / (ms * 1e-3), "steps": args.postproc_steps,
+           "nonfinite_outputs": st["nonfinite_outputs"]}
+    del b, dc
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ktable(args, stream):
+    """GCM shape (2562 x 40 x 30 x 20) with the optics from the k-table front
+    end (Sec. 2.1.3: 60 x 28 (T, p) table, gas/cloud mixing, H2/He Rayleigh):
+    fused into the solve kernel, and beside it the unfused route (the optics
+    kernel writes the cubes, then the cube solve).  The state and table fit in
+    L2; each step still streams ~1.5 GB of elimination scratch through HBM."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300 import rt
+    from paper_2203_02293_b300.solver import DeviceBatch, Solver
+    cols = rt_synth.state_columns(2562, 40, 30, 20, seed=26)
+    kt = rt_synth.ktable(n_bins=30, n_g=20, seed=11)
+    b = DeviceBatch(cols)
+    s = Solver(cols.g_weights)
+    s.set_ktable(kt)
+    o = s.ktable_optics(b)
+    fb = DeviceBatch(cols)
+    fb.dtau, fb.w0, fb.g0 = o["dtau"], o["w0"], o["g0"]
+    fb._desc = None
+
+    def timed(fn, steps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_fused = timed(lambda: s.solve_ktable(b, stream), args.ktable_steps)
+
+    def unfused():
+        rt.rt_ktable_optics(s.h, b.state_descriptor(), o["dtau"], o["w0"], o["g0"], stream)
+        s.solve(fb, stream)
+    ms_unfused = timed(unfused, args.ktable_steps)
+    st = s.stats()
+    s.close()
+    n = b.n_systems
+    out = {"workload": "2562 x 40 x 30 x 20, optics from a 60x28 k-table (fused into the solve)",
+           "systems": n, "ms_per_step": ms_fused, "value": n / (ms_fused * 1e-3), "unit": UNIT,
+           "unfused_ms_per_step": ms_unfused, "unfused_value": n / (ms_unfused * 1e-3),
+           "steps": args.ktable_steps, "nonfinite_outputs": st["nonfinite_outputs"],
+           "invalid_inputs": st["invalid_inputs"]}
+    del b, fb, o
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_serving(args):
     """Config 4: Poisson arrivals (mean 200/s), requests of logU[1, 2562]
     columns x U{40..100} layers x U{30..300} bins x 20 g sliced from a
@@ -273,6 +359,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--uneven-steps", type=int, default=10)
+    ap.add_argument("--postproc-steps", type=int, default=20)
+    ap.add_argument("--ktable-steps", type=int, default=200)
     ap.add_argument("--serving-seconds", type=float, default=20.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
@@ -433,6 +521,8 @@ def main():
         del batch, host, dev
         torch.cuda.empty_cache()
         line["uneven"] = run_uneven(args, stream)
+        line["postproc"] = run_postproc(args, stream)
+        line["ktable"] = run_ktable(args, stream)
         line["serving"] = run_serving(args)
     if rank == 0 and not args.no_cpu_baseline:
         v, passes, el = time_oracle(cols, 10.0)

@@ -59,6 +59,9 @@ enum { RT_NONISOTHERMAL = 0, RT_ISOTHERMAL = 1 };
  * resonance test near |D| = 1e-5), or FP64 with the paper's literal
  * formulas. */
 enum { RT_FP32_FORM = 0, RT_FP64_PLAIN = 1 };
+/* Where the FP32 solve reads the bin-integrated Planck values (no effect on
+ * results, which are bitwise the same either way). */
+enum { RT_STAGE_AUTO = 0, RT_STAGE_SHARED = 1, RT_STAGE_DIRECT = 2 };
 /* Beam singularity of Eq. B8 at D = 4 E mu*^2 (E - w0)(1 - w0 g0) - 1 = 0
  * (Eq. 11): PAPER switches D to 2 mu* when |D| < 1e-5 (text after Eq. 11);
  * LIMIT uses the exact (finite) solution at every mu*. */
@@ -87,6 +90,17 @@ typedef struct {
                                     form, 64..512 for FP64); 0 = default (256) */
     int32_t ctas_per_sm;         /* cap on resident CTAs per SM of the persistent grid;
                                     0 = as many as fit */
+    int32_t planck_staging;      /* FP32 form, where the solve reads B(T) per bin:
+                                    RT_STAGE_AUTO, RT_STAGE_SHARED (staged per
+                                    warp in shared memory; pays off when many
+                                    g-points share a bin) or RT_STAGE_DIRECT
+                                    (read from the per-column table in device
+                                    memory; for few g-points per bin) */
+    int32_t n_edges;             /* 0: NB bins of equal width on [wn_min, wn_max];
+                                    > 1: explicit bin edges, every column then has
+                                    n_edges - 1 bins (e.g. the R = 500 sampling of
+                                    the post-processing step, Sec. 2.1.3) */
+    const double *wn_edges;      /* HOST [n_edges], cm^-1, increasing; copied by rt_create */
 } rt_config;
 
 /* A packed batch of columns.  Column c has L_c layers, NB_c bins and
@@ -167,6 +181,66 @@ int rt_fluxes(rt_handle *h, double *F_up, double *F_down, double *F_net, void *s
  * Q_l = (g / c_P) (F_net[l+1] - F_net[l]) / (p[l+1] - p[l]). */
 int rt_heating(rt_handle *h, double *Q, void *stream);
 
+/* Copy the last solve's upward flux at the top of the atmosphere per bin, W
+ * m^-2 per bin, [sum_c NB_c] (column c's bins at the sum of the earlier
+ * columns' NB): the Gauss-weighted sum over the bin's g-points -- the
+ * emission plus reflected-light spectrum that post-processing turns into
+ * synthetic spectra (Sec. 2.1.3, R = 500 with one point per bin).  Host or
+ * device pointer.  Bit-reproducible for n_g <= 32. */
+int rt_toa_spectrum(rt_handle *h, double *F_up_toa, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Input front end (Sec. 2.1.3): the optics of every layer, bin and g-point
+ * derived from the column state and a premixed k-table, instead of being
+ * passed in as cubes.
+ *
+ *   kappa   = 10^(bilinear interpolation of log10 kappa in (T, log10 p))
+ *             at the layer's centre temperature T_center and pressure
+ *             sqrt(p_top p_bot); T and log10 p are clamped to the grid;
+ *   sigma_g = x_H2 sigma_H2 + x_He sigma_He, the Rayleigh cross sections of
+ *             App. C averaged over the bin in wavenumber;
+ *   w0      = (sigma_g + f_cloud sigma_scat,cloud) / E,
+ *   g0      = f_cloud sigma_scat,cloud g0_cloud / (sigma_g + f_cloud sigma_scat,cloud),
+ *             with E = sigma_g + kappa mbar + f_cloud (sigma_abs,cloud +
+ *             sigma_scat,cloud) the extinction per gas particle (the mixing
+ *             equations of Sec. 2.1.3; g0 = 0 where nothing scatters);
+ *   dtau    = E / mbar * (p_bot - p_top) / g.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_T, n_P;              /* grid sizes (the paper's tables: 60 x 28), >= 2 each */
+    const double *T_grid;          /* HOST [n_T] K, strictly increasing */
+    const double *log10p_grid;     /* HOST [n_P] log10(p / Pa), strictly increasing */
+    int32_t n_bins;                /* NB of the table; columns solved with it have NB = n_bins */
+    int32_t n_g;                   /* Gauss points of the table; must equal the handle's n_g */
+    const float *log10_kappa;      /* HOST [n_T][n_P][n_bins][n_g] log10(kappa / m^2 kg^-1) */
+    const double *sigma_scat_cloud;  /* HOST [n_bins] m^2 per cloud particle, bin averages */
+    const double *sigma_abs_cloud;   /* HOST [n_bins] m^2 per cloud particle */
+    const double *g0_cloud;          /* HOST [n_bins] asymmetry factor of the cloud */
+    double f_cloud;                /* cloud-to-gas number ratio (the paper's runs: 1e-17) */
+    double x_H2, x_He;             /* number fractions for Rayleigh scattering, >= 0 */
+    double mbar_amu;               /* mean molecular mass, amu (Table 3: 2.34) */
+} rt_ktable;
+
+/* Copy a k-table into the handle (device memory) and precompute the per-bin
+ * scattering data from the handle's bins (uniform or explicit edges).
+ * RT_EINVAL on a bad field or when the table's n_g differs from the
+ * handle's; replaces any earlier table (synchronises the device). */
+int rt_set_ktable(rt_handle *h, const rt_ktable *kt);
+
+/* Write the front end's FP32 optics for cols (whose dtau, w0, g0 must be
+ * NULL and whose columns all have NB = the table's n_bins) into DEVICE cubes
+ * dtau, w0, g0 in the packed layout of rt_columns.  Gather offsets other than
+ * cube_offset are honoured.  RT_ENOTSOLVED without a table. */
+int rt_ktable_optics(rt_handle *h, const rt_columns *cols, float *dtau, float *w0, float *g0,
+                     void *stream);
+
+/* rt_solve_columns with the optics from the front end (cols->dtau, w0, g0
+ * and cube_offset NULL).  The FP32 form evaluates the front end inside the
+ * solve kernel, so no cube is written or read; the FP64 path first writes
+ * the FP32 optics of rt_ktable_optics into handle workspace.  Outputs are
+ * read as after rt_solve_columns. */
+int rt_solve_ktable(rt_handle *h, const rt_columns *cols, void *stream);
+
 /* Branch and error counters of the last solve (synchronises the stream of
  * that solve). */
 int rt_stats(rt_handle *h, rt_stats_t *out);
@@ -185,8 +259,8 @@ void rt_destroy(rt_handle *h);
  * and loops that cannot take the device-wide synchronisation an allocation
  * may bring.
  *
- * It runs the FP32 form (cfg->precision must be RT_FP32_FORM) on a packed
- * batch in which every column has the same shape (cols->n_layers, cols->n_bins
+ * It runs the FP32 form (cfg->precision must be RT_FP32_FORM, uniform bins:
+ * cfg->n_edges = 0) on a packed batch in which every column has the same shape (cols->n_layers, cols->n_bins
  * and the gather offsets NULL; cols->L and cols->NB set), with no handle: the caller passes the inputs
  * (same layout as rt_solve_columns) and DEVICE output arrays F_up, F_down,
  * F_net [n_cols (L+1)] and Q [n_cols L], written in place (same meaning as

@@ -43,7 +43,7 @@ class _Cfg(ctypes.Structure):
         ("eps2", ctypes.c_double), ("grav", ctypes.c_double),
         ("cp", ctypes.c_double), ("T_int", ctypes.c_double),
         ("F_toa", ctypes.c_double), ("wn_min", ctypes.c_double),
-        ("wn_max", ctypes.c_double),
+        ("wn_max", ctypes.c_double), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -66,12 +66,17 @@ class OracleConfig:
     F_toa: float = 0.0
     wn_min: float = 50.0
     wn_max: float = 1.0e4 / 0.3
+    wn_edges: object = None      # None: NB uniform bins; else NB + 1 increasing edges, cm^-1
 
     def c(self) -> _Cfg:
+        edges = None
+        if self.wn_edges is not None:
+            self._edges = np.ascontiguousarray(self.wn_edges, dtype=np.float64)
+            edges = self._edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         return _Cfg(int(self.improved), int(self.isothermal),
                     0 if self.resonance == "paper" else 1, int(self.e_clamp),
                     self.eps2, self.grav, self.cp, self.T_int, self.F_toa,
-                    self.wn_min, self.wn_max)
+                    self.wn_min, self.wn_max, edges)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -109,7 +114,7 @@ class Oracle:
         L.oracle_solve_columns.restype = ctypes.c_int
         L.oracle_solve_columns.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, _I, _I,
                                            ctypes.c_int, _D, _F, _F, _F, _D, _D, _D,
-                                           _D, _D, _D, _D, _D, _D, _D, _D,
+                                           _D, _D, _D, _D, _D, _D, _D, _D, _D,
                                            ctypes.POINTER(_Stats)]
 
     # -- Planck -------------------------------------------------------
@@ -165,7 +170,8 @@ class Oracle:
         """Solve a packed batch (an ``rt_synth.Columns``).  Returns a dict with
         F_up, F_down (diffuse + beam), F_net at interfaces, Q per layer and the
         branch-hit counters; with ``per_system`` also the per-system diffuse
-        interface fluxes ``sys_up``/``sys_dn``."""
+        interface fluxes ``sys_up``/``sys_dn``.  ``F_up_toa`` is the upward
+        flux at the TOA per bin (sum over g of w_g F_up), [sum NB]."""
         nl = np.ascontiguousarray(cols.n_layers, dtype=np.int32)
         nb = np.ascontiguousarray(cols.n_bins, dtype=np.int32)
         nc = nl.size
@@ -177,6 +183,9 @@ class Oracle:
         Tc, Ti, p = f64(cols.T_center), f64(cols.T_iface), f64(cols.p_iface)
         mu, Fs, gw = f64(cols.mu_star), f64(cols.F_star), f64(cols.g_weights)
         up = np.zeros(n_if); dn = np.zeros(n_if); net = np.zeros(n_if); Q = np.zeros(n_l)
+        toa = np.zeros(int(nb.sum()))
+        if cfg.wn_edges is not None and np.any(nb != len(cfg.wn_edges) - 1):
+            raise ValueError("explicit bin edges need NB = len(wn_edges) - 1 in every column")
         if per_system:
             n_sys_if = int(((nl + 1) * nb).sum()) * cols.n_g
             su = np.zeros(n_sys_if); sd = np.zeros(n_sys_if)
@@ -189,10 +198,10 @@ class Oracle:
             ctypes.byref(c), nc, _p(nl, _I), _p(nb, _I), int(cols.n_g), _p(gw, _D),
             _p(dtau, _F), _p(w0, _F), _p(g0, _F), _p(Tc, _D), _p(Ti, _D), _p(p, _D),
             _p(mu, _D), _p(Fs, _D), _p(up, _D), _p(dn, _D), _p(net, _D), _p(Q, _D),
-            psu, psd, ctypes.byref(st))
+            psu, psd, _p(toa, _D), ctypes.byref(st))
         if rc != 0:
             raise MemoryError("oracle_solve_columns failed")
-        out = dict(F_up=up, F_down=dn, F_net=net, Q=Q,
+        out = dict(F_up=up, F_down=dn, F_net=net, Q=Q, F_up_toa=toa,
                    stats=dict(resonance_hits=st.resonance_hits, etau_hits=st.etau_hits,
                               eclamp_hits=st.eclamp_hits, nonfinite=st.nonfinite))
         if per_system:

@@ -66,6 +66,8 @@ typedef struct {
     double T_int;           /* K, interior temperature; 0 -> F_BOA = 0 */
     double F_toa;           /* diffuse downward flux at the TOA, W m^-2 */
     double wn_min, wn_max;  /* bin range, cm^-1, bins uniform in wavenumber */
+    const double *wn_edges; /* NULL, or the NB + 1 increasing bin edges (cm^-1)
+                               shared by every column; then wn_min/wn_max unused */
 } oracle_cfg;
 
 typedef struct {
@@ -602,7 +604,7 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                          const double *p_iface, const double *mu_star,
                          const double *F_star, double *F_up, double *F_dn,
                          double *F_net, double *Q, double *sys_up,
-                         double *sys_dn, oracle_stats *stats_out)
+                         double *sys_dn, double *toa_up, oracle_stats *stats_out)
 {
     gl_init();
     int64_t *cube_off = malloc(sizeof(int64_t) * (n_cols + 1));
@@ -650,6 +652,13 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                 double dwn = (cfg->wn_max - cfg->wn_min) / NB;
                 for (int b = 0; b < NB; ++b) {
                     double lo = cfg->wn_min + b * dwn, hi = lo + dwn;
+                    if (cfg->wn_edges) {
+                        lo = cfg->wn_edges[b];
+                        hi = cfg->wn_edges[b + 1];
+                    }
+                    /* emergent spectrum: the g-weighted upward flux at the TOA
+                     * of this bin (the quantity post-processing samples) */
+                    double toa_b = 0.0;
                     for (int l = 0; l < L; ++l) Bc[l] = oracle_planck_bin(Tc[l], lo, hi);
                     for (int i = 0; i <= L; ++i) Bi[i] = oracle_planck_bin(Ti[i], lo, hi);
                     double F_BOA = OR_PI * oracle_planck_bin(cfg->T_int, lo, hi);  /* Eq. 10 */
@@ -689,6 +698,7 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                             /* interfaces: API interface i sits at level
                              * (L - i) (isothermal) or 2 (L - i). */
                             double wg = g_w[g];
+                            toa_b += wg * fu[cfg->isothermal ? L : 2 * L];
                             for (int i = 0; i <= L; ++i) {
                                 int lev = cfg->isothermal ? (L - i) : 2 * (L - i);
                                 sum_up[i] += wg * fu[lev];
@@ -706,6 +716,7 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                         free(A); free(Bm); free(C); free(D); free(Cp); free(Dp); free(X);
                         free_work(&w);
                     }
+                    if (toa_up) toa_up[bin_off[c] + b] = toa_b;
                 }
                 for (int i = 0; i <= L; ++i) {
                     up[i] = sum_up[i];

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,16 @@ struct rt_handle {
     int sm_count = 0;
     double *d_gw = nullptr;
     float *d_gw32 = nullptr;
+    std::vector<double> edges;
+    double *d_edges = nullptr;
+    float *d_edges32 = nullptr;   // [n_edges] edges, then [n_edges - 1] widths, FP32
+    // k-table front end
+    bool kt_set = false;
+    int kt_nT = 0, kt_nP = 0, kt_NB = 0;
+    float *d_klk = nullptr;
+    float4 *d_kbin = nullptr;
+    double *d_kT = nullptr, *d_klp = nullptr;
+    DevBuf kcube;                  // FP64 path: front-end optics cubes
     // plan
     DevBuf plan;                  // n_layers, n_bins, order (int32) + offsets (int64)
     std::vector<int32_t> plan_nl, plan_nb;
@@ -51,7 +62,7 @@ struct rt_handle {
     bool done_valid = false;       // done_ev marks the last solve (false when it was captured)
     cudaStream_t last_stream = nullptr;
     bool solved = false;
-    int64_t n_cols = 0, n_if = 0, n_lay = 0, n_sys = 0;
+    int64_t n_cols = 0, n_if = 0, n_lay = 0, n_sys = 0, n_bins = 0;
     std::string err;
 };
 
@@ -82,14 +93,15 @@ struct Plan {
     int64_t n_units = 0;
     int Lmax = 0, NBmax = 0;
     // launch
-    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0;
+    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0;
     size_t smem = 0;
     int64_t n_slots = 0;
     // workspace layout (bytes); the plan blob is int32 arrays then int64 arrays
-    size_t i32_count = 0, plan_bytes = 0, out_bytes = 0, scr_bytes = 0, aux_bytes = 0;
+    size_t i32_count = 0, plan_bytes = 0, out_bytes = 0, scr_bytes = 0, aux_bytes = 0, kcube_bytes = 0;
+    bool kt = false;              // optics from the k-table front end
 };
 
-int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
+int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
     const rt_config &cfg = h->cfg;
     const int n = c->n_cols;
     const bool fp64 = cfg.precision == RT_FP64_PLAIN;
@@ -102,7 +114,12 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
             return fail(h, RT_EINVAL, "column %d: n_layers %d outside [1, %d]", i, P.nl[i], cfg.max_layers);
         if (P.nb[i] < 1 || P.nb[i] > cfg.max_bins)
             return fail(h, RT_EINVAL, "column %d: n_bins %d outside [1, %d]", i, P.nb[i], cfg.max_bins);
+        if (cfg.n_edges > 1 && P.nb[i] != cfg.n_edges - 1)
+            return fail(h, RT_EINVAL, "column %d: n_bins %d but %d explicit bin edges", i, P.nb[i], cfg.n_edges);
+        if (kt && P.nb[i] != h->kt_NB)
+            return fail(h, RT_EINVAL, "column %d: n_bins %d but the k-table has %d", i, P.nb[i], h->kt_NB);
     }
+    P.kt = kt;
     const int64_t *gath[5] = {c->cube_offset, c->center_offset, c->iface_offset, c->bin_offset, c->col_index};
     for (int g = 0; g < 5; ++g)
         if (gath[g])
@@ -175,8 +192,13 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
                 if (occ > 0) P.grid = (int)std::min<int64_t>(n, (int64_t)occ * h->sm_count);
             } else {
                 P.nbw = rt::bins_per_chunk(32, cfg.n_g, P.NBmax);
-                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw);
-                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw);
+                // staging B per warp pays off when several lanes share a bin;
+                // with few g-points per bin it only costs shared memory
+                // (occupancy), so the lanes read the table directly
+                P.direct = cfg.planck_staging == RT_STAGE_DIRECT ||
+                           (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g < 4);
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct);
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct);
                 occ = rt::occupancy(0, P.block, P.smem);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
@@ -197,15 +219,19 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P) {
     }
     P.i32_count = 4 * (size_t)n + 2 * (size_t)P.n_units;
     P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
-    P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256);
+    P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256) +
+                  align_up(sizeof(double) * (size_t)P.n_bins, 256);
     P.scr_bytes = (size_t)P.n_slots *
                   (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
                         : rt::fp32_scratch_per_slot(P.Lmax));
-    // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf
+    // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf [| kt_lay]
     P.aux_bytes = fp64 ? 0
                        : align_up(sizeof(float) * (size_t)P.n_part, 256) + align_up(sizeof(int32_t) * (size_t)n, 256) +
                              align_up(sizeof(float) * (size_t)P.n_planck, 256) +
-                             2 * align_up(sizeof(float) * (size_t)P.n_bins, 256) + align_up(sizeof(float4) * (size_t)n, 256);
+                             2 * align_up(sizeof(float) * (size_t)P.n_bins, 256) + align_up(sizeof(float4) * (size_t)n, 256) +
+                             (kt ? align_up(sizeof(float4) * (size_t)P.n_lay, 256) : 0);
+    // FP64 path with the front end: the optics cubes
+    P.kcube_bytes = (kt && fp64) ? 3 * align_up(sizeof(float) * (size_t)P.n_cube, 256) : 0;
     return RT_OK;
 }
 
@@ -236,17 +262,25 @@ int grow(rt_handle *h, DevBuf &b, size_t need, bool capturing, const char *what)
     return RT_OK;
 }
 
-int check_columns(rt_handle *h, const rt_columns *c) {
+int check_columns(rt_handle *h, const rt_columns *c, bool kt = false) {
     if (!c) return fail(h, RT_EINVAL, "columns descriptor is NULL");
+    if (kt && !h->kt_set) return fail(h, RT_ENOTSOLVED, "no k-table set (rt_set_ktable)");
     if (c->n_cols < 0) return fail(h, RT_EINVAL, "n_cols %d < 0", c->n_cols);
     if (c->n_cols == 0) return RT_OK;
     if (!c->n_layers && c->L < 1) return fail(h, RT_EINVAL, "uniform L %d < 1", c->L);
     if (!c->n_bins && c->NB < 1) return fail(h, RT_EINVAL, "uniform NB %d < 1", c->NB);
     const void *ptrs[] = {c->dtau, c->w0, c->g0, c->T_center, c->T_iface, c->p_iface, c->mu_star, c->F_star};
     const char *names[] = {"dtau", "w0", "g0", "T_center", "T_iface", "p_iface", "mu_star", "F_star"};
-    for (int i = 0; i < 8; ++i)
+    for (int i = kt ? 3 : 0; i < 8; ++i)
         if (!ptrs[i]) return fail(h, RT_EINVAL, "%s is NULL", names[i]);
+    if (kt && (c->dtau || c->w0 || c->g0 || c->cube_offset))
+        return fail(h, RT_EINVAL, "the k-table front end takes no dtau, w0, g0 or cube_offset");
     return RT_OK;
+}
+
+// Optics descriptor for a k-table solve: NULL cubes select the front end.
+bool wants_kt(const rt_handle *h, const rt_columns *c) {
+    return c && h->kt_set && !c->dtau && !c->w0 && !c->g0;
 }
 
 }  // namespace
@@ -269,6 +303,12 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
         (cfg->block_threads % 32 || cfg->block_threads < 64 || cfg->block_threads > rt::kMaxBlock))
         return RT_EINVAL;
     if (cfg->ctas_per_sm < 0) return RT_EINVAL;
+    if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_DIRECT) return RT_EINVAL;
+    if (cfg->n_edges < 0 || cfg->n_edges == 1 || (cfg->n_edges > 1 && !cfg->wn_edges)) return RT_EINVAL;
+    for (int i = 0; i < cfg->n_edges; ++i) {
+        if (!(cfg->wn_edges[i] >= 0.0)) return RT_EINVAL;
+        if (i > 0 && !(cfg->wn_edges[i] > cfg->wn_edges[i - 1])) return RT_EINVAL;
+    }
     for (int i = 0; i < cfg->n_g; ++i)
         if (!(cfg->g_weights[i] >= 0.0)) return RT_EINVAL;
 
@@ -277,6 +317,8 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     if (h->cfg.block_threads == 0) h->cfg.block_threads = 256;
     h->gw.assign(cfg->g_weights, cfg->g_weights + cfg->n_g);
     h->cfg.g_weights = h->gw.data();
+    if (cfg->n_edges > 1) h->edges.assign(cfg->wn_edges, cfg->wn_edges + cfg->n_edges);
+    h->cfg.wn_edges = h->edges.empty() ? nullptr : h->edges.data();
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = rt::init_kernels();
@@ -285,6 +327,19 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     std::vector<float> gw32(h->gw.begin(), h->gw.end());
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_gw32, sizeof(float) * cfg->n_g);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_gw32, gw32.data(), sizeof(float) * cfg->n_g, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h->edges.empty()) {
+        const size_t ne = h->edges.size();
+        e = cudaMalloc((void **)&h->d_edges, sizeof(double) * ne);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_edges, h->edges.data(), sizeof(double) * ne, cudaMemcpyHostToDevice);
+        // FP32 copies for the FP32 form (the width is formed before rounding)
+        std::vector<float> e32(2 * ne - 1);
+        for (size_t i = 0; i < ne; ++i) e32[i] = (float)h->edges[i];
+        for (size_t i = 0; i + 1 < ne; ++i) e32[ne + i] = (float)(h->edges[i + 1] - h->edges[i]);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_edges32, sizeof(float) * e32.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_edges32, e32.data(), sizeof(float) * e32.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_counter, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_stats, sizeof(unsigned long long) * rt::ST_COUNT);
     if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT);
@@ -302,25 +357,33 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
 int rt_query_bytes(const rt_handle *hc, const rt_columns *cols, size_t *bytes) {
     rt_handle *h = const_cast<rt_handle *>(hc);
     if (!h || !bytes) return RT_EINVAL;
-    int rc = check_columns(h, cols);
+    const bool kt = wants_kt(h, cols);
+    int rc = check_columns(h, cols, kt);
     if (rc) return rc;
     Plan P;
-    rc = build_plan(h, cols, P);
+    rc = build_plan(h, cols, P, kt);
     if (rc) return rc;
-    *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes;
+    *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes + P.kcube_bytes;
     return RT_OK;
 }
 
-int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// The whole path for one batch.  kt: optics from the front end.  With
+// optics_out set (three device cubes) only the front end runs and writes
+// them; the handle's outputs are left alone.
+int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, float *const *optics_out) {
     if (!h) return RT_EINVAL;
     h->err.clear();
-    int rc = check_columns(h, cols);
+    int rc = check_columns(h, cols, kt);
     if (rc) return rc;
     Plan P;
-    rc = build_plan(h, cols, P);
+    rc = build_plan(h, cols, P, kt);
     if (rc) return rc;
     const rt_config &cfg = h->cfg;
-    const size_t ws_bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes;
+    const size_t ws_bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes + P.kcube_bytes;
     if (cfg.hbm_budget_bytes && ws_bytes > cfg.hbm_budget_bytes)
         return fail(h, RT_EBUDGET, "workspace %zu bytes exceeds budget %zu", ws_bytes, cfg.hbm_budget_bytes);
     cudaStream_t s = (cudaStream_t)stream;
@@ -337,6 +400,7 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     if ((rc = grow(h, h->out, std::max<size_t>(P.out_bytes, 256), cap, "output"))) return rc;
     if ((rc = grow(h, h->scr, std::max<size_t>(P.scr_bytes, 256), cap, "scratch"))) return rc;
     if ((rc = grow(h, h->aux, std::max<size_t>(P.aux_bytes, 256), cap, "partial-sum"))) return rc;
+    if (P.kcube_bytes && (rc = grow(h, h->kcube, P.kcube_bytes, cap, "optics"))) return rc;
 
     char *pb = (char *)h->plan.p;
     int32_t *d_nl = (int32_t *)pb;
@@ -418,12 +482,17 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     double *F_dn = F_up + P.n_if;
     double *F_net = F_dn + P.n_if;
     double *Q = (double *)(ob + align_up(sizeof(double) * 3 * (size_t)P.n_if, 256));
+    double *toa = (double *)((char *)Q + align_up(sizeof(double) * (size_t)P.n_lay, 256));
 
-    cudaError_t e = cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT, s);
+    cudaError_t e = cudaSuccess;
+    if (!optics_out) {
+        e = cudaMemsetAsync(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT, s);
+        if (e == cudaSuccess && P.n_bins) e = cudaMemsetAsync(toa, 0, sizeof(double) * (size_t)P.n_bins, s);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counter, 0, sizeof(int32_t), s);
     int32_t *d_done = nullptr;
     float *d_part = nullptr, *d_planck = nullptr, *d_fs = nullptr, *d_fboa = nullptr;
-    float4 *d_colf = nullptr;
+    float4 *d_colf = nullptr, *d_klay = nullptr;
     if (P.aux_bytes) {
         char *a = (char *)h->aux.p;
         d_part = (float *)a;
@@ -437,7 +506,9 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         d_fboa = (float *)a;
         a += align_up(sizeof(float) * (size_t)P.n_bins, 256);
         d_colf = (float4 *)a;
-        if (e == cudaSuccess) e = cudaMemsetAsync(d_done, 0, sizeof(int32_t) * (size_t)n, s);
+        a += align_up(sizeof(float4) * (size_t)n, 256);
+        if (P.kt) d_klay = (float4 *)a;
+        if (e == cudaSuccess && !optics_out) e = cudaMemsetAsync(d_done, 0, sizeof(int32_t) * (size_t)n, s);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
 
@@ -485,6 +556,10 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         kp.F_toa = cfg.F_toa_diffuse;
         kp.wn_min = cfg.wn_min;
         kp.wn_max = cfg.wn_max;
+        kp.edges = h->d_edges;
+        kp.edges32 = h->d_edges32;
+        kp.dnu32 = h->d_edges32 ? h->d_edges32 + h->edges.size() : nullptr;
+        kp.toa = toa;
         kp.Lmax = P.Lmax;
         kp.nb_chunk = P.nb_chunk;
         kp.unit_col = d_ucol;
@@ -496,16 +571,44 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
         kp.n_units = (int32_t)P.n_units;
         kp.warp_floats = P.warp_floats;
         kp.nbw = P.nbw;
+        kp.direct = P.direct;
         kp.planck32 = d_planck;
         kp.planck_off = d_pkoff;
         kp.fs32 = d_fs;
         kp.fboa32 = d_fboa;
         kp.colf = d_colf;
         kp.g_w32 = h->d_gw32;
+        if (P.kt) {
+            kp.kt_lk = h->d_klk;
+            kp.kt_bin = h->d_kbin;
+            kp.kt_T = h->d_kT;
+            kp.kt_lp = h->d_klp;
+            kp.kt_nT = h->kt_nT;
+            kp.kt_nP = h->kt_nP;
+            kp.kt_lay = d_klay;
+        }
+        if (optics_out) {
+            e = rt::launch_kt_optics(kp, d_cube, optics_out[0], optics_out[1], optics_out[2], s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "front-end launch");
+            return RT_OK;
+        }
+        if (P.kt && cfg.precision == RT_FP64_PLAIN) {
+            // the FP64 path solves from cubes: write the front end's optics first
+            char *kc = (char *)h->kcube.p;
+            const size_t cb = align_up(sizeof(float) * (size_t)P.n_cube, 256);
+            float *cd = (float *)kc, *cw = (float *)(kc + cb), *cg = (float *)(kc + 2 * cb);
+            e = rt::launch_kt_optics(kp, d_cube, cd, cw, cg, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "front-end launch");
+            kp.dtau = cd;
+            kp.w0 = cw;
+            kp.g0 = cg;
+            kp.kt_lk = nullptr;
+        }
         e = cfg.precision == RT_FP64_PLAIN ? rt::launch_fp64(kp, P.grid, P.block, P.smem, s)
                                            : rt::launch_fp32(kp, P.grid, P.block, P.smem, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     }
+    if (optics_out) return RT_OK;
     // A solve captured into a graph completes when the graph is replayed; the
     // caller orders later reads after the replay (same stream or a sync).
     if (!cap) {
@@ -519,6 +622,156 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
     h->n_if = P.n_if;
     h->n_lay = P.n_lay;
     h->n_sys = P.n_sys;
+    h->n_bins = P.n_bins;
+    return RT_OK;
+}
+
+// ---- k-table set-up on the host -------------------------------------------------
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n).
+void gauss_nodes(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(pi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Rayleigh cross section per molecule, m^2 (App. C): 24 pi^3 / (N^2 lambda^4)
+// ((n^2 - 1) / (n^2 + 2))^2 with King factor 1; the index is passed as n - 1.
+double rayleigh(double lam_m, double n_minus_1, double n_ref) {
+    const double pi = 3.14159265358979323846;
+    const double d = n_minus_1 * (2.0 + n_minus_1);           // n^2 - 1
+    const double f = d / (3.0 + d);                           // (n^2 - 1) / (n^2 + 2)
+    const double l2 = lam_m * lam_m;
+    return 24.0 * pi * pi * pi / (n_ref * n_ref * l2 * l2) * f * f;
+}
+
+// H2 + He mixture at wavenumber nu (cm^-1), App. C indices and reference densities.
+double sigma_h2_he(double nu, double x_h2, double x_he) {
+    const double lam_um = 1.0e4 / nu, lam_m = 1.0e-2 / nu;
+    const double il2 = 1.0 / (lam_um * lam_um);
+    const double n_h2 = 1.358e-4 * (1.0 + 7.52e-3 * il2);
+    const double n_he = 1.0e-8 * (2283.0 + 1.8102e13 / (1.5342e10 - il2));
+    return x_h2 * rayleigh(lam_m, n_h2, 2.68678e25) + x_he * rayleigh(lam_m, n_he, 2.546899e25);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream) {
+    return solve_impl(h, cols, stream, false, nullptr);
+}
+
+int rt_solve_ktable(rt_handle *h, const rt_columns *cols, void *stream) {
+    if (!h) return RT_EINVAL;
+    return solve_impl(h, cols, stream, true, nullptr);
+}
+
+int rt_ktable_optics(rt_handle *h, const rt_columns *cols, float *dtau, float *w0, float *g0, void *stream) {
+    if (!h) return RT_EINVAL;
+    if (!dtau || !w0 || !g0) return fail(h, RT_EINVAL, "optics outputs are NULL");
+    float *const outs[3] = {dtau, w0, g0};
+    return solve_impl(h, cols, stream, true, outs);
+}
+
+int rt_set_ktable(rt_handle *h, const rt_ktable *kt) {
+    if (!h) return RT_EINVAL;
+    h->err.clear();
+    if (!kt) return fail(h, RT_EINVAL, "k-table is NULL");
+    const rt_config &cfg = h->cfg;
+    if (kt->n_T < 2 || kt->n_P < 2) return fail(h, RT_EINVAL, "k-table grid needs >= 2 points per axis");
+    if (!kt->T_grid || !kt->log10p_grid || !kt->log10_kappa || !kt->sigma_scat_cloud || !kt->sigma_abs_cloud ||
+        !kt->g0_cloud)
+        return fail(h, RT_EINVAL, "k-table array is NULL");
+    if (kt->n_bins < 1 || kt->n_bins > cfg.max_bins) return fail(h, RT_EINVAL, "k-table n_bins %d", kt->n_bins);
+    if (kt->n_g != cfg.n_g) return fail(h, RT_EINVAL, "k-table n_g %d but the handle has %d", kt->n_g, cfg.n_g);
+    if (cfg.n_edges > 1 && kt->n_bins != cfg.n_edges - 1)
+        return fail(h, RT_EINVAL, "k-table n_bins %d but %d bin edges", kt->n_bins, cfg.n_edges);
+    for (int i = 1; i < kt->n_T; ++i)
+        if (!(kt->T_grid[i] > kt->T_grid[i - 1])) return fail(h, RT_EINVAL, "T grid not increasing");
+    for (int i = 1; i < kt->n_P; ++i)
+        if (!(kt->log10p_grid[i] > kt->log10p_grid[i - 1])) return fail(h, RT_EINVAL, "log10 p grid not increasing");
+    if (!std::isfinite(kt->T_grid[0]) || !std::isfinite(kt->T_grid[kt->n_T - 1]) ||
+        !std::isfinite(kt->log10p_grid[0]) || !std::isfinite(kt->log10p_grid[kt->n_P - 1]))
+        return fail(h, RT_EINVAL, "k-table grid not finite");
+    if (!(kt->f_cloud >= 0.0) || !(kt->x_H2 >= 0.0) || !(kt->x_He >= 0.0) || !(kt->mbar_amu > 0.0))
+        return fail(h, RT_EINVAL, "f_cloud, x_H2, x_He must be >= 0 and mbar > 0");
+    const int64_t S = (int64_t)kt->n_bins * cfg.n_g;
+    const int64_t n_tab = (int64_t)kt->n_T * kt->n_P * S;
+    if (n_tab >= INT32_MAX) return fail(h, RT_EINVAL, "k-table too large (%lld entries)", (long long)n_tab);
+    for (int b = 0; b < kt->n_bins; ++b)
+        if (!(kt->sigma_scat_cloud[b] >= 0.0) || !(kt->sigma_abs_cloud[b] >= 0.0) || !(fabs(kt->g0_cloud[b]) < 1.0))
+            return fail(h, RT_EINVAL, "bin %d: cloud data out of range", b);
+
+    // per-bin scattering and cloud absorption per unit mass, and g0
+    std::vector<double> gx, gwt;
+    gauss_nodes(8, gx, gwt);
+    const double mbar = kt->mbar_amu * 1.66053906660e-27;
+    std::vector<float4> bin(kt->n_bins);
+    for (int b = 0; b < kt->n_bins; ++b) {
+        const double lo = cfg.wn_edges ? cfg.wn_edges[b] : cfg.wn_min + b * (cfg.wn_max - cfg.wn_min) / kt->n_bins;
+        const double hi = cfg.wn_edges ? cfg.wn_edges[b + 1]
+                                       : cfg.wn_min + (b + 1) * (cfg.wn_max - cfg.wn_min) / kt->n_bins;
+        // bin mean of the gas cross section: 8 sub-intervals x 8-point Gauss-Legendre
+        const int nsub = 8;
+        const double h_sub = (hi - lo) / nsub;
+        double acc = 0.0;
+        for (int k = 0; k < nsub; ++k) {
+            const double mid = lo + (k + 0.5) * h_sub;
+            for (int j = 0; j < 8; ++j) {
+                const double nu = mid + 0.5 * h_sub * gx[j];
+                if (nu > 0.0) acc += 0.5 * h_sub * gwt[j] * sigma_h2_he(nu, kt->x_H2, kt->x_He);
+            }
+        }
+        const double sg = acc / (hi - lo);
+        const double scat = sg + kt->f_cloud * kt->sigma_scat_cloud[b];
+        const double g0 = scat > 0.0 ? kt->f_cloud * kt->sigma_scat_cloud[b] / scat * kt->g0_cloud[b] : 0.0;
+        bin[b] = make_float4((float)(scat / mbar), (float)(kt->f_cloud * kt->sigma_abs_cloud[b] / mbar), (float)g0, 0.f);
+    }
+
+    cudaError_t e = cudaDeviceSynchronize();      // earlier solves may still read the old table
+    cudaFree(h->d_klk);
+    cudaFree(h->d_kbin);
+    cudaFree(h->d_kT);
+    cudaFree(h->d_klp);
+    h->d_klk = nullptr;
+    h->d_kbin = nullptr;
+    h->d_kT = h->d_klp = nullptr;
+    h->kt_set = false;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_klk, sizeof(float) * (size_t)n_tab);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_klk, kt->log10_kappa, sizeof(float) * (size_t)n_tab, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_kbin, sizeof(float4) * bin.size());
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_kbin, bin.data(), sizeof(float4) * bin.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_kT, sizeof(double) * kt->n_T);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_kT, kt->T_grid, sizeof(double) * kt->n_T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_klp, sizeof(double) * kt->n_P);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_klp, kt->log10p_grid, sizeof(double) * kt->n_P, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(h, e, "k-table upload");
+    }
+    h->kt_nT = kt->n_T;
+    h->kt_nP = kt->n_P;
+    h->kt_NB = kt->n_bins;
+    h->kt_set = true;
     return RT_OK;
 }
 
@@ -558,6 +811,20 @@ int rt_heating(rt_handle *h, double *Q, void *stream) {
     return copy_out(h, Q, q, sizeof(double) * (size_t)h->n_lay, s);
 }
 
+int rt_toa_spectrum(rt_handle *h, double *F_up_toa, void *stream) {
+    if (!h) return RT_EINVAL;
+    if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_toa_spectrum before rt_solve_columns");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->done_valid && s != h->last_stream && !stream_capturing(s)) {
+        cudaError_t e = cudaStreamWaitEvent(s, h->done_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
+    }
+    const char *ob = (const char *)h->out.p;
+    const char *q = ob + align_up(sizeof(double) * 3 * (size_t)h->n_if, 256);
+    const double *toa = (const double *)(q + align_up(sizeof(double) * (size_t)h->n_lay, 256));
+    return copy_out(h, F_up_toa, toa, sizeof(double) * (size_t)h->n_bins, s);
+}
+
 int rt_stats(rt_handle *h, rt_stats_t *out) {
     if (!h || !out) return RT_EINVAL;
     if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_stats before rt_solve_columns");
@@ -582,6 +849,13 @@ void rt_destroy(rt_handle *h) {
     cudaDeviceSynchronize();
     cudaFree(h->d_gw);
     cudaFree(h->d_gw32);
+    cudaFree(h->d_edges);
+    cudaFree(h->d_edges32);
+    cudaFree(h->d_klk);
+    cudaFree(h->d_kbin);
+    cudaFree(h->d_kT);
+    cudaFree(h->d_klp);
+    cudaFree(h->kcube.p);
     cudaFree(h->plan.p);
     cudaFree(h->out.p);
     cudaFree(h->scr.p);

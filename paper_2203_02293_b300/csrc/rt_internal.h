@@ -57,20 +57,31 @@ struct KParams {
     float4 *colf;                // [n_cols] (mu, 1/mu, beam?, 0)
     const float *g_w32;          // [n_g] Gauss weights in FP32
     int32_t nbw;                 // bins one warp's 32 systems can touch
+    int32_t direct;              // 1: read B from planck32 directly (no staging)
     // scheduling and counters
     int32_t *counter;
     unsigned long long *stats;
     // method switches and constants
     int32_t improved, isothermal, resonance_paper, e_clamp;
     double eps2, grav, cp, T_int, F_toa, wn_min, wn_max;
+    const double *edges;         // [NB+1] explicit bin edges (cm^-1) or nullptr (uniform)
+    const float *edges32;        // the same edges rounded to FP32 (FP32 form)
+    const float *dnu32;          // [NB] bin widths formed in FP64, rounded to FP32
+    double *toa;                 // [sum NB] TOA upward flux per bin (zeroed before the solve)
+    // k-table front end (set when the optics come from the table)
+    const float *kt_lk;          // [nT][nP][NB * n_g] log10 kappa
+    const float4 *kt_bin;        // [NB] (scattering, cloud absorption per unit mass, g0, 0)
+    const double *kt_T, *kt_lp;  // grids [nT] K, [nP] log10(p / Pa)
+    int32_t kt_nT, kt_nP;
+    float4 *kt_lay;              // [sum L] per layer: (corner offset bits, wT, wP, dp / g)
     float inv_eps2;
     int32_t Lmax;                // largest L in this batch
     int32_t nb_chunk;            // bins covered by one chunk of systems (smem sizing)
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nbw);
-int fp32_warp_floats(int Lmax, int nbw);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct);
+int fp32_warp_floats(int Lmax, int nbw, int direct);
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);
@@ -85,6 +96,10 @@ int occupancy(int precision_fp64, int block, size_t smem);
 // Launch the fused column kernels.  Return cudaGetLastError().
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
+// Front end alone: FP32 optics of every (column, layer, bin, g) into packed
+// cubes (cube offsets of the packed layout in pcube_off).
+cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float *dtau, float *w0,
+                             float *g0, cudaStream_t s);
 
 // Largest L the kernels support.
 constexpr int kMaxLayers = 1024;

@@ -427,6 +427,7 @@ __device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float B
 //   sB    R      [(2 Lmax + 1) nb_chunk]        Planck at levels (2i iface, 2i+1 centre)
 //   sFs   R      [nb_chunk]                     stellar flux per bin
 //   sFB   R      [nb_chunk]                     F_BOA per bin
+//   stoa  R      [block]                        weighted TOA F_up per system
 // ---------------------------------------------------------------------
 template <typename R>
 __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk) {
@@ -435,16 +436,18 @@ __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk
     b += sizeof(R) * 2 * (size_t)(Lmax + 1) * nw;
     b += sizeof(R) * (size_t)(2 * Lmax + 1) * nb_chunk;
     b += sizeof(R) * 2 * (size_t)nb_chunk;
+    b += sizeof(R) * (size_t)block;
     return b;
 }
 
-int fp32_warp_floats(int Lmax, int nbw) {
-    // Planck [(2 Lmax + 1) nbw] + F* [nbw] + F_BOA [nbw] + transpose [16][2][33]
-    int n = (2 * Lmax + 1) * nbw + 2 * nbw + 16 * 2 * 33;
+int fp32_warp_floats(int Lmax, int nbw, int direct) {
+    // Planck [(2 Lmax + 1) nbw] (staged mode only) + F* [nbw] + F_BOA [nbw]
+    // + transpose [16][2][33]
+    int n = (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw + 16 * 2 * 33;
     return (n + 3) & ~3;
 }
-size_t fp32_smem_bytes(int block, int Lmax, int nbw) {
-    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct) {
+    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct);
 }
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
@@ -460,13 +463,14 @@ int bins_per_chunk(int block, int n_g, int max_bins) {
 template <typename R>
 struct Smem {
     double *acc;
-    R *wpart, *sB, *sFs, *sFB;
+    R *wpart, *sB, *sFs, *sFB, *stoa;
     __device__ Smem(unsigned char *raw, int Lmax, int nb_chunk, int nwarps) {
         acc = reinterpret_cast<double *>(raw);
         wpart = reinterpret_cast<R *>(acc + 2 * (Lmax + 1));
         sB = wpart + 2 * (Lmax + 1) * nwarps;
         sFs = sB + (2 * Lmax + 1) * nb_chunk;
         sFB = sFs + nb_chunk;
+        stoa = sFB + nb_chunk;
     }
 };
 
@@ -504,10 +508,11 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
                                              Smem<R> &sm) {
     const int nlev = 2 * ci.L + 1;
     const double dwn = (kp.wn_max - kp.wn_min) / ci.NB;
+    auto edge = [&](int e) { return kp.edges ? kp.edges[e] : kp.wn_min + e * dwn; };
     for (int i = threadIdx.x; i < nlev * nbc; i += blockDim.x) {
         const int lev = i / nbc, bb = i - lev * nbc, b = b_lo + bb;
         const double T = (lev & 1) ? kp.T_center[ci.tc_in + (lev >> 1)] : kp.T_iface[ci.if_in + (lev >> 1)];
-        const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
+        const double wlo = edge(b), whi = edge(b + 1);
         if constexpr (sizeof(R) == 4)
             sm.sB[i] = planck_bin_f((float)T, (float)wlo, (float)whi);
         else
@@ -515,7 +520,7 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
     }
     for (int bb = threadIdx.x; bb < nbc; bb += blockDim.x) {
         const int b = b_lo + bb;
-        const double wlo = kp.wn_min + b * dwn, whi = kp.wn_min + (b + 1) * dwn;
+        const double wlo = edge(b), whi = edge(b + 1);
         sm.sFs[bb] = (R)kp.F_star[ci.fs_in + b];
         if constexpr (sizeof(R) == 4)
             sm.sFB[bb] = kPiF * planck_bin_f((float)kp.T_int, (float)wlo, (float)whi);
@@ -588,26 +593,147 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 // One (column, level) per warp: lane e evaluates the Planck integral at bin
 // edge e (whichever of S(x) or P(x) that edge needs), and bin b takes edges b
 // and b+1 from its lane and the next (shuffle).  31 bins per pass.
-__device__ __forceinline__ void planck_level_warp(float T, int NB, float dwn, float wmin, float scale,
+// x^3 / (e^x - 1), the Planck integrand in x = h c nu / (k T).  Below x = 1/2
+// e^x - 1 is formed from its Taylor series (expm1(x) / x to x^6 / 7!,
+// truncation < 2e-7 relative) so that small x keeps its digits.
+__device__ __forceinline__ float planck_integrand_f(float x) {
+    if (x < 0.5f) {
+        const float q = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 5040.f, 1.f / 720.f),
+                                                          1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
+        return x * x * frcp(q);
+    }
+    return x * x * x * frcp(__expf(x) - 1.f);
+}
+
+// Bins narrower than this in x = h c nu / (k T) are integrated by quadrature.
+constexpr float kNarrowBin = 0.5f;
+// Narrow bins below this width, and below 2% of their centre x, take
+// 2-point Gauss-Legendre (nodes -+1/sqrt(3), weights 1); wider ones 4 points.
+constexpr float kTwoPointBin = 0.1f;
+constexpr float kGL2x = 0.57735026918962576f;
+// 4-point Gauss-Legendre on [-1, 1]: outer and inner nodes with their weights.
+__constant__ float kGL4x[2] = {0.86113631159405258f, 0.33998104358485626f};
+__constant__ float kGL4w[2] = {0.34785484513745386f, 0.65214515486254614f};
+
+__device__ __forceinline__ void planck_level_warp(float T, int NB, float dwn, float wmin,
+                                                  const float *edges, const float *dnu, float scale,
                                                   float *dst, int lane) {
     const float a = (T > 0.f) ? (float)(kC2 * 100.0) * frcp(T) : 0.f;
     const float T2 = T * T;
     const float pref = (float)kPlanckK * (T2 * T2) * scale;
     for (int b0 = 0; b0 < NB; b0 += 31) {
         const int e = b0 + lane;
-        const float x = a * fmaf((float)e, dwn, wmin);
-        const float v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
+        const float wn = edges ? __ldg(edges + min(e, NB)) : fmaf((float)e, dwn, wmin);
+        const float x = a * wn;
         const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
-        const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
         const int bin = e;
+        const bool narrow = !(lane < 31 && bin < NB) || (x1 - x < kNarrowBin);
+        // the edge series are needed only when some bin of this pass is wide
+        float v = 0.f;
+        if (!__all_sync(0xffffffffu, narrow)) v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
+        const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
         if (lane < 31 && bin < NB) {
             float d;
-            if (x >= 2.f) d = v - v1;
-            else if (x1 <= 2.f) d = v1 - v;
-            else d = ((float)kPi4Over15 - v) - v1;
+            if (narrow) {
+                // narrow bin (e.g. R = 500): the edge difference would lose
+                // the digits that the edges' own FP32 rounding carries, so
+                // integrate x^3/(e^x - 1) over the bin by Gauss-Legendre (2
+                // or 4 points), the width formed from the FP64 edges before
+                // rounding (no FP64 arithmetic here: it is slow on this part)
+                const float dnu_b = edges ? __ldg(dnu + bin) : dwn;
+                const float hh = 0.5f * a * dnu_b;        // half width in x
+                const float xm = x + hh;
+                float acc;
+                if (hh < 0.5f * kTwoPointBin && hh < 0.01f * xm) {
+                    // 2 points: below 2e-8 relative for these widths
+                    acc = planck_integrand_f(fmaf(-hh, kGL2x, xm)) + planck_integrand_f(fmaf(hh, kGL2x, xm));
+                } else {
+                    acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float t = (k < 2) ? -kGL4x[k] : kGL4x[3 - k];
+                        const float xk = fmaf(hh, t, xm);
+                        acc = fmaf(kGL4w[k < 2 ? k : 3 - k], planck_integrand_f(xk), acc);
+                    }
+                }
+                d = hh * acc;
+            } else if (x >= 2.f) {
+                d = v - v1;
+            } else if (x1 <= 2.f) {
+                d = v1 - v;
+            } else {
+                d = ((float)kPi4Over15 - v) - v1;
+            }
             dst[bin] = (T > 0.f) ? pref * d : 0.f;
         }
     }
+}
+
+// ---------------------------------------------------------------------
+// Input front end (Sec. 2.1.3): optics from the column state and a premixed
+// k-table.  Per layer (kt_layer): the bracketing grid cell of (T_center,
+// log10 sqrt(p_top p_bot)), clamped, its bilinear weights and the column
+// mass dp / g.  Per system (kt_mix): log10 kappa interpolated bilinearly,
+// kappa = 10^x, extinction per unit mass E = kappa + s_b + a_b (s_b, a_b:
+// the bin's scattering and cloud absorption per unit mass), dtau = E dp / g,
+// w0 = s_b / E and the bin's g0.  Every operation is an explicitly rounded
+// intrinsic, so that the fused solve and the standalone optics kernel
+// produce the same bits.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void kt_bracket(const double *grid, int n, double v, int &i, float &w) {
+    v = fmin(fmax(v, grid[0]), grid[n - 1]);
+    int lo = 0, hi = n - 1;                       // grid[lo] <= v <= grid[hi]
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (grid[m] <= v) lo = m;
+        else hi = m;
+    }
+    i = lo;
+    w = (float)__ddiv_rn(__dsub_rn(v, grid[lo]), __dsub_rn(grid[lo + 1], grid[lo]));
+}
+
+__device__ __forceinline__ float4 kt_layer(const KParams &kp, double T, double p_top, double p_bot, int S) {
+    int iT, iP;
+    float wT, wP;
+    kt_bracket(kp.kt_T, kp.kt_nT, T, iT, wT);
+    kt_bracket(kp.kt_lp, kp.kt_nP, log10(sqrt(__dmul_rn(p_top, p_bot))), iP, wP);
+    const int off = (iT * kp.kt_nP + iP) * S;
+    return make_float4(__int_as_float(off), wT, wP, (float)__ddiv_rn(__dsub_rn(p_bot, p_top), kp.grav));
+}
+
+struct Optics {
+    float dt, w0, g0;
+};
+
+constexpr float kLog2Of10 = 3.32192809488736234787f;
+
+__device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float k11, float4 l4, float4 bq) {
+    const float a0 = __fmaf_rn(l4.z, __fsub_rn(k01, k00), k00);     // along log p at T_i
+    const float a1 = __fmaf_rn(l4.z, __fsub_rn(k11, k10), k10);     // along log p at T_i+1
+    const float x = __fmaf_rn(l4.y, __fsub_rn(a1, a0), a0);         // log10 kappa
+    const float kappa = exp2f(__fmul_rn(x, kLog2Of10));
+    const float ext = __fadd_rn(__fadd_rn(kappa, bq.x), bq.y);
+    Optics o;
+    o.dt = __fmul_rn(ext, l4.w);
+    o.w0 = ext > 0.f ? __fdiv_rn(bq.x, ext) : 0.f;
+    o.g0 = bq.z;
+    return o;
+}
+
+// The four table corners of system s for a layer whose cell starts at l4.x.
+struct Corners {
+    float k00, k01, k10, k11;
+};
+
+__device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int S, int s) {
+    const float *t = kp.kt_lk + __float_as_int(l4.x) + s;
+    const int sP = S, sT = kp.kt_nP * S;
+    Corners c;
+    c.k00 = __ldg(t);
+    c.k01 = __ldg(t + sP);
+    c.k10 = __ldg(t + sT);
+    c.k11 = __ldg(t + sT + sP);
+    return c;
 }
 
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
@@ -623,13 +749,19 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         __syncthreads();                          // previous column done with sT
         for (int lev = threadIdx.x; lev < nlev; lev += blockDim.x)
             sT[lev] = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
+        if (kp.kt_lk)
+            for (int l = threadIdx.x; l < L; l += blockDim.x)
+                kp.kt_lay[kp.lay_off[c] + l] =
+                    kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], NB * kp.n_g);
         __syncthreads();
         // levels 0..2L, then one extra task for the per-bin and per-column data
         for (int lev = warp; lev <= nlev; lev += nw) {
             if (lev < nlev) {
-                planck_level_warp(sT[lev], NB, dwn, wmin, 1.f, B + (long long)lev * NB, lane);
+                planck_level_warp(sT[lev], NB, dwn, wmin, kp.edges32, kp.dnu32, 1.f, B + (long long)lev * NB,
+                                  lane);
             } else {
-                planck_level_warp((float)kp.T_int, NB, dwn, wmin, kPiF, kp.fboa32 + b0, lane);
+                planck_level_warp((float)kp.T_int, NB, dwn, wmin, kp.edges32, kp.dnu32, kPiF, kp.fboa32 + b0,
+                                  lane);
                 for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
                 if (lane == 0) {
                     const double mu = kp.mu_star[kp.mu_idx[c]];
@@ -667,7 +799,16 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     }
 }
 
-template <bool ISO>
+// Planck values of a lane's bin: staged in the warp's shared memory (level
+// stride nbc) or, when few g-points share a bin (DIRECT), read straight from
+// the pre-kernel's table (level stride NB) through the read-only path.
+template <bool DIRECT>
+__device__ __forceinline__ float ldB(const float *p) {
+    if constexpr (DIRECT) return __ldg(p);
+    else return *p;
+}
+
+template <bool ISO, bool DIRECT, bool KT>
 __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
     extern __shared__ __align__(16) float smem32[];
     const int lane = threadIdx.x & 31;
@@ -675,8 +816,8 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
     float *wsm = smem32 + (size_t)warp * kp.warp_floats;
     const int NG = kp.n_g;
     const int nbw = kp.nbw;
-    float *sB = wsm;                               // [(2 L + 1) nbc]
-    float *sFs = wsm + (2 * kp.Lmax + 1) * nbw;    // [nbc]
+    float *sB = wsm;                               // [(2 L + 1) nbc], staged mode
+    float *sFs = wsm + (DIRECT ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [16][2][33]
     const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -705,9 +846,11 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         {
             const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
             const int nlev = 2 * L + 1;
-            for (int i = lane; i < nlev * nbc; i += 32) {
-                const int lev = i / nbc, bb = i - lev * nbc;
-                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+            if constexpr (!DIRECT) {
+                for (int i = lane; i < nlev * nbc; i += 32) {
+                    const int lev = i / nbc, bb = i - lev * nbc;
+                    sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+                }
             }
             if (lane < nbc) {
                 sFs[lane] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + lane);
@@ -725,26 +868,72 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         const int b = s / NG;
         const int bb = b - b_lo;
         const float wg = active ? kp.g_w32[s - b * NG] : 0.f;
-        const float *Bp = sB + bb;                 // level stride nbc
+        const int bst = DIRECT ? NB : nbc;         // level stride of Bp
+        const float *Bp = DIRECT ? kp.planck32 + kp.planck_off[c] + b : sB + bb;
 
-        // forward elimination, TOA -> BOA, departure variables
+        // forward elimination, TOA -> BOA, departure variables; the B of a
+        // layer's bottom interface is carried as the next layer's top
+        float Bt = ldB<DIRECT>(Bp), Bc = ldB<DIRECT>(Bp + bst), Bb = ldB<DIRECT>(Bp + 2 * bst);
         float al = 1.f;                                      // alpha' = 1 - a'
-        float bl = (float)kp.F_toa - kPiF * Bp[0];           // b' at the TOA
+        float bl = (float)kp.F_toa - kPiF * Bt;              // b' at the TOA
         float Fb = beam ? mu * sFs[bb] : 0.f;
-        const float *pd = kp.dtau + cube0 + s, *pw = kp.w0 + cube0 + s, *pg = kp.g0 + cube0 + s;
-        float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);
+        // optics: read from the cubes, or (KT) from the k-table corners of
+        // the layer's grid cell, fetched one layer ahead
+        const float *pd = nullptr, *pw = nullptr, *pg = nullptr;
+        float nd = 0.f, nw = 0.f, ng = 0.f;
+        const float4 *klay = nullptr;
+        float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next, kb = kl_next;
+        Corners kc = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (KT) {
+            klay = kp.kt_lay + kp.lay_off[c];
+            kb = __ldg(kp.kt_bin + b);
+            kl_next = klay[0];
+            kl_after = L > 1 ? klay[1] : kl_next;
+            kc = kt_corners(kp, kl_next, S, s);
+        } else {
+            pd = kp.dtau + cube0 + s;
+            pw = kp.w0 + cube0 + s;
+            pg = kp.g0 + cube0 + s;
+            nd = __ldcs(pd);
+            nw = __ldcs(pw);
+            ng = __ldcs(pg);
+        }
         float4 *sp = kp.scr32 + slot;
         for (int l = 0; l < L; ++l) {
-            const float dt = nd, w0 = nw, g0 = ng;
-            if (l + 1 < L) {                         // prefetch the next layer
-                pd += S; pw += S; pg += S;
-                nd = __ldcs(pd);
-                nw = __ldcs(pw);
-                ng = __ldcs(pg);
+            float dt, w0, g0;
+            float nBc = 0.f, nBb = 0.f;
+            if constexpr (KT) {
+                const Corners cur = kc;
+                const float4 kl = kl_next;
+                if (l + 1 < L) {                     // prefetch the next layer's corners
+                    kl_next = kl_after;
+                    kc = kt_corners(kp, kl_next, S, s);
+                    if (l + 2 < L) kl_after = klay[l + 2];
+                    nBc = ldB<DIRECT>(Bp + 3 * bst);
+                    nBb = ldB<DIRECT>(Bp + 4 * bst);
+                }
+                const Optics o = kt_mix(cur.k00, cur.k01, cur.k10, cur.k11, kl, kb);
+                dt = o.dt;
+                w0 = o.w0;
+                g0 = o.g0;
+            } else {
+                dt = nd;
+                w0 = nw;
+                g0 = ng;
+                if (l + 1 < L) {                     // prefetch the next layer
+                    pd += S; pw += S; pg += S;
+                    nd = __ldcs(pd);
+                    nw = __ldcs(pw);
+                    ng = __ldcs(pg);
+                    nBc = ldB<DIRECT>(Bp + 3 * bst);
+                    nBb = ldB<DIRECT>(Bp + 4 * bst);
+                }
             }
-            const Layer32 ly = layer32<ISO>(dt, w0, g0, Bp[0], Bp[nbc], Bp[2 * nbc], mu, imu, mu_d, beam,
-                                            Fb, kp, cn);
-            Bp += 2 * nbc;
+            const Layer32 ly = layer32<ISO>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn);
+            Bp += 2 * bst;
+            Bt = Bb;
+            Bc = nBc;
+            Bb = nBb;
             const float omr = ly.omtr + ly.T;                // 1 - R
             const float ipv = frcp(fmaf(ly.R, al, omr));     // 1 / (1 - R a')
             float4 st;
@@ -772,8 +961,9 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         float uu = (FBOA + Fb + bl) * frcp(al);
         bool bad = !isfinite(uu);   // NaN and Inf propagate up the substitution
         float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
-        // Bp points at level 2L (the BOA interface)
-        tb[lane] = wg * fmaf(kPiF, Bp[0], uu);
+        // Bp points at level 2L (the BOA interface), whose B is Bt
+        tb[lane] = wg * fmaf(kPiF, Bt, uu);
+        float nBi = ldB<DIRECT>(Bp - 2 * bst);     // B one interface up
         tb[33 + lane] = wg * FBOA;
         int gi = 1;              // slots used in the current group of 16 interfaces
         int gtop = L;            // interface held in slot 0 of the group
@@ -786,9 +976,12 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
                     sp -= sstride;
                     nst = __ldcg(sp);
                 }
-                Bp -= 2 * nbc;
+                Bp -= 2 * bst;
+                const float Bi = nBi;
+                if (i > 0) nBi = ldB<DIRECT>(Bp - 2 * bst);
                 uu = fmaf(st.x, uu, st.y);
-                const float fup = fmaf(kPiF, Bp[0], uu);
+                const float fup = fmaf(kPiF, Bi, uu);
+                Bt = Bi;
                 const float fnet = fmaf(st.z, uu, -st.w);
                 tb[(gi * 2) * 33 + lane] = wg * fup;
                 tb[(gi * 2 + 1) * 33 + lane] = wg * fnet;
@@ -812,6 +1005,23 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         }
         bad |= !isfinite(uu);
         if (active && bad) cn.nonfinite++;
+
+        // TOA spectrum: uu and Bp are now at interface 0; each bin's lanes
+        // are summed in lane order and added once per unit (a bin of n_g <= 32
+        // systems meets at most two units, so the FP64 sum is order-free)
+        if (kp.toa) {
+            tb[lane] = wg * fmaf(kPiF, Bt, uu);
+            __syncwarp();
+            if (lane < nbc) {
+                const int bt = b_lo + lane;
+                const int j0 = max(0, bt * NG - s0);
+                const int j1 = min(min(32, S - s0), (bt + 1) * NG - s0);
+                float acc = 0.f;
+                for (int j = j0; j < j1; ++j) acc += tb[j];
+                atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
+            }
+            __syncwarp();
+        }
 
         // the warp that completes a column's last unit writes the column
         __threadfence();
@@ -1027,8 +1237,19 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
                 }
             }
             if (active && bad) cn.nonfinite++;
+            sm.stoa[tid] = active ? wg * fu : 0.0;       // fu is now at interface 0 (TOA)
             __syncthreads();
             fold_warps<double>(ci.L, nwarps, sm);
+            if (kp.toa && tid < nbc) {
+                // one thread per bin sums its systems in order; a bin split
+                // across chunks is continued by the same CTA after a barrier
+                const int bt = b_lo + tid;
+                const int j0 = max(0, bt * NG - s0);
+                const int j1 = min(min((int)blockDim.x, ci.S - s0), (bt + 1) * NG - s0);
+                double acc = 0.0;
+                for (int j = j0; j < j1; ++j) acc += sm.stoa[j];
+                kp.toa[ci.bin0 + bt] += acc;
+            }
             __syncthreads();
         }
         write_column(kp, ci, sm.acc);
@@ -1037,11 +1258,40 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
     flush_counters(cn, kp.stats);
 }
 
+// Front end alone: one CTA per column (grid-stride), the column's per-layer
+// set-up in shared memory, then every (layer, bin, g) element.
+__global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_t *pcube_off, float *dtau,
+                                                         float *w0, float *g0) {
+    extern __shared__ float4 sl[];                // [Lmax]
+    const int NG = kp.n_g;
+    for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
+        const int L = kp.n_layers[c], NB = kp.n_bins[c], S = NB * NG;
+        const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], base = pcube_off[c];
+        __syncthreads();
+        for (int l = threadIdx.x; l < L; l += blockDim.x)
+            sl[l] = kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], S);
+        __syncthreads();
+        const long long n = (long long)L * S;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const int l = (int)(i / S), s = (int)(i - (long long)l * S);
+            const float4 l4 = sl[l];
+            const Corners k = kt_corners(kp, l4, S, s);
+            const Optics o = kt_mix(k.k00, k.k01, k.k10, k.k11, l4, __ldg(kp.kt_bin + s / NG));
+            dtau[base + i] = o.dt;
+            w0[base + i] = o.w0;
+            g0[base + i] = o.g0;
+        }
+    }
+}
+
 constexpr int kMaxDynSmem = 200 * 1024;
 
 cudaError_t init_kernels() {
     cudaError_t e = cudaSuccess;
-    for (auto f : {fp32_units<false>, fp32_units<true>}) {
+    for (auto f : {fp32_units<false, false, false>, fp32_units<true, false, false>,
+                   fp32_units<false, true, false>, fp32_units<true, true, false>,
+                   fp32_units<false, false, true>, fp32_units<true, false, true>,
+                   fp32_units<false, true, true>, fp32_units<true, true, true>}) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1056,7 +1306,7 @@ int occupancy(int precision_fp64, int block, size_t smem) {
     int n = 0;
     cudaError_t e = precision_fp64
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false>, block, smem);
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false>, block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -1065,10 +1315,24 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 1), s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (kp.isothermal)
-        fp32_units<true><<<grid, block, smem, s>>>(kp);
-    else
-        fp32_units<false><<<grid, block, smem, s>>>(kp);
+    const int sel = (kp.isothermal ? 1 : 0) | (kp.direct ? 2 : 0) | (kp.kt_lk ? 4 : 0);
+    switch (sel) {
+        case 0: fp32_units<false, false, false><<<grid, block, smem, s>>>(kp); break;
+        case 1: fp32_units<true, false, false><<<grid, block, smem, s>>>(kp); break;
+        case 2: fp32_units<false, true, false><<<grid, block, smem, s>>>(kp); break;
+        case 3: fp32_units<true, true, false><<<grid, block, smem, s>>>(kp); break;
+        case 4: fp32_units<false, false, true><<<grid, block, smem, s>>>(kp); break;
+        case 5: fp32_units<true, false, true><<<grid, block, smem, s>>>(kp); break;
+        case 6: fp32_units<false, true, true><<<grid, block, smem, s>>>(kp); break;
+        default: fp32_units<true, true, true><<<grid, block, smem, s>>>(kp); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float *dtau, float *w0,
+                             float *g0, cudaStream_t s) {
+    const int grid = kp.n_cols < 8 * 148 ? kp.n_cols : 8 * 148;
+    kt_optics_kernel<<<grid, 256, sizeof(float4) * kp.Lmax, s>>>(kp, pcube_off, dtau, w0, g0);
     return cudaGetLastError();
 }
 

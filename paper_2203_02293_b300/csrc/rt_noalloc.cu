@@ -97,6 +97,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
                                         double *F_down, double *F_net, double *Q, void *stream) {
     if (!cfg || !cols || !F_up || !F_down || !F_net || !Q) return RT_EINVAL;
     if (cfg->precision != RT_FP32_FORM) return RT_EINVAL;
+    if (cfg->n_edges != 0) return RT_EINVAL;                   // uniform bins only
     if (cfg->n_g < 1 || cfg->n_g > kMaxG || !cfg->g_weights) return RT_EINVAL;
     if (!(cfg->wn_max > cfg->wn_min) || !(cfg->wn_min >= 0.0) || !(cfg->eps2 > 0.0) || !(cfg->cp > 0.0) ||
         !(cfg->T_int >= 0.0))
@@ -154,7 +155,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     int grid = 0;
     for (;; block -= 32) {
         if (block < 64) return RT_EBUDGET;
-        smem = rt::fp32_smem_bytes(block, (int)L, nbw);
+        smem = rt::fp32_smem_bytes(block, (int)L, nbw, 0);
         const int occ = rt::occupancy(0, block, smem);
         const int64_t by_scr = slots_fit / block;
         int64_t g = (int64_t)occ * sms;
@@ -259,7 +260,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.partial = (float *)(base + o_part);
     kp.col_done = done;
     kp.n_units = (int32_t)nu;
-    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw);
+    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0);
     kp.nbw = nbw;
     kp.planck32 = (float *)(base + o_planck);
     kp.planck_off = a.pk;

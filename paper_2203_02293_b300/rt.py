@@ -21,6 +21,7 @@ RT_IMPROVED, RT_REGULAR = 0, 1
 RT_NONISOTHERMAL, RT_ISOTHERMAL = 0, 1
 RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
 RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
+RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT = 0, 1, 2
 
 _STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
            -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}
@@ -37,7 +38,8 @@ class rt_config(ctypes.Structure):
         ("T_int", ctypes.c_double), ("F_toa_diffuse", ctypes.c_double),
         ("max_layers", ctypes.c_int32), ("max_bins", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
-        ("ctas_per_sm", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32), ("planck_staging", ctypes.c_int32),
+        ("n_edges", ctypes.c_int32), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -52,6 +54,20 @@ class rt_columns(ctypes.Structure):
         ("cube_offset", ctypes.POINTER(ctypes.c_int64)), ("center_offset", ctypes.POINTER(ctypes.c_int64)),
         ("iface_offset", ctypes.POINTER(ctypes.c_int64)), ("bin_offset", ctypes.POINTER(ctypes.c_int64)),
         ("col_index", ctypes.POINTER(ctypes.c_int64)),
+    ]
+
+
+class rt_ktable(ctypes.Structure):
+    _fields_ = [
+        ("n_T", ctypes.c_int32), ("n_P", ctypes.c_int32),
+        ("T_grid", ctypes.POINTER(ctypes.c_double)), ("log10p_grid", ctypes.POINTER(ctypes.c_double)),
+        ("n_bins", ctypes.c_int32), ("n_g", ctypes.c_int32),
+        ("log10_kappa", ctypes.POINTER(ctypes.c_float)),
+        ("sigma_scat_cloud", ctypes.POINTER(ctypes.c_double)),
+        ("sigma_abs_cloud", ctypes.POINTER(ctypes.c_double)),
+        ("g0_cloud", ctypes.POINTER(ctypes.c_double)),
+        ("f_cloud", ctypes.c_double), ("x_H2", ctypes.c_double), ("x_He", ctypes.c_double),
+        ("mbar_amu", ctypes.c_double),
     ]
 
 
@@ -72,6 +88,11 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_solve_columns.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p]
     lib.rt_fluxes.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_heating.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_toa_spectrum.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_set_ktable.argtypes = [H, ctypes.POINTER(rt_ktable)]
+    lib.rt_ktable_optics.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    lib.rt_solve_ktable.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p]
     lib.rt_stats.argtypes = [H, ctypes.POINTER(rt_stats_t)]
     lib.rt_last_error.argtypes = [H]
     lib.rt_last_error.restype = ctypes.c_char_p
@@ -82,7 +103,7 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_solve_uniform_noalloc.restype = ctypes.c_int
     for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
-              "rt_stats"):
+              "rt_toa_spectrum", "rt_stats", "rt_set_ktable", "rt_ktable_optics", "rt_solve_ktable"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -147,16 +168,27 @@ class Config:
     hbm_budget_bytes: int = 0
     block_threads: int = 0
     ctas_per_sm: int = 0
+    planck_staging: int = 0              # RT_STAGE_AUTO / RT_STAGE_SHARED / RT_STAGE_DIRECT
+    wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins
+
+
+def _config(cfg: Config):
+    """The C struct for ``cfg``; the returned arrays must outlive the call."""
+    PD = ctypes.POINTER(ctypes.c_double)
+    gw = np.ascontiguousarray(cfg.g_weights, dtype=np.float64)
+    ed = None if cfg.wn_edges is None else np.ascontiguousarray(cfg.wn_edges, dtype=np.float64)
+    c = rt_config(len(gw), gw.ctypes.data_as(PD), cfg.wn_min,
+                  cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
+                  cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
+                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
+                  cfg.ctas_per_sm, cfg.planck_staging, 0 if ed is None else ed.size,
+                  None if ed is None else ed.ctypes.data_as(PD))
+    return c, (gw, ed)
 
 
 def rt_create(cfg: Config):
     """Create a handle (returns an opaque ctypes pointer)."""
-    gw = np.ascontiguousarray(cfg.g_weights, dtype=np.float64)
-    c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
-                  cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
-                  cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
-                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
-                  cfg.ctas_per_sm)
+    c, keep = _config(cfg)
     h = ctypes.c_void_p()
     _check(lib().rt_create(ctypes.byref(c), ctypes.byref(h)))
     return h
@@ -203,6 +235,38 @@ def rt_heating(h, Q, stream=None):
     _check(lib().rt_heating(h, _ptr(Q), _stream_ptr(stream)), h)
 
 
+def rt_set_ktable(h, kt: dict):
+    """Copy a k-table (a dict with the fields of rt_ktable, as drawn by
+    ``rt_synth.ktable``) into the handle."""
+    PD = ctypes.POINTER(ctypes.c_double)
+    d = lambda k: np.ascontiguousarray(kt[k], dtype=np.float64)
+    T, lp = d("T_grid"), d("log10p_grid")
+    lk = np.ascontiguousarray(kt["log10_kappa"], dtype=np.float32)
+    ss, sa, gc = d("sigma_scat_cloud"), d("sigma_abs_cloud"), d("g0_cloud")
+    nT, nP, NB, NG = lk.shape
+    if T.size != nT or lp.size != nP or ss.size != NB or sa.size != NB or gc.size != NB:
+        raise ValueError("k-table arrays disagree with log10_kappa's shape")
+    c = rt_ktable(nT, nP, T.ctypes.data_as(PD), lp.ctypes.data_as(PD), NB, NG,
+                  lk.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ss.ctypes.data_as(PD),
+                  sa.ctypes.data_as(PD), gc.ctypes.data_as(PD), float(kt["f_cloud"]),
+                  float(kt["x_h2"]), float(kt["x_he"]), float(kt["mbar_amu"]))
+    _check(lib().rt_set_ktable(h, ctypes.byref(c)), h)
+
+
+def rt_ktable_optics(h, cols, dtau, w0, g0, stream=None):
+    _check(lib().rt_ktable_optics(h, ctypes.byref(cols), _ptr(dtau), _ptr(w0), _ptr(g0),
+                                  _stream_ptr(stream)), h)
+
+
+def rt_solve_ktable(h, cols, stream=None):
+    _check(lib().rt_solve_ktable(h, ctypes.byref(cols), _stream_ptr(stream)), h)
+
+
+def rt_toa_spectrum(h, F_up_toa, stream=None):
+    """Per-bin upward flux at the TOA of the last solve, [sum NB] float64."""
+    _check(lib().rt_toa_spectrum(h, _ptr(F_up_toa), _stream_ptr(stream)), h)
+
+
 def rt_stats(h) -> dict:
     s = rt_stats_t()
     _check(lib().rt_stats(h, ctypes.byref(s)), h)
@@ -223,12 +287,7 @@ def rt_solve_uniform_noalloc(cfg: Config, cols, F_up, F_down, F_net, Q, stream=N
 
     ``cols`` is an rt_columns descriptor with NULL shape arrays and L, NB set;
     the four outputs are device tensors written in place."""
-    gw = np.ascontiguousarray(cfg.g_weights, dtype=np.float64)
-    c = rt_config(len(gw), gw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cfg.wn_min,
-                  cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
-                  cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
-                  cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
-                  cfg.ctas_per_sm)
+    c, keep = _config(cfg)
     code = lib().rt_solve_uniform_noalloc(ctypes.byref(c), ctypes.byref(cols), _ptr(F_up),
                                           _ptr(F_down), _ptr(F_net), _ptr(Q), _stream_ptr(stream))
     if code != RT_OK:

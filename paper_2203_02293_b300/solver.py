@@ -72,6 +72,14 @@ class DeviceBatch:
     def input_bytes(self) -> int:
         return sum(getattr(self, f).numel() * getattr(self, f).element_size() for f in self.FIELDS)
 
+    def state_descriptor(self):
+        """Descriptor without optics (for the k-table front end)."""
+        if getattr(self, "_sdesc", None) is None:
+            self._sdesc = rt.make_columns(self.n_cols, self.n_layers, self.n_bins, None, None, None,
+                                          self.T_center, self.T_iface, self.p_iface, self.mu_star,
+                                          self.F_star)
+        return self._sdesc
+
     def descriptor(self):
         if self._desc is None:
             self._desc = rt.make_columns(self.n_cols, self.n_layers, self.n_bins, self.dtau, self.w0,
@@ -104,6 +112,21 @@ class Solver:
     def solve(self, batch: DeviceBatch, stream=None):
         rt.rt_solve_columns(self.h, batch.descriptor(), stream)
 
+    def set_ktable(self, kt: dict):
+        rt.rt_set_ktable(self.h, kt)
+
+    def solve_ktable(self, batch: DeviceBatch, stream=None):
+        """Solve with the optics from the k-table front end (``batch``'s
+        dtau/w0/g0 are not read)."""
+        rt.rt_solve_ktable(self.h, batch.state_descriptor(), stream)
+
+    def ktable_optics(self, batch: DeviceBatch, stream=None) -> dict:
+        """The front end's FP32 optics cubes for ``batch``."""
+        n = int((batch.n_layers.astype(np.int64) * batch.n_bins).sum()) * batch.n_g
+        o = {k: torch.empty(n, dtype=torch.float32, device="cuda") for k in ("dtau", "w0", "g0")}
+        rt.rt_ktable_optics(self.h, batch.state_descriptor(), o["dtau"], o["w0"], o["g0"], stream)
+        return o
+
     def outputs(self, batch: DeviceBatch, stream=None, device="cuda") -> dict:
         """Interface fluxes and heating of the last solve as tensors."""
         o = {k: torch.empty(batch.n_if, dtype=torch.float64, device=device)
@@ -122,9 +145,16 @@ class Solver:
         torch.cuda.synchronize()
         return o
 
+    def toa_spectrum(self, batch: DeviceBatch, stream=None, device="cuda"):
+        """Upward flux at the TOA per bin of the last solve, [sum NB]."""
+        t = torch.empty(int(batch.n_bins.astype(np.int64).sum()), dtype=torch.float64, device=device)
+        rt.rt_toa_spectrum(self.h, t, stream)
+        return t
+
     def solve_numpy(self, batch: DeviceBatch) -> dict:
         self.solve(batch)
         o = self.outputs(batch)
+        o["F_up_toa"] = self.toa_spectrum(batch)
         torch.cuda.synchronize()
         return {k: v.cpu().numpy() for k, v in o.items()}
 

@@ -113,9 +113,9 @@ def stellar_flux_bins(n_bins: int, wn_min: float = WN_MIN, wn_max: float = WN_MA
     return np.pi * b_mid * width * (R_STAR / A_ORBIT) ** 2
 
 
-def _profile(rng, L: int):
+def _profile(rng, L: int, p_top_bar: float = P_TOP_BAR):
     """Pressure grid (Pa) and temperatures of one column, layer 0 at the top."""
-    lp = np.linspace(np.log(P_TOP_BAR), np.log(P_BOT_BAR), L + 1)
+    lp = np.linspace(np.log(p_top_bar), np.log(P_BOT_BAR), L + 1)
     p_if = np.exp(lp) * 1.0e5
     lpc = 0.5 * (lp[1:] + lp[:-1])
     frac = (lpc - lp[0]) / (lp[-1] - lp[0])
@@ -370,3 +370,189 @@ def config3_device(n_cols: int = 4096, seed: int = 3, device="cuda") -> DeviceCo
     """Uneven batch on the device: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g."""
     L, NB = uneven_shapes(n_cols, seed)
     return device_generate(L, NB, 20, seed, device, name=f"config3 {n_cols} uneven (device)")
+
+
+# ----------------------------------------------------------------------
+# Post-processing workload (Sec. 2.1.3 and the run protocol of Sec. 3):
+# after the GCM run the radiative transfer is repeated once on a
+# high-resolution spectral grid -- opacity sampling at R = lambda / dlambda =
+# 500, 3255 wavelength points log-spaced over 0.3-200 um, one g-point per
+# bin -- on columns whose top is extended to 1 ubar with isothermal layers at
+# the top-most model layer's temperature.
+# ----------------------------------------------------------------------
+POST_BINS = 3255
+POST_P_MIN_BAR = 1e-6          # lowest pressure of the isothermal extension
+POST_LAYERS_PER_DECADE = 4     # extension layers per decade of pressure
+POST_L_MODEL = 40
+
+
+def postproc_edges(n_bins: int = POST_BINS):
+    """Bin edges (cm^-1) log-spaced over [WN_MIN, WN_MAX]: R = nu / dnu ~ 500."""
+    return np.geomspace(WN_MIN, WN_MAX, n_bins + 1)
+
+
+def stellar_flux_edges(edges_cm):
+    """Stand-in stellar spectrum per bin for explicit edges (cm^-1)."""
+    e = np.asarray(edges_cm, np.float64) * 100.0
+    mid = 0.5 * (e[1:] + e[:-1])
+    x = _H * _C * mid / (_KB * T_STAR)
+    b_mid = 2.0 * _H * _C ** 2 * mid ** 3 / np.expm1(x)
+    return np.pi * b_mid * np.diff(e) * (R_STAR / A_ORBIT) ** 2
+
+
+def extend_isothermal(p_if, Tc, Ti, p_min_bar: float = POST_P_MIN_BAR,
+                      per_decade: int = POST_LAYERS_PER_DECADE):
+    """Extend one column above its top (layer 0) to ``p_min_bar`` with
+    isothermal layers at the top-most layer's temperature.  The new layers
+    are log-spaced in pressure, ``per_decade`` per decade (rounded up); a
+    column whose top is already at or above p_min is returned unchanged.
+    Returns (p_if, Tc, Ti, n_ext)."""
+    p_top = p_if[0]
+    p_min = p_min_bar * 1.0e5
+    if p_top <= p_min:
+        return p_if, Tc, Ti, 0
+    n_ext = int(np.ceil(per_decade * np.log10(p_top / p_min)))
+    p_ext = np.geomspace(p_min, p_top, n_ext + 1)[:-1]       # new interfaces above the old top
+    p_if = np.concatenate([p_ext, p_if])
+    Tc = np.concatenate([np.full(n_ext, Tc[0]), Tc])
+    Ti = np.concatenate([np.full(n_ext, Tc[n_ext]), Ti])
+    return p_if, Tc, Ti, n_ext
+
+
+def postproc_profiles(n_cols: int, seed: int, L_model: int = POST_L_MODEL):
+    """Per-column profiles of the post-processing workload: a model top
+    log-uniform in [1e-7, 1e-3] bar (the day-to-night spread of the model top
+    in Sec. 4), the model's L_model layers below it, then the isothermal
+    extension to 1 ubar; mu* uniform in [-1, 1] with the night side (<= 0)
+    set to 0 (no beam)."""
+    rng = np.random.default_rng(seed)
+    p_top = np.exp(rng.uniform(np.log(1e-7), np.log(1e-3), n_cols))
+    mu = np.maximum(rng.uniform(-1.0, 1.0, n_cols), 0.0)
+    prof, L = [], np.empty(n_cols, np.int32)
+    for c in range(n_cols):
+        p_if, Tc, Ti = _profile(rng, L_model, float(p_top[c]))
+        p_if, Tc, Ti, n_ext = extend_isothermal(p_if, Tc, Ti)
+        prof.append((p_if, Tc, Ti))
+        L[c] = L_model + n_ext
+    return L, prof, mu, rng
+
+
+def postproc(n_cols: int = 64, seed: int = 5) -> Columns:
+    """Post-processing batch on the host (opacity sampling, NG = 1):
+    k ~ logU[1e-8, 1] m^2/kg per (layer, bin), dtau = k dp / g, w0 ~ U[0,
+    0.95], g0 ~ U[0, 0.8].  Bins: ``postproc_edges()``."""
+    L, prof, mu, rng = postproc_profiles(n_cols, seed)
+    NB = POST_BINS
+    cubes = {k: [] for k in ("dtau", "w0", "g0")}
+    for c in range(n_cols):
+        p_if = prof[c][0]
+        shape = (int(L[c]), NB)
+        k = np.exp(rng.uniform(np.log(1e-8), np.log(1.0), shape))
+        cubes["dtau"].append((k * np.diff(p_if)[:, None] / GRAV).astype(np.float32).ravel())
+        cubes["w0"].append(rng.uniform(0.0, 0.95, shape).astype(np.float32).ravel())
+        cubes["g0"].append(rng.uniform(0.0, 0.8, shape).astype(np.float32).ravel())
+    edges = postproc_edges()
+    consts = dict(_consts(), wn_edges=edges)
+    return Columns(n_layers=L, n_bins=np.full(n_cols, NB, np.int32), n_g=1,
+                   g_weights=np.array([1.0]), dtau=np.concatenate(cubes["dtau"]),
+                   w0=np.concatenate(cubes["w0"]), g0=np.concatenate(cubes["g0"]),
+                   T_center=np.concatenate([p[1] for p in prof]),
+                   T_iface=np.concatenate([p[2] for p in prof]),
+                   p_iface=np.concatenate([p[0] for p in prof]), mu_star=mu,
+                   F_star=np.tile(stellar_flux_edges(edges), n_cols), consts=consts,
+                   name=f"postproc {n_cols}x~{int(L.mean())}x{NB}x1")
+
+
+def postproc_device(n_cols: int = 2562, seed: int = 5, device="cuda") -> DeviceColumns:
+    """The post-processing workload with its cubes drawn on the device (same
+    distributions as ``postproc``, torch's generator): 2562 columns by
+    default, ~8.3M (column, bin) systems."""
+    import torch
+    L, prof, mu, _ = postproc_profiles(n_cols, seed)
+    NB = POST_BINS
+    n_cube = int(L.astype(np.int64).sum()) * NB
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+    p_all = np.concatenate([p[0] for p in prof])
+    dp = np.concatenate([np.diff(p[0]) for p in prof]) / GRAV               # per layer
+    dtau = _device_uniform(n_cube, 1e-8, 1.0, gen, device, log=True)
+    dtau.view(-1, NB).mul_(torch.from_numpy(dp.astype(np.float32)).to(device)[:, None])
+    t = dict(dtau=dtau, w0=_device_uniform(n_cube, 0.0, 0.95, gen, device),
+             g0=_device_uniform(n_cube, 0.0, 0.8, gen, device))
+    t["T_center"] = dev(np.concatenate([p[1] for p in prof]))
+    t["T_iface"] = dev(np.concatenate([p[2] for p in prof]))
+    t["p_iface"] = dev(p_all)
+    t["mu_star"] = dev(mu)
+    edges = postproc_edges()
+    t["F_star"] = dev(np.tile(stellar_flux_edges(edges), n_cols))
+    return DeviceColumns(L, np.full(n_cols, NB, np.int32), 1, np.array([1.0]), t,
+                         dict(_consts(), wn_edges=edges), f"postproc {n_cols} (device)")
+
+
+# ----------------------------------------------------------------------
+# Synthetic premixed k-table and cloud data for the input front end
+# (Sec. 2.1.3): 60 temperatures on [50, 3000] K, 28 pressures log-spaced on
+# [1e-6, 1e3] bar, NB bins x NG Gauss points, log10 kappa ascending over g
+# within each (T, p, bin) as a sorted k-distribution is.  The enstatite
+# LX-MIE cross sections are replaced by smooth stand-ins for 1 um particles.
+# ----------------------------------------------------------------------
+KT_NT, KT_NP = 60, 28
+F_CLOUD = 1e-17          # cloud-to-gas number ratio used in the paper
+X_H2, X_HE = 0.85, 0.15  # number fractions for Rayleigh scattering
+MBAR_AMU = 2.34          # Table 3
+
+
+def ktable(n_bins: int = 30, n_g: int = 20, seed: int = 11, edges=None):
+    """Seeded synthetic k-table.  Returns a dict with T_grid, log10p_grid,
+    log10_kappa [nT, nP, NB, NG] (float32), sigma_scat_cloud,
+    sigma_abs_cloud, g0_cloud [NB], f_cloud, x_h2, x_he, mbar_amu, edges.
+
+    log10 kappa = base_b + spread_b q_g + alpha_b log10(p / 1 bar) / 2
+                  + beta_b (T - 1000 K) / 1000 K + N(0, 0.05), clipped to
+    [-12, 3], then sorted over g;  q_g in [-1, 1] increasing, base_b ~
+    U[-6, 0], spread_b ~ U[0.5, 3], alpha_b ~ U[0, 1], beta_b ~ U[-0.5, 0.5]."""
+    rng = np.random.default_rng(seed)
+    if edges is None:
+        edges = np.linspace(WN_MIN, WN_MAX, n_bins + 1)
+    edges = np.asarray(edges, np.float64)
+    NB = edges.size - 1
+    T_grid = np.linspace(50.0, 3000.0, KT_NT)
+    lp_grid = np.linspace(np.log10(1e-6 * 1e5), np.log10(1e3 * 1e5), KT_NP)
+    base = rng.uniform(-6.0, 0.0, NB)
+    spread = rng.uniform(0.5, 3.0, NB)
+    alpha = rng.uniform(0.0, 1.0, NB)
+    beta = rng.uniform(-0.5, 0.5, NB)
+    q = np.linspace(-1.0, 1.0, n_g) if n_g > 1 else np.zeros(1)
+    lk = (base[None, None, :, None] + spread[None, None, :, None] * q[None, None, None, :]
+          + alpha[None, None, :, None] * (lp_grid[None, :, None, None] - 5.0) / 2.0
+          + beta[None, None, :, None] * (T_grid[:, None, None, None] - 1000.0) / 1000.0)
+    lk = lk + rng.normal(0.0, 0.05, lk.shape)
+    lk = np.sort(np.clip(lk, -12.0, 3.0), axis=-1).astype(np.float32)
+    # cloud stand-in: 1 um particles, size parameter x = 2 pi r / lambda
+    lam_um = 1.0e4 / (0.5 * (edges[1:] + edges[:-1]))
+    x = 2.0 * np.pi * 1.0 / lam_um
+    geo = np.pi * (1.0e-6) ** 2
+    q_scat = 2.0 * x ** 4 / (1.0 + x ** 4)
+    q_abs = 0.05 + 0.6 * np.exp(-0.5 * ((lam_um - 10.0) / 1.5) ** 2)
+    g0c = 0.85 * x ** 2 / (1.0 + x ** 2)
+    return dict(T_grid=T_grid, log10p_grid=lp_grid, log10_kappa=lk,
+                sigma_scat_cloud=geo * q_scat, sigma_abs_cloud=geo * q_abs, g0_cloud=g0c,
+                f_cloud=F_CLOUD, x_h2=X_H2, x_he=X_HE, mbar_amu=MBAR_AMU, edges=edges)
+
+
+def state_columns(n_cols: int, L: int, NB: int, n_g: int, seed: int, name: str = "") -> Columns:
+    """Column state without optics (for the k-table front end): profiles,
+    mu and F* as ``generate_fast``; dtau/w0/g0 are empty."""
+    rng = np.random.default_rng(seed)
+    gx, gw = gauss_legendre_01(n_g)
+    prof = [_profile(rng, L) for _ in range(n_cols)]
+    mu = rng.uniform(0.1, 1.0, n_cols)
+    e = np.zeros(0, np.float32)
+    return Columns(n_layers=np.full(n_cols, L, np.int32), n_bins=np.full(n_cols, NB, np.int32),
+                   n_g=n_g, g_weights=gw, dtau=e, w0=e, g0=e,
+                   T_center=np.concatenate([p[1] for p in prof]),
+                   T_iface=np.concatenate([p[2] for p in prof]),
+                   p_iface=np.concatenate([p[0] for p in prof]), mu_star=mu,
+                   F_star=np.tile(stellar_flux_bins(NB), n_cols), consts=_consts(),
+                   name=name or f"state {n_cols}x{L}x{NB}x{n_g}")

@@ -11,6 +11,9 @@ Tolerances (from the stated accuracy targets):
       max(1e-3 |Q_ref|, (g/c_P) 1e-6 F*_col / dp_l) for the heating rate,
       with F*_col = sum over the column's bins of the stellar flux normal to
       the beam (an absolute floor of one millionth of the stellar flux).
+  Per-bin TOA spectrum F_up_toa: the flux bound with the column floor shared
+      out over the bins, 1e-6 F*_col / NB_c per bin (so the per-bin floors add
+      up to the column's).
 """
 from __future__ import annotations
 
@@ -34,7 +37,8 @@ def oracle_solve(cols, opts):
     cfg = oracle.OracleConfig(improved=opts["improved"], isothermal=opts["isothermal"],
                               resonance=opts["resonance"], e_clamp=opts["e_clamp"],
                               eps2=opts["eps2"], T_int=opts["T_int"], F_toa=opts["F_toa"],
-                              wn_min=cols.consts["wn_min"], wn_max=cols.consts["wn_max"])
+                              wn_min=cols.consts["wn_min"], wn_max=cols.consts["wn_max"],
+                              wn_edges=cols.consts.get("wn_edges"))
     return oracle.get().solve_columns(cfg, cols)
 
 
@@ -48,7 +52,7 @@ def gpu_solver(cols, opts, precision, **extra):
                   resonance=rt.RT_RESONANCE_PAPER if opts["resonance"] == "paper" else rt.RT_RESONANCE_LIMIT,
                   e_clamp=int(opts["e_clamp"]), eps2=opts["eps2"], T_int=opts["T_int"],
                   F_toa_diffuse=opts["F_toa"], wn_min=cols.consts["wn_min"],
-                  wn_max=cols.consts["wn_max"], **extra)
+                  wn_max=cols.consts["wn_max"], wn_edges=cols.consts.get("wn_edges"), **extra)
 
 
 def gpu_solve(cols, opts, precision, **extra):
@@ -77,6 +81,13 @@ def column_floors(cols):
     return f_if, f_q
 
 
+def bin_floors(cols):
+    o = cols.offsets()
+    NB = cols.n_bins.astype(np.int64)
+    fstar = np.array([cols.F_star[o["bins"][c]:o["bins"][c + 1]].sum() for c in range(cols.n_cols)])
+    return np.repeat(1e-6 * fstar / NB, NB)
+
+
 def errors(cols, got, ref, precision):
     """Largest |error| / tolerance per quantity (<= 1 passes)."""
     f_if, f_q = column_floors(cols)
@@ -93,6 +104,11 @@ def errors(cols, got, ref, precision):
     tol = (1e-8 if precision == "fp64" else 1e-3) * np.abs(r)
     tol = np.maximum(tol, (1e-8 if precision == "fp64" else 1.0) * f_q)
     res["Q"] = float(np.max(np.abs(g - r) / tol)) if r.size else 0.0
+    if "F_up_toa" in got and "F_up_toa" in ref:
+        g, r = got["F_up_toa"], ref["F_up_toa"]
+        fb = bin_floors(cols)
+        tol = 1e-10 * np.maximum(np.abs(r), fb) if precision == "fp64" else np.maximum(1e-4 * np.abs(r), fb)
+        res["F_up_toa"] = float(np.max(np.abs(g - r) / tol)) if r.size else 0.0
     return res
 
 
@@ -112,3 +128,21 @@ def assert_parity(cols, got, ref, precision, label=""):
     bad = {k: v for k, v in e.items() if not (v <= 1.0)}
     assert not bad, f"{label} {precision} parity failed (error/tolerance): {e}"
     return e
+
+
+def oracle_ktable_solve(cols, kt, opts, edges=None):
+    """The oracle front end (FP64 optics, rounded to the float32 the solver
+    takes) followed by the oracle solve."""
+    from dataclasses import replace
+    import oracle.frontend as FE
+    K = FE.KTable(**{k: kt[k] for k in ("T_grid", "log10p_grid", "log10_kappa", "sigma_scat_cloud",
+                                        "sigma_abs_cloud", "g0_cloud", "f_cloud", "x_h2", "x_he",
+                                        "mbar_amu")})
+    if edges is None:
+        edges = cols.consts.get("wn_edges")
+    if edges is None:
+        edges = np.linspace(cols.consts["wn_min"], cols.consts["wn_max"], int(cols.n_bins[0]) + 1)
+    o = FE.optics(K, cols, edges, GRAV)
+    full = replace(cols, dtau=o["dtau"].astype(np.float32), w0=o["w0"].astype(np.float32),
+                   g0=o["g0"].astype(np.float32))
+    return oracle_solve(full, opts), o

@@ -60,7 +60,7 @@ def _c_layout(tmp_path, struct, fields):
     return vals[0], vals[1:]
 
 
-@pytest.mark.parametrize("name", ["rt_config", "rt_columns", "rt_stats_t"])
+@pytest.mark.parametrize("name", ["rt_config", "rt_columns", "rt_stats_t", "rt_ktable"])
 def test_ctypes_structs_match_c_layout(librt, tmp_path, name):
     cls = getattr(librt, name)
     fields = [f for f, _ in cls._fields_]
@@ -90,7 +90,9 @@ def test_create_without_a_gpu_fails_loudly(librt):
 def test_bad_config_is_rejected_before_touching_the_device(librt):
     import numpy as np
     for bad in (dict(eps2=0.0), dict(max_layers=0), dict(block_threads=48), dict(precision=7),
-                dict(wn_min=100.0, wn_max=50.0)):
+                dict(wn_min=100.0, wn_max=50.0), dict(wn_edges=np.array([50.0])),
+                dict(wn_edges=np.array([50.0, 40.0, 60.0])), dict(wn_edges=np.array([-1.0, 40.0])),
+                dict(wn_edges=np.array([50.0, np.nan]))):
         cfg = librt.Config(g_weights=np.ones(1), **bad)
         with pytest.raises(librt.RTError) as e:
             librt.rt_create(cfg)

@@ -145,6 +145,8 @@ def test_gathered_columns_equal_packed_columns():
         got["Q"] = torch.empty(n_lay, dtype=torch.float64, device="cuda")
         rt.rt_fluxes(s.h, got["F_up"], got["F_down"], got["F_net"])
         rt.rt_heating(s.h, got["Q"])
+        got["F_up_toa"] = torch.empty(int(sub.n_bins.sum()), dtype=torch.float64, device="cuda")
+        rt.rt_toa_spectrum(s.h, got["F_up_toa"])
         torch.cuda.synchronize()
         ref = s.solve_numpy(DeviceBatch(sub))
         for k in ref:

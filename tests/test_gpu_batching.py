@@ -35,7 +35,8 @@ def slice_outputs(dc, out, idx):
     o = dc.offsets()
     cat = lambda a, key: np.concatenate([a[o[key][i]:o[key][i + 1]] for i in idx])
     return {"F_up": cat(out["F_up"], "iface"), "F_down": cat(out["F_down"], "iface"),
-            "F_net": cat(out["F_net"], "iface"), "Q": cat(out["Q"], "lay")}
+            "F_net": cat(out["F_net"], "iface"), "Q": cat(out["Q"], "lay"),
+            "F_up_toa": cat(out["F_up_toa"], "bins")}
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
@@ -64,6 +65,7 @@ def test_graph_replay_equals_eager(cfg3):
         g.replay()
     torch.cuda.synchronize()
     o = s.outputs(b)
+    o["F_up_toa"] = s.toa_spectrum(b)
     torch.cuda.synchronize()
     for k in eager:
         assert np.array_equal(o[k].cpu().numpy(), eager[k]), k

@@ -1,0 +1,158 @@
+"""The input front end on the GPU (Sec. 2.1.3: k-table interpolation, gas
+and cloud mixing; App. C Rayleigh): the standalone optics kernel against the
+oracle's FP64 front end, the fused solve against the oracle end to end, and
+the fused solve bitwise against optics-then-solve."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import assert_parity, method_opts, oracle_ktable_solve, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2203_02293_b300 import rt  # noqa: E402
+from paper_2203_02293_b300.solver import DeviceBatch, Solver  # noqa: E402
+
+# FP32 front end: log10 kappa (|x| <= 12) goes through three lerps and a
+# scaled exp2 (a few e-6 relative in kappa), then one add, one multiply and
+# one division: 3e-5 relative covers dtau and w0; g0 is a cast of an FP64
+# value, 1e-6.
+RTOL_OPTICS = 3e-5
+
+
+@pytest.fixture(scope="module")
+def kt():
+    return rt_synth.ktable(n_bins=30, n_g=20, seed=11)
+
+
+def opts_solver(cols, precision="fp32", iso=False, **kw):
+    from parity import gpu_solver
+    return gpu_solver(cols, method_opts(isothermal=iso), precision, **kw)
+
+
+def test_optics_kernel_matches_the_oracle_front_end(kt):
+    cols = rt_synth.state_columns(3, 13, 30, 20, seed=21)
+    _, ref = oracle_ktable_solve(cols, kt, method_opts())
+    s = opts_solver(cols)
+    s.set_ktable(kt)
+    got = {k: v.cpu().numpy() for k, v in s.ktable_optics(DeviceBatch(cols)).items()}
+    s.close()
+    for k, tol in (("dtau", RTOL_OPTICS), ("w0", RTOL_OPTICS), ("g0", 1e-6)):
+        err = np.max(np.abs(got[k] - ref[k]) / np.maximum(np.abs(ref[k]), 1e-30))
+        assert err <= tol, (k, err)
+
+
+@pytest.mark.parametrize("iso", [False, True])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_fused_solve_equals_optics_then_solve(kt, iso, prec):
+    cols = rt_synth.state_columns(4, 17, 30, 20, seed=22)
+    s = opts_solver(cols, prec, iso=iso)
+    s.set_ktable(kt)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    fused = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    o = s.ktable_optics(b)
+    torch.cuda.synchronize()
+    full = replace(cols, **{k: v.cpu().numpy() for k, v in o.items()})
+    plain = s.solve_numpy(DeviceBatch(full))
+    s.close()
+    for k in fused:
+        assert np.array_equal(fused[k], plain[k]), k
+
+
+def test_fused_solve_matches_the_oracle(kt):
+    cols = rt_synth.state_columns(5, 21, 30, 20, seed=23)
+    ref, _ = oracle_ktable_solve(cols, kt, method_opts())
+    s = opts_solver(cols)
+    s.set_ktable(kt)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    got = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    got["F_up_toa"] = s.toa_spectrum(b).cpu().numpy()
+    s.close()
+    assert_parity(cols, got, ref, "fp32", "k-table fused")
+
+
+def test_fp64_path_on_the_front_end_optics(kt):
+    """FP64: the solve part to 1e-10 against the oracle on the GPU's own FP32
+    optics (the optics themselves are checked against the oracle above)."""
+    cols = rt_synth.state_columns(3, 9, 30, 20, seed=24)
+    s = opts_solver(cols, "fp64")
+    s.set_ktable(kt)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    got = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    o = {k: v.cpu().numpy() for k, v in s.ktable_optics(b).items()}
+    s.close()
+    full = replace(cols, **o)
+    assert_parity(full, got, oracle_solve(full, method_opts()), "fp64", "k-table fp64")
+
+
+def test_postproc_shape_with_a_ktable():
+    """Explicit R = 500 edges, one g-point, isothermal extension."""
+    edges = rt_synth.postproc_edges()
+    ktp = rt_synth.ktable(n_g=1, seed=12, edges=edges)
+    L, prof, mu, _ = rt_synth.postproc_profiles(3, seed=25)
+    base = rt_synth.postproc(3, seed=25)
+    e = np.zeros(0, np.float32)
+    cols = replace(base, dtau=e, w0=e, g0=e)
+    ref, _ = oracle_ktable_solve(cols, ktp, method_opts(), edges=edges)
+    s = opts_solver(cols)
+    s.set_ktable(ktp)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    got = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    got["F_up_toa"] = s.toa_spectrum(b).cpu().numpy()
+    s.close()
+    assert_parity(cols, got, ref, "fp32", "postproc k-table")
+
+
+def test_gcm_shape_full_size_sampled(kt):
+    """2562 x 40 x 30 x 20 with the fused front end; sampled columns."""
+    cols = rt_synth.state_columns(2562, 40, 30, 20, seed=26)
+    s = opts_solver(cols)
+    s.set_ktable(kt)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    out = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    st = s.stats()
+    s.close()
+    assert st["invalid_inputs"] == 0 and st["nonfinite_outputs"] == 0
+    idx = np.array([0, 1, 977, 2000, 2561])
+    sub = cols.subset(idx)
+    ref, _ = oracle_ktable_solve(sub, kt, method_opts())
+    o = cols.offsets()
+    cat = lambda a, key: np.concatenate([a[o[key][i]:o[key][i + 1]] for i in idx])
+    got = {"F_up": cat(out["F_up"], "iface"), "F_down": cat(out["F_down"], "iface"),
+           "F_net": cat(out["F_net"], "iface"), "Q": cat(out["Q"], "lay")}
+    assert_parity(sub, got, ref, "fp32", "k-table 2562 sampled")
+
+
+def test_front_end_errors(kt):
+    cols = rt_synth.state_columns(2, 5, 30, 20, seed=27)
+    b = DeviceBatch(cols)
+    s = opts_solver(cols)
+    with pytest.raises(rt.RTError) as e:
+        s.solve_ktable(b)                       # no table yet
+    assert e.value.code == rt.RT_ENOTSOLVED
+    bad = dict(kt, T_grid=kt["T_grid"][::-1].copy())
+    with pytest.raises(rt.RTError) as e:
+        s.set_ktable(bad)
+    assert e.value.code == rt.RT_EINVAL
+    s.set_ktable(rt_synth.ktable(n_bins=12, n_g=20))
+    with pytest.raises(rt.RTError) as e:
+        s.solve_ktable(b)                       # 30-bin columns, 12-bin table
+    assert e.value.code == rt.RT_EINVAL
+    s.close()
+    g3 = rt_synth.ktable(n_bins=30, n_g=3)
+    s = opts_solver(cols)
+    with pytest.raises(rt.RTError) as e:
+        s.set_ktable(g3)                        # table n_g differs from the handle's
+    assert e.value.code == rt.RT_EINVAL
+    s.close()

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_spectrum as spec
 
 MUTATIONS = {
     "mu_star_sign": ("double mus = -mu;   /* Malik sign", "double mus = mu;   /* Malik sign"),
@@ -31,6 +32,8 @@ MUTATIONS = {
     "planck_wien": ("nu * nu * nu / expm1(x);", "nu * nu * nu / exp(x);"),
     "zeta_minus_sign": ("c->zeta_m = 0.5 * (1.0 - c->k);", "c->zeta_m = 0.5 * (1.0 + c->k);"),
     "sublayer_full_depth": ("w->dtau_s[2 * j + h] = 0.5 * d;", "w->dtau_s[2 * j + h] = d;"),
+    "toa_spectrum_at_boa": ("toa_b += wg * fu[cfg->isothermal ? L : 2 * L];", "toa_b += wg * fu[0];"),
+    "explicit_edge_shift": ("lo = cfg->wn_edges[b];", "lo = cfg->wn_edges[b > 0 ? b - 1 : 0];"),
 }
 
 
@@ -47,6 +50,8 @@ def battery(orc):
         ("conservation", lambda: pins.test_pure_scattering_conserves_net_flux(orc, False)),
         ("batch", lambda: pins.test_batch_matches_ode_and_quadrature(orc, False)),
         ("telescoping", lambda: pins.test_heating_telescopes_to_boundary_net_fluxes(orc)),
+        ("toa_opaque", lambda: spec.test_opaque_isothermal_column_emits_pi_B_per_bin(orc, False)),
+        ("toa_transparent", lambda: spec.test_transparent_column_passes_the_boa_spectrum(orc)),
     ]
     failed = []
     for name, fn in checks:
