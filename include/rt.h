@@ -96,6 +96,10 @@ typedef struct {
                                     g-points share a bin) or RT_STAGE_DIRECT
                                     (read from the per-column table in device
                                     memory; for few g-points per bin) */
+    int32_t systems_per_lane;    /* FP32 form: systems each GPU lane carries, 1 or 2
+                                    (0 = 2: two systems share the paired FP32
+                                    instructions of sm_100+); results differ only
+                                    in rounding */
     int32_t n_edges;             /* 0: NB bins of equal width on [wn_min, wn_max];
                                     > 1: explicit bin edges, every column then has
                                     n_edges - 1 bins (e.g. the R = 500 sampling of

@@ -93,7 +93,7 @@ struct Plan {
     int64_t n_units = 0;
     int Lmax = 0, NBmax = 0;
     // launch
-    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0;
+    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, ns = 1;
     size_t smem = 0;
     int64_t n_slots = 0;
     // workspace layout (bytes); the plan blob is int32 arrays then int64 arrays
@@ -120,6 +120,8 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
             return fail(h, RT_EINVAL, "column %d: n_bins %d but the k-table has %d", i, P.nb[i], h->kt_NB);
     }
     P.kt = kt;
+    P.ns = fp64 ? 1 : (cfg.systems_per_lane == 1 ? 1 : 2);
+    const int spu = 32 * P.ns;                    // systems per FP32 work unit
     const int64_t *gath[5] = {c->cube_offset, c->center_offset, c->iface_offset, c->bin_offset, c->col_index};
     for (int g = 0; g < 5; ++g)
         if (gath[g])
@@ -148,7 +150,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
         P.planck_off[i] = planck;
         planck += (int64_t)(2 * P.nl[i] + 1) * P.nb[i];
         const int64_t S = (int64_t)P.nb[i] * cfg.n_g;
-        P.col_units[i] = (int32_t)((S + 31) / 32);
+        P.col_units[i] = (int32_t)((S + spu - 1) / spu);
         cube += (int64_t)P.nl[i] * S;
         lay += P.nl[i];
         bins += P.nb[i];
@@ -191,7 +193,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
                 occ = rt::occupancy(1, P.block, P.smem);
                 if (occ > 0) P.grid = (int)std::min<int64_t>(n, (int64_t)occ * h->sm_count);
             } else {
-                P.nbw = rt::bins_per_chunk(32, cfg.n_g, P.NBmax);
+                P.nbw = rt::bins_per_chunk(spu, cfg.n_g, P.NBmax);
                 // staging B per warp pays off when several lanes share a bin;
                 // with few g-points per bin it only costs shared memory
                 // (occupancy), so the lanes read the table directly
@@ -199,7 +201,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
                            (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g < 4);
                 P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct);
                 P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct);
-                occ = rt::occupancy(0, P.block, P.smem);
+                occ = rt::occupancy(0, P.block, P.smem, P.ns);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
@@ -215,7 +217,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
                 return fail(h, RT_EINVAL, "no launch shape fits shared memory (L=%d, NB=%d)", P.Lmax, P.NBmax);
             P.block -= 32;
         }
-        P.n_slots = (int64_t)P.grid * P.block;
+        P.n_slots = (int64_t)P.grid * P.block * P.ns;
     }
     P.i32_count = 4 * (size_t)n + 2 * (size_t)P.n_units;
     P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
@@ -304,6 +306,7 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
         return RT_EINVAL;
     if (cfg->ctas_per_sm < 0) return RT_EINVAL;
     if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_DIRECT) return RT_EINVAL;
+    if (cfg->systems_per_lane < 0 || cfg->systems_per_lane > 2) return RT_EINVAL;
     if (cfg->n_edges < 0 || cfg->n_edges == 1 || (cfg->n_edges > 1 && !cfg->wn_edges)) return RT_EINVAL;
     for (int i = 0; i < cfg->n_edges; ++i) {
         if (!(cfg->wn_edges[i] >= 0.0)) return RT_EINVAL;
@@ -572,6 +575,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.warp_floats = P.warp_floats;
         kp.nbw = P.nbw;
         kp.direct = P.direct;
+        kp.ns = P.ns;
         kp.planck32 = d_planck;
         kp.planck_off = d_pkoff;
         kp.fs32 = d_fs;

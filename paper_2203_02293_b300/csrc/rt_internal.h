@@ -58,6 +58,7 @@ struct KParams {
     const float *g_w32;          // [n_g] Gauss weights in FP32
     int32_t nbw;                 // bins one warp's 32 systems can touch
     int32_t direct;              // 1: read B from planck32 directly (no staging)
+    int32_t ns;                  // systems per lane (1 or 2; 0 counts as 1)
     // scheduling and counters
     int32_t *counter;
     unsigned long long *stats;
@@ -92,7 +93,7 @@ int bins_per_chunk(int block, int n_g, int max_bins);
 // One-time per-device set-up (dynamic shared-memory limits).
 cudaError_t init_kernels();
 // Resident CTAs per SM for a launch shape (0 if it does not fit).
-int occupancy(int precision_fp64, int block, size_t smem);
+int occupancy(int precision_fp64, int block, size_t smem, int ns = 1);
 // Launch the fused column kernels.  Return cudaGetLastError().
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);

@@ -30,6 +30,7 @@
 //   fp64_columns  -- FP64 with the paper's literal formulas, scalar Thomas on
 //                    every level (sub-layers not merged).
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include <cmath>
 #include <cstdint>
@@ -197,9 +198,7 @@ __device__ double planck_bin_d(double T, double wlo, double whi) {
 // ---------------------------------------------------------------------
 struct Counters {
     unsigned res, etau, eclamp, inv, nonfinite, fp64;
-    unsigned on;   // 1 while the thread works on a real system, 0 on padding lanes
-    // FP32 form: raw per-system counts, added (masked by `on`) once per system
-    unsigned s_inv, s_ecl, s_etau;
+    unsigned on;   // FP64 path: 1 while the thread works on a real system, 0 on padding lanes
 };
 
 __device__ __forceinline__ void flush_counters(const Counters &cn, unsigned long long *stats) {
@@ -259,162 +258,275 @@ __device__ __noinline__ double resonance_D_fp64(float w0f, float g0f, double mu,
 // Two identical sub-layers (half the optical depth each) are merged into one
 // layer with T_L = t^2/(1-r^2), R_L = r (1 + T_L) and combined sources.
 // ---------------------------------------------------------------------
+// ---------------------------------------------------------------------
+// Values of one system (float) or of two systems carried by one lane (V2).
+// V2 arithmetic maps onto sm_100+'s paired FP32 instructions (FFMA2, FMUL2,
+// FADD2: two IEEE-rounded operations per instruction), so a lane that
+// carries two systems issues about half as many FP32 instructions per
+// system.  MUFU operations, compares and selects stay per component.
+// ---------------------------------------------------------------------
+// Stored as a float2 so that the pair stays in an aligned register pair,
+// which the paired instructions read and write.
+struct V2 {
+    float2 v;
+    __device__ __forceinline__ V2() {}
+    __device__ __forceinline__ V2(float a) : v(make_float2(a, a)) {}
+    __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit V2(float2 a) : v(a) {}
+};
+struct M2 {
+    bool x, y;
+};
+struct U2 {
+    unsigned x, y;
+};
+
+__device__ __forceinline__ float2 f2(V2 a) { return a.v; }
+__device__ __forceinline__ V2 v2(float2 a) { return V2(a); }
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return v2(__fadd2_rn(f2(a), f2(b))); }
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return v2(__fmul2_rn(f2(a), f2(b))); }
+// a - b as a + (-1) b: one rounding, like the scalar subtraction
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return v2(__ffma2_rn(f2(b), make_float2(-1.f, -1.f), f2(a))); }
+__device__ __forceinline__ V2 operator-(V2 a) { return V2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ M2 operator<(V2 a, V2 b) { return M2{a.v.x < b.v.x, a.v.y < b.v.y}; }
+__device__ __forceinline__ M2 operator<=(V2 a, V2 b) { return M2{a.v.x <= b.v.x, a.v.y <= b.v.y}; }
+__device__ __forceinline__ M2 operator>(V2 a, V2 b) { return M2{a.v.x > b.v.x, a.v.y > b.v.y}; }
+__device__ __forceinline__ M2 operator>=(V2 a, V2 b) { return M2{a.v.x >= b.v.x, a.v.y >= b.v.y}; }
+__device__ __forceinline__ M2 operator==(V2 a, V2 b) { return M2{a.v.x == b.v.x, a.v.y == b.v.y}; }
+__device__ __forceinline__ M2 operator&(M2 a, M2 b) { return M2{a.x && b.x, a.y && b.y}; }
+__device__ __forceinline__ M2 operator&(M2 a, bool b) { return M2{a.x && b, a.y && b}; }
+__device__ __forceinline__ M2 operator!(M2 a) { return M2{!a.x, !a.y}; }
+
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c) { return v2(__ffma2_rn(f2(a), f2(b), f2(c))); }
+__device__ __forceinline__ float vrcp(float a) { return frcp(a); }
+__device__ __forceinline__ V2 vrcp(V2 a) { return V2(frcp(a.v.x), frcp(a.v.y)); }
+__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ V2 vrsqrt(V2 a) { return V2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
+__device__ __forceinline__ float vexp(float a) { return fexp(a); }
+__device__ __forceinline__ V2 vexp(V2 a) { return V2(fexp(a.v.x), fexp(a.v.y)); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ V2 vabs(V2 a) { return V2(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ float vsel(bool m, float a, float b) { return m ? a : b; }
+__device__ __forceinline__ V2 vsel(M2 m, V2 a, V2 b) { return V2(m.x ? a.v.x : b.v.x, m.y ? a.v.y : b.v.y); }
+__device__ __forceinline__ bool vany(bool m) { return m; }
+__device__ __forceinline__ bool vany(M2 m) { return m.x || m.y; }
+__device__ __forceinline__ void vcount(unsigned &c, bool m) { c += m ? 1u : 0u; }
+__device__ __forceinline__ void vcount(U2 &c, M2 m) {
+    c.x += m.x ? 1u : 0u;
+    c.y += m.y ? 1u : 0u;
+}
+// per-component counts added only for systems that are real (`on`)
+__device__ __forceinline__ unsigned vmasked(unsigned c, bool on) { return on ? c : 0u; }
+__device__ __forceinline__ unsigned vmasked(U2 c, M2 on) { return (on.x ? c.x : 0u) + (on.y ? c.y : 0u); }
+__device__ __forceinline__ unsigned vmasked(bool m, bool on) { return (m && on) ? 1u : 0u; }
+__device__ __forceinline__ unsigned vmasked(M2 m, M2 on) { return (m.x && on.x ? 1u : 0u) + (m.y && on.y ? 1u : 0u); }
+
+template <class V> struct VTraits;
+template <> struct VTraits<float> {
+    using M = bool;
+    using C = unsigned;
+};
+template <> struct VTraits<V2> {
+    using M = M2;
+    using C = U2;
+};
+
+template <class V>
+__device__ __forceinline__ V u_series_v(V x) {
+    V p = V(-1.f / 40320.f);
+    p = vfma(p, x, V(1.f / 5040.f));
+    p = vfma(p, x, V(-1.f / 720.f));
+    p = vfma(p, x, V(1.f / 120.f));
+    p = vfma(p, x, V(-1.f / 24.f));
+    p = vfma(p, x, V(1.f / 6.f));
+    p = vfma(p, x, V(-0.5f));
+    return vfma(p, x, V(1.f));
+}
+
+// Per-system branch counts of one unit (added to the CTA counters for the
+// real systems once the unit is done).
+template <class V>
+struct SysCounts {
+    typename VTraits<V>::C inv, ecl, etau;
+};
+
+// The paper's resonance switch for the systems whose FP32 |D| is near 1e-5:
+// decide |D| < 1e-5 in FP64, and (paper mode) replace the beam source terms
+// by the literal G+- of Eq. B8 with D := 2 mu* = -2 mu.
+__device__ __forceinline__ void resonance_fix(bool near, bool on, float w0, float g0, float mu, float imu,
+                                              double mu_d, float A, float iq, float G0h, float omtr, float r,
+                                              float t, float omm, float m, const KParams &kp, Counters &cn,
+                                              float &bu, float &bd) {
+    bool sw = false;
+    if (near) {
+        cn.fp64 += on ? 1u : 0u;
+        const double D = resonance_D_fp64(w0, g0, mu_d, kp.improved, kp.e_clamp);
+        if (fabs(D) < 1e-5) {
+            cn.res += on ? 1u : 0u;
+            sw = kp.resonance_paper != 0;
+        }
+    }
+    if (sw) {
+        const float c1 = 0.5f * iq;
+        const float lead = -0.5f * A * imu;
+        const float Gp = 0.5f * lead * (c1 - mu) + G0h;
+        const float Gm = -0.5f * lead * (c1 + mu) - G0h;
+        bu = -Gp * (omtr + r + t * omm) + r * Gm;     // Gp (t m - 1) + r Gm
+        bd = Gm * (omm - omtr - r) + r * Gp * m;      // Gm (t - m) + r Gp m
+    }
+}
+__device__ __forceinline__ void resonance_fix(M2 near, M2 on, V2 w0, V2 g0, float mu, float imu, double mu_d,
+                                              V2 A, V2 iq, V2 G0h, V2 omtr, V2 r, V2 t, V2 omm, V2 m,
+                                              const KParams &kp, Counters &cn, V2 &bu, V2 &bd) {
+    resonance_fix(near.x, on.x, w0.v.x, g0.v.x, mu, imu, mu_d, A.v.x, iq.v.x, G0h.v.x, omtr.v.x, r.v.x, t.v.x,
+                  omm.v.x, m.v.x, kp, cn, bu.v.x, bd.v.x);
+    resonance_fix(near.y, on.y, w0.v.y, g0.v.y, mu, imu, mu_d, A.v.y, iq.v.y, G0h.v.y, omtr.v.y, r.v.y, t.v.y,
+                  omm.v.y, m.v.y, kp, cn, bu.v.y, bd.v.y);
+}
+
+template <class V>
 struct Layer32 {
-    float T, R, Su, Sd, omtr, opr, mlay;
+    V T, R, Su, Sd, omtr, opr, mlay;
 };
 
 // Products are grouped by hand: float multiplication is not reassociated by
 // the compiler, and shared factors (1/h and 1/p from one reciprocal of h p,
-// 2q, w0 g0, ...) are formed once per layer.
-template <bool ISO>
-__device__ __forceinline__ Layer32 layer32(float dt, float w0, float g0, float Bt, float Bc, float Bb,
-                                           float mu, float imu, double mu_d, bool beam, float Fb,
-                                           const KParams &kp, Counters &cn) {
-    const bool valid = (dt >= 0.f) && (w0 >= 0.f) && (w0 <= 1.f) && (fabsf(g0) < 1.f);
-    cn.s_inv += valid ? 0u : 1u;
+// 2q, w0 g0, ...) are formed once per layer.  Multiply-adds are written as
+// vfma so that the scalar and the paired forms round alike.
+template <bool ISO, class V>
+__device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb, float mu, float imu,
+                                              double mu_d, bool beam, V Fb, const KParams &kp, Counters &cn,
+                                              SysCounts<V> &sc, typename VTraits<V>::M on) {
+    using M = typename VTraits<V>::M;
+    const M valid = (dt >= V(0.f)) & (w0 >= V(0.f)) & (w0 <= V(1.f)) & (vabs(g0) < V(1.f));
+    vcount(sc.inv, !valid);
     // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
-    const float wg = w0 * g0;
-    float em1 = fmaf(g0, fmaf(-0.07465f, g0, -0.1582f), fmaf(w0, fmaf(-0.05582f, w0, -0.1777f), 0.225f));
-    em1 = fmaf(0.2351f, wg, em1);
-    em1 = (kp.improved && w0 > 0.1f) ? em1 : 0.f;
-    const bool clamp = kp.e_clamp && em1 < 0.f;
-    cn.s_ecl += clamp ? 1u : 0u;
-    em1 = clamp ? 0.f : em1;
-    const float omw = 1.f - w0;
-    const float ewm = em1 + omw;                 // E - w0
-    const float q = (1.f + em1) * (1.f - wg);    // E (1 - w0 g0)
-    const float iq = frcp(q);
-    const bool cons = ewm == 0.f;                // E = w0 = 1: k = 0, Pi := pi
-    const float k = cons ? 0.f : ewm * rsqrtf(ewm * q);
-    const float piw = kPiF * frcp(ewm);
-    const float Pi = cons ? kPiF : omw * piw;
-    const float dPi = cons ? 0.f : -em1 * piw;  // Pi - pi
-    const float ip = frcp(1.f + k);
-    const float eps = (1.f - k) * ip;
-    const float dts = ISO ? dt : 0.5f * dt;
+    const V wg = w0 * g0;
+    V em1 = vfma(g0, vfma(V(-0.07465f), g0, V(-0.1582f)), vfma(w0, vfma(V(-0.05582f), w0, V(-0.1777f)), V(0.225f)));
+    em1 = vfma(V(0.2351f), wg, em1);
+    em1 = vsel((w0 > V(0.1f)) & (kp.improved != 0), em1, V(0.f));
+    const M clamp = (em1 < V(0.f)) & (kp.e_clamp != 0);
+    vcount(sc.ecl, clamp);
+    em1 = vsel(clamp, V(0.f), em1);
+    const V omw = V(1.f) - w0;
+    const V ewm = em1 + omw;                      // E - w0
+    const V q = (V(1.f) + em1) * (V(1.f) - wg);   // E (1 - w0 g0)
+    const V iq = vrcp(q);
+    const M cons = ewm == V(0.f);                 // E = w0 = 1: k = 0, Pi := pi
+    const V k = vsel(cons, V(0.f), ewm * vrsqrt(ewm * q));
+    const V piw = V(kPiF) * vrcp(ewm);
+    const V Pi = vsel(cons, V(kPiF), omw * piw);
+    const V dPi = vsel(cons, V(0.f), -em1 * piw);  // Pi - pi
+    const V ip = vrcp(V(1.f) + k);
+    const V eps = (V(1.f) - k) * ip;
+    const V dts = ISO ? dt : V(0.5f) * dt;
 
-    const float q2 = q + q;
-    const float q2d = q2 * dts;
-    const float x = q2d * k;
-    const float Tm = fexp(-x);
-    const float u = one_minus_exp_over_x(x, Tm);
-    const float qd = q2d * u;                    // (1 - T)/k
-    const float h = fmaf(Tm + Tm, ip, qd);
-    const float p = fmaf(eps, Tm, 1.f);
-    const float ihp = frcp(h * p);
-    const float ih = p * ihp, ipp = h * ihp;     // 1/h, 1/p
-    const float ipihp = ip * ihp;
-    const float t = (4.f * Tm) * (ip * ipihp);
-    const float Y = fmaf(qd, Tm, qd);            // (1 - T^2)/k = qd (1 + T)
-    const float r = (eps * ihp) * Y;
-    const float k2 = k * k;
-    const float omtr = (k2 + k2) * (qd * ip) * ipp;      // 1 - t - r
-    const float omr = omtr + t;                          // 1 - r
+    const V q2 = q + q;
+    const V q2d = q2 * dts;
+    const V x = q2d * k;
+    const V Tm = vexp(-x);
+    const V u = vsel(vabs(x) < V(0.25f), u_series_v(x), (V(1.f) - Tm) * vrcp(x));
+    const V qd = q2d * u;                         // (1 - T)/k
+    const V h = vfma(Tm + Tm, ip, qd);
+    const V p = vfma(eps, Tm, V(1.f));
+    const V ihp = vrcp(h * p);
+    const V ih = p * ihp, ipp = h * ihp;          // 1/h, 1/p
+    const V ipihp = ip * ihp;
+    const V t = (V(4.f) * Tm) * (ip * ipihp);
+    const V Y = vfma(qd, Tm, qd);                 // (1 - T^2)/k = qd (1 + T)
+    const V r = (eps * ihp) * Y;
+    const V k2 = k * k;
+    const V omtr = ((k2 + k2) * (qd * ip)) * ipp; // 1 - t - r
+    const V omr = omtr + t;                       // 1 - r
 
-    float suU, sdU, suL = 0.f, sdL = 0.f;
+    V suU, sdU, suL = V(0.f), sdL = V(0.f);
     if (!ISO) {
-        const bool fb = dts < 1e-4f;
-        cn.s_etau += fb ? 1u : 0u;
+        const M fb = dts < V(1e-4f);
+        vcount(sc.etau, fb);
         // Gradient form  su = dPi ((1-r) B1 - t B2) + G (B2 - B1),
         //                sd = dPi ((1-r) B2 - t B1) - G (B2 - B1),
         // with G = Pi 2u/((1+k) h).  The e_tau fallback (isothermal at the mean
         // B, Sec. 2.2.1) is the same expression with B1 = B2 = mean B and
         // G = pi (1 - r + t)/2, so only the inputs are selected.
-        const float pig = Pi * (2.f * u) * (ip * ih);
-        const float side = (0.5f * kPiF) * (omtr + 2.f * t);
-        const float G = fb ? side : pig;
-        const float mU = 0.5f * (Bt + Bc), mL = 0.5f * (Bc + Bb);
-        const float tU = fb ? mU : Bt, cU = fb ? mU : Bc;    // upper sub-layer ends
-        const float cL = fb ? mL : Bc, bL = fb ? mL : Bb;    // lower sub-layer ends
-        const float gU = G * (Bc - Bt), gL = G * (Bb - Bc);
-        suU = fmaf(dPi, fmaf(omr, tU, -t * cU), gU);
-        sdU = fmaf(dPi, fmaf(omr, cU, -t * tU), -gU);
-        suL = fmaf(dPi, fmaf(omr, cL, -t * bL), gL);
-        sdL = fmaf(dPi, fmaf(omr, bL, -t * cL), -gL);
+        const V pig = (Pi * (V(2.f) * u)) * (ip * ih);
+        const V side = V(0.5f * kPiF) * vfma(V(2.f), t, omtr);
+        const V G = vsel(fb, side, pig);
+        const V mU = V(0.5f) * (Bt + Bc), mL = V(0.5f) * (Bc + Bb);
+        const V tU = vsel(fb, mU, Bt), cU = vsel(fb, mU, Bc);   // upper sub-layer ends
+        const V cL = vsel(fb, mL, Bc), bL = vsel(fb, mL, Bb);   // lower sub-layer ends
+        const V gU = G * (Bc - Bt), gL = G * (Bb - Bc);
+        suU = vfma(dPi, vfma(omr, tU, -(t * cU)), gU);
+        sdU = vfma(dPi, vfma(omr, cU, -(t * tU)), -gU);
+        suL = vfma(dPi, vfma(omr, cL, -(t * bL)), gL);
+        sdL = vfma(dPi, vfma(omr, bL, -(t * cL)), -gL);
     } else {
-        const float base = dPi * Bc * omtr;
-        suU = base + kPiF * (omr * (Bc - Bt) - t * (Bc - Bb));
-        sdU = base + kPiF * (omr * (Bc - Bb) - t * (Bc - Bt));
+        const V base = (dPi * Bc) * omtr;
+        suU = vfma(V(kPiF), vfma(omr, Bc - Bt, -(t * (Bc - Bb))), base);
+        sdU = vfma(V(kPiF), vfma(omr, Bc - Bb, -(t * (Bc - Bt))), base);
     }
 
-    float m = 1.f;
+    V m = V(1.f);
     if (beam) {
-        const float dl = dts * imu;
-        m = fexp(-dl);
-        const float omm = (dl < 0.25f) ? dl * u_series(dl) : 1.f - m;   // 1 - m
-        const float q2k = q2 * k;
-        const float rho = mu * q2k;
-        const float ie2 = kp.inv_eps2;
-        const float A = w0 * fmaf(g0, ie2, q2);
-        const float G0h = wg * (0.25f * ie2) * iq;            // G0/2 of Eq. B8
-        const float r2 = r + r;
-        const float tm1r = -fmaf(t, omm, omtr + r2);           // (t m - 1) - r
-        const float rmtm = fmaf(r, m, (omtr + r) - omm);      // r m - (t - m)
+        const V dl = dts * V(imu);
+        m = vexp(-dl);
+        const V omm = vsel(dl < V(0.25f), dl * u_series_v(dl), V(1.f) - m);   // 1 - m
+        const V q2k = q2 * k;
+        const V rho = V(mu) * q2k;
+        const V ie2 = V(kp.inv_eps2);
+        const V A = w0 * vfma(g0, ie2, q2);
+        const V G0h = (wg * V(0.25f * kp.inv_eps2)) * iq;       // G0/2 of Eq. B8
+        const V r2 = r + r;
+        const V tm1r = -vfma(t, omm, omtr + r2);                // (t m - 1) - r
+        const V rmtm = vfma(r, m, (omtr + r) - omm);            // r m - (t - m)
         // stable form: the 1/D of G+- divided out (see the block comment)
-        const float omrho = 1.f - rho;
-        const float z = omrho * dl;
-        const float lam_s = (m * dl) * u_series(-z);
-        const float lam_d = (Tm - m) * frcp(omrho);
-        const float Lam = (fabsf(z) < 0.25f) ? lam_s : lam_d;
-        const float SA2 = (0.5f * A) * (ip * ipihp) * (iq * frcp(1.f + rho));   // 2 SA
-        const float tq = mu * q2;
-        const float TL = Tm * Lam;
-        float bu = fmaf(SA2, fmaf((1.f + k) * Y, 1.f, (TL + TL) * (1.f - tq)), G0h * tm1r);
-        const float cl = fmaf(Y, fmaf(tq, k2, 1.f), (1.f + tq) * fmaf(Tm, Tm, 1.f));
-        float bd = fmaf(SA2, fmaf(Lam, cl, -(Tm * (1.f - k)) * Y), G0h * rmtm);
+        const V omrho = V(1.f) - rho;
+        const V z = omrho * dl;
+        const V lam_s = (m * dl) * u_series_v(-z);
+        const V lam_d = (Tm - m) * vrcp(omrho);
+        const V Lam = vsel(vabs(z) < V(0.25f), lam_s, lam_d);
+        const V SA2 = ((V(0.5f) * A) * (ip * ipihp)) * (iq * vrcp(V(1.f) + rho));   // 2 SA
+        const V tq = V(mu) * q2;
+        const V TL = Tm * Lam;
+        V bu = vfma(SA2, vfma((V(1.f) + k), Y, (TL + TL) * (V(1.f) - tq)), G0h * tm1r);
+        const V cl = vfma(Y, vfma(tq, k2, V(1.f)), (V(1.f) + tq) * vfma(Tm, Tm, V(1.f)));
+        V bd = vfma(SA2, vfma(Lam, cl, -((Tm * (V(1.f) - k)) * Y)), G0h * rmtm);
         // resonance test of Eq. 11 (rare): the FP64 decision, and the paper's
         // switch to D := 2 mu* when |D| < 1e-5, run only if a lane needs them
-        const float D32 = fmaf(rho, rho, -1.f);
-        const bool near = fabsf(D32) < 2e-5f;
-        if (__any_sync(0xffffffffu, near)) {
-            bool sw = false;
-            if (near) {
-                cn.fp64 += cn.on;
-                const double D = resonance_D_fp64(w0, g0, mu_d, kp.improved, kp.e_clamp);
-                if (fabs(D) < 1e-5) {
-                    cn.res += cn.on;
-                    sw = kp.resonance_paper != 0;
-                }
-            }
-            if (sw) {
-                // paper: D := 2 mu* = -2 mu, literal G+- (no singularity left)
-                const float c1 = 0.5f * iq;
-                const float lead = -0.5f * A * imu;
-                const float Gp = 0.5f * lead * (c1 - mu) + G0h;
-                const float Gm = -0.5f * lead * (c1 + mu) - G0h;
-                bu = -Gp * (omtr + r + t * omm) + r * Gm;     // Gp (t m - 1) + r Gm
-                bd = Gm * (omm - omtr - r) + r * Gp * m;      // Gm (t - m) + r Gp m
-            }
+        const V D32 = vfma(rho, rho, V(-1.f));
+        const M near = vabs(D32) < V(2e-5f);
+        if (__any_sync(0xffffffffu, vany(near))) {
+            resonance_fix(near, on, w0, g0, mu, imu, mu_d, A, iq, G0h, omtr, r, t, omm, m, kp, cn, bu, bd);
         }
-        suU = fmaf(Fb, bu, suU);
-        sdU = fmaf(Fb, bd, sdU);
+        suU = vfma(Fb, bu, suU);
+        sdU = vfma(Fb, bd, sdU);
         if (!ISO) {
-            const float Fc = Fb * m;
-            suL = fmaf(Fc, bu, suL);
-            sdL = fmaf(Fc, bd, sdL);
+            const V Fc = Fb * m;
+            suL = vfma(Fc, bu, suL);
+            sdL = vfma(Fc, bd, sdL);
         }
     }
 
-    Layer32 o;
+    Layer32<V> o;
     if (ISO) {
         o.T = t;
         o.R = r;
         o.Su = suU;
         o.Sd = sdU;
         o.omtr = omtr;
-        o.opr = omtr + 2.f * t;
+        o.opr = vfma(V(2.f), t, omtr);
         o.mlay = m;
     } else {
         // merge upper (top -> centre) and lower (centre -> bottom) sub-layers
-        const float opr1 = 1.f + r;
-        const float Dr = frcp(omr * opr1);      // 1 / (1 - r^2)
-        const float tD = t * Dr;
+        const V opr1 = V(1.f) + r;
+        const V Dr = vrcp(omr * opr1);            // 1 / (1 - r^2)
+        const V tD = t * Dr;
         o.T = t * tD;
-        o.R = fmaf(r, o.T, r);
-        o.Su = fmaf(tD, fmaf(r, sdU, suL), suU);
-        o.Sd = fmaf(tD, fmaf(r, suL, sdU), sdL);
-        o.omtr = (omtr * (omtr + 2.f * t)) * (opr1 * Dr);   // (1-r-t)(1-r+t)/(1-r)
-        o.opr = fmaf(omr, o.T, omr);
+        o.R = vfma(r, o.T, r);
+        o.Su = vfma(tD, vfma(r, sdU, suL), suU);
+        o.Sd = vfma(tD, vfma(r, suL, sdU), sdL);
+        o.omtr = (omtr * vfma(V(2.f), t, omtr)) * (opr1 * Dr);   // (1-r-t)(1-r+t)/(1-r)
+        o.opr = vfma(omr, o.T, omr);
         o.mlay = m * m;
     }
     return o;
@@ -615,58 +727,51 @@ constexpr float kGL2x = 0.57735026918962576f;
 __constant__ float kGL4x[2] = {0.86113631159405258f, 0.33998104358485626f};
 __constant__ float kGL4w[2] = {0.34785484513745386f, 0.65214515486254614f};
 
-__device__ __forceinline__ void planck_level_warp(float T, int NB, float dwn, float wmin,
-                                                  const float *edges, const float *dnu, float scale,
-                                                  float *dst, int lane) {
+// B of one level for the warp's chunk of 31 bins [b0, b0 + 31): lane e
+// holds edge b0 + e at x = a wn (x1: the next edge, from lane e + 1).
+__device__ __forceinline__ float planck_chunk_level(float T, float scale, float wn, float dnu_b, bool inb,
+                                                    int lane) {
     const float a = (T > 0.f) ? (float)(kC2 * 100.0) * frcp(T) : 0.f;
     const float T2 = T * T;
     const float pref = (float)kPlanckK * (T2 * T2) * scale;
-    for (int b0 = 0; b0 < NB; b0 += 31) {
-        const int e = b0 + lane;
-        const float wn = edges ? __ldg(edges + min(e, NB)) : fmaf((float)e, dwn, wmin);
-        const float x = a * wn;
-        const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
-        const int bin = e;
-        const bool narrow = !(lane < 31 && bin < NB) || (x1 - x < kNarrowBin);
-        // the edge series are needed only when some bin of this pass is wide
-        float v = 0.f;
-        if (!__all_sync(0xffffffffu, narrow)) v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
-        const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
-        if (lane < 31 && bin < NB) {
-            float d;
-            if (narrow) {
-                // narrow bin (e.g. R = 500): the edge difference would lose
-                // the digits that the edges' own FP32 rounding carries, so
-                // integrate x^3/(e^x - 1) over the bin by Gauss-Legendre (2
-                // or 4 points), the width formed from the FP64 edges before
-                // rounding (no FP64 arithmetic here: it is slow on this part)
-                const float dnu_b = edges ? __ldg(dnu + bin) : dwn;
-                const float hh = 0.5f * a * dnu_b;        // half width in x
-                const float xm = x + hh;
-                float acc;
-                if (hh < 0.5f * kTwoPointBin && hh < 0.01f * xm) {
-                    // 2 points: below 2e-8 relative for these widths
-                    acc = planck_integrand_f(fmaf(-hh, kGL2x, xm)) + planck_integrand_f(fmaf(hh, kGL2x, xm));
-                } else {
-                    acc = 0.f;
+    const float x = a * wn;
+    const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
+    const bool narrow = !inb || (x1 - x < kNarrowBin);
+    // the edge series are needed only when some bin of this chunk is wide
+    float v = 0.f;
+    if (!__all_sync(0xffffffffu, narrow)) v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
+    const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
+    float d;
+    if (narrow) {
+        // narrow bin (e.g. R = 500): the edge difference would lose the
+        // digits that the edges' own FP32 rounding carries, so integrate
+        // x^3/(e^x - 1) over the bin by Gauss-Legendre (2 or 4 points), the
+        // width formed from the FP64 edges before rounding (no FP64
+        // arithmetic here: it is slow on this part)
+        const float hh = 0.5f * a * dnu_b;        // half width in x
+        const float xm = x + hh;
+        float acc;
+        if (hh < 0.5f * kTwoPointBin && hh < 0.01f * xm) {
+            // 2 points: below 2e-8 relative for these widths
+            acc = planck_integrand_f(fmaf(-hh, kGL2x, xm)) + planck_integrand_f(fmaf(hh, kGL2x, xm));
+        } else {
+            acc = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float t = (k < 2) ? -kGL4x[k] : kGL4x[3 - k];
-                        const float xk = fmaf(hh, t, xm);
-                        acc = fmaf(kGL4w[k < 2 ? k : 3 - k], planck_integrand_f(xk), acc);
-                    }
-                }
-                d = hh * acc;
-            } else if (x >= 2.f) {
-                d = v - v1;
-            } else if (x1 <= 2.f) {
-                d = v1 - v;
-            } else {
-                d = ((float)kPi4Over15 - v) - v1;
+            for (int k = 0; k < 4; ++k) {
+                const float t = (k < 2) ? -kGL4x[k] : kGL4x[3 - k];
+                const float xk = fmaf(hh, t, xm);
+                acc = fmaf(kGL4w[k < 2 ? k : 3 - k], planck_integrand_f(xk), acc);
             }
-            dst[bin] = (T > 0.f) ? pref * d : 0.f;
         }
+        d = hh * acc;
+    } else if (x >= 2.f) {
+        d = v - v1;
+    } else if (x1 <= 2.f) {
+        d = v1 - v;
+    } else {
+        d = ((float)kPi4Over15 - v) - v1;
     }
+    return (T > 0.f) ? pref * d : 0.f;
 }
 
 // ---------------------------------------------------------------------
@@ -736,8 +841,13 @@ __device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int 
     return c;
 }
 
+// One CTA per column (grid-stride).  Warp tasks are (chunk of 31 bins, run
+// of levels): the chunk's edges are loaded once and the levels' B computed
+// from the shared temperatures; the runs are short enough that every warp
+// has work when a column has few bins.  Level 2L+1 stands for T_int (F_BOA =
+// pi B(T_int), Eq. 10).
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
-    extern __shared__ float sT[];                 // [2 Lmax + 1] temperatures of one column
+    extern __shared__ float sT[];                 // [2 Lmax + 2] temperatures of one column, then T_int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
         const int L = kp.n_layers[c], NB = kp.n_bins[c];
@@ -747,26 +857,39 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         const float wmin = (float)kp.wn_min;
         const int nlev = 2 * L + 1;
         __syncthreads();                          // previous column done with sT
-        for (int lev = threadIdx.x; lev < nlev; lev += blockDim.x)
-            sT[lev] = (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
+        for (int lev = threadIdx.x; lev <= nlev; lev += blockDim.x)
+            sT[lev] = lev == nlev ? (float)kp.T_int
+                                  : (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
         if (kp.kt_lk)
             for (int l = threadIdx.x; l < L; l += blockDim.x)
                 kp.kt_lay[kp.lay_off[c] + l] =
                     kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], NB * kp.n_g);
+        if (warp == 0) {
+            for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
+            if (lane == 0) {
+                const double mu = kp.mu_star[kp.mu_idx[c]];
+                kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
+            }
+        }
         __syncthreads();
-        // levels 0..2L, then one extra task for the per-bin and per-column data
-        for (int lev = warp; lev <= nlev; lev += nw) {
-            if (lev < nlev) {
-                planck_level_warp(sT[lev], NB, dwn, wmin, kp.edges32, kp.dnu32, 1.f, B + (long long)lev * NB,
-                                  lane);
-            } else {
-                planck_level_warp((float)kp.T_int, NB, dwn, wmin, kp.edges32, kp.dnu32, kPiF, kp.fboa32 + b0,
-                                  lane);
-                for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
-                if (lane == 0) {
-                    const double mu = kp.mu_star[kp.mu_idx[c]];
-                    kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f,
-                                             mu > 0.0 ? 1.f : 0.f, 0.f);
+        const int nchunk = (NB + 30) / 31;
+        const int nl = nlev + 1;                  // levels including T_int
+        int run = (int)(((long long)nl * nchunk + nw - 1) / nw);
+        run = run < nl ? run : nl;
+        const int nrun = (nl + run - 1) / run;
+        for (int task = warp; task < nchunk * nrun; task += nw) {
+            const int ch = task % nchunk, r0 = (task / nchunk) * run;
+            const int e = ch * 31 + lane, bin = e;
+            const bool inb = lane < 31 && bin < NB;
+            const float wn = kp.edges32 ? __ldg(kp.edges32 + min(e, NB)) : fmaf((float)e, dwn, wmin);
+            const float dnu_b = kp.edges32 ? __ldg(kp.dnu32 + min(bin, NB - 1)) : dwn;
+            const int r1 = min(r0 + run, nl);
+            for (int lev = r0; lev < r1; ++lev) {
+                const bool tint = lev == nlev;
+                const float v = planck_chunk_level(sT[lev], tint ? kPiF : 1.f, wn, dnu_b, inb, lane);
+                if (inb) {
+                    if (tint) kp.fboa32[b0 + bin] = v;
+                    else B[(long long)lev * NB + bin] = v;
                 }
             }
         }
@@ -808,8 +931,30 @@ __device__ __forceinline__ float ldB(const float *p) {
     else return *p;
 }
 
-template <bool ISO, bool DIRECT, bool KT>
-__global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
+// Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
+// back.  `after` is a value loaded from that line: the compare that reads it
+// makes the discard issue only once the load has returned.
+__device__ __forceinline__ void discard_l2_after(const float4 *p, float after) {
+    asm volatile(
+        "{\n\t.reg .pred d;\n\tsetp.ne.f32 d, %1, %1;\n\tdiscard.global.L2 [%0], 128;\n\t}" ::"l"(p),
+        "f"(after)
+        : "memory");
+}
+
+// Component access for per-system values (one system per lane: float; two:
+// V2) and per-system loads.
+__device__ __forceinline__ float &cmp(float &v, int) { return v; }
+__device__ __forceinline__ float &cmp(V2 &v, int i) { return i ? v.v.y : v.v.x; }
+__device__ __forceinline__ float hsum(float v) { return v; }
+__device__ __forceinline__ float hsum(V2 v) { return v.v.x + v.v.y; }
+__device__ __forceinline__ bool &cmpm(bool &m, int) { return m; }
+__device__ __forceinline__ bool &cmpm(M2 &m, int i) { return i ? m.y : m.x; }
+
+template <bool ISO, bool DIRECT, bool KT, int NS>
+__global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KParams kp) {
+    using V = typename std::conditional<NS == 2, V2, float>::type;
+    using M = typename VTraits<V>::M;
+    constexpr int SPU = 32 * NS;                   // systems per work unit
     extern __shared__ __align__(16) float smem32[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -820,9 +965,11 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
     float *sFs = wsm + (DIRECT ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [16][2][33]
+    // scratch slots: component i of this thread at slot + i * (threads in the grid)
     const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
     const long long sstride = kp.n_slots;
-    Counters cn = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cn = {0, 0, 0, 0, 0, 0, 0};
 
     for (;;) {
         int unit = 0;
@@ -838,9 +985,9 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
         const float mu = cf.x, imu = cf.y;
         const double mu_d = kp.mu_star[kp.mu_idx[c]];   // only for the rare FP64 resonance test
         const bool beam = cf.z != 0.f;
-        const int s0 = ku * 32;
+        const int s0 = ku * SPU;
         const int b_lo = s0 / NG;
-        const int nbc = min(NB - 1, (s0 + 31) / NG) - b_lo + 1;
+        const int nbc = min(NB - 1, (s0 + SPU - 1) / NG) - b_lo + 1;
 
         // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
         {
@@ -852,139 +999,195 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
                     sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
                 }
             }
-            if (lane < nbc) {
-                sFs[lane] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + lane);
-                sFB[lane] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + lane);
+            for (int j = lane; j < nbc; j += 32) {
+                sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
+                sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
             }
         }
         __syncwarp();
 
-        // padding lanes of a column's last unit repeat system s0 with zero
-        // weight, so the loops below need no per-lane predicates
-        const bool active = s0 + lane < S;
-        const int s = active ? s0 + lane : s0;
-        cn.on = active ? 1u : 0u;
-        cn.s_inv = cn.s_ecl = cn.s_etau = 0u;
-        const int b = s / NG;
-        const int bb = b - b_lo;
-        const float wg = active ? kp.g_w32[s - b * NG] : 0.f;
+        // component i of this lane is system s0 + 32 i + lane; padding
+        // systems of a column's last unit repeat system s0 with zero weight,
+        // so the loops below need no per-lane predicates
+        M on;
+        int sI[NS], bI[NS];
+        V wg, Fb, Bt, Bc, Bb;
+        const float *Bp[NS];
         const int bst = DIRECT ? NB : nbc;         // level stride of Bp
-        const float *Bp = DIRECT ? kp.planck32 + kp.planck_off[c] + b : sB + bb;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const bool act = s0 + 32 * i + lane < S;
+            cmpm(on, i) = act;
+            sI[i] = act ? s0 + 32 * i + lane : s0;
+            bI[i] = sI[i] / NG;
+            cmp(wg, i) = act ? kp.g_w32[sI[i] - bI[i] * NG] : 0.f;
+            Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo);
+            cmp(Fb, i) = beam ? mu * sFs[bI[i] - b_lo] : 0.f;
+            // the B of a layer's bottom interface is carried as the next layer's top
+            cmp(Bt, i) = ldB<DIRECT>(Bp[i]);
+            cmp(Bc, i) = ldB<DIRECT>(Bp[i] + bst);
+            cmp(Bb, i) = ldB<DIRECT>(Bp[i] + 2 * bst);
+        }
+        SysCounts<V> sc;
+        sc.inv = sc.ecl = sc.etau = typename VTraits<V>::C{};
 
-        // forward elimination, TOA -> BOA, departure variables; the B of a
-        // layer's bottom interface is carried as the next layer's top
-        float Bt = ldB<DIRECT>(Bp), Bc = ldB<DIRECT>(Bp + bst), Bb = ldB<DIRECT>(Bp + 2 * bst);
-        float al = 1.f;                                      // alpha' = 1 - a'
-        float bl = (float)kp.F_toa - kPiF * Bt;              // b' at the TOA
-        float Fb = beam ? mu * sFs[bb] : 0.f;
+        // forward elimination, TOA -> BOA, departure variables
+        V al = V(1.f);                                       // alpha' = 1 - a'
+        V bl = vfma(V(-kPiF), Bt, V((float)kp.F_toa));       // b' at the TOA
         // optics: read from the cubes, or (KT) from the k-table corners of
         // the layer's grid cell, fetched one layer ahead
-        const float *pd = nullptr, *pw = nullptr, *pg = nullptr;
-        float nd = 0.f, nw = 0.f, ng = 0.f;
+        V nd = V(0.f), nw = V(0.f), ng = V(0.f);
+        const float *pd[NS], *pw[NS], *pg[NS];
         const float4 *klay = nullptr;
-        float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next, kb = kl_next;
-        Corners kc = {0.f, 0.f, 0.f, 0.f};
+        float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next;
+        float4 kb[NS];
+        Corners kc[NS];
         if constexpr (KT) {
             klay = kp.kt_lay + kp.lay_off[c];
-            kb = __ldg(kp.kt_bin + b);
             kl_next = klay[0];
             kl_after = L > 1 ? klay[1] : kl_next;
-            kc = kt_corners(kp, kl_next, S, s);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                kb[i] = __ldg(kp.kt_bin + bI[i]);
+                kc[i] = kt_corners(kp, kl_next, S, sI[i]);
+            }
         } else {
-            pd = kp.dtau + cube0 + s;
-            pw = kp.w0 + cube0 + s;
-            pg = kp.g0 + cube0 + s;
-            nd = __ldcs(pd);
-            nw = __ldcs(pw);
-            ng = __ldcs(pg);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const long long e = cube0 + sI[i];
+                pd[i] = kp.dtau + e;
+                pw[i] = kp.w0 + e;
+                pg[i] = kp.g0 + e;
+                cmp(nd, i) = __ldcs(pd[i]);
+                cmp(nw, i) = __ldcs(pw[i]);
+                cmp(ng, i) = __ldcs(pg[i]);
+            }
         }
         float4 *sp = kp.scr32 + slot;
         for (int l = 0; l < L; ++l) {
-            float dt, w0, g0;
-            float nBc = 0.f, nBb = 0.f;
+            V dt, w0, g0;
+            V nBc = V(0.f), nBb = V(0.f);
             if constexpr (KT) {
-                const Corners cur = kc;
                 const float4 kl = kl_next;
+                Corners cur[NS];
+#pragma unroll
+                for (int i = 0; i < NS; ++i) cur[i] = kc[i];
                 if (l + 1 < L) {                     // prefetch the next layer's corners
                     kl_next = kl_after;
-                    kc = kt_corners(kp, kl_next, S, s);
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) kc[i] = kt_corners(kp, kl_next, S, sI[i]);
                     if (l + 2 < L) kl_after = klay[l + 2];
-                    nBc = ldB<DIRECT>(Bp + 3 * bst);
-                    nBb = ldB<DIRECT>(Bp + 4 * bst);
                 }
-                const Optics o = kt_mix(cur.k00, cur.k01, cur.k10, cur.k11, kl, kb);
-                dt = o.dt;
-                w0 = o.w0;
-                g0 = o.g0;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const Optics o = kt_mix(cur[i].k00, cur[i].k01, cur[i].k10, cur[i].k11, kl, kb[i]);
+                    cmp(dt, i) = o.dt;
+                    cmp(w0, i) = o.w0;
+                    cmp(g0, i) = o.g0;
+                }
             } else {
                 dt = nd;
                 w0 = nw;
                 g0 = ng;
                 if (l + 1 < L) {                     // prefetch the next layer
-                    pd += S; pw += S; pg += S;
-                    nd = __ldcs(pd);
-                    nw = __ldcs(pw);
-                    ng = __ldcs(pg);
-                    nBc = ldB<DIRECT>(Bp + 3 * bst);
-                    nBb = ldB<DIRECT>(Bp + 4 * bst);
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) {
+                        pd[i] += S;
+                        pw[i] += S;
+                        pg[i] += S;
+                        cmp(nd, i) = __ldcs(pd[i]);
+                        cmp(nw, i) = __ldcs(pw[i]);
+                        cmp(ng, i) = __ldcs(pg[i]);
+                    }
+                }
+
+            }
+            if (l + 1 < L) {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    cmp(nBc, i) = ldB<DIRECT>(Bp[i] + 3 * bst);
+                    cmp(nBb, i) = ldB<DIRECT>(Bp[i] + 4 * bst);
                 }
             }
-            const Layer32 ly = layer32<ISO>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn);
-            Bp += 2 * bst;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) Bp[i] += 2 * bst;   // level 2 (l + 1)
+            const Layer32<V> ly = layer32<ISO, V>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
             Bt = Bb;
             Bc = nBc;
             Bb = nBb;
-            const float omr = ly.omtr + ly.T;                // 1 - R
-            const float ipv = frcp(fmaf(ly.R, al, omr));     // 1 / (1 - R a')
-            float4 st;
-            st.x = ly.T * ipv;                               // P
-            st.y = fmaf(ly.R, bl, ly.Su) * ipv;              // Q
-            st.z = al;                                       // alpha' at interface l
-            st.w = bl + Fb;                                  // e = b' + F_beam
-            __stcg(sp, st);
+            const V omr = ly.omtr + ly.T;                      // 1 - R
+            const V ipv = vrcp(vfma(ly.R, al, omr));           // 1 / (1 - R a')
+            const V P = ly.T * ipv;
+            const V Qv = vfma(ly.R, bl, ly.Su) * ipv;
+            const V eb = bl + Fb;                              // b' + F_beam
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                V Pc = P, Qc = Qv, ac = al, ec = eb;
+                __stcg(sp + i * gthreads, make_float4(cmp(Pc, i), cmp(Qc, i), cmp(ac, i), cmp(ec, i)));
+            }
             sp += sstride;
-            const float al_n = fmaf(al, fmaf(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
-            const float bl_n = ly.Sd + ly.T * fmaf(1.f - al, ly.Su, bl) * ipv;
+            const V al_n = vfma(al, vfma(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
+            const V bl_n = vfma(ly.T * vfma(V(1.f) - al, ly.Su, bl), ipv, ly.Sd);
             al = al_n;
             bl = bl_n;
-            Fb *= ly.mlay;
+            Fb = Fb * ly.mlay;
         }
 
-        if (active) {
-            cn.inv += cn.s_inv;
-            cn.eclamp += cn.s_ecl;
-            cn.etau += (ISO ? 1u : 2u) * cn.s_etau;
-        }
+        cn.inv += vmasked(sc.inv, on);
+        cn.eclamp += vmasked(sc.ecl, on);
+        cn.etau += (ISO ? 1u : 2u) * vmasked(sc.etau, on);
         // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b';
         // back-substitution to the TOA; interface sums through the transpose
-        const float FBOA = sFB[bb];
-        float uu = (FBOA + Fb + bl) * frcp(al);
-        bool bad = !isfinite(uu);   // NaN and Inf propagate up the substitution
+        V FBOA;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) cmp(FBOA, i) = sFB[bI[i] - b_lo];
+        V uu = ((FBOA + Fb) + bl) * vrcp(al);
+        bool bad[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) bad[i] = !isfinite(cmp(uu, i));   // NaN and Inf propagate upwards
         float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
-        // Bp points at level 2L (the BOA interface), whose B is Bt
-        tb[lane] = wg * fmaf(kPiF, Bt, uu);
-        float nBi = ldB<DIRECT>(Bp - 2 * bst);     // B one interface up
-        tb[33 + lane] = wg * FBOA;
+        // Bt holds B at level 2L (the BOA interface)
+        tb[lane] = hsum(wg * vfma(V(kPiF), Bt, uu));
+        tb[33 + lane] = hsum(wg * FBOA);
+        V nBi;                   // Bp is at level 2L; prefetch one interface up
+#pragma unroll
+        for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldB<DIRECT>(Bp[i] - 2 * bst);
         int gi = 1;              // slots used in the current group of 16 interfaces
         int gtop = L;            // interface held in slot 0 of the group
         sp -= sstride;           // interface L-1
-        float4 nst = __ldcg(sp);
+        float4 nst[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) nst[i] = __ldcg(sp + i * gthreads);
         for (int i = L - 1; i >= -1; --i) {
             if (i >= 0) {
-                const float4 st = nst;
+                V Pv, Qq, av, ev;
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    cmp(Pv, j) = nst[j].x;
+                    cmp(Qq, j) = nst[j].y;
+                    cmp(av, j) = nst[j].z;
+                    cmp(ev, j) = nst[j].w;
+                    // this level's scratch is dead once read: drop its L2
+                    // lines (one per 8 lanes) so they are not written back
+                    if ((lane & 7) == 0) discard_l2_after(sp + j * gthreads, nst[j].x);
+                }
+                const V Bi = nBi;
+#pragma unroll
+                for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
                 if (i > 0) {
                     sp -= sstride;
-                    nst = __ldcg(sp);
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        nst[j] = __ldcg(sp + j * gthreads);
+                        cmp(nBi, j) = ldB<DIRECT>(Bp[j] - 2 * bst);
+                    }
                 }
-                Bp -= 2 * bst;
-                const float Bi = nBi;
-                if (i > 0) nBi = ldB<DIRECT>(Bp - 2 * bst);
-                uu = fmaf(st.x, uu, st.y);
-                const float fup = fmaf(kPiF, Bi, uu);
+                uu = vfma(Pv, uu, Qq);
+                const V fup = vfma(V(kPiF), Bi, uu);
                 Bt = Bi;
-                const float fnet = fmaf(st.z, uu, -st.w);
-                tb[(gi * 2) * 33 + lane] = wg * fup;
-                tb[(gi * 2 + 1) * 33 + lane] = wg * fnet;
+                const V fnet = vfma(av, uu, -ev);
+                tb[(gi * 2) * 33 + lane] = hsum(wg * fup);
+                tb[(gi * 2 + 1) * 33 + lane] = hsum(wg * fnet);
                 ++gi;
             }
             if (gi == 16 || (i < 0 && gi > 0)) {
@@ -1003,19 +1206,23 @@ __global__ void __launch_bounds__(kMaxBlock32, 3) fp32_units(KParams kp) {
                 gi = 0;
             }
         }
-        bad |= !isfinite(uu);
-        if (active && bad) cn.nonfinite++;
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            if (cmpm(on, i) && (bad[i] || !isfinite(cmp(uu, i)))) cn.nonfinite++;
 
-        // TOA spectrum: uu and Bp are now at interface 0; each bin's lanes
-        // are summed in lane order and added once per unit (a bin of n_g <= 32
-        // systems meets at most two units, so the FP64 sum is order-free)
+        // TOA spectrum: uu and Bt are now at interface 0; each bin's systems
+        // are summed in system order and added once per unit (a bin of
+        // n_g <= 32 NS systems meets at most two units, so the FP64 sum is
+        // order-free)
         if (kp.toa) {
-            tb[lane] = wg * fmaf(kPiF, Bt, uu);
+            V ft = wg * vfma(V(kPiF), Bt, uu);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) tb[32 * i + lane] = cmp(ft, i);
             __syncwarp();
-            if (lane < nbc) {
-                const int bt = b_lo + lane;
+            for (int jb = lane; jb < nbc; jb += 32) {
+                const int bt = b_lo + jb;
                 const int j0 = max(0, bt * NG - s0);
-                const int j1 = min(min(32, S - s0), (bt + 1) * NG - s0);
+                const int j1 = min(min(SPU, S - s0), (bt + 1) * NG - s0);
                 float acc = 0.f;
                 for (int j = j0; j < j1; ++j) acc += tb[j];
                 atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
@@ -1139,7 +1346,7 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
     const int NG = kp.n_g;
     const long long slot = (long long)blockIdx.x * blockDim.x + tid;
     double2 *scr = kp.scr64 + slot;           // element (2 lev + j) n_slots + slot
-    Counters cn = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cn = {0, 0, 0, 0, 0, 0, 0};
     ColInfo ci;
     const bool iso = kp.isothermal;
 
@@ -1288,10 +1495,14 @@ constexpr int kMaxDynSmem = 200 * 1024;
 
 cudaError_t init_kernels() {
     cudaError_t e = cudaSuccess;
-    for (auto f : {fp32_units<false, false, false>, fp32_units<true, false, false>,
-                   fp32_units<false, true, false>, fp32_units<true, true, false>,
-                   fp32_units<false, false, true>, fp32_units<true, false, true>,
-                   fp32_units<false, true, true>, fp32_units<true, true, true>}) {
+    for (auto f : {fp32_units<false, false, false, 1>, fp32_units<true, false, false, 1>,
+                   fp32_units<false, true, false, 1>, fp32_units<true, true, false, 1>,
+                   fp32_units<false, false, true, 1>, fp32_units<true, false, true, 1>,
+                   fp32_units<false, true, true, 1>, fp32_units<true, true, true, 1>,
+                   fp32_units<false, false, false, 2>, fp32_units<true, false, false, 2>,
+                   fp32_units<false, true, false, 2>, fp32_units<true, true, false, 2>,
+                   fp32_units<false, false, true, 2>, fp32_units<true, false, true, 2>,
+                   fp32_units<false, true, true, 2>, fp32_units<true, true, true, 2>}) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1301,30 +1512,40 @@ cudaError_t init_kernels() {
     return cudaFuncSetAttribute(fp64_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
-int occupancy(int precision_fp64, int block, size_t smem) {
+int occupancy(int precision_fp64, int block, size_t smem, int ns) {
     if (smem > (size_t)kMaxDynSmem) return 0;
     int n = 0;
-    cudaError_t e = precision_fp64
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false>, block, smem);
+    cudaError_t e = precision_fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
+                    : ns == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 2>,
+                                                                            block, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 1>,
+                                                                            block, smem);
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
     const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
-    fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 1), s>>>(kp);
+    fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 2), s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int sel = (kp.isothermal ? 1 : 0) | (kp.direct ? 2 : 0) | (kp.kt_lk ? 4 : 0);
+    const int sel = (kp.isothermal ? 1 : 0) | (kp.direct ? 2 : 0) | (kp.kt_lk ? 4 : 0) | (kp.ns == 2 ? 8 : 0);
     switch (sel) {
-        case 0: fp32_units<false, false, false><<<grid, block, smem, s>>>(kp); break;
-        case 1: fp32_units<true, false, false><<<grid, block, smem, s>>>(kp); break;
-        case 2: fp32_units<false, true, false><<<grid, block, smem, s>>>(kp); break;
-        case 3: fp32_units<true, true, false><<<grid, block, smem, s>>>(kp); break;
-        case 4: fp32_units<false, false, true><<<grid, block, smem, s>>>(kp); break;
-        case 5: fp32_units<true, false, true><<<grid, block, smem, s>>>(kp); break;
-        case 6: fp32_units<false, true, true><<<grid, block, smem, s>>>(kp); break;
-        default: fp32_units<true, true, true><<<grid, block, smem, s>>>(kp); break;
+        case 0: fp32_units<false, false, false, 1><<<grid, block, smem, s>>>(kp); break;
+        case 1: fp32_units<true, false, false, 1><<<grid, block, smem, s>>>(kp); break;
+        case 2: fp32_units<false, true, false, 1><<<grid, block, smem, s>>>(kp); break;
+        case 3: fp32_units<true, true, false, 1><<<grid, block, smem, s>>>(kp); break;
+        case 4: fp32_units<false, false, true, 1><<<grid, block, smem, s>>>(kp); break;
+        case 5: fp32_units<true, false, true, 1><<<grid, block, smem, s>>>(kp); break;
+        case 6: fp32_units<false, true, true, 1><<<grid, block, smem, s>>>(kp); break;
+        case 7: fp32_units<true, true, true, 1><<<grid, block, smem, s>>>(kp); break;
+        case 8: fp32_units<false, false, false, 2><<<grid, block, smem, s>>>(kp); break;
+        case 9: fp32_units<true, false, false, 2><<<grid, block, smem, s>>>(kp); break;
+        case 10: fp32_units<false, true, false, 2><<<grid, block, smem, s>>>(kp); break;
+        case 11: fp32_units<true, true, false, 2><<<grid, block, smem, s>>>(kp); break;
+        case 12: fp32_units<false, false, true, 2><<<grid, block, smem, s>>>(kp); break;
+        case 13: fp32_units<true, false, true, 2><<<grid, block, smem, s>>>(kp); break;
+        case 14: fp32_units<false, true, true, 2><<<grid, block, smem, s>>>(kp); break;
+        default: fp32_units<true, true, true, 2><<<grid, block, smem, s>>>(kp); break;
     }
     return cudaGetLastError();
 }

@@ -39,6 +39,7 @@ class rt_config(ctypes.Structure):
         ("max_layers", ctypes.c_int32), ("max_bins", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32), ("planck_staging", ctypes.c_int32),
+        ("systems_per_lane", ctypes.c_int32),
         ("n_edges", ctypes.c_int32), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -169,6 +170,7 @@ class Config:
     block_threads: int = 0
     ctas_per_sm: int = 0
     planck_staging: int = 0              # RT_STAGE_AUTO / RT_STAGE_SHARED / RT_STAGE_DIRECT
+    systems_per_lane: int = 0            # FP32 form: 1 or 2 (0 = 2)
     wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins
 
 
@@ -181,7 +183,7 @@ def _config(cfg: Config):
                   cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
                   cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
                   cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
-                  cfg.ctas_per_sm, cfg.planck_staging, 0 if ed is None else ed.size,
+                  cfg.ctas_per_sm, cfg.planck_staging, cfg.systems_per_lane, 0 if ed is None else ed.size,
                   None if ed is None else ed.ctypes.data_as(PD))
     return c, (gw, ed)
 

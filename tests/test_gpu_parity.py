@@ -97,6 +97,32 @@ def test_method_switches_on_ragged_batch(mode, precision):
     assert got["stats"]["etau_hits"] == ref["stats"]["etau_hits"]
 
 
+@pytest.mark.parametrize("spl", [1, 2])
+def test_config1_one_and_two_systems_per_lane(cfg1, cfg1_ref, spl):
+    """The FP32 form with one system per lane and with two (paired FP32
+    instructions), each against the oracle on the full GCM-shaped batch."""
+    got = gpu_solve(cfg1, method_opts(), "fp32", systems_per_lane=spl)
+    e = assert_parity(cfg1, got, cfg1_ref, "fp32", f"config1 {spl}/lane")
+    print("systems per lane", spl, "config1 error/tol", e)
+    assert got["stats"]["etau_hits"] == cfg1_ref["stats"]["etau_hits"]
+    assert got["stats"]["resonance_hits"] == cfg1_ref["stats"]["resonance_hits"]
+
+
+@pytest.mark.parametrize("spl", [1, 2])
+@pytest.mark.parametrize("mode", ["iso", "direct", "ng1", "ng45"])
+def test_systems_per_lane_variants_on_ragged_batches(spl, mode):
+    n_g = {"ng1": 1, "ng45": 45}.get(mode, 20)
+    cols = rt_synth.generate([37, 3, 1, 64, 12], [9, 40, 2, 5, 31], n_g, seed=41, optics="ktable")
+    opts = method_opts(isothermal=(mode == "iso"))
+    extra = dict(systems_per_lane=spl)
+    if mode == "direct":
+        extra["planck_staging"] = 2
+    ref = oracle_solve(cols, opts)
+    got = gpu_solve(cols, opts, "fp32", **extra)
+    assert_parity(cols, got, ref, "fp32", f"{mode} {spl}/lane")
+    assert got["stats"]["invalid_inputs"] == 0 and got["stats"]["nonfinite_outputs"] == 0
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_ktable_ragged_many_bins(precision):
     """Columns up to 200 layers and 300 bins with k-table optical depths."""
