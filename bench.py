@@ -48,8 +48,9 @@ def dist_env():
 
 
 # FP32 operations of the chosen form per (column, bin, g) system of the GCM
-# workload (FFMA counted as 2, FADD and FMUL as 1), from the executed
-# instruction counters of the solve kernel on that workload; see the design doc.
+# workload (FFMA counted as 2, FADD and FMUL as 1, the paired FFMA2 as 4 and
+# FADD2/FMUL2 as 2), from the executed instruction counters of the solve
+# kernel on that workload.
 FLOP_PER_SYSTEM = None   # filled from profiles/fp32_units_gcm2562.txt when current
 FP32_LANES_PER_SM = 128
 N_SM = 148
@@ -323,6 +324,90 @@ def run_ktable(args, stream):
     return out
 
 
+def _oracle_rate(cols, seconds, threads=None):
+    """Oracle solves/s on this host: all cores in-process, or ``threads`` cores
+    in a child process (OpenMP reads its thread count at start-up)."""
+    if threads is None:
+        v, _, _ = time_oracle(cols, seconds)
+        return v
+    import pickle
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "cols.pkl")
+        with open(f, "wb") as fh:
+            pickle.dump(cols, fh)
+        code = ("import pickle, sys; sys.path.insert(0, %r); import bench; "
+                "cols = pickle.load(open(%r, 'rb')); print(bench.time_oracle(cols, %r)[0])" % (ROOT, f, seconds))
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def run_table(args):
+    """One JSON line per workload (configs 0-3): FP32 form and FP64 plain
+    GPU throughput with inputs resident, the HBM bytes each FP32 step moves
+    over its time, and the CPU oracle on one core and on all cores (bounded
+    samples of the same workload, shapes as drawn)."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300 import rt
+    from paper_2203_02293_b300.solver import DeviceBatch, Solver
+    peak_gbs, _ = read_peaks()
+    stream = torch.cuda.Stream()
+
+    def gpu_ms(b, g_weights, precision, steps):
+        s = Solver(g_weights, precision=precision)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                s.solve(b, stream)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                s.solve(b, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        return e0.elapsed_time(e1) / steps
+
+    cases = [
+        ("config0 64x40x30x1", lambda: rt_synth.config0(), None),
+        ("config1 2562x40x30x20", lambda: rt_synth.config1(), 64),
+        ("config2 2562x40x30x20 stress", lambda: rt_synth.config2(), 64),
+        ("config3 4096 uneven", None, 24),
+    ]
+    for name, make, n_sample in cases:
+        if make is not None:
+            cols = make()
+            b = DeviceBatch(cols)
+            n_sys, g_w = cols.n_systems, cols.g_weights
+            sample = cols if n_sample is None else cols.subset(np.arange(n_sample))
+            in_bytes = b.input_bytes
+        else:
+            dc = rt_synth.config3_device()
+            b = DeviceBatch.from_device(dc)
+            n_sys, g_w = dc.n_systems, dc.g_weights
+            sample = dc.host_subset(np.arange(n_sample))
+            in_bytes = b.input_bytes
+        steps32 = 200 if n_sys < 4_000_000 else 20
+        ms32 = gpu_ms(b, g_w, rt.RT_FP32_FORM, steps32)
+        ms64 = gpu_ms(b, g_w, rt.RT_FP64_PLAIN, 3 if n_sys < 4_000_000 else 1)
+        out_bytes = 8 * (3 * b.n_if + b.n_lay)
+        line = {"table": name, "systems": n_sys,
+                "fp32_solves_per_s": n_sys / (ms32 * 1e-3), "fp32_ms": ms32,
+                "fp64_solves_per_s": n_sys / (ms64 * 1e-3), "fp64_ms": ms64, "fp32_over_fp64": ms64 / ms32,
+                "fp32_hbm_frac": (in_bytes + out_bytes) / (ms32 * 1e-3) / 1e9 / peak_gbs}
+        del b
+        torch.cuda.empty_cache()
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = {
+                "all_cores": _oracle_rate(sample, 3.0), "one_core": _oracle_rate(sample, 3.0, threads=1),
+                "cores": cpu_cores(), "kind": "oracle", "unit": UNIT,
+                "sample": "all columns" if n_sample is None else f"{n_sample} columns of the workload"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Config 4: Poisson arrivals (mean 200/s), requests of logU[1, 2562]
     columns x U{40..100} layers x U{30..300} bins x 20 g sliced from a
@@ -361,14 +446,19 @@ def main():
     ap.add_argument("--uneven-steps", type=int, default=10)
     ap.add_argument("--postproc-steps", type=int, default=20)
     ap.add_argument("--ktable-steps", type=int, default=200)
+    ap.add_argument("--kernel-timing-steps", type=int, default=50)
     ap.add_argument("--serving-seconds", type=float, default=20.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
+    ap.add_argument("--table", action="store_true",
+                    help="per-workload table (configs 0-3, FP32/FP64 GPU, CPU oracle 1 core / all cores)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.table:
+        return run_table(args)
 
     import torch
     import rt_synth
@@ -469,9 +559,21 @@ def main():
                  + 8 * (cols.mu_star.size + cols.F_star.size)
                  + 8 * (3 * batch.n_if + batch.n_lay))          # outputs
     prof = read_profile()
-    # kernel time alone (the Planck pre-kernel is timed out of the step)
-    kshare = float(prof["solve_kernel_share"]) if prof else 1.0
-    ms_kernel = ms32 * kshare
+    # the solve kernel's own launch duration, measured live: CUDA events on
+    # the launching stream around each kernel (rt_kernel_times), averaged
+    # over a stretch of solves after the timed region
+    st_ = Solver(cols.g_weights, precision=rt.RT_FP32_FORM, kernel_timing=1)
+    kt_prep, kt_solve = [], []
+    with torch.cuda.stream(stream):
+        for i in range(args.kernel_timing_steps + 3):
+            st_.solve(batch, stream)
+            a, b = rt.rt_kernel_times(st_.h)
+            if i >= 3:
+                kt_prep.append(a)
+                kt_solve.append(b)
+    st_.close()
+    ms_kernel = float(np.mean(kt_solve))
+    ms_prep = float(np.mean(kt_prep))
     achieved_gbs = alg_bytes / (ms_kernel * 1e-3) / 1e9
     max_mhz = 2032.0
     try:
@@ -486,7 +588,8 @@ def main():
         roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved_tf / peak_tflops,
                     "traffic": float(prof["dram_bytes_per_launch"]),
-                    "kernel": "fp32_units", "kernel_ms": ms_kernel,
+                    "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
+                    "kernel_ms_source": f"CUDA events around each launch, mean of {len(kt_solve)} solves",
                     "flop_per_system": flop_per_sys,
                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock",
                     "hbm": {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
@@ -495,6 +598,7 @@ def main():
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                     "frac": achieved_gbs / peak_gbs, "traffic": None, "peak_source": peak_src,
+                    "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "note": "no current ncu summary for this kernel source"}
     stats = s32.stats()

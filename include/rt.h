@@ -100,6 +100,8 @@ typedef struct {
                                     (0 = 2: two systems share the paired FP32
                                     instructions of sm_100+); results differ only
                                     in rounding */
+    int32_t kernel_timing;       /* 1: record CUDA events around each kernel of a
+                                    solve (read with rt_kernel_times) */
     int32_t n_edges;             /* 0: NB bins of equal width on [wn_min, wn_max];
                                     > 1: explicit bin edges, every column then has
                                     n_edges - 1 bins (e.g. the R = 500 sampling of
@@ -244,6 +246,12 @@ int rt_ktable_optics(rt_handle *h, const rt_columns *cols, float *dtau, float *w
  * the FP32 optics of rt_ktable_optics into handle workspace.  Outputs are
  * read as after rt_solve_columns. */
 int rt_solve_ktable(rt_handle *h, const rt_columns *cols, void *stream);
+
+/* Device durations (ms, CUDA events on the solve's stream) of the last
+ * solve's kernels: the Planck/front-end pre-kernel and the solve kernel (for
+ * the FP64 path: 0 and the solve).  Needs cfg->kernel_timing; synchronises
+ * on the last solve.  RT_ENOTSOLVED before a timed solve. */
+int rt_kernel_times(rt_handle *h, float *prep_ms, float *solve_ms);
 
 /* Branch and error counters of the last solve (synchronises the stream of
  * that solve). */

@@ -59,6 +59,8 @@ struct rt_handle {
     int32_t *d_counter = nullptr;
     unsigned long long *d_stats = nullptr;
     cudaEvent_t done_ev = nullptr;
+    cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};   // kernel timing (cfg.kernel_timing)
+    bool kev_valid = false, kev_fp64 = false;
     bool done_valid = false;       // done_ev marks the last solve (false when it was captured)
     cudaStream_t last_stream = nullptr;
     bool solved = false;
@@ -348,6 +350,7 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     if (e == cudaSuccess) e = cudaMemset(h->d_stats, 0, sizeof(unsigned long long) * rt::ST_COUNT);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming);
+    for (int i = 0; i < 3 && e == cudaSuccess && cfg->kernel_timing; ++i) e = cudaEventCreate(&h->kev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         rt_destroy(h);
@@ -608,9 +611,14 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
             kp.g0 = cg;
             kp.kt_lk = nullptr;
         }
+        const bool timing = cfg.kernel_timing && !cap;
+        if (timing && cfg.precision == RT_FP64_PLAIN) cudaEventRecord(h->kev[1], s);
         e = cfg.precision == RT_FP64_PLAIN ? rt::launch_fp64(kp, P.grid, P.block, P.smem, s)
-                                           : rt::launch_fp32(kp, P.grid, P.block, P.smem, s);
+                                           : rt::launch_fp32(kp, P.grid, P.block, P.smem, s, timing ? h->kev : nullptr);
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+        if (timing && cfg.precision == RT_FP64_PLAIN) cudaEventRecord(h->kev[2], s);
+        h->kev_valid = timing;
+        h->kev_fp64 = cfg.precision == RT_FP64_PLAIN;
     }
     if (optics_out) return RT_OK;
     // A solve captured into a graph completes when the graph is replayed; the
@@ -829,6 +837,19 @@ int rt_toa_spectrum(rt_handle *h, double *F_up_toa, void *stream) {
     return copy_out(h, F_up_toa, toa, sizeof(double) * (size_t)h->n_bins, s);
 }
 
+int rt_kernel_times(rt_handle *h, float *prep_ms, float *solve_ms) {
+    if (!h) return RT_EINVAL;
+    if (!h->kev_valid) return fail(h, RT_ENOTSOLVED, "no timed solve (cfg.kernel_timing)");
+    cudaError_t e = cudaEventSynchronize(h->kev[2]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess && !h->kev_fp64) e = cudaEventElapsedTime(&a, h->kev[0], h->kev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, h->kev[1], h->kev[2]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rt_kernel_times");
+    if (prep_ms) *prep_ms = a;
+    if (solve_ms) *solve_ms = b;
+    return RT_OK;
+}
+
 int rt_stats(rt_handle *h, rt_stats_t *out) {
     if (!h || !out) return RT_EINVAL;
     if (!h->solved) return fail(h, RT_ENOTSOLVED, "rt_stats before rt_solve_columns");
@@ -869,6 +890,8 @@ void rt_destroy(rt_handle *h) {
     if (h->h_stage) cudaFreeHost(h->h_stage);
     if (h->done_ev) cudaEventDestroy(h->done_ev);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    for (int i = 0; i < 3; ++i)
+        if (h->kev[i]) cudaEventDestroy(h->kev[i]);
     cudaGetLastError();
     delete h;
 }

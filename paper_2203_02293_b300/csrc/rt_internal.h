@@ -95,7 +95,10 @@ cudaError_t init_kernels();
 // Resident CTAs per SM for a launch shape (0 if it does not fit).
 int occupancy(int precision_fp64, int block, size_t smem, int ns = 1);
 // Launch the fused column kernels.  Return cudaGetLastError().
-cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
+// ev (optional): three events recorded before the pre-kernel, between the
+// two kernels and after the solve kernel.
+cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
+                        cudaEvent_t const *ev = nullptr);
 cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
 // Front end alone: FP32 optics of every (column, layer, bin, g) into packed
 // cubes (cube offsets of the packed layout in pcube_off).

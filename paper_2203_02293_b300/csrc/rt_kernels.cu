@@ -941,6 +941,29 @@ __device__ __forceinline__ void discard_l2_after(const float4 *p, float after) {
         : "memory");
 }
 
+// Elimination scratch of one interface: (P, Q, alpha', e) of one system in a
+// float4; for a lane with two systems, (P, Q) of both and (alpha', e) of
+// both in two float4 (component pairs stay in their register pairs).
+__device__ __forceinline__ void scr_store(float4 *sp, long long, float P, float Q, float a, float e) {
+    __stcg(sp, make_float4(P, Q, a, e));
+}
+__device__ __forceinline__ void scr_store(float4 *sp, long long other, V2 P, V2 Q, V2 a, V2 e) {
+    __stcg(sp, make_float4(P.v.x, P.v.y, Q.v.x, Q.v.y));
+    __stcg(sp + other, make_float4(a.v.x, a.v.y, e.v.x, e.v.y));
+}
+__device__ __forceinline__ void scr_unpack(const float4 *n, float &P, float &Q, float &a, float &e) {
+    P = n[0].x;
+    Q = n[0].y;
+    a = n[0].z;
+    e = n[0].w;
+}
+__device__ __forceinline__ void scr_unpack(const float4 *n, V2 &P, V2 &Q, V2 &a, V2 &e) {
+    P = V2(n[0].x, n[0].y);
+    Q = V2(n[0].z, n[0].w);
+    a = V2(n[1].x, n[1].y);
+    e = V2(n[1].z, n[1].w);
+}
+
 // Component access for per-system values (one system per lane: float; two:
 // V2) and per-system loads.
 __device__ __forceinline__ float &cmp(float &v, int) { return v; }
@@ -1119,12 +1142,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
             const V ipv = vrcp(vfma(ly.R, al, omr));           // 1 / (1 - R a')
             const V P = ly.T * ipv;
             const V Qv = vfma(ly.R, bl, ly.Su) * ipv;
-            const V eb = bl + Fb;                              // b' + F_beam
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                V Pc = P, Qc = Qv, ac = al, ec = eb;
-                __stcg(sp + i * gthreads, make_float4(cmp(Pc, i), cmp(Qc, i), cmp(ac, i), cmp(ec, i)));
-            }
+            scr_store(sp, gthreads, P, Qv, al, bl + Fb);      // e = b' + F_beam
             sp += sstride;
             const V al_n = vfma(al, vfma(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
             const V bl_n = vfma(ly.T * vfma(V(1.f) - al, ly.Su, bl), ipv, ly.Sd);
@@ -1161,12 +1179,9 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
         for (int i = L - 1; i >= -1; --i) {
             if (i >= 0) {
                 V Pv, Qq, av, ev;
+                scr_unpack(nst, Pv, Qq, av, ev);
 #pragma unroll
                 for (int j = 0; j < NS; ++j) {
-                    cmp(Pv, j) = nst[j].x;
-                    cmp(Qq, j) = nst[j].y;
-                    cmp(av, j) = nst[j].z;
-                    cmp(ev, j) = nst[j].w;
                     // this level's scratch is dead once read: drop its L2
                     // lines (one per 8 lanes) so they are not written back
                     if ((lane & 7) == 0) discard_l2_after(sp + j * gthreads, nst[j].x);
@@ -1523,11 +1538,14 @@ int occupancy(int precision_fp64, int block, size_t smem, int ns) {
     return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
+cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
+                        cudaEvent_t const *ev) {
     const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
+    if (ev) cudaEventRecord(ev[0], s);
     fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 2), s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
     const int sel = (kp.isothermal ? 1 : 0) | (kp.direct ? 2 : 0) | (kp.kt_lk ? 4 : 0) | (kp.ns == 2 ? 8 : 0);
     switch (sel) {
         case 0: fp32_units<false, false, false, 1><<<grid, block, smem, s>>>(kp); break;
@@ -1547,7 +1565,9 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
         case 14: fp32_units<false, true, true, 2><<<grid, block, smem, s>>>(kp); break;
         default: fp32_units<true, true, true, 2><<<grid, block, smem, s>>>(kp); break;
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    return e;
 }
 
 cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float *dtau, float *w0,

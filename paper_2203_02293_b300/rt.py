@@ -39,7 +39,7 @@ class rt_config(ctypes.Structure):
         ("max_layers", ctypes.c_int32), ("max_bins", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_size_t), ("block_threads", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32), ("planck_staging", ctypes.c_int32),
-        ("systems_per_lane", ctypes.c_int32),
+        ("systems_per_lane", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
         ("n_edges", ctypes.c_int32), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -95,6 +95,7 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_solve_ktable.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p]
     lib.rt_stats.argtypes = [H, ctypes.POINTER(rt_stats_t)]
+    lib.rt_kernel_times.argtypes = [H, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.rt_last_error.argtypes = [H]
     lib.rt_last_error.restype = ctypes.c_char_p
     lib.rt_destroy.argtypes = [H]
@@ -104,7 +105,8 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_solve_uniform_noalloc.restype = ctypes.c_int
     for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
-              "rt_toa_spectrum", "rt_stats", "rt_set_ktable", "rt_ktable_optics", "rt_solve_ktable"):
+              "rt_toa_spectrum", "rt_stats", "rt_set_ktable", "rt_ktable_optics", "rt_solve_ktable",
+              "rt_kernel_times"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -171,6 +173,7 @@ class Config:
     ctas_per_sm: int = 0
     planck_staging: int = 0              # RT_STAGE_AUTO / RT_STAGE_SHARED / RT_STAGE_DIRECT
     systems_per_lane: int = 0            # FP32 form: 1 or 2 (0 = 2)
+    kernel_timing: int = 0               # 1: CUDA events around each kernel (rt_kernel_times)
     wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins
 
 
@@ -183,7 +186,8 @@ def _config(cfg: Config):
                   cfg.wn_max, cfg.two_stream, cfg.layers, cfg.precision, cfg.resonance,
                   cfg.e_clamp, cfg.eps2, cfg.grav, cfg.cp, cfg.T_int, cfg.F_toa_diffuse,
                   cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
-                  cfg.ctas_per_sm, cfg.planck_staging, cfg.systems_per_lane, 0 if ed is None else ed.size,
+                  cfg.ctas_per_sm, cfg.planck_staging, cfg.systems_per_lane, cfg.kernel_timing,
+                  0 if ed is None else ed.size,
                   None if ed is None else ed.ctypes.data_as(PD))
     return c, (gw, ed)
 
@@ -267,6 +271,13 @@ def rt_solve_ktable(h, cols, stream=None):
 def rt_toa_spectrum(h, F_up_toa, stream=None):
     """Per-bin upward flux at the TOA of the last solve, [sum NB] float64."""
     _check(lib().rt_toa_spectrum(h, _ptr(F_up_toa), _stream_ptr(stream)), h)
+
+
+def rt_kernel_times(h):
+    """(pre-kernel ms, solve-kernel ms) of the last solve (needs kernel_timing)."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(lib().rt_kernel_times(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
 
 
 def rt_stats(h) -> dict:

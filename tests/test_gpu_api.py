@@ -165,3 +165,21 @@ def test_negative_gather_offset_is_rejected():
         rt.rt_solve_columns(s.h, desc)
     assert e.value.code == rt.RT_EINVAL
     s.close()
+
+
+def test_kernel_times_are_recorded_on_request():
+    cols = rt_synth.generate([20, 35], [30, 12], 20, seed=70, optics="ktable")
+    b = DeviceBatch(cols)
+    s = Solver(cols.g_weights)
+    s.solve(b)
+    with pytest.raises(rt.RTError) as e:
+        rt.rt_kernel_times(s.h)                 # timing not asked for
+    assert e.value.code == rt.RT_ENOTSOLVED
+    s.close()
+    for prec in (rt.RT_FP32_FORM, rt.RT_FP64_PLAIN):
+        s = Solver(cols.g_weights, precision=prec, kernel_timing=1)
+        s.solve(b)
+        prep, solve = rt.rt_kernel_times(s.h)
+        assert solve > 0.0 and prep >= 0.0
+        assert (prep > 0.0) == (prec == rt.RT_FP32_FORM)
+        s.close()

@@ -31,6 +31,7 @@ def test_postproc_columns_match_the_oracle(prec):
     ref = oracle_solve(cols, method_opts())
     got = gpu_solve(cols, method_opts(), prec)
     e = assert_parity(cols, got, ref, prec, "postproc 6 cols")
+    print(prec, "postproc 6 cols error/tol", e)
     assert "F_up_toa" in e
 
 
@@ -90,7 +91,8 @@ def test_postproc_full_size_sampled_columns():
     got = dict(F_up=pick(full["F_up"], "iface"), F_down=pick(full["F_down"], "iface"),
                F_net=pick(full["F_net"], "iface"), Q=pick(full["Q"], "lay"),
                F_up_toa=pick(full["F_up_toa"], "bins"))
-    assert_parity(host, got, ref, "fp32", "postproc 2562 sampled")
+    e = assert_parity(host, got, ref, "fp32", "postproc 2562 sampled")
+    print("fp32 postproc 2562 sampled error/tol", e)
     del b, dc
     torch.cuda.empty_cache()
 
