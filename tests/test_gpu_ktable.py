@@ -159,3 +159,23 @@ def test_front_end_errors(kt):
         s.set_ktable(g3)                        # table n_g differs from the handle's
     assert e.value.code == rt.RT_EINVAL
     s.close()
+
+
+def test_state_outside_the_table_grid_is_clamped_like_the_oracle(kt):
+    """Columns hotter and colder than the 50-3000 K grid and reaching above
+    1e-6 bar / below 1e3 bar: both sides clamp to the grid edges."""
+    cols = rt_synth.state_columns(3, 12, 30, 20, seed=28)
+    L = 12
+    cols.T_center = cols.T_center.copy()
+    cols.T_center[:L] = np.linspace(10.0, 40.0, L)          # below the grid
+    cols.T_center[L:2 * L] = np.linspace(3100.0, 4000.0, L)  # above the grid
+    cols.p_iface = cols.p_iface.copy()
+    cols.p_iface[2 * (L + 1):] = np.geomspace(1e-4, 1e9, L + 1)   # past both pressure ends
+    ref, _ = oracle_ktable_solve(cols, kt, method_opts())
+    s = opts_solver(cols)
+    s.set_ktable(kt)
+    b = DeviceBatch(cols)
+    s.solve_ktable(b)
+    got = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
+    s.close()
+    assert_parity(cols, got, ref, "fp32", "k-table clamped")
