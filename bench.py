@@ -214,8 +214,9 @@ def run_uneven(args, stream):
     from paper_2203_02293_b300.tuning import GraphSolve, autotune
     dc = rt_synth.config3_device()
     b = DeviceBatch.from_device(dc)
+    from paper_2203_02293_b300.tuning import KNOBS
     tune = autotune(b, dc.g_weights, reps=3)
-    s = Solver(dc.g_weights, block_threads=tune["block_threads"], ctas_per_sm=tune["ctas_per_sm"])
+    s = Solver(dc.g_weights, **{k: tune[k] for k in KNOBS if k in tune})
     g = GraphSolve(s, b, stream)
     for _ in range(3):
         g.replay()
@@ -231,7 +232,7 @@ def run_uneven(args, stream):
     out = {"workload": "4096 cols, L~U{20..200}, NB~U{30..300}, 20 g, one launch (CUDA graph replay)",
            "systems": dc.n_systems, "input_bytes": int(3 * 4 * dc.dtau.numel()),
            "ms_per_step": ms, "value": dc.n_systems / (ms * 1e-3), "unit": UNIT,
-           "steps": args.uneven_steps, "autotune": {k: tune[k] for k in ("block_threads", "ctas_per_sm", "stable")},
+           "steps": args.uneven_steps, "autotune": {k: tune[k] for k in (*KNOBS, "stable") if k in tune},
            "autotune_table": tune["table"]}
     del g, b, dc
     torch.cuda.empty_cache()

@@ -72,14 +72,18 @@ def test_graph_replay_equals_eager(cfg3):
     s.close()
 
 
-def test_autotuner_candidates_agree_bitwise():
+def test_autotuner_candidates_agree():
     L, NB = rt_synth.uneven_shapes(300, seed=77, L_range=(20, 120), NB_range=(30, 200))
     cols = rt_synth.generate(L, NB, 20, seed=78, optics="uniform")
     b = DeviceBatch(cols)
-    res = autotune(b, cols.g_weights, candidates=[(64, 0), (128, 2), (256, 0), (256, 1)], reps=2)
+    cands = [dict(block_threads=bt, ctas_per_sm=c, systems_per_lane=n)
+             for n in (1, 2) for bt, c in ((64, 0), (128, 2), (256, 0), (256, 1))]
+    cands.append(dict(block_threads=128, ctas_per_sm=0, systems_per_lane=2, planck_staging=rt.RT_STAGE_DIRECT))
+    res = autotune(b, cols.g_weights, candidates=cands, reps=2)
     assert res["stable"], res["table"]
     assert res["block_threads"] in (64, 128, 256)
     ref = oracle_solve(cols, method_opts())
-    s = Solver(cols.g_weights, block_threads=res["block_threads"], ctas_per_sm=res["ctas_per_sm"])
+    from paper_2203_02293_b300.tuning import KNOBS
+    s = Solver(cols.g_weights, **{k: res[k] for k in KNOBS if k in res})
     assert_parity(cols, s.solve_numpy(b), ref, "fp32", "autotuned")
     s.close()
