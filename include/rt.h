@@ -205,11 +205,12 @@ int rt_toa_spectrum(rt_handle *h, double *F_up_toa, void *stream);
  *             sqrt(p_top p_bot); T and log10 p are clamped to the grid;
  *   sigma_g = x_H2 sigma_H2 + x_He sigma_He, the Rayleigh cross sections of
  *             App. C averaged over the bin in wavenumber;
- *   w0      = (sigma_g + f_cloud sigma_scat,cloud) / E,
- *   g0      = f_cloud sigma_scat,cloud g0_cloud / (sigma_g + f_cloud sigma_scat,cloud),
+ *   w0      = (sigma_g + f_cloud sigma_scat,cloud) / E,                (Eq. 17)
+ *   g0      = f_cloud sigma_scat,cloud g0_cloud / (sigma_g + f_cloud sigma_scat,cloud),   (Eq. 18)
  *             with E = sigma_g + kappa mbar + f_cloud (sigma_abs,cloud +
- *             sigma_scat,cloud) the extinction per gas particle (the mixing
- *             equations of Sec. 2.1.3; g0 = 0 where nothing scatters);
+ *             sigma_scat,cloud) the extinction per gas particle (g0 = 0
+ *             where nothing scatters); kappa is the premixed opacity of
+ *             Eq. 16, summed over species when the table was built;
  *   dtau    = E / mbar * (p_bot - p_top) / g.
  * ------------------------------------------------------------------------- */
 typedef struct {

@@ -17,10 +17,10 @@ What it computes (Deitrick et al., arXiv 2203.02293):
   * gas scattering is Rayleigh scattering by H2 and He (App. C), the number-
     fraction-weighted sum of the two cross sections, averaged over the bin
     in wavenumber (Sec. 2.1.3: per-bin averages when k-tables are used);
-  * w0 and g0 follow the mixing formulas of Sec. 2.1.3 (the equations for
-    the total single-scattering albedo and asymmetry factor): extinction per
-    gas particle sigma_scat,gas + kappa mbar + f_cloud (sigma_abs,cloud +
-    sigma_scat,cloud); gas scatters isotropically;
+  * w0 and g0 follow Eqs. 17-18 (Sec. 2.1.3): extinction per gas particle
+    sigma_scat,gas + kappa mbar + f_cloud (sigma_abs,cloud +
+    sigma_scat,cloud); gas scatters isotropically; kappa is the premixed
+    opacity of Eq. 16, already summed over species in the table;
   * the layer optical depth is that extinction per unit mass times the layer
     column mass dp / g.
 Where the scattering cross section is zero, g0 is 0 (no scatterers).

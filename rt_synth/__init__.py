@@ -375,7 +375,7 @@ def config3_device(n_cols: int = 4096, seed: int = 3, device="cuda") -> DeviceCo
 # ----------------------------------------------------------------------
 # Post-processing workload (Sec. 2.1.3 and the run protocol of Sec. 3):
 # after the GCM run the radiative transfer is repeated once on a
-# high-resolution spectral grid -- opacity sampling at R = lambda / dlambda =
+# high-resolution spectral grid -- opacity sampling at R = lambda / dlambda (Eq. 1) =
 # 500, 3255 wavelength points log-spaced over 0.3-200 um, one g-point per
 # bin -- on columns whose top is extended to 1 ubar with isothermal layers at
 # the top-most model layer's temperature.
