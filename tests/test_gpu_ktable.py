@@ -179,3 +179,33 @@ def test_state_outside_the_table_grid_is_clamped_like_the_oracle(kt):
     got = {k: v.cpu().numpy() for k, v in s.outputs(b).items()}
     s.close()
     assert_parity(cols, got, ref, "fp32", "k-table clamped")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_gathered_state_equals_packed_state(kt, prec):
+    """Columns picked out of a state pool by offsets (reordered, repeated)
+    solve to the same bits as the same columns packed."""
+    pool = rt_synth.state_columns(6, 14, 30, 20, seed=29)
+    pb = DeviceBatch(pool)
+    o = pool.offsets()
+    idx = np.array([4, 1, 4, 0])
+    gather = dict(center_offset=o["lay"][idx], iface_offset=o["iface"][idx], bin_offset=o["bins"][idx],
+                  col_index=idx)
+    desc = rt.make_columns(len(idx), pool.n_layers[idx], pool.n_bins[idx], None, None, None,
+                           pb.T_center, pb.T_iface, pb.p_iface, pb.mu_star, pb.F_star, gather=gather)
+    s = opts_solver(pool, prec)
+    s.set_ktable(kt)
+    rt.rt_solve_ktable(s.h, desc)
+    sub = pool.subset(idx)
+    n_if, n_lay = int((sub.n_layers + 1).sum()), int(sub.n_layers.sum())
+    got = {k: torch.empty(n_if, dtype=torch.float64, device="cuda") for k in ("F_up", "F_down", "F_net")}
+    got["Q"] = torch.empty(n_lay, dtype=torch.float64, device="cuda")
+    rt.rt_fluxes(s.h, got["F_up"], got["F_down"], got["F_net"])
+    rt.rt_heating(s.h, got["Q"])
+    torch.cuda.synchronize()
+    sb = DeviceBatch(sub)
+    s.solve_ktable(sb)
+    ref = {k: v.cpu().numpy() for k, v in s.outputs(sb).items()}
+    s.close()
+    for k in ref:
+        assert np.array_equal(got[k].cpu().numpy(), ref[k]), k
