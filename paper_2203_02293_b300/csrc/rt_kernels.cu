@@ -1,34 +1,32 @@
 // rt_kernels.cu -- fused column kernels for sm_103a.
 //
-// One persistent CTA handles one column at a time (columns are taken from a
-// largest-first list through an atomic counter).  Inside a column the CTA
-// walks the column's (bin, g) systems in chunks of blockDim, one thread per
-// system, g fastest, so that a warp reads 32 consecutive floats of each
-// optical-property cube per layer.  For each chunk the CTA:
-//   1. evaluates the Planck function per bin at every interface and layer
-//      centre of the column into shared memory (bin-integrated B, Sec. 2.2.1);
-//   2. per thread: walks the layers from the TOA down, forming the layer
-//      coefficients (App. B), the stellar beam (Eq. B6) and its source terms
-//      (Eq. B7-B8), the thermal source terms (Eqs. 2-9), and eliminates
-//      towards the BOA (Thomas forward sweep, Sec. 2.2.2), keeping per
-//      interface what the back-substitution needs in a global scratch laid
-//      out [level][thread slot];
-//   3. closes the system at the BOA (Eq. 10) and substitutes back to the TOA,
-//      reducing the Gauss-weighted fluxes of the 32 systems of each warp with
-//      a fixed butterfly, then across warps in a fixed order.
-// After the last chunk it writes the column's interface fluxes, net flux and
-// heating rate.  Every reduction runs in a fixed order, so a column gives the
-// same bits whatever else is in the batch (for a fixed block size).
+// The path for one batch (Sec. 2.2, App. B): per (column, bin, g) system the
+// layer coefficients (App. B, Eq. 19), the stellar beam (Eq. B6) and its
+// source terms (Eqs. B7-B8), the thermal sources (Eqs. 2-9), the Thomas
+// elimination towards the BOA, the BOA closure (Eq. 10) and the substitution
+// back to the TOA (Eqs. 12-15); then the Gauss-weighted sum over g and bins,
+// net flux and heating.  Every reduction runs in a fixed order, so a column
+// gives the same bits whatever else is in the batch.
 //
-// Two arithmetic variants:
-//   fp32_units    -- the FP32 "chosen form": cancellation-free transmission,
-//                    reflection and absorption forms, a beam source with the
-//                    removable singularity at mu* alpha = 1 divided out, and
-//                    departure variables u = F - pi B at every level.  FP64 is
-//                    used only to decide the paper's resonance switch when the
-//                    FP32 estimate of D lies within 2e-5 of zero.
-//   fp64_columns  -- FP64 with the paper's literal formulas, scalar Thomas on
-//                    every level (sub-layers not merged).
+// Kernels:
+//   fp32_prep        Planck per bin at every level of every column (and at
+//                    T_int), F*, mu, and the k-table cells when the front end
+//                    is on; one CTA per column.
+//   fp32_units       the FP32 "chosen form": a persistent grid of warps takes
+//                    work units of 32 or 64 consecutive systems of a column
+//                    (one or two per lane; two use the paired FP32
+//                    instructions) from a largest-column-first list;
+//                    cancellation-free transmission, reflection and absorption
+//                    forms, a beam source with the removable singularity at
+//                    mu* alpha = 1 divided out, departure variables u = F - pi
+//                    B, merged sub-layers; FP64 only to decide the paper's
+//                    resonance switch near |D| = 1e-5.  The warp that finishes
+//                    a column's last unit writes the column.
+//   kt_optics_kernel the input front end alone (k-table interpolation and
+//                    mixing), writing optics cubes.
+//   fp64_columns     FP64 with the paper's literal formulas, one CTA per
+//                    column, one thread per system, scalar Thomas on every
+//                    level (sub-layers not merged).
 #include <cuda_runtime.h>
 #include <type_traits>
 
