@@ -20,8 +20,8 @@
  *     stay valid until the work enqueued on the stream has finished.  Host
  *     pointers are read before the call returns.
  *   - Work is asynchronous on the caller's CUDA stream (cudaStream_t passed
- *     as void*; NULL = the legacy default stream).  rt_stats() is the only
- *     call that synchronises.
+ *     as void*; NULL = the legacy default stream).  Only rt_stats(),
+ *     rt_kernel_times() and rt_set_ktable() synchronise.
  *   - A handle is not thread-safe; use one handle per host thread.
  *   - Nothing in the library calls back into the host or waits on the
  *     device inside a kernel; no kernel spins.
