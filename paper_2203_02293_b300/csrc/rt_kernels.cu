@@ -779,7 +779,7 @@ __device__ __forceinline__ float planck_chunk_level(float T, float scale, float 
 // mass dp / g.  Per system (kt_mix): log10 kappa interpolated bilinearly,
 // kappa = 10^x, extinction per unit mass E = kappa + s_b + a_b (s_b, a_b:
 // the bin's scattering and cloud absorption per unit mass), dtau = E dp / g,
-// w0 = s_b / E and the bin's g0.  Every operation is an explicitly rounded
+// w0 = s_b / E (capped at 1) and the bin's g0.  Every operation is an explicitly rounded
 // intrinsic, so that the fused solve and the standalone optics kernel
 // produce the same bits.
 // ---------------------------------------------------------------------
@@ -818,7 +818,9 @@ __device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float 
     const float ext = __fadd_rn(__fadd_rn(kappa, bq.x), bq.y);
     Optics o;
     o.dt = __fmul_rn(ext, l4.w);
-    o.w0 = ext > 0.f ? __fdiv_rn(bq.x, ext) : 0.f;
+    // w0 = s / E by the approximate reciprocal (a few ulp), capped at 1 so
+    // that s = E (nothing absorbs) stays a valid albedo
+    o.w0 = ext > 0.f ? fminf(__fmul_rn(bq.x, frcp(ext)), 1.f) : 0.f;
     o.g0 = bq.z;
     return o;
 }

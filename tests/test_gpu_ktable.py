@@ -49,10 +49,10 @@ def test_optics_kernel_matches_the_oracle_front_end(kt):
 
 
 @pytest.mark.parametrize("iso", [False, True])
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_fused_solve_equals_optics_then_solve(kt, iso, prec):
+@pytest.mark.parametrize("prec,spl", [("fp32", 1), ("fp32", 2), ("fp64", 0)])
+def test_fused_solve_equals_optics_then_solve(kt, iso, prec, spl):
     cols = rt_synth.state_columns(4, 17, 30, 20, seed=22)
-    s = opts_solver(cols, prec, iso=iso)
+    s = opts_solver(cols, prec, iso=iso, systems_per_lane=spl)
     s.set_ktable(kt)
     b = DeviceBatch(cols)
     s.solve_ktable(b)
