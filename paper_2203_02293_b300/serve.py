@@ -5,9 +5,10 @@ at given times.  Their inputs are slices of a device-resident pool: the
 batch descriptor points into the pool through per-column gather offsets, so
 no input is copied per request.  The server keeps a ring of slots (a CUDA
 stream and a library handle each).  Whenever a slot is free and requests are
-waiting, it admits waiting requests in arrival order while the bytes of the
-batches in flight stay within the HBM budget, and launches them as one solve
-on that slot's stream; batches on different slots overlap on the device.  A
+waiting, it admits waiting requests (in arrival order, or smallest first with
+``policy="sjf"``) while the bytes of the batches in flight stay within the HBM
+budget, and launches them as one solve on that slot's stream; batches on
+different slots overlap on the device.  A
 request's latency runs from its arrival to the host seeing its batch's
 completion event.  Requests that can never fit the budget are refused; a
 request may be cancelled while it waits or refused after a waiting timeout.
@@ -73,7 +74,7 @@ class Pool:
         for L in Ls:
             self.tc_off[L], self.if_off[L] = ntc, nif
             for _ in range(n_pool):
-                p, Tc, Ti = draw._profile(rng, L)
+                p, Tc, Ti = draw.column_profile(rng, L)
                 tc.append(Tc); ti.append(Ti); pi.append(p)
             ntc += n_pool * L
             nif += n_pool * (L + 1)
@@ -92,9 +93,9 @@ class Pool:
             cube_elems = n_pool * L_range[1] * NB_range[1] * n_g
         gen = torch.Generator(device=device)
         gen.manual_seed(777)
-        self.dtau = draw._device_uniform(cube_elems, 1e-6, 10.0, gen, device, log=True)
-        self.w0 = draw._device_uniform(cube_elems, 0.0, 0.95, gen, device)
-        self.g0 = draw._device_uniform(cube_elems, 0.0, 0.8, gen, device)
+        self.dtau = draw.device_uniform(cube_elems, 1e-6, 10.0, gen, device, log=True)
+        self.w0 = draw.device_uniform(cube_elems, 0.0, 0.95, gen, device)
+        self.g0 = draw.device_uniform(cube_elems, 0.0, 0.8, gen, device)
         self.cube_elems = cube_elems
         _, self.g_weights = draw.gauss_legendre_01(n_g)
 

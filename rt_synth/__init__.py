@@ -556,3 +556,9 @@ def state_columns(n_cols: int, L: int, NB: int, n_g: int, seed: int, name: str =
                    p_iface=np.concatenate([p[0] for p in prof]), mu_star=mu,
                    F_star=np.tile(stellar_flux_bins(NB), n_cols), consts=_consts(),
                    name=name or f"state {n_cols}x{L}x{NB}x{n_g}")
+
+
+# public names for the pieces other modules reuse (the serving pool draws its
+# own profiles and cubes with them)
+column_profile = _profile
+device_uniform = _device_uniform

@@ -112,7 +112,7 @@ def test_postproc_grid_is_R500_log_spaced():
 
 def test_isothermal_extension_above_the_model_top():
     rng = np.random.default_rng(7)
-    p_if, Tc, Ti = rt_synth._profile(rng, 10, 1e-3)
+    p_if, Tc, Ti = rt_synth.column_profile(rng, 10, 1e-3)
     p2, Tc2, Ti2, n = rt_synth.extend_isothermal(p_if, Tc, Ti, 1e-6, 4)
     assert n == 12 and p2.size == p_if.size + n and Tc2.size == Tc.size + n
     assert p2[0] == pytest.approx(1e-6 * 1e5) and np.all(np.diff(p2) > 0)
@@ -121,6 +121,6 @@ def test_isothermal_extension_above_the_model_top():
     np.testing.assert_array_equal(Ti2[n:], Ti)
     assert np.all(Tc2[:n] == Tc[0]) and np.all(Ti2[:n] == Tc[0])
     # a column already reaching 1 ubar is left as it is
-    p_if, Tc, Ti = rt_synth._profile(rng, 10, 1e-7)
+    p_if, Tc, Ti = rt_synth.column_profile(rng, 10, 1e-7)
     p3, _, _, n3 = rt_synth.extend_isothermal(p_if, Tc, Ti, 1e-6, 4)
     assert n3 == 0 and p3 is p_if
