@@ -625,16 +625,24 @@ def main():
     except OSError:
         pass
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    flop_per_sys = float(prof["flop_per_system"]) if prof else None
-    if flop_per_sys:
+    peak_tops = N_SM * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    ops_per_sys = float(prof["fp32_pipe_ops_per_system"]) if prof and "fp32_pipe_ops_per_system" in prof else None
+    if ops_per_sys:
+        # the FP32 pipes' bound: FMA-pipe operations per system (FFMA, FMUL
+        # and FADD one each, the paired forms two) over 148 SMs x 128 lanes
+        # x clock; FLOP/s (FFMA = 2) beside it
+        achieved_tops = ops_per_sys * n_sys / (ms_kernel * 1e-3) / 1e12
+        flop_per_sys = float(prof["flop_per_system"])
         achieved_tf = flop_per_sys * n_sys / (ms_kernel * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved_tf / peak_tflops,
+        roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
+                    "unit": "T FP32-pipe ops/s", "frac": achieved_tops / peak_tops,
                     "traffic": float(prof["dram_bytes_per_launch"]),
                     "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
                     "kernel_ms_source": f"CUDA events around each launch, mean of {len(kt_solve)} solves",
-                    "flop_per_system": flop_per_sys,
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "fp32_pipe_ops_per_system": ops_per_sys,
+                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
+                    "flops": {"achieved": achieved_tf, "peak": peak_tflops, "unit": "TFLOP/s",
+                              "frac": achieved_tf / peak_tflops, "flop_per_system": flop_per_sys},
                     "hbm": {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                             "frac": achieved_gbs / peak_gbs, "peak_source": peak_src,
                             "algorithmic_bytes_per_launch": alg_bytes}}
