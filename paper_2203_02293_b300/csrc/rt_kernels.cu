@@ -95,25 +95,6 @@ __device__ __forceinline__ float frcp(float x) {
 }
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 
-// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.25
-// (7 terms, truncation below 2e-9), else from the exponential e = exp(-x)
-// (relative error of 1 - e below 5e-7 there).
-__device__ __forceinline__ float u_series(float x) {
-    float p = -1.f / 40320.f;
-    p = fmaf(p, x, 1.f / 5040.f);
-    p = fmaf(p, x, -1.f / 720.f);
-    p = fmaf(p, x, 1.f / 120.f);
-    p = fmaf(p, x, -1.f / 24.f);
-    p = fmaf(p, x, 1.f / 6.f);
-    p = fmaf(p, x, -0.5f);
-    return fmaf(p, x, 1.f);
-}
-__device__ __forceinline__ float one_minus_exp_over_x(float x, float e) {
-    const float s = u_series(x);
-    const float d = (1.f - e) * frcp(x);
-    return (fabsf(x) < 0.25f) ? s : d;
-}
-
 // FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
 //   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms.
 __device__ __forceinline__ float planck_upper_f(float x) {
@@ -330,10 +311,12 @@ template <> struct VTraits<V2> {
     using C = U2;
 };
 
+// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.25
+// (7 terms, truncation below 2e-9); above that the callers use the exponential
+// e = exp(-x) directly (relative error of 1 - e below 5e-7 there).
 template <class V>
 __device__ __forceinline__ V u_series_v(V x) {
-    V p = V(-1.f / 40320.f);
-    p = vfma(p, x, V(1.f / 5040.f));
+    V p = V(1.f / 5040.f);
     p = vfma(p, x, V(-1.f / 720.f));
     p = vfma(p, x, V(1.f / 120.f));
     p = vfma(p, x, V(-1.f / 24.f));
@@ -444,20 +427,22 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
         vcount(sc.etau, fb);
         // Gradient form  su = dPi ((1-r) B1 - t B2) + G (B2 - B1),
         //                sd = dPi ((1-r) B2 - t B1) - G (B2 - B1),
-        // with G = Pi 2u/((1+k) h).  The e_tau fallback (isothermal at the mean
-        // B, Sec. 2.2.1) is the same expression with B1 = B2 = mean B and
-        // G = pi (1 - r + t)/2, so only the inputs are selected.
+        // with G = Pi 2u/((1+k) h), rewritten about the mean B = (B1 + B2)/2 as
+        //   su = dPi (1-r-t) B + G' (B2 - B1),  sd = dPi (1-r-t) B - G' (B2 - B1),
+        //   G' = G - dPi (1-r+t)/2.
+        // The e_tau fallback (isothermal at the mean B, Sec. 2.2.1, written in
+        // departures from pi B1 and pi B2) is the same expression with
+        // G' = pi (1-r+t)/2, so only G' is selected.
         const V pig = (Pi * (V(2.f) * u)) * (ip * ih);
-        const V side = V(0.5f * kPiF) * vfma(V(2.f), t, omtr);
-        const V G = vsel(fb, side, pig);
-        const V mU = V(0.5f) * (Bt + Bc), mL = V(0.5f) * (Bc + Bb);
-        const V tU = vsel(fb, mU, Bt), cU = vsel(fb, mU, Bc);   // upper sub-layer ends
-        const V cL = vsel(fb, mL, Bc), bL = vsel(fb, mL, Bb);   // lower sub-layer ends
+        const V hopr = V(0.5f) * vfma(V(2.f), t, omtr);         // (1 - r + t)/2
+        const V G = vsel(fb, V(kPiF) * hopr, vfma(-dPi, hopr, pig));
+        const V dom = dPi * omtr;
+        const V aU = dom * (V(0.5f) * (Bt + Bc)), aL = dom * (V(0.5f) * (Bc + Bb));
         const V gU = G * (Bc - Bt), gL = G * (Bb - Bc);
-        suU = vfma(dPi, vfma(omr, tU, -(t * cU)), gU);
-        sdU = vfma(dPi, vfma(omr, cU, -(t * tU)), -gU);
-        suL = vfma(dPi, vfma(omr, cL, -(t * bL)), gL);
-        sdL = vfma(dPi, vfma(omr, bL, -(t * cL)), -gL);
+        suU = aU + gU;
+        sdU = aU - gU;
+        suL = aL + gL;
+        sdL = aL - gL;
     } else {
         const V base = (dPi * Bc) * omtr;
         suU = vfma(V(kPiF), vfma(omr, Bc - Bt, -(t * (Bc - Bb))), base);
@@ -1087,6 +1072,11 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
             }
         }
         float4 *sp = kp.scr32 + slot;
+        // two layers per trip: the carried values (B at the levels, the
+        // prefetched optics, alpha' and b') alternate between two register
+        // sets instead of being copied at the end of every layer (not with
+        // the k-table front end, whose prefetched corners would spill)
+#pragma unroll(KT ? 1 : 2)
         for (int l = 0; l < L; ++l) {
             V dt, w0, g0;
             V nBc = V(0.f), nBb = V(0.f);
