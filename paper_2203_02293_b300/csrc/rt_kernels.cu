@@ -86,14 +86,28 @@ __device__ __forceinline__ float planck_lower_f(float x) {
 }
 
 // Fast FP32 primitives: MUFU reciprocal, reciprocal square root and
-// exponential (ex2 with the argument scaled by log2 e).  Each is accurate to a
-// few ulp, far inside the 1e-4 target.
+// exponential (exp(x) = 2^(x log2 e), the PTX ex2 after one multiply).  Each
+// is accurate to a few ulp, far inside the 1e-4 target.  The flush-to-zero
+// forms are safe here: the solve never feeds them subnormal arguments (E - w0
+// and the optical depths are either 0, handled by selects, or far above
+// 1e-38), and subnormal exponentials are below every flux floor.
 __device__ __forceinline__ float frcp(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ float fex2(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float frsqrt(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+constexpr float kLog2E = 1.44269504088896340736f;
 
 // FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
 //   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms.
@@ -280,10 +294,14 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ V2 vfma(V2 a, V2 b, V2 c) { return v2(__ffma2_rn(f2(a), f2(b), f2(c))); }
 __device__ __forceinline__ float vrcp(float a) { return frcp(a); }
 __device__ __forceinline__ V2 vrcp(V2 a) { return V2(frcp(a.v.x), frcp(a.v.y)); }
-__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
-__device__ __forceinline__ V2 vrsqrt(V2 a) { return V2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
-__device__ __forceinline__ float vexp(float a) { return fexp(a); }
-__device__ __forceinline__ V2 vexp(V2 a) { return V2(fexp(a.v.x), fexp(a.v.y)); }
+__device__ __forceinline__ float vrsqrt(float a) { return frsqrt(a); }
+__device__ __forceinline__ V2 vrsqrt(V2 a) { return V2(frsqrt(a.v.x), frsqrt(a.v.y)); }
+// exp(-a) = 2^(-a log2 e): one (paired) multiply, then ex2 per component
+__device__ __forceinline__ float vexpn(float a) { return fex2(a * -kLog2E); }
+__device__ __forceinline__ V2 vexpn(V2 a) {
+    const float2 y = __fmul2_rn(a.v, make_float2(-kLog2E, -kLog2E));
+    return V2(fex2(y.x), fex2(y.y));
+}
 __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 __device__ __forceinline__ V2 vabs(V2 a) { return V2(fabsf(a.v.x), fabsf(a.v.y)); }
 __device__ __forceinline__ float vsel(bool m, float a, float b) { return m ? a : b; }
@@ -406,7 +424,7 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
     const V q2 = q + q;
     const V q2d = q2 * dts;
     const V x = q2d * k;
-    const V Tm = vexp(-x);
+    const V Tm = vexpn(x);
     const V u = vsel(vabs(x) < V(0.25f), u_series_v(x), (V(1.f) - Tm) * vrcp(x));
     const V qd = q2d * u;                         // (1 - T)/k
     const V h = vfma(Tm + Tm, ip, qd);
@@ -452,7 +470,7 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
     V m = V(1.f);
     if (beam) {
         const V dl = dts * V(imu);
-        m = vexp(-dl);
+        m = vexpn(dl);
         const V omm = vsel(dl < V(0.25f), dl * u_series_v(dl), V(1.f) - m);   // 1 - m
         const V q2k = q2 * k;
         const V rho = V(mu) * q2k;
