@@ -59,9 +59,9 @@ enum { RT_NONISOTHERMAL = 0, RT_ISOTHERMAL = 1 };
  * resonance test near |D| = 1e-5), or FP64 with the paper's literal
  * formulas. */
 enum { RT_FP32_FORM = 0, RT_FP64_PLAIN = 1 };
-/* Where the FP32 solve reads the bin-integrated Planck values (no effect on
- * results, which are bitwise the same either way). */
-enum { RT_STAGE_AUTO = 0, RT_STAGE_SHARED = 1, RT_STAGE_DIRECT = 2 };
+/* Where the FP32 solve gets the bin-integrated Planck values (no effect on
+ * results, which are bitwise the same every way). */
+enum { RT_STAGE_AUTO = 0, RT_STAGE_SHARED = 1, RT_STAGE_DIRECT = 2, RT_STAGE_INLINE = 3 };
 /* Beam singularity of Eq. B8 at D = 4 E mu*^2 (E - w0)(1 - w0 g0) - 1 = 0
  * (Eq. 11): PAPER switches D to 2 mu* when |D| < 1e-5 (text after Eq. 11);
  * LIMIT uses the exact (finite) solution at every mu*. */
@@ -90,12 +90,20 @@ typedef struct {
                                     form, 64..512 for FP64); 0 = default (256) */
     int32_t ctas_per_sm;         /* cap on resident CTAs per SM of the persistent grid;
                                     0 = as many as fit */
-    int32_t planck_staging;      /* FP32 form, where the solve reads B(T) per bin:
-                                    RT_STAGE_AUTO, RT_STAGE_SHARED (staged per
+    int32_t planck_staging;      /* FP32 form, where the solve gets B(T) per bin:
+                                    RT_STAGE_AUTO, RT_STAGE_SHARED (a pre-kernel
+                                    tabulates B per column and level; staged per
                                     warp in shared memory; pays off when many
-                                    g-points share a bin) or RT_STAGE_DIRECT
-                                    (read from the per-column table in device
-                                    memory; for few g-points per bin) */
+                                    g-points share a bin), RT_STAGE_DIRECT (read
+                                    from that table in device memory) or
+                                    RT_STAGE_INLINE (no table: the solve kernel
+                                    evaluates B for each system at each level;
+                                    for one g-point on narrow bins, where the
+                                    table's write and reads cost more than the
+                                    sums).  AUTO: INLINE for n_g = 1 with
+                                    explicit edges all at most 1% of their lower
+                                    edge apart, else DIRECT for n_g < 4, else
+                                    SHARED */
     int32_t systems_per_lane;    /* FP32 form: systems each GPU lane carries, 1 or 2
                                     (0 = 2: two systems share the paired FP32
                                     instructions of sm_100+); results differ only

@@ -37,6 +37,7 @@ struct rt_handle {
     std::vector<double> edges;
     double *d_edges = nullptr;
     float *d_edges32 = nullptr;   // [n_edges] edges, then [n_edges - 1] widths, FP32
+    bool narrow_edges = false;    // every explicit bin at most 1% of its lower edge wide
     // k-table front end
     bool kt_set = false;
     int kt_nT = 0, kt_nP = 0, kt_NB = 0;
@@ -95,7 +96,7 @@ struct Plan {
     int64_t n_units = 0;
     int Lmax = 0, NBmax = 0;
     // launch
-    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, ns = 1;
+    int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, inline_b = 0, ns = 1;
     size_t smem = 0;
     int64_t n_slots = 0;
     // workspace layout (bytes); the plan blob is int32 arrays then int64 arrays
@@ -198,8 +199,14 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
                 P.nbw = rt::bins_per_chunk(spu, cfg.n_g, P.NBmax);
                 // staging B per warp pays off when several lanes share a bin;
                 // with few g-points per bin it only costs shared memory
-                // (occupancy), so the lanes read the table directly
-                P.direct = cfg.planck_staging == RT_STAGE_DIRECT ||
+                // (occupancy), so the lanes read the table directly.  With
+                // one g-point on narrow bins (the R = 500 shape) the solve
+                // kernel evaluates B itself, each value once, instead of a
+                // table written and read back through HBM (wide bins need
+                // edge series, which the pre-kernel shares between bins).
+                P.inline_b = cfg.planck_staging == RT_STAGE_INLINE ||
+                             (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g == 1 && h->narrow_edges);
+                P.direct = P.inline_b || cfg.planck_staging == RT_STAGE_DIRECT ||
                            (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g < 4);
                 P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct);
                 P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct);
@@ -220,6 +227,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
             P.block -= 32;
         }
         P.n_slots = (int64_t)P.grid * P.block * P.ns;
+        if (P.inline_b) P.n_planck = 0;           // no B table: the solve kernel evaluates B
     }
     P.i32_count = 4 * (size_t)n + 2 * (size_t)P.n_units;
     P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
@@ -228,6 +236,8 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
     P.scr_bytes = (size_t)P.n_slots *
                   (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
                         : rt::fp32_scratch_per_slot(P.Lmax));
+    // inline B: the interfaces' B for the back-substitution, after the elimination scratch
+    if (P.inline_b) P.scr_bytes = align_up(P.scr_bytes, 256) + sizeof(float) * (size_t)P.n_slots * P.Lmax;
     // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf [| kt_lay]
     P.aux_bytes = fp64 ? 0
                        : align_up(sizeof(float) * (size_t)P.n_part, 256) + align_up(sizeof(int32_t) * (size_t)n, 256) +
@@ -307,7 +317,7 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
         (cfg->block_threads % 32 || cfg->block_threads < 64 || cfg->block_threads > rt::kMaxBlock))
         return RT_EINVAL;
     if (cfg->ctas_per_sm < 0) return RT_EINVAL;
-    if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_DIRECT) return RT_EINVAL;
+    if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_INLINE) return RT_EINVAL;
     if (cfg->systems_per_lane < 0 || cfg->systems_per_lane > 2) return RT_EINVAL;
     if (cfg->n_edges < 0 || cfg->n_edges == 1 || (cfg->n_edges > 1 && !cfg->wn_edges)) return RT_EINVAL;
     for (int i = 0; i < cfg->n_edges; ++i) {
@@ -324,6 +334,9 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     h->cfg.g_weights = h->gw.data();
     if (cfg->n_edges > 1) h->edges.assign(cfg->wn_edges, cfg->wn_edges + cfg->n_edges);
     h->cfg.wn_edges = h->edges.empty() ? nullptr : h->edges.data();
+    h->narrow_edges = !h->edges.empty();
+    for (size_t i = 0; i + 1 < h->edges.size(); ++i)
+        h->narrow_edges = h->narrow_edges && h->edges[i + 1] - h->edges[i] <= 0.01 * h->edges[i];
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = rt::init_kernels();
@@ -578,6 +591,9 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.warp_floats = P.warp_floats;
         kp.nbw = P.nbw;
         kp.direct = P.direct;
+        kp.inline_b = P.inline_b;
+        if (P.inline_b)
+            kp.scrB = (char *)h->scr.p + align_up((size_t)P.n_slots * rt::fp32_scratch_per_slot(P.Lmax), 256);
         kp.ns = P.ns;
         kp.planck32 = d_planck;
         kp.planck_off = d_pkoff;

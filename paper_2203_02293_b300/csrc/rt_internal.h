@@ -58,6 +58,8 @@ struct KParams {
     const float *g_w32;          // [n_g] Gauss weights in FP32
     int32_t nbw;                 // bins one warp's 32 systems can touch
     int32_t direct;              // 1: read B from planck32 directly (no staging)
+    int32_t inline_b;            // 1: the solve kernel evaluates B per system (no planck32 levels)
+    void *scrB;                  // inline_b: B per interface, [level][thread slot] x systems per lane
     int32_t ns;                  // systems per lane (1 or 2; 0 counts as 1)
     // scheduling and counters
     int32_t *counter;

@@ -28,7 +28,9 @@
 //                    column, one thread per system, scalar Thomas on every
 //                    level (sub-layers not merged).
 #include <cuda_runtime.h>
+#include <array>
 #include <type_traits>
+#include <utility>
 
 #include <cmath>
 #include <cstdint>
@@ -123,24 +125,6 @@ __device__ __forceinline__ float planck_upper_f(float x) {
         en *= e;
     }
     return s;
-}
-
-// Bin-integrated Planck function (W m^-2 sr^-1) between two wavenumbers
-// (cm^-1), FP32.  The difference is taken in the form without cancellation.
-__device__ float planck_bin_f(float T, float wlo, float whi) {
-    if (!(T > 0.f)) return 0.f;
-    const float a = (float)(kC2 * 100.0) * frcp(T);
-    const float xlo = a * wlo, xhi = a * whi;
-    float d;
-    if (xlo >= 2.f) {
-        d = planck_upper_f(xlo) - planck_upper_f(xhi);
-    } else if (xhi <= 2.f) {
-        d = planck_lower_f(xhi) - planck_lower_f(xlo);
-    } else {
-        d = ((float)kPi4Over15 - planck_lower_f(xlo)) - planck_upper_f(xhi);
-    }
-    const float T2 = T * T;
-    return (float)kPlanckK * (T2 * T2) * d;
 }
 
 // FP64 versions (terms to k = 30 below x = 2, 20 exponential terms above).
@@ -622,23 +606,16 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
     const int nlev = 2 * ci.L + 1;
     const double dwn = (kp.wn_max - kp.wn_min) / ci.NB;
     auto edge = [&](int e) { return kp.edges ? kp.edges[e] : kp.wn_min + e * dwn; };
+    static_assert(sizeof(R) == 8, "the FP32 form stages B in fp32_units");
     for (int i = threadIdx.x; i < nlev * nbc; i += blockDim.x) {
         const int lev = i / nbc, bb = i - lev * nbc, b = b_lo + bb;
         const double T = (lev & 1) ? kp.T_center[ci.tc_in + (lev >> 1)] : kp.T_iface[ci.if_in + (lev >> 1)];
-        const double wlo = edge(b), whi = edge(b + 1);
-        if constexpr (sizeof(R) == 4)
-            sm.sB[i] = planck_bin_f((float)T, (float)wlo, (float)whi);
-        else
-            sm.sB[i] = planck_bin_d(T, wlo, whi);
+        sm.sB[i] = planck_bin_d(T, edge(b), edge(b + 1));
     }
     for (int bb = threadIdx.x; bb < nbc; bb += blockDim.x) {
         const int b = b_lo + bb;
-        const double wlo = edge(b), whi = edge(b + 1);
         sm.sFs[bb] = (R)kp.F_star[ci.fs_in + b];
-        if constexpr (sizeof(R) == 4)
-            sm.sFB[bb] = kPiF * planck_bin_f((float)kp.T_int, (float)wlo, (float)whi);
-        else
-            sm.sFB[bb] = kPi * planck_bin_d(kp.T_int, wlo, whi);
+        sm.sFB[bb] = kPi * planck_bin_d(kp.T_int, edge(b), edge(b + 1));
     }
 }
 
@@ -706,16 +683,42 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 // One (column, level) per warp: lane e evaluates the Planck integral at bin
 // edge e (whichever of S(x) or P(x) that edge needs), and bin b takes edges b
 // and b+1 from its lane and the next (shuffle).  31 bins per pass.
-// x^3 / (e^x - 1), the Planck integrand in x = h c nu / (k T).  Below x = 1/2
-// e^x - 1 is formed from its Taylor series (expm1(x) / x to x^6 / 7!,
-// truncation < 2e-7 relative) so that small x keeps its digits.
-__device__ __forceinline__ float planck_integrand_f(float x) {
-    if (x < 0.5f) {
-        const float q = fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 5040.f, 1.f / 720.f),
-                                                          1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
-        return x * x * frcp(q);
-    }
-    return x * x * x * frcp(__expf(x) - 1.f);
+// x^3 / (e^x - 1), the Planck integrand in x = h c nu / (k T), as num/den so
+// that two quadrature nodes share one reciprocal:
+//   x < 1/2:  x^2 / q,  q = (e^x - 1)/x from its Taylor series (to x^6 / 7!,
+//             truncation < 2e-7 relative), so that small x keeps its digits;
+//   x >= 1/2: x^3 m / (1 - m),  m = e^-x  (1 - m >= 0.39: no cancellation,
+//             and no overflow however large x is).
+// Written over V (one value, or two on the paired instructions) with every
+// operation rounded on its own, so that the pre-kernel's table, the solve
+// kernel's own evaluation (RT_STAGE_INLINE) and one or two systems per lane
+// all give the same bits.
+template <class V>
+struct PlanckND {
+    V num, den;
+};
+template <class V>
+__device__ __forceinline__ PlanckND<V> planck_nd(V x) {
+    V q = V(1.f / 5040.f);
+    q = vfma(q, x, V(1.f / 720.f));
+    q = vfma(q, x, V(1.f / 120.f));
+    q = vfma(q, x, V(1.f / 24.f));
+    q = vfma(q, x, V(1.f / 6.f));
+    q = vfma(q, x, V(0.5f));
+    q = vfma(q, x, V(1.f));
+    const V xx = x * x;
+    const V m = vexpn(x);
+    const auto small = x < V(0.5f);
+    PlanckND<V> r;
+    r.num = vsel(small, xx, (xx * x) * m);
+    r.den = vsel(small, q, V(1.f) - m);
+    return r;
+}
+// f(xa) + f(xb) with one reciprocal
+template <class V>
+__device__ __forceinline__ V planck_pair(V xa, V xb) {
+    const PlanckND<V> a = planck_nd(xa), b = planck_nd(xb);
+    return vfma(a.num, b.den, b.num * a.den) * vrcp(a.den * b.den);
 }
 
 // Bins narrower than this in x = h c nu / (k T) are integrated by quadrature.
@@ -725,54 +728,81 @@ constexpr float kNarrowBin = 0.5f;
 constexpr float kTwoPointBin = 0.1f;
 constexpr float kGL2x = 0.57735026918962576f;
 // 4-point Gauss-Legendre on [-1, 1]: outer and inner nodes with their weights.
-__constant__ float kGL4x[2] = {0.86113631159405258f, 0.33998104358485626f};
-__constant__ float kGL4w[2] = {0.34785484513745386f, 0.65214515486254614f};
+constexpr float kGL4xo = 0.86113631159405258f, kGL4xi = 0.33998104358485626f;
+constexpr float kGL4wo = 0.34785484513745386f, kGL4wi = 0.65214515486254614f;
+
+// Integral of x^3/(e^x - 1) over a narrow bin [x, x + 2 hh] (e.g. R = 500)
+// by Gauss-Legendre: the edge difference would lose the digits that the
+// edges' own FP32 rounding carries, so the half width hh comes from the
+// bin width formed in FP64 before rounding.  2 points are below 2e-8
+// relative for the widths that take them.
+template <class V>
+__device__ __forceinline__ V planck_two_point(V x, V hh) {
+    const V xm = x + hh;
+    return hh * planck_pair(vfma(hh, V(-kGL2x), xm), vfma(hh, V(kGL2x), xm));
+}
+__device__ __forceinline__ bool planck_takes_two_points(float x, float hh) {
+    return hh < 0.5f * kTwoPointBin && hh < __fmul_rn(0.01f, __fadd_rn(x, hh));
+}
+__device__ __forceinline__ float planck_narrow_f(float x, float hh) {
+    if (planck_takes_two_points(x, hh)) return planck_two_point(x, hh);
+    const float xm = __fadd_rn(x, hh);
+    const float outer = planck_pair(fmaf(hh, -kGL4xo, xm), fmaf(hh, kGL4xo, xm));
+    const float inner = planck_pair(fmaf(hh, -kGL4xi, xm), fmaf(hh, kGL4xi, xm));
+    return __fmul_rn(hh, fmaf(kGL4wo, outer, __fmul_rn(kGL4wi, inner)));
+}
+
+// One edge's series value: S(x) below x = 2, P(x) above.
+__device__ __forceinline__ float planck_edge_f(float x) { return (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x); }
+
+// Integral of x^3/(e^x - 1) over a wide bin [x0, x1] from the edge series
+// v0, v1 (planck_edge_f), in the difference without cancellation.
+__device__ __forceinline__ float planck_wide_f(float x0, float x1, float v0, float v1) {
+    if (x0 >= 2.f) return __fsub_rn(v0, v1);
+    if (x1 < 2.f) return __fsub_rn(v1, v0);
+    return __fsub_rn(__fsub_rn((float)kPi4Over15, v0), v1);
+}
+
+// Per-level factors of the bin-integrated Planck function B = K T^4 d(x):
+// a = c2 / T (x = a nu) and K T^4 (times `scale`).
+struct PlanckLevel {
+    float a, pref;
+};
+__device__ __forceinline__ PlanckLevel planck_level(float T, float scale) {
+    PlanckLevel lv;
+    lv.a = (T > 0.f) ? __fmul_rn((float)(kC2 * 100.0), frcp(T)) : 0.f;
+    const float T2 = __fmul_rn(T, T);
+    lv.pref = (T > 0.f) ? __fmul_rn(__fmul_rn((float)kPlanckK, __fmul_rn(T2, T2)), scale) : 0.f;
+    return lv;
+}
+
+// B of one bin [wn0, wn1] (cm^-1, FP32 edges; dnu its width formed in FP64).
+__device__ __forceinline__ float planck_bin32(PlanckLevel lv, float wn0, float wn1, float dnu) {
+    const float x0 = __fmul_rn(lv.a, wn0), x1 = __fmul_rn(lv.a, wn1);
+    float d;
+    if (__fsub_rn(x1, x0) < kNarrowBin)
+        d = planck_narrow_f(x0, __fmul_rn(0.5f, __fmul_rn(lv.a, dnu)));
+    else
+        d = planck_wide_f(x0, x1, planck_edge_f(x0), planck_edge_f(x1));
+    return __fmul_rn(lv.pref, d);
+}
 
 // B of one level for the warp's chunk of 31 bins [b0, b0 + 31): lane e
-// holds edge b0 + e at x = a wn (x1: the next edge, from lane e + 1).
+// holds edge b0 + e at x = a wn (x1: the next edge, from lane e + 1); the
+// wide bins share their edges' series values with the neighbouring lane.
 __device__ __forceinline__ float planck_chunk_level(float T, float scale, float wn, float dnu_b, bool inb,
                                                     int lane) {
-    const float a = (T > 0.f) ? (float)(kC2 * 100.0) * frcp(T) : 0.f;
-    const float T2 = T * T;
-    const float pref = (float)kPlanckK * (T2 * T2) * scale;
-    const float x = a * wn;
+    const PlanckLevel lv = planck_level(T, scale);
+    const float x = __fmul_rn(lv.a, wn);
     const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
-    const bool narrow = !inb || (x1 - x < kNarrowBin);
+    const bool narrow = !inb || (__fsub_rn(x1, x) < kNarrowBin);
     // the edge series are needed only when some bin of this chunk is wide
     float v = 0.f;
-    if (!__all_sync(0xffffffffu, narrow)) v = (x < 2.f) ? planck_lower_f(x) : planck_upper_f(x);
+    if (!__all_sync(0xffffffffu, narrow)) v = planck_edge_f(x);
     const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
-    float d;
-    if (narrow) {
-        // narrow bin (e.g. R = 500): the edge difference would lose the
-        // digits that the edges' own FP32 rounding carries, so integrate
-        // x^3/(e^x - 1) over the bin by Gauss-Legendre (2 or 4 points), the
-        // width formed from the FP64 edges before rounding (no FP64
-        // arithmetic here: it is slow on this part)
-        const float hh = 0.5f * a * dnu_b;        // half width in x
-        const float xm = x + hh;
-        float acc;
-        if (hh < 0.5f * kTwoPointBin && hh < 0.01f * xm) {
-            // 2 points: below 2e-8 relative for these widths
-            acc = planck_integrand_f(fmaf(-hh, kGL2x, xm)) + planck_integrand_f(fmaf(hh, kGL2x, xm));
-        } else {
-            acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float t = (k < 2) ? -kGL4x[k] : kGL4x[3 - k];
-                const float xk = fmaf(hh, t, xm);
-                acc = fmaf(kGL4w[k < 2 ? k : 3 - k], planck_integrand_f(xk), acc);
-            }
-        }
-        d = hh * acc;
-    } else if (x >= 2.f) {
-        d = v - v1;
-    } else if (x1 <= 2.f) {
-        d = v1 - v;
-    } else {
-        d = ((float)kPi4Over15 - v) - v1;
-    }
-    return (T > 0.f) ? pref * d : 0.f;
+    const float d = narrow ? planck_narrow_f(x, __fmul_rn(0.5f, __fmul_rn(lv.a, dnu_b)))
+                           : planck_wide_f(x, x1, v, v1);
+    return __fmul_rn(lv.pref, d);
 }
 
 // ---------------------------------------------------------------------
@@ -867,26 +897,27 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             for (int l = threadIdx.x; l < L; l += blockDim.x)
                 kp.kt_lay[kp.lay_off[c] + l] =
                     kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], NB * kp.n_g);
-        if (warp == 0) {
-            for (int b = lane; b < NB; b += 32) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
-            if (lane == 0) {
-                const double mu = kp.mu_star[kp.mu_idx[c]];
-                kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
-            }
+        for (int b = threadIdx.x; b < NB; b += blockDim.x) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
+        if (threadIdx.x == 0) {
+            const double mu = kp.mu_star[kp.mu_idx[c]];
+            kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
         }
         __syncthreads();
         const int nchunk = (NB + 30) / 31;
-        const int nl = nlev + 1;                  // levels including T_int
+        // levels [lev0, nlev]: the 2L+1 levels, then T_int (T_int alone when
+        // the solve kernel evaluates B itself)
+        const int lev0 = kp.inline_b ? nlev : 0;
+        const int nl = nlev + 1 - lev0;
         int run = (int)(((long long)nl * nchunk + nw - 1) / nw);
         run = run < nl ? run : nl;
         const int nrun = (nl + run - 1) / run;
         for (int task = warp; task < nchunk * nrun; task += nw) {
-            const int ch = task % nchunk, r0 = (task / nchunk) * run;
+            const int ch = task % nchunk, r0 = lev0 + (task / nchunk) * run;
             const int e = ch * 31 + lane, bin = e;
             const bool inb = lane < 31 && bin < NB;
             const float wn = kp.edges32 ? __ldg(kp.edges32 + min(e, NB)) : fmaf((float)e, dwn, wmin);
             const float dnu_b = kp.edges32 ? __ldg(kp.dnu32 + min(bin, NB - 1)) : dwn;
-            const int r1 = min(r0 + run, nl);
+            const int r1 = min(r0 + run, nlev + 1);
             for (int lev = r0; lev < r1; ++lev) {
                 const bool tint = lev == nlev;
                 const float v = planck_chunk_level(sT[lev], tint ? kPiF : 1.f, wn, dnu_b, inb, lane);
@@ -925,6 +956,12 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     }
 }
 
+// Where the solve kernel gets a system's B at the levels: staged per unit in
+// the warp's shared memory from the pre-kernel's table, read straight from
+// that table, or evaluated per system in the kernel (no table; the per-bin
+// work is not shared when few g-points share a bin).
+constexpr int kStageShared = 0, kStageDirect = 1, kStageInline = 2;
+
 // Planck values of a lane's bin: staged in the warp's shared memory (level
 // stride nbc) or, when few g-points share a bin (DIRECT), read straight from
 // the pre-kernel's table (level stride NB) through the read-only path.
@@ -937,7 +974,7 @@ __device__ __forceinline__ float ldB(const float *p) {
 // Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
 // back.  `after` is a value loaded from that line: the compare that reads it
 // makes the discard issue only once the load has returned.
-__device__ __forceinline__ void discard_l2_after(const float4 *p, float after) {
+__device__ __forceinline__ void discard_l2_after(const void *p, float after) {
     asm volatile(
         "{\n\t.reg .pred d;\n\tsetp.ne.f32 d, %1, %1;\n\tdiscard.global.L2 [%0], 128;\n\t}" ::"l"(p),
         "f"(after)
@@ -967,28 +1004,378 @@ __device__ __forceinline__ void scr_unpack(const float4 *n, V2 &P, V2 &Q, V2 &a,
     e = V2(n[1].z, n[1].w);
 }
 
+// B at the interfaces kept for the back-substitution (RT_STAGE_INLINE):
+// [interface][thread slot], the lane's systems side by side.
+__device__ __forceinline__ void stB(float *p, float v) { __stcg(p, v); }
+__device__ __forceinline__ void stB(V2 *p, V2 v) { __stcg((float2 *)p, v.v); }
+__device__ __forceinline__ float ldB_cg(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ V2 ldB_cg(const V2 *p) { return V2(__ldcg((const float2 *)p)); }
+
 // Component access for per-system values (one system per lane: float; two:
 // V2) and per-system loads.
 __device__ __forceinline__ float &cmp(float &v, int) { return v; }
 __device__ __forceinline__ float &cmp(V2 &v, int i) { return i ? v.v.y : v.v.x; }
+__device__ __forceinline__ float cmp(const float &v, int) { return v; }
+__device__ __forceinline__ float cmp(const V2 &v, int i) { return i ? v.v.y : v.v.x; }
 __device__ __forceinline__ float hsum(float v) { return v; }
 __device__ __forceinline__ float hsum(V2 v) { return v.v.x + v.v.y; }
 __device__ __forceinline__ bool &cmpm(bool &m, int) { return m; }
 __device__ __forceinline__ bool &cmpm(M2 &m, int i) { return i ? m.y : m.x; }
 
-template <bool ISO, bool DIRECT, bool KT, int NS>
-__global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KParams kp) {
+// One work unit: SPU = 32 NS consecutive systems of one column, starting at
+// system s0 = ku SPG of the column (SPG: the kernel's unit stride).
+template <bool ISO, int ST, bool KT, int NS, int SPG>
+__device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
+                                          float *tb, long long slot, long long gthreads, long long sstride,
+                                          Counters &cn) {
     using V = typename std::conditional<NS == 2, V2, float>::type;
     using M = typename VTraits<V>::M;
-    constexpr int SPU = 32 * NS;                   // systems per work unit
+    constexpr bool DIRECT = ST != kStageShared;    // B not staged in shared memory
+    constexpr bool INL = ST == kStageInline;       // B evaluated here, per system
+    constexpr int SPU = 32 * NS;                   // systems in this unit
+    const int NG = kp.n_g;
+    const int c = kp.unit_col[unit];
+    const int ku = kp.unit_k[unit];
+    const int L = kp.n_layers[c], NB = kp.n_bins[c];
+    const int S = NB * NG;
+    const long long cube0 = kp.cube_off[c];
+    const float4 cf = kp.colf[c];
+    const float mu = cf.x, imu = cf.y;
+    const double mu_d = kp.mu_star[kp.mu_idx[c]];   // only for the rare FP64 resonance test
+    const bool beam = cf.z != 0.f;
+    const int s0 = ku * SPG;
+    const int b_lo = s0 / NG;
+    const int nbc = min(NB - 1, (s0 + SPU - 1) / NG) - b_lo + 1;
+
+    // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
+    {
+        const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
+        const int nlev = 2 * L + 1;
+        if constexpr (!DIRECT) {
+            for (int i = lane; i < nlev * nbc; i += 32) {
+                const int lev = i / nbc, bb = i - lev * nbc;
+                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+            }
+        }
+        for (int j = lane; j < nbc; j += 32) {
+            sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
+            sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
+        }
+    }
+    __syncwarp();
+
+    // component i of this lane is system s0 + 32 i + lane; padding
+    // systems of a column's last unit repeat system s0 with zero weight,
+    // so the loops below need no per-lane predicates
+    M on;
+    int sI[NS], bI[NS];
+    V wg, Fb, Bt, Bc, Bb;
+    const float *Bp[NS];
+    const int bst = DIRECT ? NB : nbc;         // level stride of Bp
+    // INL: the bins' edges and FP64-formed widths, and the level temperatures
+    float wn0[NS], wn1[NS], dnu[NS];
+    const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c];
+    V wn0v, wn1v, dnuv;
+    auto B_at = [&](int lev, V &B) {           // B of the lane's systems at level lev
+        const double Td = (lev & 1) ? __ldg(kp.T_center + tc0 + (lev >> 1)) : __ldg(kp.T_iface + ifi + (lev >> 1));
+        const PlanckLevel lv = planck_level((float)Td, 1.f);
+        // narrow bins that take two quadrature points (the R = 500 shape):
+        // the lane's systems together on the paired instructions; any other
+        // bin through the per-system rule (the same bits either way)
+        const V a = V(lv.a);
+        const V x0 = a * wn0v, hh = V(0.5f) * (a * dnuv), w = a * wn1v - x0;
+        bool fast = true;
+#pragma unroll
+        for (int i = 0; i < NS; ++i)
+            fast = fast && cmp(w, i) < kNarrowBin && planck_takes_two_points(cmp(x0, i), cmp(hh, i));
+        if (__all_sync(0xffffffffu, fast)) {
+            B = V(lv.pref) * planck_two_point(x0, hh);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) cmp(B, i) = planck_bin32(lv, wn0[i], wn1[i], dnu[i]);
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const bool act = s0 + 32 * i + lane < S;
+        cmpm(on, i) = act;
+        sI[i] = act ? s0 + 32 * i + lane : s0;
+        bI[i] = sI[i] / NG;
+        cmp(wg, i) = act ? kp.g_w32[sI[i] - bI[i] * NG] : 0.f;
+        Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo);
+        cmp(Fb, i) = beam ? mu * sFs[bI[i] - b_lo] : 0.f;
+        if constexpr (INL) {
+            if (kp.edges32) {
+                wn0[i] = __ldg(kp.edges32 + bI[i]);
+                wn1[i] = __ldg(kp.edges32 + bI[i] + 1);
+                dnu[i] = __ldg(kp.dnu32 + bI[i]);
+            } else {
+                const float dwn = (float)((kp.wn_max - kp.wn_min) / NB), wmin = (float)kp.wn_min;
+                wn0[i] = fmaf((float)bI[i], dwn, wmin);
+                wn1[i] = fmaf((float)(bI[i] + 1), dwn, wmin);
+                dnu[i] = dwn;
+            }
+        } else {
+            // the B of a layer's bottom interface is carried as the next layer's top
+            cmp(Bt, i) = ldB<DIRECT>(Bp[i]);
+            cmp(Bc, i) = ldB<DIRECT>(Bp[i] + bst);
+            cmp(Bb, i) = ldB<DIRECT>(Bp[i] + 2 * bst);
+        }
+    }
+    if constexpr (INL) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            cmp(wn0v, i) = wn0[i];
+            cmp(wn1v, i) = wn1[i];
+            cmp(dnuv, i) = dnu[i];
+        }
+        B_at(0, Bt);
+        B_at(1, Bc);
+        B_at(2, Bb);
+    }
+    SysCounts<V> sc;
+    sc.inv = sc.ecl = sc.etau = typename VTraits<V>::C{};
+
+    // forward elimination, TOA -> BOA, departure variables
+    V al = V(1.f);                                       // alpha' = 1 - a'
+    V bl = vfma(V(-kPiF), Bt, V((float)kp.F_toa));       // b' at the TOA
+    // optics: read from the cubes, or (KT) from the k-table corners of
+    // the layer's grid cell, fetched one layer ahead
+    V nd = V(0.f), nw = V(0.f), ng = V(0.f);
+    const float *pd[NS], *pw[NS], *pg[NS];
+    const float4 *klay = nullptr;
+    float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next;
+    float4 kb[NS];
+    Corners kc[NS];
+    if constexpr (KT) {
+        klay = kp.kt_lay + kp.lay_off[c];
+        kl_next = klay[0];
+        kl_after = L > 1 ? klay[1] : kl_next;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            kb[i] = __ldg(kp.kt_bin + bI[i]);
+            kc[i] = kt_corners(kp, kl_next, S, sI[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const long long e = cube0 + sI[i];
+            pd[i] = kp.dtau + e;
+            pw[i] = kp.w0 + e;
+            pg[i] = kp.g0 + e;
+            cmp(nd, i) = __ldcs(pd[i]);
+            cmp(nw, i) = __ldcs(pw[i]);
+            cmp(ng, i) = __ldcs(pg[i]);
+        }
+    }
+    float4 *sp = kp.scr32 + slot;
+    V *spB = INL ? (V *)kp.scrB + slot : nullptr;
+    // two layers per trip: the carried values (B at the levels, the
+    // prefetched optics, alpha' and b') alternate between two register
+    // sets instead of being copied at the end of every layer (not with the
+    // k-table front end or inline B, whose extra live values would spill)
+#pragma unroll((KT || INL) ? 1 : 2)
+    for (int l = 0; l < L; ++l) {
+        V dt, w0, g0;
+        V nBc = V(0.f), nBb = V(0.f);
+        if constexpr (KT) {
+            const float4 kl = kl_next;
+            Corners cur[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) cur[i] = kc[i];
+            if (l + 1 < L) {                     // prefetch the next layer's corners
+                kl_next = kl_after;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) kc[i] = kt_corners(kp, kl_next, S, sI[i]);
+                if (l + 2 < L) kl_after = klay[l + 2];
+            }
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                const Optics o = kt_mix(cur[i].k00, cur[i].k01, cur[i].k10, cur[i].k11, kl, kb[i]);
+                cmp(dt, i) = o.dt;
+                cmp(w0, i) = o.w0;
+                cmp(g0, i) = o.g0;
+            }
+        } else {
+            dt = nd;
+            w0 = nw;
+            g0 = ng;
+            if (l + 1 < L) {                     // prefetch the next layer
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    pd[i] += S;
+                    pw[i] += S;
+                    pg[i] += S;
+                    cmp(nd, i) = __ldcs(pd[i]);
+                    cmp(nw, i) = __ldcs(pw[i]);
+                    cmp(ng, i) = __ldcs(pg[i]);
+                }
+            }
+
+        }
+        if (l + 1 < L) {
+            if constexpr (INL) {
+                B_at(2 * l + 3, nBc);
+                B_at(2 * l + 4, nBb);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    cmp(nBc, i) = ldB<DIRECT>(Bp[i] + 3 * bst);
+                    cmp(nBb, i) = ldB<DIRECT>(Bp[i] + 4 * bst);
+                }
+            }
+        }
+        if constexpr (INL) {
+            stB(spB, Bt);                         // B at interface l, for the back-substitution
+            spB += gthreads;
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Bp[i] += 2 * bst;   // level 2 (l + 1)
+        const Layer32<V> ly = layer32<ISO, V>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
+        Bt = Bb;
+        Bc = nBc;
+        Bb = nBb;
+        const V omr = ly.omtr + ly.T;                      // 1 - R
+        const V ipv = vrcp(vfma(ly.R, al, omr));           // 1 / (1 - R a')
+        const V P = ly.T * ipv;
+        const V Qv = vfma(ly.R, bl, ly.Su) * ipv;
+        scr_store(sp, gthreads, P, Qv, al, bl + Fb);      // e = b' + F_beam
+        sp += sstride;
+        const V al_n = vfma(al, vfma(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
+        const V bl_n = vfma(ly.T * vfma(V(1.f) - al, ly.Su, bl), ipv, ly.Sd);
+        al = al_n;
+        bl = bl_n;
+        Fb = Fb * ly.mlay;
+    }
+
+    cn.inv += vmasked(sc.inv, on);
+    cn.eclamp += vmasked(sc.ecl, on);
+    cn.etau += (ISO ? 1u : 2u) * vmasked(sc.etau, on);
+    // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b';
+    // back-substitution to the TOA; interface sums through the transpose
+    V FBOA;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) cmp(FBOA, i) = sFB[bI[i] - b_lo];
+    V uu = ((FBOA + Fb) + bl) * vrcp(al);
+    bool bad[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) bad[i] = !isfinite(cmp(uu, i));   // NaN and Inf propagate upwards
+    float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
+    // Bt holds B at level 2L (the BOA interface)
+    tb[lane] = hsum(wg * vfma(V(kPiF), Bt, uu));
+    tb[33 + lane] = hsum(wg * FBOA);
+    V nBi;                   // Bp is at level 2L; prefetch one interface up
+    if constexpr (INL) {
+        spB -= gthreads;     // interface L-1
+        nBi = ldB_cg(spB);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldB<DIRECT>(Bp[i] - 2 * bst);
+    }
+    int gi = 1;              // slots used in the current group of 16 interfaces
+    int gtop = L;            // interface held in slot 0 of the group
+    sp -= sstride;           // interface L-1
+    float4 nst[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) nst[i] = __ldcg(sp + i * gthreads);
+    for (int i = L - 1; i >= -1; --i) {
+        if (i >= 0) {
+            V Pv, Qq, av, ev;
+            scr_unpack(nst, Pv, Qq, av, ev);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                // this level's scratch is dead once read: drop its L2
+                // lines (one per 8 lanes) so they are not written back
+                if ((lane & 7) == 0) discard_l2_after(sp + j * gthreads, nst[j].x);
+            }
+            const V Bi = nBi;
+            if constexpr (INL) {
+                if ((lane & (32 / NS - 1)) == 0) discard_l2_after(spB, cmp(nBi, 0));
+            }
+#pragma unroll
+            for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
+            if (i > 0) {
+                sp -= sstride;
+#pragma unroll
+                for (int j = 0; j < NS; ++j) nst[j] = __ldcg(sp + j * gthreads);
+                if constexpr (INL) {
+                    spB -= gthreads;
+                    nBi = ldB_cg(spB);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldB<DIRECT>(Bp[j] - 2 * bst);
+                }
+            }
+            uu = vfma(Pv, uu, Qq);
+            const V fup = vfma(V(kPiF), Bi, uu);
+            Bt = Bi;
+            const V fnet = vfma(av, uu, -ev);
+            tb[(gi * 2) * 33 + lane] = hsum(wg * fup);
+            tb[(gi * 2 + 1) * 33 + lane] = hsum(wg * fnet);
+            ++gi;
+        }
+        if (gi == 16 || (i < 0 && gi > 0)) {
+            __syncwarp();
+            // lane j sums row (slot j & 15, quantity j >> 4) over the 32 lanes
+            const int sl = lane & 15, qq = lane >> 4;
+            if (sl < gi) {
+                const float *row = tb + (sl * 2 + qq) * 33;
+                float acc = 0.f;
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) acc += row[j];
+                part[2 * (gtop - sl) + qq] = acc;
+            }
+            __syncwarp();
+            gtop -= gi;
+            gi = 0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+        if (cmpm(on, i) && (bad[i] || !isfinite(cmp(uu, i)))) cn.nonfinite++;
+
+    // TOA spectrum: uu and Bt are now at interface 0; each bin's systems
+    // are summed in system order and added once per unit (a bin of
+    // n_g <= 32 NS systems meets at most two units, so the FP64 sum is
+    // order-free)
+    if (kp.toa) {
+        V ft = wg * vfma(V(kPiF), Bt, uu);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) tb[32 * i + lane] = cmp(ft, i);
+        __syncwarp();
+        for (int jb = lane; jb < nbc; jb += 32) {
+            const int bt = b_lo + jb;
+            const int j0 = max(0, bt * NG - s0);
+            const int j1 = min(min(SPU, S - s0), (bt + 1) * NG - s0);
+            float acc = 0.f;
+            for (int j = j0; j < j1; ++j) acc += tb[j];
+            atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
+        }
+        __syncwarp();
+    }
+
+    // the warp that completes a column's last unit writes the column
+    __threadfence();
+    int done = 0;
+    if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == kp.col_units[c] - 1) {
+        __threadfence();
+        finalize_column(kp, c, lane);
+    }
+    __syncwarp();
+}
+
+template <bool ISO, int ST, bool KT, int NS>
+__global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KParams kp) {
+    constexpr int SPG = 32 * NS;                   // unit stride within a column
     extern __shared__ __align__(16) float smem32[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float *wsm = smem32 + (size_t)warp * kp.warp_floats;
-    const int NG = kp.n_g;
     const int nbw = kp.nbw;
     float *sB = wsm;                               // [(2 L + 1) nbc], staged mode
-    float *sFs = wsm + (DIRECT ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
+    float *sFs = wsm + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [16][2][33]
     // scratch slots: component i of this thread at slot + i * (threads in the grid)
@@ -1002,267 +1389,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        const int c = kp.unit_col[unit];
-        const int ku = kp.unit_k[unit];
-        const int L = kp.n_layers[c], NB = kp.n_bins[c];
-        const int S = NB * NG;
-        const long long cube0 = kp.cube_off[c];
-        const float4 cf = kp.colf[c];
-        const float mu = cf.x, imu = cf.y;
-        const double mu_d = kp.mu_star[kp.mu_idx[c]];   // only for the rare FP64 resonance test
-        const bool beam = cf.z != 0.f;
-        const int s0 = ku * SPU;
-        const int b_lo = s0 / NG;
-        const int nbc = min(NB - 1, (s0 + SPU - 1) / NG) - b_lo + 1;
-
-        // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
-        {
-            const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
-            const int nlev = 2 * L + 1;
-            if constexpr (!DIRECT) {
-                for (int i = lane; i < nlev * nbc; i += 32) {
-                    const int lev = i / nbc, bb = i - lev * nbc;
-                    sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
-                }
-            }
-            for (int j = lane; j < nbc; j += 32) {
-                sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
-                sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
-            }
-        }
-        __syncwarp();
-
-        // component i of this lane is system s0 + 32 i + lane; padding
-        // systems of a column's last unit repeat system s0 with zero weight,
-        // so the loops below need no per-lane predicates
-        M on;
-        int sI[NS], bI[NS];
-        V wg, Fb, Bt, Bc, Bb;
-        const float *Bp[NS];
-        const int bst = DIRECT ? NB : nbc;         // level stride of Bp
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const bool act = s0 + 32 * i + lane < S;
-            cmpm(on, i) = act;
-            sI[i] = act ? s0 + 32 * i + lane : s0;
-            bI[i] = sI[i] / NG;
-            cmp(wg, i) = act ? kp.g_w32[sI[i] - bI[i] * NG] : 0.f;
-            Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo);
-            cmp(Fb, i) = beam ? mu * sFs[bI[i] - b_lo] : 0.f;
-            // the B of a layer's bottom interface is carried as the next layer's top
-            cmp(Bt, i) = ldB<DIRECT>(Bp[i]);
-            cmp(Bc, i) = ldB<DIRECT>(Bp[i] + bst);
-            cmp(Bb, i) = ldB<DIRECT>(Bp[i] + 2 * bst);
-        }
-        SysCounts<V> sc;
-        sc.inv = sc.ecl = sc.etau = typename VTraits<V>::C{};
-
-        // forward elimination, TOA -> BOA, departure variables
-        V al = V(1.f);                                       // alpha' = 1 - a'
-        V bl = vfma(V(-kPiF), Bt, V((float)kp.F_toa));       // b' at the TOA
-        // optics: read from the cubes, or (KT) from the k-table corners of
-        // the layer's grid cell, fetched one layer ahead
-        V nd = V(0.f), nw = V(0.f), ng = V(0.f);
-        const float *pd[NS], *pw[NS], *pg[NS];
-        const float4 *klay = nullptr;
-        float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next;
-        float4 kb[NS];
-        Corners kc[NS];
-        if constexpr (KT) {
-            klay = kp.kt_lay + kp.lay_off[c];
-            kl_next = klay[0];
-            kl_after = L > 1 ? klay[1] : kl_next;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                kb[i] = __ldg(kp.kt_bin + bI[i]);
-                kc[i] = kt_corners(kp, kl_next, S, sI[i]);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) {
-                const long long e = cube0 + sI[i];
-                pd[i] = kp.dtau + e;
-                pw[i] = kp.w0 + e;
-                pg[i] = kp.g0 + e;
-                cmp(nd, i) = __ldcs(pd[i]);
-                cmp(nw, i) = __ldcs(pw[i]);
-                cmp(ng, i) = __ldcs(pg[i]);
-            }
-        }
-        float4 *sp = kp.scr32 + slot;
-        // two layers per trip: the carried values (B at the levels, the
-        // prefetched optics, alpha' and b') alternate between two register
-        // sets instead of being copied at the end of every layer (not with
-        // the k-table front end, whose prefetched corners would spill)
-#pragma unroll(KT ? 1 : 2)
-        for (int l = 0; l < L; ++l) {
-            V dt, w0, g0;
-            V nBc = V(0.f), nBb = V(0.f);
-            if constexpr (KT) {
-                const float4 kl = kl_next;
-                Corners cur[NS];
-#pragma unroll
-                for (int i = 0; i < NS; ++i) cur[i] = kc[i];
-                if (l + 1 < L) {                     // prefetch the next layer's corners
-                    kl_next = kl_after;
-#pragma unroll
-                    for (int i = 0; i < NS; ++i) kc[i] = kt_corners(kp, kl_next, S, sI[i]);
-                    if (l + 2 < L) kl_after = klay[l + 2];
-                }
-#pragma unroll
-                for (int i = 0; i < NS; ++i) {
-                    const Optics o = kt_mix(cur[i].k00, cur[i].k01, cur[i].k10, cur[i].k11, kl, kb[i]);
-                    cmp(dt, i) = o.dt;
-                    cmp(w0, i) = o.w0;
-                    cmp(g0, i) = o.g0;
-                }
-            } else {
-                dt = nd;
-                w0 = nw;
-                g0 = ng;
-                if (l + 1 < L) {                     // prefetch the next layer
-#pragma unroll
-                    for (int i = 0; i < NS; ++i) {
-                        pd[i] += S;
-                        pw[i] += S;
-                        pg[i] += S;
-                        cmp(nd, i) = __ldcs(pd[i]);
-                        cmp(nw, i) = __ldcs(pw[i]);
-                        cmp(ng, i) = __ldcs(pg[i]);
-                    }
-                }
-
-            }
-            if (l + 1 < L) {
-#pragma unroll
-                for (int i = 0; i < NS; ++i) {
-                    cmp(nBc, i) = ldB<DIRECT>(Bp[i] + 3 * bst);
-                    cmp(nBb, i) = ldB<DIRECT>(Bp[i] + 4 * bst);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NS; ++i) Bp[i] += 2 * bst;   // level 2 (l + 1)
-            const Layer32<V> ly = layer32<ISO, V>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
-            Bt = Bb;
-            Bc = nBc;
-            Bb = nBb;
-            const V omr = ly.omtr + ly.T;                      // 1 - R
-            const V ipv = vrcp(vfma(ly.R, al, omr));           // 1 / (1 - R a')
-            const V P = ly.T * ipv;
-            const V Qv = vfma(ly.R, bl, ly.Su) * ipv;
-            scr_store(sp, gthreads, P, Qv, al, bl + Fb);      // e = b' + F_beam
-            sp += sstride;
-            const V al_n = vfma(al, vfma(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
-            const V bl_n = vfma(ly.T * vfma(V(1.f) - al, ly.Su, bl), ipv, ly.Sd);
-            al = al_n;
-            bl = bl_n;
-            Fb = Fb * ly.mlay;
-        }
-
-        cn.inv += vmasked(sc.inv, on);
-        cn.eclamp += vmasked(sc.ecl, on);
-        cn.etau += (ISO ? 1u : 2u) * vmasked(sc.etau, on);
-        // BOA (Eq. 10): u - d = F_BOA + F_beam with d = (1 - alpha') u + b';
-        // back-substitution to the TOA; interface sums through the transpose
-        V FBOA;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) cmp(FBOA, i) = sFB[bI[i] - b_lo];
-        V uu = ((FBOA + Fb) + bl) * vrcp(al);
-        bool bad[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) bad[i] = !isfinite(cmp(uu, i));   // NaN and Inf propagate upwards
-        float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
-        // Bt holds B at level 2L (the BOA interface)
-        tb[lane] = hsum(wg * vfma(V(kPiF), Bt, uu));
-        tb[33 + lane] = hsum(wg * FBOA);
-        V nBi;                   // Bp is at level 2L; prefetch one interface up
-#pragma unroll
-        for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldB<DIRECT>(Bp[i] - 2 * bst);
-        int gi = 1;              // slots used in the current group of 16 interfaces
-        int gtop = L;            // interface held in slot 0 of the group
-        sp -= sstride;           // interface L-1
-        float4 nst[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) nst[i] = __ldcg(sp + i * gthreads);
-        for (int i = L - 1; i >= -1; --i) {
-            if (i >= 0) {
-                V Pv, Qq, av, ev;
-                scr_unpack(nst, Pv, Qq, av, ev);
-#pragma unroll
-                for (int j = 0; j < NS; ++j) {
-                    // this level's scratch is dead once read: drop its L2
-                    // lines (one per 8 lanes) so they are not written back
-                    if ((lane & 7) == 0) discard_l2_after(sp + j * gthreads, nst[j].x);
-                }
-                const V Bi = nBi;
-#pragma unroll
-                for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
-                if (i > 0) {
-                    sp -= sstride;
-#pragma unroll
-                    for (int j = 0; j < NS; ++j) {
-                        nst[j] = __ldcg(sp + j * gthreads);
-                        cmp(nBi, j) = ldB<DIRECT>(Bp[j] - 2 * bst);
-                    }
-                }
-                uu = vfma(Pv, uu, Qq);
-                const V fup = vfma(V(kPiF), Bi, uu);
-                Bt = Bi;
-                const V fnet = vfma(av, uu, -ev);
-                tb[(gi * 2) * 33 + lane] = hsum(wg * fup);
-                tb[(gi * 2 + 1) * 33 + lane] = hsum(wg * fnet);
-                ++gi;
-            }
-            if (gi == 16 || (i < 0 && gi > 0)) {
-                __syncwarp();
-                // lane j sums row (slot j & 15, quantity j >> 4) over the 32 lanes
-                const int sl = lane & 15, qq = lane >> 4;
-                if (sl < gi) {
-                    const float *row = tb + (sl * 2 + qq) * 33;
-                    float acc = 0.f;
-#pragma unroll 8
-                    for (int j = 0; j < 32; ++j) acc += row[j];
-                    part[2 * (gtop - sl) + qq] = acc;
-                }
-                __syncwarp();
-                gtop -= gi;
-                gi = 0;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NS; ++i)
-            if (cmpm(on, i) && (bad[i] || !isfinite(cmp(uu, i)))) cn.nonfinite++;
-
-        // TOA spectrum: uu and Bt are now at interface 0; each bin's systems
-        // are summed in system order and added once per unit (a bin of
-        // n_g <= 32 NS systems meets at most two units, so the FP64 sum is
-        // order-free)
-        if (kp.toa) {
-            V ft = wg * vfma(V(kPiF), Bt, uu);
-#pragma unroll
-            for (int i = 0; i < NS; ++i) tb[32 * i + lane] = cmp(ft, i);
-            __syncwarp();
-            for (int jb = lane; jb < nbc; jb += 32) {
-                const int bt = b_lo + jb;
-                const int j0 = max(0, bt * NG - s0);
-                const int j1 = min(min(SPU, S - s0), (bt + 1) * NG - s0);
-                float acc = 0.f;
-                for (int j = j0; j < j1; ++j) acc += tb[j];
-                atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
-            }
-            __syncwarp();
-        }
-
-        // the warp that completes a column's last unit writes the column
-        __threadfence();
-        int done = 0;
-        if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
-        done = __shfl_sync(0xffffffffu, done, 0);
-        if (done == kp.col_units[c] - 1) {
-            __threadfence();
-            finalize_column(kp, c, lane);
-        }
-        __syncwarp();
+        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
     }
     flush_counters(cn, kp.stats);
 }
@@ -1546,6 +1673,18 @@ int occupancy(int precision_fp64, int block, size_t smem, int ns) {
     return e == cudaSuccess ? n : 0;
 }
 
+// fp32_units instantiations, indexed by isothermal + 2 stage + 6 k-table + 12 (two systems per lane)
+template <int SEL>
+void units_launch(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
+    fp32_units<(SEL & 1) != 0, (SEL / 2) % 3, (SEL / 6) % 2 != 0, SEL / 12 + 1><<<grid, block, smem, s>>>(kp);
+}
+using UnitsLaunch = void (*)(const KParams &, int, int, size_t, cudaStream_t);
+template <int... I>
+constexpr std::array<UnitsLaunch, sizeof...(I)> units_table(std::integer_sequence<int, I...>) {
+    return {&units_launch<I>...};
+}
+constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, 24>{});
+
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
                         cudaEvent_t const *ev) {
     const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
@@ -1554,25 +1693,9 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    const int sel = (kp.isothermal ? 1 : 0) | (kp.direct ? 2 : 0) | (kp.kt_lk ? 4 : 0) | (kp.ns == 2 ? 8 : 0);
-    switch (sel) {
-        case 0: fp32_units<false, false, false, 1><<<grid, block, smem, s>>>(kp); break;
-        case 1: fp32_units<true, false, false, 1><<<grid, block, smem, s>>>(kp); break;
-        case 2: fp32_units<false, true, false, 1><<<grid, block, smem, s>>>(kp); break;
-        case 3: fp32_units<true, true, false, 1><<<grid, block, smem, s>>>(kp); break;
-        case 4: fp32_units<false, false, true, 1><<<grid, block, smem, s>>>(kp); break;
-        case 5: fp32_units<true, false, true, 1><<<grid, block, smem, s>>>(kp); break;
-        case 6: fp32_units<false, true, true, 1><<<grid, block, smem, s>>>(kp); break;
-        case 7: fp32_units<true, true, true, 1><<<grid, block, smem, s>>>(kp); break;
-        case 8: fp32_units<false, false, false, 2><<<grid, block, smem, s>>>(kp); break;
-        case 9: fp32_units<true, false, false, 2><<<grid, block, smem, s>>>(kp); break;
-        case 10: fp32_units<false, true, false, 2><<<grid, block, smem, s>>>(kp); break;
-        case 11: fp32_units<true, true, false, 2><<<grid, block, smem, s>>>(kp); break;
-        case 12: fp32_units<false, false, true, 2><<<grid, block, smem, s>>>(kp); break;
-        case 13: fp32_units<true, false, true, 2><<<grid, block, smem, s>>>(kp); break;
-        case 14: fp32_units<false, true, true, 2><<<grid, block, smem, s>>>(kp); break;
-        default: fp32_units<true, true, true, 2><<<grid, block, smem, s>>>(kp); break;
-    }
+    const int st = kp.inline_b ? kStageInline : (kp.direct ? kStageDirect : kStageShared);
+    const int sel = (kp.isothermal ? 1 : 0) + 2 * st + (kp.kt_lk ? 6 : 0) + (kp.ns == 2 ? 12 : 0);
+    kUnitsLaunch[sel](kp, grid, block, smem, s);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;

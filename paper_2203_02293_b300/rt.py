@@ -21,7 +21,7 @@ RT_IMPROVED, RT_REGULAR = 0, 1
 RT_NONISOTHERMAL, RT_ISOTHERMAL = 0, 1
 RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
 RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
-RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT = 0, 1, 2
+RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT, RT_STAGE_INLINE = 0, 1, 2, 3
 
 _STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
            -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}
@@ -171,7 +171,7 @@ class Config:
     hbm_budget_bytes: int = 0
     block_threads: int = 0
     ctas_per_sm: int = 0
-    planck_staging: int = 0              # RT_STAGE_AUTO / RT_STAGE_SHARED / RT_STAGE_DIRECT
+    planck_staging: int = 0              # RT_STAGE_AUTO / _SHARED / _DIRECT / _INLINE
     systems_per_lane: int = 0            # FP32 form: 1 or 2 (0 = 2)
     kernel_timing: int = 0               # 1: CUDA events around each kernel (rt_kernel_times)
     wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins

@@ -8,8 +8,8 @@ the batch plan exist before capture.
 ``autotune`` times the persistent kernel's variants on the actual batch with
 CUDA events and keeps the fastest: warps per CTA, resident CTAs per SM,
 systems per lane (one, or two on the paired FP32 instructions) and where
-the Planck values are read from (staged in shared memory or straight from
-the table).  Work units are 32 x (systems per lane) systems of one column
+the Planck values come from (the pre-kernel's table staged in shared memory
+or read directly, or evaluated in the solve kernel).  Work units are 32 x (systems per lane) systems of one column
 whatever the shape, and each column is summed in unit order, so candidates
 with the same systems per lane must give the same bits; one that does not
 is rejected (stability check).  Across systems per lane only the rounding
@@ -32,7 +32,8 @@ KNOBS = ("block_threads", "ctas_per_sm", "systems_per_lane", "planck_staging")
 
 
 def default_candidates(n_g: int) -> list[dict]:
-    staging = (rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT) if n_g < 8 else (rt.RT_STAGE_SHARED,)
+    staging = ((rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE) if n_g < 8
+               else (rt.RT_STAGE_SHARED,))
     return [dict(block_threads=b, ctas_per_sm=c, systems_per_lane=n, planck_staging=st)
             for n in (1, 2) for st in staging for b in (128, 256) for c in (0, 2)]
 

@@ -92,7 +92,8 @@ def test_bad_config_is_rejected_before_touching_the_device(librt):
     for bad in (dict(eps2=0.0), dict(max_layers=0), dict(block_threads=48), dict(precision=7),
                 dict(wn_min=100.0, wn_max=50.0), dict(wn_edges=np.array([50.0])),
                 dict(wn_edges=np.array([50.0, 40.0, 60.0])), dict(wn_edges=np.array([-1.0, 40.0])),
-                dict(wn_edges=np.array([50.0, np.nan]))):
+                dict(wn_edges=np.array([50.0, np.nan])), dict(planck_staging=4), dict(planck_staging=-1),
+                dict(systems_per_lane=3)):
         cfg = librt.Config(g_weights=np.ones(1), **bad)
         with pytest.raises(librt.RTError) as e:
             librt.rt_create(cfg)

@@ -79,6 +79,7 @@ def test_autotuner_candidates_agree():
     cands = [dict(block_threads=bt, ctas_per_sm=c, systems_per_lane=n)
              for n in (1, 2) for bt, c in ((64, 0), (128, 2), (256, 0), (256, 1))]
     cands.append(dict(block_threads=128, ctas_per_sm=0, systems_per_lane=2, planck_staging=rt.RT_STAGE_DIRECT))
+    cands.append(dict(block_threads=256, ctas_per_sm=0, systems_per_lane=2, planck_staging=rt.RT_STAGE_INLINE))
     res = autotune(b, cols.g_weights, candidates=cands, reps=2)
     assert res["stable"], res["table"]
     assert res["block_threads"] in (64, 128, 256)

@@ -109,14 +109,16 @@ def test_config1_one_and_two_systems_per_lane(cfg1, cfg1_ref, spl):
 
 
 @pytest.mark.parametrize("spl", [1, 2])
-@pytest.mark.parametrize("mode", ["iso", "direct", "ng1", "ng45"])
+@pytest.mark.parametrize("mode", ["iso", "direct", "inline", "inline1", "ng1", "ng45"])
 def test_systems_per_lane_variants_on_ragged_batches(spl, mode):
-    n_g = {"ng1": 1, "ng45": 45}.get(mode, 20)
+    n_g = {"ng1": 1, "ng45": 45, "inline1": 1}.get(mode, 20)
     cols = rt_synth.generate([37, 3, 1, 64, 12], [9, 40, 2, 5, 31], n_g, seed=41, optics="ktable")
     opts = method_opts(isothermal=(mode == "iso"))
     extra = dict(systems_per_lane=spl)
     if mode == "direct":
         extra["planck_staging"] = 2
+    if mode.startswith("inline"):
+        extra["planck_staging"] = 3
     ref = oracle_solve(cols, opts)
     got = gpu_solve(cols, opts, "fp32", **extra)
     assert_parity(cols, got, ref, "fp32", f"{mode} {spl}/lane")

@@ -126,16 +126,44 @@ def test_spectrum_before_any_solve_is_refused():
     s.close()
 
 
+MODES = (rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE)
+
+
 @pytest.mark.parametrize("n_g", [1, 3, 20])
 @pytest.mark.parametrize("iso", [False, True])
-def test_planck_staged_and_direct_reads_agree_bitwise(n_g, iso):
+@pytest.mark.parametrize("spl", [1, 2])
+def test_planck_staged_direct_and_inline_agree_bitwise(n_g, iso, spl):
+    """B from the pre-kernel's table (staged or read directly) and B
+    evaluated in the solve kernel give the same bits: wide uniform bins."""
     cols = rt_synth.generate([9, 33, 4], [61, 17, 40], n_g, seed=60 + n_g, optics="ktable")
     b = DeviceBatch(cols)
     outs = []
-    for mode in (rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT):
-        s = Solver(cols.g_weights, planck_staging=mode,
+    for mode in MODES:
+        s = Solver(cols.g_weights, planck_staging=mode, systems_per_lane=spl,
                    layers=rt.RT_ISOTHERMAL if iso else rt.RT_NONISOTHERMAL)
         outs.append(s.solve_numpy(b))
         s.close()
+    for o in outs[1:]:
+        for k in outs[0]:
+            assert np.array_equal(outs[0][k], o[k]), k
+
+
+@pytest.mark.parametrize("spl", [1, 2])
+def test_inline_planck_on_the_postproc_shape(spl):
+    """Narrow R = 500 bins (Gauss-Legendre quadrature): the inline evaluation
+    equals the table bit for bit and meets the oracle."""
+    cols = rt_synth.postproc(4, seed=9)
+    b = DeviceBatch(cols)
+    outs = []
+    for mode in (rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE):
+        s = Solver(cols.g_weights, planck_staging=mode, systems_per_lane=spl, wn_edges=cols.consts["wn_edges"])
+        s.solve(b)
+        o = s.outputs(b)
+        o["F_up_toa"] = s.toa_spectrum(b)
+        outs.append({k: v.cpu().numpy() for k, v in o.items()})
+        s.close()
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
+    ref = oracle_solve(cols, method_opts())
+    got = gpu_solve(cols, method_opts(), "fp32", planck_staging=rt.RT_STAGE_INLINE, systems_per_lane=spl)
+    assert_parity(cols, got, ref, "fp32", "postproc inline")
