@@ -112,19 +112,22 @@ __device__ __forceinline__ float frsqrt(float x) {
 constexpr float kLog2E = 1.44269504088896340736f;
 
 // FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
-//   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms.
+//   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms,
+// regrouped as e (x^3 A1 + 3 x^2 A2 + 6 x A3 + 6 A4) with
+// A_k = sum_n e^(n-1) / n^k evaluated by Horner in e = e^-x <= e^-2.
 __device__ __forceinline__ float planck_upper_f(float x) {
     const float e = fexp(-x);
-    const float x2 = x * x, x3 = x2 * x;
-    float en = e, s = 0.f;
+    float a1 = 1.f / 8.f, a2 = 1.f / 64.f, a3 = 1.f / 512.f, a4 = 1.f / 4096.f;
 #pragma unroll
-    for (int n = 1; n <= 8; ++n) {
+    for (int n = 7; n >= 1; --n) {
         const float y = 1.0f / (float)n;
-        const float poly = y * fmaf(y, fmaf(y, fmaf(6.f, y, 6.f * x), 3.f * x2), x3);
-        s = fmaf(en, poly, s);
-        en *= e;
+        a1 = fmaf(a1, e, y);
+        a2 = fmaf(a2, e, y * y);
+        a3 = fmaf(a3, e, y * y * y);
+        a4 = fmaf(a4, e, y * y * y * y);
     }
-    return s;
+    const float poly = fmaf(x * x, fmaf(x, a1, 3.f * a2), fmaf(6.f * x, a3, 6.f * a4));
+    return e * poly;
 }
 
 // FP64 versions (terms to k = 30 below x = 2, 20 exponential terms above).
@@ -828,11 +831,13 @@ __device__ __forceinline__ void kt_bracket(const double *grid, int n, double v, 
     w = (float)__ddiv_rn(__dsub_rn(v, grid[lo]), __dsub_rn(grid[lo + 1], grid[lo]));
 }
 
-__device__ __forceinline__ float4 kt_layer(const KParams &kp, double T, double p_top, double p_bot, int S) {
+// gT, gP: the table's T and log10 p grids (in shared memory where staged)
+__device__ __forceinline__ float4 kt_layer(const KParams &kp, const double *gT, const double *gP, double T,
+                                           double p_top, double p_bot, int S) {
     int iT, iP;
     float wT, wP;
-    kt_bracket(kp.kt_T, kp.kt_nT, T, iT, wT);
-    kt_bracket(kp.kt_lp, kp.kt_nP, log10(sqrt(__dmul_rn(p_top, p_bot))), iP, wP);
+    kt_bracket(gT, kp.kt_nT, T, iT, wT);
+    kt_bracket(gP, kp.kt_nP, __dmul_rn(0.5, log10(__dmul_rn(p_top, p_bot))), iP, wP);   // log10 sqrt(p_top p_bot)
     const int off = (iT * kp.kt_nP + iP) * S;
     return make_float4(__int_as_float(off), wT, wP, (float)__ddiv_rn(__dsub_rn(p_bot, p_top), kp.grav));
 }
@@ -847,7 +852,7 @@ __device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float 
     const float a0 = __fmaf_rn(l4.z, __fsub_rn(k01, k00), k00);     // along log p at T_i
     const float a1 = __fmaf_rn(l4.z, __fsub_rn(k11, k10), k10);     // along log p at T_i+1
     const float x = __fmaf_rn(l4.y, __fsub_rn(a1, a0), a0);         // log10 kappa
-    const float kappa = exp2f(__fmul_rn(x, kLog2Of10));
+    const float kappa = fex2(__fmul_rn(x, kLog2Of10));
     const float ext = __fadd_rn(__fadd_rn(kappa, bq.x), bq.y);
     Optics o;
     o.dt = __fmul_rn(ext, l4.w);
@@ -881,7 +886,11 @@ __device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int 
 // pi B(T_int), Eq. 10).
 __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
     extern __shared__ float sT[];                 // [2 Lmax + 2] temperatures of one column, then T_int
+    double *sG = (double *)(sT + 2 * kp.Lmax + 2);  // k-table T and log10 p grids (binary searches)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (kp.kt_lk)
+        for (int i = threadIdx.x; i < kp.kt_nT + kp.kt_nP; i += blockDim.x)
+            sG[i] = i < kp.kt_nT ? kp.kt_T[i] : kp.kt_lp[i - kp.kt_nT];   // read after the loop's first barrier
     for (int c = blockIdx.x; c < kp.n_cols; c += gridDim.x) {
         const int L = kp.n_layers[c], NB = kp.n_bins[c];
         const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], b0 = kp.bin_off[c], fsi = kp.fs_off[c];
@@ -896,7 +905,8 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         if (kp.kt_lk)
             for (int l = threadIdx.x; l < L; l += blockDim.x)
                 kp.kt_lay[kp.lay_off[c] + l] =
-                    kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], NB * kp.n_g);
+                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
+                             NB * kp.n_g);
         for (int b = threadIdx.x; b < NB; b += blockDim.x) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
         if (threadIdx.x == 0) {
             const double mu = kp.mu_star[kp.mu_idx[c]];
@@ -1626,7 +1636,8 @@ __global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_
         const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], base = pcube_off[c];
         __syncthreads();
         for (int l = threadIdx.x; l < L; l += blockDim.x)
-            sl[l] = kt_layer(kp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1], S);
+            sl[l] = kt_layer(kp, kp.kt_T, kp.kt_lp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
+                             S);
         __syncthreads();
         const long long n = (long long)L * S;
         for (long long i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1689,7 +1700,8 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
                         cudaEvent_t const *ev) {
     const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
     if (ev) cudaEventRecord(ev[0], s);
-    fp32_prep<<<pgrid, 256, sizeof(float) * (2 * kp.Lmax + 2), s>>>(kp);
+    const size_t psmem = sizeof(float) * (2 * kp.Lmax + 2) + (kp.kt_lk ? sizeof(double) * (kp.kt_nT + kp.kt_nP) : 0);
+    fp32_prep<<<pgrid, 256, psmem, s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
