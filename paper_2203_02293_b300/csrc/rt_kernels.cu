@@ -1182,9 +1182,10 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     V *spB = INL ? (V *)kp.scrB + slot : nullptr;
     // two layers per trip: the carried values (B at the levels, the
     // prefetched optics, alpha' and b') alternate between two register
-    // sets instead of being copied at the end of every layer (not with the
-    // k-table front end or inline B, whose extra live values would spill)
-#pragma unroll((KT || INL) ? 1 : 2)
+    // sets instead of being copied at the end of every layer (not with
+    // inline B, whose extra live values would spill; the k-table front end
+    // spills a few bytes and still gains)
+#pragma unroll(INL ? 1 : 2)
     for (int l = 0; l < L; ++l) {
         V dt, w0, g0;
         V nBc = V(0.f), nBb = V(0.f);
