@@ -66,6 +66,24 @@ def test_fused_solve_equals_optics_then_solve(kt, iso, prec, spl):
         assert np.array_equal(fused[k], plain[k]), k
 
 
+@pytest.mark.parametrize("spl", [1, 2])
+def test_fused_solve_planck_stagings_agree_bitwise(kt, spl):
+    """The fused front end with B staged, read from the table or evaluated
+    in the solve kernel: the same bits."""
+    cols = rt_synth.state_columns(5, 23, 30, 20, seed=27)
+    b = DeviceBatch(cols)
+    outs = []
+    for mode in (rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE):
+        s = opts_solver(cols, systems_per_lane=spl, planck_staging=mode)
+        s.set_ktable(kt)
+        s.solve_ktable(b)
+        outs.append({k: v.cpu().numpy() for k, v in s.outputs(b).items()})
+        s.close()
+    for o in outs[1:]:
+        for k in outs[0]:
+            assert np.array_equal(outs[0][k], o[k]), k
+
+
 def test_fused_solve_matches_the_oracle(kt):
     cols = rt_synth.state_columns(5, 21, 30, 20, seed=23)
     ref, _ = oracle_ktable_solve(cols, kt, method_opts())
