@@ -87,7 +87,8 @@ typedef struct {
     int32_t max_bins;            /* largest NB of any column, >= 1 */
     size_t hbm_budget_bytes;     /* workspace cap; 0 = no cap */
     int32_t block_threads;       /* threads per CTA (multiple of 32; 64..256 for the FP32
-                                    form, 64..512 for FP64); 0 = default (256) */
+                                    form, 64..512 for FP64); 0 = default (128 for the
+                                    FP32 form, 256 for FP64) */
     int32_t ctas_per_sm;         /* cap on resident CTAs per SM of the persistent grid;
                                     0 = as many as fit */
     int32_t planck_staging;      /* FP32 form, where the solve gets B(T) per bin:
