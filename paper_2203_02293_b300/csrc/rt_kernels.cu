@@ -1699,10 +1699,14 @@ constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, 24>{})
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
                         cudaEvent_t const *ev) {
-    const int pgrid = kp.n_cols < 4 * 148 ? kp.n_cols : 4 * 148;
+    // pre-kernel: 4-warp CTAs when it tabulates B at every level (more columns in flight),
+    // 8-warp CTAs when it forms the T_int row alone (the bins are the parallel work)
+    const int pblock = kp.inline_b ? 256 : 128;
+    const int pcap = (kp.inline_b ? 4 : 8) * 148;
+    const int pgrid = kp.n_cols < pcap ? kp.n_cols : pcap;
     if (ev) cudaEventRecord(ev[0], s);
     const size_t psmem = sizeof(float) * (2 * kp.Lmax + 2) + (kp.kt_lk ? sizeof(double) * (kp.kt_nT + kp.kt_nP) : 0);
-    fp32_prep<<<pgrid, 256, psmem, s>>>(kp);
+    fp32_prep<<<pgrid, pblock, psmem, s>>>(kp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
