@@ -1,0 +1,60 @@
+"""The benchmark's contract pieces that run without a GPU: the reference arm
+(the oracle timed on the host on a bounded sample) prints one JSON line with
+the contract's keys, and the ncu-summary reader accepts only a summary taken
+on the current kernel source."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def reference_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT, check=True)
+    lines = [l for l in out.stdout.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line_has_the_contract_keys(reference_line):
+    l = reference_line
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"):
+        assert k in l, k
+    assert l["impl"] == "reference" and l["n_gpus"] == 1 and l["steps"] == 1 and l["warmup"] == 3
+    assert l["higher_is_better"] is True and l["value"] > 0 and l["ms_per_step"] > 0
+    assert "workload" in l["config"]
+    assert l["e2e"]["value"] == l["value"] and l["e2e"]["h2d_bytes_per_step"] == 0
+    cb = l["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == l["value"] and cb["sample"]
+
+
+def test_reference_arm_uses_the_main_metric(reference_line):
+    assert reference_line["metric"] == bench.METRIC and reference_line["unit"] == bench.UNIT
+
+
+def test_profile_summary_is_used_only_for_the_current_source(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    body = "# header\nflop_per_system: 10.0\nfp32_pipe_ops_per_system: 7.0\ndram_bytes_per_launch: 5\n"
+    (prof / "x.txt").write_text(body + f"source_sha1: {bench.kernel_source_sha1()}\n")
+    (prof / "y.txt").write_text(body + "source_sha1: 0000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the hash of the kernel sources is read from the real tree
+    monkeypatch.setattr(bench, "kernel_source_sha1", lambda: (prof / "x.txt").read_text().split()[-1])
+    got = bench.read_profile("x.txt")
+    assert got is not None and float(got["fp32_pipe_ops_per_system"]) == 7.0
+    assert bench.read_profile("y.txt") is None
+    assert bench.read_profile("missing.txt") is None
+
+
+def test_kernel_source_hash_is_stable():
+    assert bench.kernel_source_sha1() == bench.kernel_source_sha1()
+    assert len(bench.kernel_source_sha1()) == 40
