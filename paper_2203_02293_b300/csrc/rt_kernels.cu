@@ -790,22 +790,55 @@ __device__ __forceinline__ float planck_bin32(PlanckLevel lv, float wn0, float w
     return __fmul_rn(lv.pref, d);
 }
 
-// B of one level for the warp's chunk of 31 bins [b0, b0 + 31): lane e
-// holds edge b0 + e at x = a wn (x1: the next edge, from lane e + 1); the
-// wide bins share their edges' series values with the neighbouring lane.
-__device__ __forceinline__ float planck_chunk_level(float T, float scale, float wn, float dnu_b, bool inb,
-                                                    int lane) {
-    const PlanckLevel lv = planck_level(T, scale);
-    const float x = __fmul_rn(lv.a, wn);
-    const float x1 = __shfl_down_sync(0xffffffffu, x, 1);
-    const bool narrow = !inb || (__fsub_rn(x1, x) < kNarrowBin);
-    // the edge series are needed only when some bin of this chunk is wide
-    float v = 0.f;
-    if (!__all_sync(0xffffffffu, narrow)) v = planck_edge_f(x);
-    const float v1 = __shfl_down_sync(0xffffffffu, v, 1);
-    const float d = narrow ? planck_narrow_f(x, __fmul_rn(0.5f, __fmul_rn(lv.a, dnu_b)))
-                           : planck_wide_f(x, x1, v, v1);
-    return __fmul_rn(lv.pref, d);
+// B at NQ levels for the warp's chunk of 31 bins [b0, b0 + 31) (the
+// pre-kernel's inner loop): lane e holds edge b0 + e at x = a wn (x1: the
+// next edge, from lane e + 1); a wide bin takes the difference of its
+// edges' series values, the lower edge's from its own lane, the upper's
+// from the next lane; a narrow bin its own quadrature.  One vote serves the
+// group and the series and the wide-bin difference are formed by selects,
+// so that the NQ evaluation chains are independent and can overlap.  The
+// values equal planck_bin32's for the same bin and level.
+template <int NQ>
+__device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const float (&scale)[NQ], float wn,
+                                                    float dnu_b, bool inb, float (&out)[NQ]) {
+    PlanckLevel lv[NQ];
+    float x[NQ], x1[NQ], v[NQ], v1[NQ], d[NQ];
+    bool nar[NQ];
+    bool alln = true, anyn = false;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        lv[q] = planck_level(T[q], scale[q]);
+        x[q] = __fmul_rn(lv[q].a, wn);
+        x1[q] = __shfl_down_sync(0xffffffffu, x[q], 1);
+        nar[q] = !inb || (__fsub_rn(x1[q], x[q]) < kNarrowBin);
+        alln = alln && nar[q];
+        anyn = anyn || (inb && nar[q]);
+    }
+    // the edge series only when some bin of this chunk is wide
+    if (!__all_sync(0xffffffffu, alln)) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float lo = planck_lower_f(x[q]), up = planck_upper_f(x[q]);
+            v[q] = (x[q] < 2.f) ? lo : up;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) v[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        v1[q] = __shfl_down_sync(0xffffffffu, v[q], 1);
+        const float dh = __fsub_rn(v[q], v1[q]), dl = __fsub_rn(v1[q], v[q]);
+        const float dm = __fsub_rn(__fsub_rn((float)kPi4Over15, v[q]), v1[q]);
+        d[q] = (x[q] >= 2.f) ? dh : ((x1[q] < 2.f) ? dl : dm);     // planck_wide_f
+    }
+    if (__any_sync(0xffffffffu, anyn)) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (nar[q]) d[q] = planck_narrow_f(x[q], __fmul_rn(0.5f, __fmul_rn(lv[q].a, dnu_b)));
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = __fmul_rn(lv[q].pref, d[q]);
 }
 
 // ---------------------------------------------------------------------
@@ -928,12 +961,23 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             const float wn = kp.edges32 ? __ldg(kp.edges32 + min(e, NB)) : fmaf((float)e, dwn, wmin);
             const float dnu_b = kp.edges32 ? __ldg(kp.dnu32 + min(bin, NB - 1)) : dwn;
             const int r1 = min(r0 + run, nlev + 1);
-            for (int lev = r0; lev < r1; ++lev) {
-                const bool tint = lev == nlev;
-                const float v = planck_chunk_level(sT[lev], tint ? kPiF : 1.f, wn, dnu_b, inb, lane);
-                if (inb) {
-                    if (tint) kp.fboa32[b0 + bin] = v;
-                    else B[(long long)lev * NB + bin] = v;
+            // four levels per pass: independent evaluation chains
+            for (int lev = r0; lev < r1; lev += 4) {
+                float Tq[4], sq[4], vq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int lq = min(lev + q, r1 - 1);
+                    Tq[q] = sT[lq];
+                    sq[q] = lq == nlev ? kPiF : 1.f;
+                }
+                planck_chunk_levels<4>(Tq, sq, wn, dnu_b, inb, vq);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int lq = lev + q;
+                    if (inb && lq < r1) {
+                        if (lq == nlev) kp.fboa32[b0 + bin] = vq[q];
+                        else B[(long long)lq * NB + bin] = vq[q];
+                    }
                 }
             }
         }

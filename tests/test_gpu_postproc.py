@@ -149,14 +149,17 @@ def test_planck_staged_direct_and_inline_agree_bitwise(n_g, iso, spl):
 
 
 @pytest.mark.parametrize("spl", [1, 2])
-def test_inline_planck_on_the_postproc_shape(spl):
+@pytest.mark.parametrize("iso", [False, True])
+def test_inline_planck_on_the_postproc_shape(spl, iso):
     """Narrow R = 500 bins (Gauss-Legendre quadrature): the inline evaluation
     equals the table bit for bit and meets the oracle."""
     cols = rt_synth.postproc(4, seed=9)
     b = DeviceBatch(cols)
     outs = []
+    layers = rt.RT_ISOTHERMAL if iso else rt.RT_NONISOTHERMAL
     for mode in (rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE):
-        s = Solver(cols.g_weights, planck_staging=mode, systems_per_lane=spl, wn_edges=cols.consts["wn_edges"])
+        s = Solver(cols.g_weights, planck_staging=mode, systems_per_lane=spl, wn_edges=cols.consts["wn_edges"],
+                   layers=layers)
         s.solve(b)
         o = s.outputs(b)
         o["F_up_toa"] = s.toa_spectrum(b)
@@ -164,6 +167,7 @@ def test_inline_planck_on_the_postproc_shape(spl):
         s.close()
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
-    ref = oracle_solve(cols, method_opts())
-    got = gpu_solve(cols, method_opts(), "fp32", planck_staging=rt.RT_STAGE_INLINE, systems_per_lane=spl)
+    ref = oracle_solve(cols, method_opts(isothermal=iso))
+    got = gpu_solve(cols, method_opts(isothermal=iso), "fp32", planck_staging=rt.RT_STAGE_INLINE, systems_per_lane=spl)
     assert_parity(cols, got, ref, "fp32", "postproc inline")
+    assert got["stats"]["nonfinite_outputs"] == 0
