@@ -961,24 +961,29 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             const float wn = kp.edges32 ? __ldg(kp.edges32 + min(e, NB)) : fmaf((float)e, dwn, wmin);
             const float dnu_b = kp.edges32 ? __ldg(kp.dnu32 + min(bin, NB - 1)) : dwn;
             const int r1 = min(r0 + run, nlev + 1);
-            // four levels per pass: independent evaluation chains
-            for (int lev = r0; lev < r1; lev += 4) {
+            // four levels per pass (independent evaluation chains), then one at a time
+            auto store = [&](int lq, float v) {
+                if (inb) {
+                    if (lq == nlev) kp.fboa32[b0 + bin] = v;
+                    else B[(long long)lq * NB + bin] = v;
+                }
+            };
+            int lev = r0;
+            for (; lev + 4 <= r1; lev += 4) {
                 float Tq[4], sq[4], vq[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int lq = min(lev + q, r1 - 1);
-                    Tq[q] = sT[lq];
-                    sq[q] = lq == nlev ? kPiF : 1.f;
+                    Tq[q] = sT[lev + q];
+                    sq[q] = lev + q == nlev ? kPiF : 1.f;
                 }
                 planck_chunk_levels<4>(Tq, sq, wn, dnu_b, inb, vq);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int lq = lev + q;
-                    if (inb && lq < r1) {
-                        if (lq == nlev) kp.fboa32[b0 + bin] = vq[q];
-                        else B[(long long)lq * NB + bin] = vq[q];
-                    }
-                }
+                for (int q = 0; q < 4; ++q) store(lev + q, vq[q]);
+            }
+            for (; lev < r1; ++lev) {
+                float Tq[1] = {sT[lev]}, sq[1] = {lev == nlev ? kPiF : 1.f}, vq[1];
+                planck_chunk_levels<1>(Tq, sq, wn, dnu_b, inb, vq);
+                store(lev, vq[0]);
             }
         }
     }
