@@ -935,11 +935,6 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         for (int lev = threadIdx.x; lev <= nlev; lev += blockDim.x)
             sT[lev] = lev == nlev ? (float)kp.T_int
                                   : (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
-        if (kp.kt_lk)
-            for (int l = threadIdx.x; l < L; l += blockDim.x)
-                kp.kt_lay[kp.lay_off[c] + l] =
-                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
-                             NB * kp.n_g);
         for (int b = threadIdx.x; b < NB; b += blockDim.x) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
         if (threadIdx.x == 0) {
             const double mu = kp.mu_star[kp.mu_idx[c]];
@@ -986,6 +981,13 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
                 store(lev, vq[0]);
             }
         }
+        // the layers' k-table cells (FP64, on the FP64 pipe) after the
+        // Planck tasks, so that they overlap other warps' FP32 work
+        if (kp.kt_lk)
+            for (int l = threadIdx.x; l < L; l += blockDim.x)
+                kp.kt_lay[kp.lay_off[c] + l] =
+                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
+                             NB * kp.n_g);
     }
 }
 
