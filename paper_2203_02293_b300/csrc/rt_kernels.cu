@@ -316,16 +316,18 @@ template <> struct VTraits<V2> {
     using C = U2;
 };
 
-// (1 - exp(-x)) / x from its Taylor series sum_n (-x)^n / (n+1)! for |x| < 0.25
-// (7 terms, truncation below 2e-9); above that the callers use the exponential
-// e = exp(-x) directly (relative error of 1 - e below 5e-7 there).
+// (1 - exp(-x)) / x for |x| < 0.25 as a degree-5 polynomial fitted for the least
+// maximum relative error on [-0.25, 0.25], constant term fixed at 1 (csrc/fit_series.py):
+// 2.9e-9 relative with the FP32 coefficients, 6.1e-8 evaluated in FP32 -- as
+// close as the 7-term Taylor sum sum_n (-x)^n / (n+1)! with one multiply-add fewer.
+// Above 0.25 the callers use the exponential e = exp(-x) directly (relative error
+// of 1 - e below 5e-7 there).
 template <class V>
 __device__ __forceinline__ V u_series_v(V x) {
-    V p = V(1.f / 5040.f);
-    p = vfma(p, x, V(-1.f / 720.f));
-    p = vfma(p, x, V(1.f / 120.f));
-    p = vfma(p, x, V(-1.f / 24.f));
-    p = vfma(p, x, V(1.f / 6.f));
+    V p = V(-0.0013885563239455223f);
+    p = vfma(p, x, V(0.008350598625838757f));
+    p = vfma(p, x, V(-0.04166680946946144f));
+    p = vfma(p, x, V(0.16666632890701294f));
     p = vfma(p, x, V(-0.5f));
     return vfma(p, x, V(1.f));
 }
@@ -688,8 +690,11 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 // and b+1 from its lane and the next (shuffle).  31 bins per pass.
 // x^3 / (e^x - 1), the Planck integrand in x = h c nu / (k T), as num/den so
 // that two quadrature nodes share one reciprocal:
-//   x < 1/2:  x^2 / q,  q = (e^x - 1)/x from its Taylor series (to x^6 / 7!,
-//             truncation < 2e-7 relative), so that small x keeps its digits;
+//   x < 1/2:  x^2 / q,  q = (e^x - 1)/x as a degree-4 polynomial fitted for
+//             the least maximum relative error on [0, 1/2], constant term 1
+//             (csrc/fit_series.py; 1.0e-7 relative, 1.6e-7 evaluated in FP32,
+//             against 2.1e-7 for the Taylor sum to x^6 / 7! with two more
+//             multiply-adds), so that small x keeps its digits;
 //   x >= 1/2: x^3 m / (1 - m),  m = e^-x  (1 - m >= 0.39: no cancellation,
 //             and no overflow however large x is).
 // Written over V (one value, or two on the paired instructions) with every
@@ -702,12 +707,10 @@ struct PlanckND {
 };
 template <class V>
 __device__ __forceinline__ PlanckND<V> planck_nd(V x) {
-    V q = V(1.f / 5040.f);
-    q = vfma(q, x, V(1.f / 720.f));
-    q = vfma(q, x, V(1.f / 120.f));
-    q = vfma(q, x, V(1.f / 24.f));
-    q = vfma(q, x, V(1.f / 6.f));
-    q = vfma(q, x, V(0.5f));
+    V q = V(0.010216917842626572f);
+    q = vfma(q, x, V(0.040856339037418365f));
+    q = vfma(q, x, V(0.1668008267879486f));
+    q = vfma(q, x, V(0.4999932050704956f));
     q = vfma(q, x, V(1.f));
     const V xx = x * x;
     const V m = vexpn(x);
