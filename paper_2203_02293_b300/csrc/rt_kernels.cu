@@ -853,7 +853,10 @@ __device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const 
 // the bin's scattering and cloud absorption per unit mass), dtau = E dp / g,
 // w0 = s_b / E (capped at 1) and the bin's g0.  Every operation is an explicitly rounded
 // intrinsic, so that the fused solve and the standalone optics kernel
-// produce the same bits.
+// produce the same bits.  The cell search compares in FP64 against the
+// FP64 grids; the weights, log10 p and dp / g are formed in FP32 (each a few
+// ulp: below 1e-5 relative in kappa), which keeps the FP64 pipe, 1/64 of the
+// FP32 rate on this part, out of the pre-kernel's critical path.
 // ---------------------------------------------------------------------
 __device__ __forceinline__ void kt_bracket(const double *grid, int n, double v, int &i, float &w) {
     v = fmin(fmax(v, grid[0]), grid[n - 1]);
@@ -864,7 +867,7 @@ __device__ __forceinline__ void kt_bracket(const double *grid, int n, double v, 
         else hi = m;
     }
     i = lo;
-    w = (float)__ddiv_rn(__dsub_rn(v, grid[lo]), __dsub_rn(grid[lo + 1], grid[lo]));
+    w = __fdiv_rn(__double2float_rn(__dsub_rn(v, grid[lo])), __double2float_rn(__dsub_rn(grid[lo + 1], grid[lo])));
 }
 
 // gT, gP: the table's T and log10 p grids (in shared memory where staged)
@@ -873,9 +876,12 @@ __device__ __forceinline__ float4 kt_layer(const KParams &kp, const double *gT, 
     int iT, iP;
     float wT, wP;
     kt_bracket(gT, kp.kt_nT, T, iT, wT);
-    kt_bracket(gP, kp.kt_nP, __dmul_rn(0.5, log10(__dmul_rn(p_top, p_bot))), iP, wP);   // log10 sqrt(p_top p_bot)
+    // log10 sqrt(p_top p_bot), from the FP64 product
+    const float lp = __fmul_rn(0.5f, log10f(__double2float_rn(__dmul_rn(p_top, p_bot))));
+    kt_bracket(gP, kp.kt_nP, (double)lp, iP, wP);
     const int off = (iT * kp.kt_nP + iP) * S;
-    return make_float4(__int_as_float(off), wT, wP, (float)__ddiv_rn(__dsub_rn(p_bot, p_top), kp.grav));
+    return make_float4(__int_as_float(off), wT, wP,
+                       __fdiv_rn(__double2float_rn(__dsub_rn(p_bot, p_top)), __double2float_rn(kp.grav)));
 }
 
 struct Optics {
@@ -984,8 +990,8 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
                 store(lev, vq[0]);
             }
         }
-        // the layers' k-table cells (FP64, on the FP64 pipe) after the
-        // Planck tasks, so that they overlap other warps' FP32 work
+        // the layers' k-table cells (FP64 compares) after the Planck tasks,
+        // so that they overlap other warps' FP32 work
         if (kp.kt_lk)
             for (int l = threadIdx.x; l < L; l += blockDim.x)
                 kp.kt_lay[kp.lay_off[c] + l] =
