@@ -950,6 +950,13 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
         }
         __syncthreads();
+        // the layers' k-table cells first: their loads and FP64 compares
+        // then overlap the Planck tasks of the other warps
+        if (kp.kt_lk)
+            for (int l = threadIdx.x; l < L; l += blockDim.x)
+                kp.kt_lay[kp.lay_off[c] + l] =
+                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
+                             NB * kp.n_g);
         const int nchunk = (NB + 30) / 31;
         // levels [lev0, nlev]: the 2L+1 levels, then T_int (T_int alone when
         // the solve kernel evaluates B itself)
@@ -990,13 +997,6 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
                 store(lev, vq[0]);
             }
         }
-        // the layers' k-table cells (FP64 compares) after the Planck tasks,
-        // so that they overlap other warps' FP32 work
-        if (kp.kt_lk)
-            for (int l = threadIdx.x; l < L; l += blockDim.x)
-                kp.kt_lay[kp.lay_off[c] + l] =
-                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
-                             NB * kp.n_g);
     }
 }
 
