@@ -315,47 +315,80 @@ def run_ktable(args, stream):
 
     # end to end: each step copies the column state (T, p, mu, F*) from
     # pinned host memory, solves with the fused front end and reads the
-    # fluxes and heating back; the table stays resident.  Two batches,
-    # handles and streams alternate, so step k+1's copies overlap step k's
-    # solve (as in the cube path's end-to-end figure)
+    # fluxes and heating back; the table stays resident.  The kernels run in
+    # order on one compute stream; a copy stream moves step k+1's state in and
+    # step k's results out while step k solves (two input and two output
+    # buffers, handed over by events)
     state = ("T_center", "T_iface", "p_iface", "mu_star", "F_star")
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(cols, k))).pin_memory() for k in state}
     bs = [b, DeviceBatch(cols)]
-    sols = [s, Solver(cols.g_weights)]
-    sols[1].set_ktable(kt)
-    streams = [stream, torch.cuda.Stream()]
+    cs = torch.cuda.Stream()
     outs = []
     for _ in range(2):
         o = {k: torch.empty(b.n_if, dtype=torch.float64).pin_memory() for k in ("F_up", "F_down", "F_net")}
         o["Q"] = torch.empty(b.n_lay, dtype=torch.float64).pin_memory()
         outs.append(o)
     out_dev = [{k: torch.empty_like(v, device="cuda") for k, v in o.items()} for o in outs]
+    ev = {name: [torch.cuda.Event() for _ in range(2)] for name in ("in_ready", "in_free", "out_ready", "out_free")}
 
-    def e2e_step(k):
+    def h2d(k):
         i = k % 2
-        st = streams[i]
-        with torch.cuda.stream(st):
+        cs.wait_event(ev["in_free"][i])
+        with torch.cuda.stream(cs):
             for key in state:
                 getattr(bs[i], key).copy_(host[key], non_blocking=True)
-            sols[i].solve_ktable(bs[i], st)
-            rt.rt_fluxes(sols[i].h, out_dev[i]["F_up"], out_dev[i]["F_down"], out_dev[i]["F_net"], st)
-            rt.rt_heating(sols[i].h, out_dev[i]["Q"], st)
+        ev["in_ready"][i].record(cs)
+
+    def compute(k):
+        i = k % 2
+        stream.wait_event(ev["in_ready"][i])
+        s.solve_ktable(bs[i], stream)
+        ev["in_free"][i].record(stream)
+        stream.wait_event(ev["out_free"][i])
+        rt.rt_fluxes(s.h, out_dev[i]["F_up"], out_dev[i]["F_down"], out_dev[i]["F_net"], stream)
+        rt.rt_heating(s.h, out_dev[i]["Q"], stream)
+        ev["out_ready"][i].record(stream)
+
+    def d2h(k):
+        i = k % 2
+        cs.wait_event(ev["out_ready"][i])
+        with torch.cuda.stream(cs):
             for key in outs[i]:
                 outs[i][key].copy_(out_dev[i][key], non_blocking=True)
+        ev["out_free"][i].record(cs)
 
-    for k in range(4):
-        e2e_step(k)
+    def e2e_run(n, e0=None, e1=None):
+        if e0 is not None:
+            e0.record(stream)
+        cs.wait_stream(stream)
+        for i in range(2):                       # both buffers free at the start
+            ev["in_free"][i].record(stream)
+            ev["out_free"][i].record(cs)
+        h2d(0)
+        for k in range(n):
+            if k + 1 < n:
+                h2d(k + 1)                       # overlaps compute(k)
+            compute(k)
+            d2h(k)                               # overlaps compute(k + 1)
+        stream.wait_stream(cs)
+        if e1 is not None:
+            e1.record(stream)
+
+    e2e_run(4)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(streams[0])
-    streams[1].wait_event(e0)
-    for k in range(args.ktable_steps):
-        e2e_step(k)
-    streams[0].wait_stream(streams[1])
-    e1.record(streams[0])
+    e2e_run(args.ktable_steps, e0, e1)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / args.ktable_steps
-    sols[1].close()
+    # every step carried the same state: the last step's host results must
+    # equal a resident solve's, bit for bit
+    last = outs[(args.ktable_steps - 1) % 2]
+    ref = {k: torch.empty_like(v) for k, v in out_dev[0].items()}
+    s.solve_ktable(b, stream)
+    rt.rt_fluxes(s.h, ref["F_up"], ref["F_down"], ref["F_net"], stream)
+    rt.rt_heating(s.h, ref["Q"], stream)
+    torch.cuda.synchronize()
+    e2e_match = all(torch.equal(last[k], ref[k].cpu()) for k in ref)
     outs = outs[0]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in outs.values())
@@ -367,7 +400,8 @@ def run_ktable(args, stream):
            "unfused_ms_per_step": ms_unfused, "unfused_value": n / (ms_unfused * 1e-3),
            "e2e": {"value": n / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": ms_e2e,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "pipelining": "two batches, handles and streams: step k+1's copies overlap step k's solve"},
+                   "pipelining": "one compute stream and one copy stream, two input and two output buffers: step k+1's state copy and step k's result copy overlap step k's solve",
+                   "outputs_match_resident": e2e_match},
            "steps": args.ktable_steps, "nonfinite_outputs": st["nonfinite_outputs"],
            "invalid_inputs": st["invalid_inputs"]}
     del b, bs, fb, o
