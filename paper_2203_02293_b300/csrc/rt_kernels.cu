@@ -879,7 +879,7 @@ __device__ __forceinline__ float4 kt_layer(const KParams &kp, const double *gT, 
     // log10 sqrt(p_top p_bot), from the FP64 product
     const float lp = __fmul_rn(0.5f, log10f(__double2float_rn(__dmul_rn(p_top, p_bot))));
     kt_bracket(gP, kp.kt_nP, (double)lp, iP, wP);
-    const int off = (iT * kp.kt_nP + iP) * S;
+    const int off = (iT * (kp.kt_nP - 1) + iP) * S * 2;   // float offset of the (iP, iP + 1) pairs
     return make_float4(__int_as_float(off), wT, wP,
                        __fdiv_rn(__double2float_rn(__dsub_rn(p_bot, p_top)), __double2float_rn(kp.grav)));
 }
@@ -905,19 +905,22 @@ __device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float 
     return o;
 }
 
-// The four table corners of system s for a layer whose cell starts at l4.x.
+// The four table corners of system s for a layer whose cell starts at l4.x:
+// the table keeps the two p-neighbours of a (T, p) node side by side, so the
+// corners are one 8-byte load at iT and one at iT + 1 (8-byte aligned: the
+// offsets are even and the table is a fresh allocation).
 struct Corners {
     float k00, k01, k10, k11;
 };
 
 __device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int S, int s) {
-    const float *t = kp.kt_lk + __float_as_int(l4.x) + s;
-    const int sP = S, sT = kp.kt_nP * S;
+    const float2 *t = reinterpret_cast<const float2 *>(kp.kt_lk + __float_as_int(l4.x)) + s;
+    const float2 a = __ldg(t), b = __ldg(t + (kp.kt_nP - 1) * S);
     Corners c;
-    c.k00 = __ldg(t);
-    c.k01 = __ldg(t + sP);
-    c.k10 = __ldg(t + sT);
-    c.k11 = __ldg(t + sT + sP);
+    c.k00 = a.x;
+    c.k01 = a.y;
+    c.k10 = b.x;
+    c.k11 = b.y;
     return c;
 }
 
