@@ -239,8 +239,8 @@ typedef struct {
 
 /* Copy a k-table into the handle (device memory) and precompute the per-bin
  * scattering data from the handle's bins (uniform or explicit edges).  The
- * device copy holds each node's value beside its next p-neighbour's,
- * 2 (n_P - 1) / n_P times the caller's table; the caller's arrays may be
+ * device copy holds each node's value beside its next T-neighbour's,
+ * 2 (n_T - 1) / n_T times the caller's table; the caller's arrays may be
  * freed on return.
  * RT_EINVAL on a bad field or when the table's n_g differs from the
  * handle's; replaces any earlier table (synchronises the device). */

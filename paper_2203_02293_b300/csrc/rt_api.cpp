@@ -746,10 +746,11 @@ int rt_set_ktable(rt_handle *h, const rt_ktable *kt) {
         return fail(h, RT_EINVAL, "f_cloud, x_H2, x_He must be >= 0 and mbar > 0");
     const int64_t S = (int64_t)kt->n_bins * cfg.n_g;
     const int64_t n_tab = (int64_t)kt->n_T * kt->n_P * S;
-    // device layout: the p-neighbours side by side, [n_T][n_P - 1][S][2] =
-    // (log10 kappa at iP, at iP + 1), so that a system's four cell corners
-    // are two 8-byte loads
-    const int64_t n_pair = (int64_t)kt->n_T * (kt->n_P - 1) * S * 2;
+    // device layout: the T-neighbours side by side, [n_T - 1][n_P][S][2] =
+    // (log10 kappa at iT, at iT + 1), so that a system's four cell corners
+    // are two 8-byte loads and its two interpolations along log p one paired
+    // operation
+    const int64_t n_pair = (int64_t)(kt->n_T - 1) * kt->n_P * S * 2;
     if (n_pair >= INT32_MAX) return fail(h, RT_EINVAL, "k-table too large (%lld entries)", (long long)n_tab);
     for (int b = 0; b < kt->n_bins; ++b)
         if (!(kt->sigma_scat_cloud[b] >= 0.0) || !(kt->sigma_abs_cloud[b] >= 0.0) || !(fabs(kt->g0_cloud[b]) < 1.0))
@@ -791,10 +792,10 @@ int rt_set_ktable(rt_handle *h, const rt_ktable *kt) {
     h->d_kT = h->d_klp = nullptr;
     h->kt_set = false;
     std::vector<float> pairs((size_t)n_pair);
-    for (int64_t iT = 0; iT < kt->n_T; ++iT)
-        for (int64_t iP = 0; iP + 1 < kt->n_P; ++iP) {
-            const float *lo = kt->log10_kappa + (iT * kt->n_P + iP) * S, *hi = lo + S;
-            float *d = pairs.data() + (iT * (kt->n_P - 1) + iP) * S * 2;
+    for (int64_t iT = 0; iT + 1 < kt->n_T; ++iT)
+        for (int64_t iP = 0; iP < kt->n_P; ++iP) {
+            const float *lo = kt->log10_kappa + (iT * kt->n_P + iP) * S, *hi = lo + kt->n_P * S;
+            float *d = pairs.data() + (iT * kt->n_P + iP) * S * 2;
             for (int64_t s = 0; s < S; ++s) {
                 d[2 * s] = lo[s];
                 d[2 * s + 1] = hi[s];

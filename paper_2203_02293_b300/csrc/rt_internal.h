@@ -72,7 +72,7 @@ struct KParams {
     const float *dnu32;          // [NB] bin widths formed in FP64, rounded to FP32
     double *toa;                 // [sum NB] TOA upward flux per bin (zeroed before the solve)
     // k-table front end (set when the optics come from the table)
-    const float *kt_lk;          // [nT][nP - 1][NB * n_g][2] log10 kappa at (iT, iP) and (iT, iP + 1)
+    const float *kt_lk;          // [nT - 1][nP][NB * n_g][2] log10 kappa at (iT, iP) and (iT + 1, iP)
     const float4 *kt_bin;        // [NB] (scattering, cloud absorption per unit mass, g0, 0)
     const double *kt_T, *kt_lp;  // grids [nT] K, [nP] log10(p / Pa)
     int32_t kt_nT, kt_nP;

@@ -879,7 +879,7 @@ __device__ __forceinline__ float4 kt_layer(const KParams &kp, const double *gT, 
     // log10 sqrt(p_top p_bot), from the FP64 product
     const float lp = __fmul_rn(0.5f, log10f(__double2float_rn(__dmul_rn(p_top, p_bot))));
     kt_bracket(gP, kp.kt_nP, (double)lp, iP, wP);
-    const int off = (iT * (kp.kt_nP - 1) + iP) * S * 2;   // float offset of the (iP, iP + 1) pairs
+    const int off = (iT * kp.kt_nP + iP) * S * 2;   // float offset of the (iT, iT + 1) pairs
     return make_float4(__int_as_float(off), wT, wP,
                        __fdiv_rn(__double2float_rn(__dsub_rn(p_bot, p_top)), __double2float_rn(kp.grav)));
 }
@@ -890,10 +890,13 @@ struct Optics {
 
 constexpr float kLog2Of10 = 3.32192809488736234787f;
 
-__device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float k11, float4 l4, float4 bq) {
-    const float a0 = __fmaf_rn(l4.z, __fsub_rn(k01, k00), k00);     // along log p at T_i
-    const float a1 = __fmaf_rn(l4.z, __fsub_rn(k11, k10), k10);     // along log p at T_i+1
-    const float x = __fmaf_rn(l4.y, __fsub_rn(a1, a0), a0);         // log10 kappa
+// lo = (k00, k10) and hi = (k01, k11): the corners at p_i and p_i+1 for T_i and
+// T_i+1, so the two interpolations along log p run as one paired operation
+// (each component rounded as the scalar form would round it).
+__device__ __forceinline__ Optics kt_mix(float2 lo, float2 hi, float4 l4, float4 bq) {
+    const float2 d = __ffma2_rn(lo, make_float2(-1.f, -1.f), hi);                 // k01 - k00, k11 - k10
+    const float2 a = __ffma2_rn(make_float2(l4.z, l4.z), d, lo);                  // along log p at T_i, T_i+1
+    const float x = __fmaf_rn(l4.y, __fsub_rn(a.y, a.x), a.x);                    // log10 kappa
     const float kappa = fex2(__fmul_rn(x, kLog2Of10));
     const float ext = __fadd_rn(__fadd_rn(kappa, bq.x), bq.y);
     Optics o;
@@ -906,21 +909,18 @@ __device__ __forceinline__ Optics kt_mix(float k00, float k01, float k10, float 
 }
 
 // The four table corners of system s for a layer whose cell starts at l4.x:
-// the table keeps the two p-neighbours of a (T, p) node side by side, so the
-// corners are one 8-byte load at iT and one at iT + 1 (8-byte aligned: the
+// the table keeps the two T-neighbours of a (T, p) node side by side, so the
+// corners are one 8-byte load at p_i and one at p_i+1 (8-byte aligned: the
 // offsets are even and the table is a fresh allocation).
 struct Corners {
-    float k00, k01, k10, k11;
+    float2 lo, hi;                                // (k00, k10), (k01, k11)
 };
 
 __device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int S, int s) {
     const float2 *t = reinterpret_cast<const float2 *>(kp.kt_lk + __float_as_int(l4.x)) + s;
-    const float2 a = __ldg(t), b = __ldg(t + (kp.kt_nP - 1) * S);
     Corners c;
-    c.k00 = a.x;
-    c.k01 = a.y;
-    c.k10 = b.x;
-    c.k11 = b.y;
+    c.lo = __ldg(t);
+    c.hi = __ldg(t + S);
     return c;
 }
 
@@ -1265,7 +1265,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             }
 #pragma unroll
             for (int i = 0; i < NS; ++i) {
-                const Optics o = kt_mix(cur[i].k00, cur[i].k01, cur[i].k10, cur[i].k11, kl, kb[i]);
+                const Optics o = kt_mix(cur[i].lo, cur[i].hi, kl, kb[i]);
                 cmp(dt, i) = o.dt;
                 cmp(w0, i) = o.w0;
                 cmp(g0, i) = o.g0;
@@ -1708,7 +1708,7 @@ __global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_
             const int l = (int)(i / S), s = (int)(i - (long long)l * S);
             const float4 l4 = sl[l];
             const Corners k = kt_corners(kp, l4, S, s);
-            const Optics o = kt_mix(k.k00, k.k01, k.k10, k.k11, l4, __ldg(kp.kt_bin + s / NG));
+            const Optics o = kt_mix(k.lo, k.hi, l4, __ldg(kp.kt_bin + s / NG));
             dtau[base + i] = o.dt;
             w0[base + i] = o.w0;
             g0[base + i] = o.g0;
