@@ -54,7 +54,7 @@ struct KParams {
     float *planck32;             // B per column [2L+1][NB] (levels: 2i interface, 2i+1 centre)
     const int64_t *planck_off;   // [n_cols]
     float *fs32, *fboa32;        // [sum NB] F* and F_BOA per bin
-    float4 *colf;                // [n_cols] (mu, 1/mu, beam?, 0)
+    float4 *colf;                // [n_cols] (mu, 1/mu, beam?, coldest level T or 0)
     const float *g_w32;          // [n_g] Gauss weights in FP32
     int32_t nbw;                 // bins one warp's 32 systems can touch
     int32_t direct;              // 1: read B from planck32 directly (no staging)

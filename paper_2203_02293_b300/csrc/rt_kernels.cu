@@ -948,11 +948,27 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             sT[lev] = lev == nlev ? (float)kp.T_int
                                   : (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
         for (int b = threadIdx.x; b < NB; b += blockDim.x) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
-        if (threadIdx.x == 0) {
-            const double mu = kp.mu_star[kp.mu_idx[c]];
-            kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f, 0.f);
-        }
         __syncthreads();
+        if (warp == 0) {
+            // the coldest level (largest h c / k T) bounds every level's bin
+            // widths in x, which lets the solve kernel's inline B skip the
+            // per-level narrow-bin tests; 0 when some level is not in (0, 1e20)
+            float tmin = 3.0e38f;
+            bool ok = true;
+            for (int lev = lane; lev < nlev; lev += 32) {
+                const float T = sT[lev];
+                ok = ok && T > 0.f && T < 1e20f;
+                tmin = fminf(tmin, T);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+            if (lane == 0) {
+                const double mu = kp.mu_star[kp.mu_idx[c]];
+                kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f,
+                                         ok ? tmin : 0.f);
+            }
+        }
         // the layers' k-table cells first: their loads and FP64 compares
         // then overlap the Planck tasks of the other warps
         if (kp.kt_lk)
@@ -1149,6 +1165,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     float wn0[NS], wn1[NS], dnu[NS];
     const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c];
     V wn0v, wn1v, dnuv;
+    bool unit_narrow = false;                  // INL: the unit's bins take two points at every level
     auto B_at = [&](int lev, V &B) {           // B of the lane's systems at level lev
         const double Td = (lev & 1) ? __ldg(kp.T_center + tc0 + (lev >> 1)) : __ldg(kp.T_iface + ifi + (lev >> 1));
         const PlanckLevel lv = planck_level((float)Td, 1.f);
@@ -1157,11 +1174,15 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         // bin through the per-system rule (the same bits either way)
         const V a = V(lv.a);
         const V x0 = a * wn0v, hh = V(0.5f) * (a * dnuv), w = a * wn1v - x0;
-        bool fast = true;
+        bool fast = unit_narrow;
+        if (!fast) {
+            fast = true;
 #pragma unroll
-        for (int i = 0; i < NS; ++i)
-            fast = fast && cmp(w, i) < kNarrowBin && planck_takes_two_points(cmp(x0, i), cmp(hh, i));
-        if (__all_sync(0xffffffffu, fast)) {
+            for (int i = 0; i < NS; ++i)
+                fast = fast && cmp(w, i) < kNarrowBin && planck_takes_two_points(cmp(x0, i), cmp(hh, i));
+            fast = __all_sync(0xffffffffu, fast);
+        }
+        if (fast) {
             B = V(lv.pref) * planck_two_point(x0, hh);
         } else {
 #pragma unroll
@@ -1201,6 +1222,20 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             cmp(wn0v, i) = wn0[i];
             cmp(wn1v, i) = wn1[i];
             cmp(dnuv, i) = dnu[i];
+        }
+        // every level of the column is at least as warm as cf.w, so its
+        // h c / k T is at most that level's: if the unit's bins pass the
+        // two-point tests there (with margins for the FP32 roundings of the
+        // per-level tests), they pass at every level and the tests are skipped
+        if (cf.w > 0.f) {
+            const float am = __fmul_rn(planck_level(cf.w, 1.f).a, 1.0001f);
+            bool ok = true;
+#pragma unroll
+            for (int i = 0; i < NS; ++i)
+                ok = ok && fmaf(am, wn1[i] - wn0[i], 1e-6f * am * wn1[i]) < 0.999f * kNarrowBin &&
+                     am * dnu[i] < 0.999f * kTwoPointBin &&
+                     0.5f * dnu[i] < 0.0099f * (wn0[i] + 0.5f * dnu[i]);
+            unit_narrow = __all_sync(0xffffffffu, ok);
         }
         B_at(0, Bt);
         B_at(1, Bc);
