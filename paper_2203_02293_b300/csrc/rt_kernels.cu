@@ -802,8 +802,9 @@ __device__ __forceinline__ float planck_bin32(PlanckLevel lv, float wn0, float w
 // so that the NQ evaluation chains are independent and can overlap.  The
 // values equal planck_bin32's for the same bin and level.
 template <int NQ>
-__device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const float (&scale)[NQ], float wn,
-                                                    float dnu_b, bool inb, float (&out)[NQ]) {
+__device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const float (&scale)[NQ],
+                                                    const float (&wn)[NQ], const float (&dnu_b)[NQ],
+                                                    const bool (&inb)[NQ], float (&out)[NQ]) {
     PlanckLevel lv[NQ];
     float x[NQ], x1[NQ], v[NQ], v1[NQ], d[NQ];
     bool nar[NQ];
@@ -811,11 +812,11 @@ __device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const 
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         lv[q] = planck_level(T[q], scale[q]);
-        x[q] = __fmul_rn(lv[q].a, wn);
+        x[q] = __fmul_rn(lv[q].a, wn[q]);
         x1[q] = __shfl_down_sync(0xffffffffu, x[q], 1);
-        nar[q] = !inb || (__fsub_rn(x1[q], x[q]) < kNarrowBin);
+        nar[q] = !inb[q] || (__fsub_rn(x1[q], x[q]) < kNarrowBin);
         alln = alln && nar[q];
-        anyn = anyn || (inb && nar[q]);
+        anyn = anyn || (inb[q] && nar[q]);
     }
     // the edge series only when some bin of this chunk is wide
     if (!__all_sync(0xffffffffu, alln)) {
@@ -838,7 +839,7 @@ __device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const 
     if (__any_sync(0xffffffffu, anyn)) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
-            if (nar[q]) d[q] = planck_narrow_f(x[q], __fmul_rn(0.5f, __fmul_rn(lv[q].a, dnu_b)));
+            if (nar[q]) d[q] = planck_narrow_f(x[q], __fmul_rn(0.5f, __fmul_rn(lv[q].a, dnu_b[q])));
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) out[q] = __fmul_rn(lv[q].pref, d[q]);
@@ -984,6 +985,26 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         int run = (int)(((long long)nl * nchunk + nw - 1) / nw);
         run = run < nl ? run : nl;
         const int nrun = (nl + run - 1) / run;
+        if (nl == 1) {
+            // T_int alone (inline B): four chunks per pass as independent chains
+            for (int t0 = 4 * warp; t0 < nchunk; t0 += 4 * nw) {
+                float Tq[4], sq[4], wq[4], dq[4], vq[4];
+                bool iq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = (t0 + q) * 31 + lane;
+                    iq[q] = t0 + q < nchunk && lane < 31 && e < NB;
+                    wq[q] = kp.edges32 ? __ldg(kp.edges32 + min(e, NB)) : fmaf((float)e, dwn, wmin);
+                    dq[q] = kp.edges32 ? __ldg(kp.dnu32 + min(e, NB - 1)) : dwn;
+                    Tq[q] = sT[nlev];
+                    sq[q] = kPiF;
+                }
+                planck_chunk_levels<4>(Tq, sq, wq, dq, iq, vq);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (iq[q]) kp.fboa32[b0 + (t0 + q) * 31 + lane] = vq[q];
+            }
+        } else
         for (int task = warp; task < nchunk * nrun; task += nw) {
             const int ch = task % nchunk, r0 = lev0 + (task / nchunk) * run;
             const int e = ch * 31 + lane, bin = e;
@@ -1006,13 +1027,17 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
                     Tq[q] = sT[lev + q];
                     sq[q] = lev + q == nlev ? kPiF : 1.f;
                 }
-                planck_chunk_levels<4>(Tq, sq, wn, dnu_b, inb, vq);
+                const float wq[4] = {wn, wn, wn, wn}, dq[4] = {dnu_b, dnu_b, dnu_b, dnu_b};
+                const bool iq[4] = {inb, inb, inb, inb};
+                planck_chunk_levels<4>(Tq, sq, wq, dq, iq, vq);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) store(lev + q, vq[q]);
             }
             for (; lev < r1; ++lev) {
                 float Tq[1] = {sT[lev]}, sq[1] = {lev == nlev ? kPiF : 1.f}, vq[1];
-                planck_chunk_levels<1>(Tq, sq, wn, dnu_b, inb, vq);
+                const float wq[1] = {wn}, dq[1] = {dnu_b};
+                const bool iq[1] = {inb};
+                planck_chunk_levels<1>(Tq, sq, wq, dq, iq, vq);
                 store(lev, vq[0]);
             }
         }
