@@ -2,6 +2,8 @@
 post-processing shape (Sec. 2.1.3: R = 500 opacity sampling, 3255 bins, one
 g-point, columns extended to 1 ubar with isothermal layers) against the
 oracle, and the spectrum's bin sums across work-unit boundaries."""
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -146,6 +148,45 @@ def test_planck_staged_direct_and_inline_agree_bitwise(n_g, iso, spl):
     for o in outs[1:]:
         for k in outs[0]:
             assert np.array_equal(outs[0][k], o[k]), k
+
+
+@pytest.mark.parametrize("spl", [1, 2])
+def test_inline_unit_narrow_decision_matches_the_table(spl):
+    """The solve kernel skips the per-level narrow-bin tests of inline B for a
+    unit whose bins take two points at the column's coldest level.  Columns
+    where that holds for every unit (hot), for none of the blue units (cold:
+    their bins are wide in x there), for some levels only (a profile through
+    both), and a column with a level at T = 0 (no coldest-level bound, so the
+    per-level tests run): inline B equals the table bit for bit."""
+    cols = rt_synth.postproc(4, seed=13)
+    o = cols.offsets()
+    T_c, T_i = cols.T_center.copy(), cols.T_iface.copy()
+    for c, kind in enumerate(("hot", "cold", "through", "zero")):
+        lay = slice(o["lay"][c], o["lay"][c + 1])
+        ifc = slice(o["iface"][c], o["iface"][c + 1])
+        L = o["lay"][c + 1] - o["lay"][c]
+        if kind == "hot":
+            T_c[lay], T_i[ifc] = 3000.0, 3000.0
+        elif kind == "cold":
+            T_c[lay], T_i[ifc] = 60.0, 60.0
+        elif kind == "through":
+            T_i[ifc] = np.geomspace(60.0, 3000.0, L + 1)
+            T_c[lay] = np.sqrt(T_i[ifc][:-1] * T_i[ifc][1:])
+        else:
+            T_i[o["iface"][c]] = 0.0
+    cols = replace(cols, T_center=T_c, T_iface=T_i)
+    b = DeviceBatch(cols)
+    outs = []
+    for mode in (rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE):
+        s = Solver(cols.g_weights, planck_staging=mode, systems_per_lane=spl, wn_edges=cols.consts["wn_edges"])
+        s.solve(b)
+        out = s.outputs(b)
+        out["F_up_toa"] = s.toa_spectrum(b)
+        outs.append({k: v.cpu().numpy() for k, v in out.items()})
+        s.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+        assert np.all(np.isfinite(outs[1][k])), k
 
 
 @pytest.mark.parametrize("spl", [1, 2])
