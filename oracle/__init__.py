@@ -44,6 +44,7 @@ class _Cfg(ctypes.Structure):
         ("cp", ctypes.c_double), ("T_int", ctypes.c_double),
         ("F_toa", ctypes.c_double), ("wn_min", ctypes.c_double),
         ("wn_max", ctypes.c_double), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
+        ("n_sweeps", ctypes.c_int32),
     ]
 
 
@@ -67,6 +68,7 @@ class OracleConfig:
     wn_min: float = 50.0
     wn_max: float = 1.0e4 / 0.3
     wn_edges: object = None      # None: NB uniform bins; else NB + 1 increasing edges, cm^-1
+    n_sweeps: int = 0            # 0: Thomas (Eqs. 12-15); N > 0: N sweeps of the iterative method
 
     def c(self) -> _Cfg:
         edges = None
@@ -76,7 +78,7 @@ class OracleConfig:
         return _Cfg(int(self.improved), int(self.isothermal),
                     0 if self.resonance == "paper" else 1, int(self.e_clamp),
                     self.eps2, self.grav, self.cp, self.T_int, self.F_toa,
-                    self.wn_min, self.wn_max, edges)
+                    self.wn_min, self.wn_max, edges, int(self.n_sweeps))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -111,6 +113,10 @@ class Oracle:
         L.oracle_solve_system.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, _F, _F, _F,
                                           _D, _D, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, _D, _D, _D]
+        L.oracle_sweep_system.restype = ctypes.c_int
+        L.oracle_sweep_system.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, _F, _F, _F,
+                                          _D, _D, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_int, _D, _D, _D]
         L.oracle_solve_columns.restype = ctypes.c_int
         L.oracle_solve_columns.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int, _I, _I,
                                            ctypes.c_int, _D, _F, _F, _F, _D, _D, _D,
@@ -162,6 +168,25 @@ class Oracle:
         rc = self.lib.oracle_solve_system(ctypes.byref(c), L, _p(dtau, _F), _p(w0, _F),
                                           _p(g0, _F), _p(Bc, _D), _p(Bi, _D), mu, Fstar,
                                           F_BOA, _p(up, _D), _p(dn, _D), _p(fb, _D))
+        assert rc == n
+        return up, dn, fb
+
+    def sweep_system(self, cfg: OracleConfig, dtau, w0, g0, Bc, Bi, mu, Fstar, F_BOA,
+                     n_sweeps, up0=None, dn0=None):
+        """n_sweeps sweeps of the iterative method (Sec. 2.2.2) from the
+        state (up0, dn0) at levels, BOA first (zero diffuse flux if None).
+        Returns F_up, F_dn (diffuse), F_beam, each [n+1]."""
+        dtau, w0, g0, Bc, Bi = self._sys_args(dtau, w0, g0, Bc, Bi)
+        L = dtau.size
+        n = L if cfg.isothermal else 2 * L
+        up = np.zeros(n + 1) if up0 is None else np.array(up0, dtype=np.float64)
+        dn = np.zeros(n + 1) if dn0 is None else np.array(dn0, dtype=np.float64)
+        assert up.size == n + 1 and dn.size == n + 1
+        fb = np.zeros(n + 1)
+        c = cfg.c()
+        rc = self.lib.oracle_sweep_system(ctypes.byref(c), L, _p(dtau, _F), _p(w0, _F),
+                                          _p(g0, _F), _p(Bc, _D), _p(Bi, _D), mu, Fstar,
+                                          F_BOA, int(n_sweeps), _p(up, _D), _p(dn, _D), _p(fb, _D))
         assert rc == n
         return up, dn, fb
 

@@ -18,6 +18,8 @@
  *     with the singularity check of Eq. 11 and the text after it
  *   - boundary conditions: Eq. 10 and the caption of Fig. thomas_isothermal
  *   - block-tridiagonal system and block Thomas: Eqs. 12-15 (2x2 blocks)
+ *   - the iterative method that Thomas's algorithm replaces (Sec. 2.2.2):
+ *     pairwise sweeps through the column, repeated N times
  *   - spectral sum, net flux (beam added to the downward flux, Sec. 2.2.1)
  *     and heating rate.
  * Planck per bin is the bin integral of the Planck function, done by
@@ -68,6 +70,9 @@ typedef struct {
     double wn_min, wn_max;  /* bin range, cm^-1, bins uniform in wavenumber */
     const double *wn_edges; /* NULL, or the NB + 1 increasing bin edges (cm^-1)
                                shared by every column; then wn_min/wn_max unused */
+    int32_t n_sweeps;       /* 0: Thomas's algorithm (Eqs. 12-15); N > 0: the
+                               iterative method of Sec. 2.2.2, N sweeps from zero
+                               diffuse flux (see sweeps()) */
 } oracle_cfg;
 
 typedef struct {
@@ -496,6 +501,45 @@ static void block_thomas(int n, const double *A, const double *B,
 }
 
 /* ------------------------------------------------------------------ */
+/* Iterative multiple scattering (Sec. 2.2.2, "Multiple scattering      */
+/* using Thomas's algorithm"): the older approach that the block solve  */
+/* replaces.  The pairwise two-stream relation of every sub-layer is     */
+/* applied in turn through the whole column, and the passes are         */
+/* repeated N times, so radiation is scattered N times in each          */
+/* direction.  One sweep here is:                                       */
+/*   - a downward pass from the TOA condition F_dn,n = F_TOA: each       */
+/*     sub-layer's downward relation gives F_dn at its bottom from F_dn  */
+/*     at its top (this pass) and F_up at its bottom (previous sweep);  */
+/*   - the BOA condition (Eq. 10): F_up,0 = F_dn,0 + F_BOA + F_beam,0;   */
+/*   - an upward pass: each sub-layer's upward relation gives F_up at    */
+/*     its top from F_up at its bottom (this pass) and F_dn at its top. */
+/* The paper fixes neither the order of the two passes nor the starting */
+/* state; we start from zero diffuse flux and go down first, so that    */
+/* without scattering (xi = 0: the up and down streams decouple) one    */
+/* sweep already gives the exact solution.                              */
+/* up, dn: [n+1] at levels (BOA first), the starting state on entry.    */
+/* ------------------------------------------------------------------ */
+static void sweeps(const oracle_cfg *cfg, const sys_work *w, double F_BOA,
+                   int n_sweeps, double *up, double *dn)
+{
+    int n = w->n;
+    for (int it = 0; it < n_sweeps; ++it) {
+        dn[n] = cfg->F_toa;
+        for (int s = n - 1; s >= 0; --s) {
+            /* chi F_dn,bot - psi F_dn,top + xi F_up,bot = S_dn */
+            const sub_rel *r = &w->rel[s];
+            dn[s] = (r->S_dn + r->psi * dn[s + 1] - r->xi * up[s]) / r->chi;
+        }
+        up[0] = dn[0] + F_BOA + w->Fb[0];
+        for (int s = 0; s < n; ++s) {
+            /* chi F_up,top - psi F_up,bot + xi F_dn,top = S_up */
+            const sub_rel *r = &w->rel[s];
+            up[s + 1] = (r->S_up + r->psi * up[s] - r->xi * dn[s + 1]) / r->chi;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Single-system entry points (used by the pins in the test suite).     */
 /* ------------------------------------------------------------------ */
 
@@ -580,6 +624,25 @@ int oracle_solve_system(const oracle_cfg *cfg, int L, const float *dtau,
     }
     free(A); free(B); free(C); free(D); free(X);
     return rc;
+}
+
+/* n_sweeps sweeps of the iterative method on one system.  F_up, F_dn
+ * [n+1] (levels BOA first) hold the starting state on entry and the result
+ * on return; F_beam [n+1] receives the direct beam.  Returns n, or -1. */
+int oracle_sweep_system(const oracle_cfg *cfg, int L, const float *dtau,
+                        const float *w0, const float *g0, const double *Bc,
+                        const double *Bi, double mu, double Fstar, double F_BOA,
+                        int n_sweeps, double *F_up, double *F_dn, double *F_beam)
+{
+    sys_work w;
+    if (!alloc_work(&w, L)) { free_work(&w); return -1; }
+    setup_system(cfg, L, dtau, w0, g0, 1, Bc, Bi, mu, Fstar, &w);
+    relations(cfg, mu, &w, NULL);
+    sweeps(cfg, &w, F_BOA, n_sweeps, F_up, F_dn);
+    memcpy(F_beam, w.Fb, sizeof(double) * (w.n + 1));
+    int n = w.n;
+    free_work(&w);
+    return n;
 }
 
 /* ------------------------------------------------------------------ */
@@ -685,12 +748,20 @@ int oracle_solve_columns(const oracle_cfg *cfg, int n_cols,
                         double *Dp = malloc(sizeof(double) * 2 * (n + 1));
                         double *X = malloc(sizeof(double) * 2 * (n + 1));
                         if (A && Bm && C && D && Cp && Dp && X) {
-                            assemble(cfg, &w, F_BOA, A, Bm, C, D);
-                            block_thomas(n, A, Bm, C, D, Cp, Dp, X);
+                            if (cfg->n_sweeps > 0) {
+                                /* the iterative method, from zero diffuse flux */
+                                for (int i = 0; i <= n; ++i) fu[i] = fd[i] = 0.0;
+                                sweeps(cfg, &w, F_BOA, cfg->n_sweeps, fu, fd);
+                            } else {
+                                assemble(cfg, &w, F_BOA, A, Bm, C, D);
+                                block_thomas(n, A, Bm, C, D, Cp, Dp, X);
+                                for (int i = 0; i <= n; ++i) {
+                                    fu[i] = X[2 * i];
+                                    fd[i] = X[2 * i + 1];
+                                }
+                            }
                             int bad = 0;
                             for (int i = 0; i <= n; ++i) {
-                                fu[i] = X[2 * i];
-                                fd[i] = X[2 * i + 1];
                                 fb[i] = w.Fb[i];
                                 if (!isfinite(fu[i]) || !isfinite(fd[i])) bad = 1;
                             }

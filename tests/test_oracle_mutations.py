@@ -77,3 +77,50 @@ def test_planted_mistake_is_caught(tmp_path, name):
     lib = oracle.build(path, os.path.join(tmp_path, "libmut.so"))
     failed = battery(oracle.Oracle(lib))
     assert failed, f"planted mistake {name} went unnoticed"
+
+
+# The iterative method (Sec. 2.2.2) has its own pins (tests/test_oracle_sweeps.py).
+SWEEP_MUTATIONS = {
+    "sweep_xi_sign": ("dn[s] = (r->S_dn + r->psi * dn[s + 1] - r->xi * up[s]) / r->chi;",
+                      "dn[s] = (r->S_dn + r->psi * dn[s + 1] + r->xi * up[s]) / r->chi;"),
+    "sweep_boa_drops_beam": ("up[0] = dn[0] + F_BOA + w->Fb[0];", "up[0] = dn[0] + F_BOA;"),
+    "sweep_wrong_level": ("up[s + 1] = (r->S_up + r->psi * up[s] - r->xi * dn[s + 1]) / r->chi;",
+                          "up[s + 1] = (r->S_up + r->psi * up[s] - r->xi * dn[s]) / r->chi;"),
+    "sweep_drops_toa": ("dn[n] = cfg->F_toa;", "dn[n] = 0.0;"),
+    "sweep_psi_for_chi": ("dn[s] = (r->S_dn + r->psi * dn[s + 1] - r->xi * up[s]) / r->chi;",
+                          "dn[s] = (r->S_dn + r->chi * dn[s + 1] - r->xi * up[s]) / r->psi;"),
+}
+
+
+def sweep_battery(orc):
+    import test_oracle_sweeps as sw
+    checks = [
+        ("no_scattering", lambda: sw.test_one_sweep_is_exact_without_scattering(orc, False)),
+        ("fixed_point", lambda: sw.test_block_solution_is_a_fixed_point(orc, False)),
+        ("gauss_seidel", lambda: sw.test_sweeps_are_gauss_seidel_on_the_block_rows(orc, True, 2)),
+        ("converge", lambda: sw.test_sweeps_converge_to_the_block_solution(orc, False)),
+    ]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except AssertionError:
+            failed.append(name)
+    return failed
+
+
+def test_unmutated_oracle_passes_sweep_battery():
+    assert sweep_battery(oracle.get()) == []
+
+
+@pytest.mark.parametrize("name", sorted(SWEEP_MUTATIONS))
+def test_planted_sweep_mistake_is_caught(tmp_path, name):
+    old, new = SWEEP_MUTATIONS[name]
+    src = open(oracle.SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    path = os.path.join(tmp_path, "rt_oracle_mut.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    lib = oracle.build(path, os.path.join(tmp_path, "libmut.so"))
+    failed = sweep_battery(oracle.Oracle(lib))
+    assert failed, f"planted mistake {name} went unnoticed"

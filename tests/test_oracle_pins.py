@@ -398,46 +398,3 @@ def test_resonance_rule_and_limit_mode(orc):
     cols.mu_star[:] = mu
     st = orc.solve_columns(oracle.OracleConfig(), cols)["stats"]
     assert st["resonance_hits"] == 3
-
-
-# ----------------------------------------------------------------------
-# Iterative multiple scattering (Sec. 2.2.2) converges to the Thomas solution
-# ----------------------------------------------------------------------
-
-def iterate_sweeps(A, B, C, D, n_sweeps):
-    """Repeat the pairwise two-stream sweeps over the whole column, as the
-    paper describes the older iterative approach: an upward pass that
-    updates F_up from the current F_down, then a downward pass that updates
-    F_down from the new F_up, n_sweeps times, starting from zero flux.  Uses
-    the layer relations carried by the assembled rows of Eq. 12."""
-    n = A.shape[0] - 1
-    up = np.zeros(n + 1)
-    dn = np.zeros(n + 1)
-    for _ in range(n_sweeps):
-        # BOA: F_up,0 - F_dn,0 = D[0,0]; upward relation of sub-layer i-1 in row i
-        up[0] = dn[0] + D[0, 0]
-        for i in range(1, n + 1):
-            # A[i,0,0] F_up,i-1 + B[i,0,0] F_up,i + B[i,0,1] F_dn,i = D[i,0]
-            up[i] = (D[i, 0] - A[i, 0, 0] * up[i - 1] - B[i, 0, 1] * dn[i]) / B[i, 0, 0]
-        # TOA: F_dn,n = D[n,1]; downward relation of sub-layer i in row i
-        dn[n] = D[n, 1]
-        for i in range(n - 1, -1, -1):
-            # B[i,1,0] F_up,i + B[i,1,1] F_dn,i + C[i,1,1] F_dn,i+1 = D[i,1]
-            dn[i] = (D[i, 1] - B[i, 1, 0] * up[i] - C[i, 1, 1] * dn[i + 1]) / B[i, 1, 1]
-    return up, dn
-
-
-@pytest.mark.parametrize("iso", [False, True])
-def test_iterative_sweeps_converge_to_thomas(orc, iso):
-    rng = np.random.default_rng(90 + iso)
-    dtau, w0, g0, Bc, Bi = random_column(rng, 6, 1e-3, 3.0, w_hi=0.9)
-    cfg = oracle.OracleConfig(isothermal=iso)
-    A, B, Cm, D, _ = orc.assemble(cfg, dtau, w0, g0, Bc, Bi, 0.5, 1e5, 5.0)
-    X = orc.block_thomas(A, B, Cm, D)
-    scale = np.abs(X).max()
-    errs = []
-    for N in (1, 10, 50, 200, 2000):
-        up, dn = iterate_sweeps(A, B, Cm, D, N)
-        errs.append(max(np.abs(up - X[:, 0]).max(), np.abs(dn - X[:, 1]).max()) / scale)
-    assert all(a >= b for a, b in zip(errs[:-1], errs[1:]))
-    assert errs[0] > 1e-3 and errs[-1] < 1e-10
