@@ -540,6 +540,9 @@ def main():
     ap.add_argument("--kernel-timing-steps", type=int, default=50)
     ap.add_argument("--serving-seconds", type=float, default=60.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--sweeps", default="10,200",
+                    help="sweep counts of the iterative method timed beside Thomas (empty: skip)")
+    ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
     ap.add_argument("--table", action="store_true",
                     help="per-workload table (configs 0-3, FP32/FP64 GPU, CPU oracle 1 core / all cores)")
@@ -739,6 +742,28 @@ def main():
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "note": "no current ncu summary for this kernel source"}
     stats = s32.stats()
+
+    # --- the iterative method (Sec. 2.2.2) beside Thomas on the same batch ---
+    sweeps = None
+    counts = [int(x) for x in args.sweeps.split(",") if x.strip()]
+    if counts and rank == 0:
+        ref = s32.outputs(batch, stream)
+        torch.cuda.synchronize()
+        sweeps = {"workload": WORKLOAD, "thomas_ms_per_step": ms32, "runs": []}
+        for n in counts:
+            sw = Solver(cols.g_weights, n_sweeps=n, kernel_timing=1)
+            steps = max(3, args.sweep_steps if n <= 20 else args.sweep_steps // 4)
+            ms = timed(sw, batch, steps, 3)
+            a, kms = rt.rt_kernel_times(sw.h)
+            got = sw.outputs(batch, stream)
+            torch.cuda.synchronize()
+            dev = {k: float(torch.max(torch.abs(got[k] - ref[k]) / torch.abs(ref[k]).clamp_min(1e-30)))
+                   for k in ("F_up", "F_down")}
+            sweeps["runs"].append({"n_sweeps": n, "ms_per_step": ms, "kernel_ms": kms,
+                                   "value": n_sys / (ms * 1e-3), "unit": UNIT, "steps": steps,
+                                   "slowdown_vs_thomas": ms / ms32,
+                                   "max_rel_dev_from_thomas": dev})
+            sw.close()
     s32.close()
 
     line = {
@@ -764,6 +789,8 @@ def main():
         "clocks": clk.summary(),
         "branch_counts": stats,
     }
+    if sweeps is not None:
+        line["sweeps"] = sweeps
     if rank == 0 and not args.quick:
         del batch, host, devs
         torch.cuda.empty_cache()

@@ -116,7 +116,22 @@ typedef struct {
                                     n_edges - 1 bins (e.g. the R = 500 sampling of
                                     the post-processing step, Sec. 2.1.3) */
     const double *wn_edges;      /* HOST [n_edges], cm^-1, increasing; copied by rt_create */
+    int32_t n_sweeps;            /* multiple scattering (Sec. 2.2.2).  0: Thomas's
+                                    algorithm on the block system (Eqs. 12-15).  N > 0:
+                                    the iterative method the paper replaces with it --
+                                    N sweeps of the sub-layers' pairwise two-stream
+                                    relations through the column (a downward pass from
+                                    the TOA condition, the BOA condition of Eq. 10, an
+                                    upward pass), starting from zero diffuse flux; the
+                                    result converges to Thomas's as N grows.  FP32 form,
+                                    cube optics, every column L <= RT_SWEEP_MAX_LAYERS;
+                                    RT_EINVAL otherwise.  At most 1 << 20 */
 } rt_config;
+
+/* Largest layer count of a column solved with n_sweeps > 0 (each GPU lane
+ * holds its system's per-layer transmission, reflection and level fluxes in
+ * registers). */
+#define RT_SWEEP_MAX_LAYERS 48
 
 /* A packed batch of columns.  Column c has L_c layers, NB_c bins and
  * S_c = NB_c * n_g systems.  Data of consecutive columns follow each other
@@ -146,14 +161,24 @@ typedef struct {
      * above): where column c's inputs start, in elements of each array.
      * Columns may then live anywhere in the input arrays, be shared by
      * several batch entries, or skip data -- e.g. requests that slice a
-     * device-resident pool.  The library cannot see the device arrays' sizes:
-     * offsets must keep every read inside them (RT_EINVAL only for negative
-     * offsets).  Outputs stay packed in batch order. */
+     * device-resident pool.  Outputs stay packed in batch order. */
     const int64_t *cube_offset;    /* into dtau, w0, g0 (block of L_c*NB_c*n_g) */
     const int64_t *center_offset;  /* into T_center (L_c values) */
     const int64_t *iface_offset;   /* into T_iface and p_iface (L_c+1 values) */
     const int64_t *bin_offset;     /* into F_star (NB_c values) */
     const int64_t *col_index;      /* into mu_star (1 value) */
+    /* Element counts of the device arrays (0 = not given).  The library
+     * cannot see device allocations, so these bound every read: each
+     * column's block [offset, offset + span) must lie inside its array's
+     * count, or the call returns RT_EINVAL before anything is enqueued.  A
+     * gather offset array requires the counts of the arrays it indexes; in
+     * the packed layout a given count is checked against the packed
+     * extent. */
+    int64_t n_cube;                /* elements of each of dtau, w0, g0 */
+    int64_t n_center;              /* elements of T_center */
+    int64_t n_iface;               /* elements of each of T_iface, p_iface */
+    int64_t n_fstar;               /* elements of F_star */
+    int64_t n_mu;                  /* elements of mu_star */
 } rt_columns;
 
 typedef struct {
@@ -166,13 +191,25 @@ typedef struct {
     int64_t fp64_evals;          /* FP32 form: layer-systems whose resonance test ran in FP64 */
 } rt_stats_t;
 
-/* Create a handle.  Copies cfg (and g_weights).  RT_EINVAL on a bad field,
- * RT_ECUDA if no device is usable.  The handle holds device workspace that
- * grows on demand and is freed by rt_destroy. */
+/* Create a handle for the problem statement of Sec. 2.2 (the layer model,
+ * two-stream closure and constants of rt_config: Sec. 2.2.1, Eq. 19, Table
+ * 3).  Copies cfg (and g_weights).  RT_EINVAL on a bad field, RT_ECUDA if no
+ * device is usable.  The handle holds device workspace that grows on demand
+ * and is freed by rt_destroy. */
 int rt_create(const rt_config *cfg, rt_handle **out);
 
-/* Device workspace (bytes) that a solve of cols needs, outputs included. */
+/* Device workspace (bytes) that a solve of cols needs, outputs included:
+ * the per-system elimination state of Eqs. 13-15 and the spectral sums of
+ * Sec. 2.2.6 for the batch.  Validates cols as rt_solve_columns does. */
 int rt_query_bytes(const rt_handle *h, const rt_columns *cols, size_t *bytes);
+
+/* Validate cfg and cols on the host alone -- no device, no handle: every
+ * check rt_solve_columns makes before it enqueues work (shapes, pointers,
+ * gather offsets against the element counts).  A descriptor with NULL
+ * dtau, w0 and g0 is checked as for rt_solve_ktable.  Writes a one-line
+ * reason into msg (msg_len bytes, may be NULL).  Returns RT_OK or
+ * RT_EINVAL. */
+int rt_check_columns(const rt_config *cfg, const rt_columns *cols, char *msg, size_t msg_len);
 
 /* Enqueue the whole path for cols on stream: Planck per bin, layer
  * coefficients (App. B), beam (Eq. B6), sources, Thomas elimination,
@@ -188,7 +225,9 @@ int rt_solve_columns(rt_handle *h, const rt_columns *cols, void *stream);
 
 /* Copy the last solve's interface fluxes, W m^-2, [sum_c (L_c+1)] each,
  * interface 0 = TOA, to F_up, F_down (diffuse + beam), F_net (= F_up -
- * F_down).  Pointers may be host or device memory, or NULL to skip.
+ * F_down): the Gauss-weighted sums over g-points and bins (Sec. 2.2.6), the
+ * beam added to the downward flux before the net flux is formed (Sec.
+ * 2.2.1).  Pointers may be host or device memory, or NULL to skip.
  * RT_ENOTSOLVED before a solve. */
 int rt_fluxes(rt_handle *h, double *F_up, double *F_down, double *F_net, void *stream);
 

@@ -18,6 +18,8 @@
 #include "rt.h"
 #include "rt_internal.h"
 
+static_assert(rt::kSweepMaxLayers == RT_SWEEP_MAX_LAYERS, "sweep layer limit differs between rt.h and the kernels");
+
 namespace {
 
 struct DevBuf {
@@ -97,6 +99,7 @@ struct Plan {
     int Lmax = 0, NBmax = 0;
     // launch
     int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, inline_b = 0, ns = 1;
+    bool sweeps = false;          // the iterative method (cfg.n_sweeps > 0) instead of Thomas
     size_t smem = 0;
     int64_t n_slots = 0;
     // workspace layout (bytes); the plan blob is int32 arrays then int64 arrays
@@ -104,10 +107,30 @@ struct Plan {
     bool kt = false;              // optics from the k-table front end
 };
 
-int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
+// Element counts of the input arrays: a column's block [off, off + span) of
+// an array must lie inside its count.  Gather offsets need the counts of
+// the arrays they index; in the packed layout a given count is checked too.
+int check_span(rt_handle *h, int col, const char *what, int64_t off, int64_t span, int64_t count, bool gathered) {
+    if (count < 0) return fail(h, RT_EINVAL, "%s: negative element count %lld", what, (long long)count);
+    if (count == 0) {
+        if (gathered) return fail(h, RT_EINVAL, "%s: gather offsets need the array's element count", what);
+        return RT_OK;
+    }
+    if (off > count || span > count - off)
+        return fail(h, RT_EINVAL, "column %d: %s elements [%lld, %lld) outside the array's %lld", col, what,
+                    (long long)off, (long long)(off + span), (long long)count);
+    return RT_OK;
+}
+
+// The host-side part of a plan: shapes, offsets (gather or packed), their
+// bounds, processing order and work units.  No device call.
+int validate_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
     const rt_config &cfg = h->cfg;
     const int n = c->n_cols;
     const bool fp64 = cfg.precision == RT_FP64_PLAIN;
+    P.sweeps = cfg.n_sweeps > 0;
+    if (P.sweeps && fp64) return fail(h, RT_EINVAL, "the iterative method (n_sweeps > 0) runs in the FP32 form only");
+    if (P.sweeps && kt) return fail(h, RT_EINVAL, "the iterative method (n_sweeps > 0) takes optics cubes, not the k-table");
     P.nl.resize(n);
     P.nb.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -119,11 +142,14 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
             return fail(h, RT_EINVAL, "column %d: n_bins %d outside [1, %d]", i, P.nb[i], cfg.max_bins);
         if (cfg.n_edges > 1 && P.nb[i] != cfg.n_edges - 1)
             return fail(h, RT_EINVAL, "column %d: n_bins %d but %d explicit bin edges", i, P.nb[i], cfg.n_edges);
-        if (kt && P.nb[i] != h->kt_NB)
+        if (kt && h->kt_NB >= 0 && P.nb[i] != h->kt_NB)
             return fail(h, RT_EINVAL, "column %d: n_bins %d but the k-table has %d", i, P.nb[i], h->kt_NB);
+        if (P.sweeps && P.nl[i] > rt::kSweepMaxLayers)
+            return fail(h, RT_EINVAL, "column %d: n_layers %d above %d, the iterative method's limit", i, P.nl[i],
+                        rt::kSweepMaxLayers);
     }
     P.kt = kt;
-    P.ns = fp64 ? 1 : (cfg.systems_per_lane == 1 ? 1 : 2);
+    P.ns = (fp64 || P.sweeps) ? 1 : (cfg.systems_per_lane == 1 ? 1 : 2);
     const int spu = 32 * P.ns;                    // systems per FP32 work unit
     const int64_t *gath[5] = {c->cube_offset, c->center_offset, c->iface_offset, c->bin_offset, c->col_index};
     for (int g = 0; g < 5; ++g)
@@ -161,6 +187,16 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
         P.Lmax = std::max(P.Lmax, (int)P.nl[i]);
         P.NBmax = std::max(P.NBmax, (int)P.nb[i]);
     }
+    for (int i = 0; i < n; ++i) {
+        const int64_t S = (int64_t)P.nb[i] * cfg.n_g;
+        int rc = RT_OK;
+        if (!kt) rc = check_span(h, i, "dtau/w0/g0", P.cube_off[i], (int64_t)P.nl[i] * S, c->n_cube, c->cube_offset);
+        if (!rc) rc = check_span(h, i, "T_center", P.tc_off[i], P.nl[i], c->n_center, c->center_offset);
+        if (!rc) rc = check_span(h, i, "T_iface/p_iface", P.if_off[i], P.nl[i] + 1, c->n_iface, c->iface_offset);
+        if (!rc) rc = check_span(h, i, "F_star", P.fs_off[i], P.nb[i], c->n_fstar, c->bin_offset);
+        if (!rc) rc = check_span(h, i, "mu_star", P.mu_idx[i], 1, c->n_mu, c->col_index);
+        if (rc) return rc;
+    }
     P.n_cube = cube;
     P.n_lay = lay;
     P.n_if = lay + n;
@@ -185,9 +221,43 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
         P.n_units = (int64_t)P.unit_col.size();
         if (P.n_units > INT32_MAX) return fail(h, RT_EINVAL, "too many work units");
     }
+    return RT_OK;
+}
+
+int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
+    int rc = validate_plan(h, c, P, kt);
+    if (rc) return rc;
+    const rt_config &cfg = h->cfg;
+    const int n = c->n_cols;
+    const bool fp64 = cfg.precision == RT_FP64_PLAIN;
+    const int spu = 32 * P.ns;
     // launch shape (the FP32 kernel is compiled for at most 256 threads)
     P.block = fp64 ? cfg.block_threads : std::min(cfg.block_threads, rt::kMaxBlock32);
-    if (n > 0) {
+    if (n > 0 && P.sweeps) {
+        // the sweep kernel: each warp needs ~8 KB of shared memory per 10
+        // layers, so take the CTA size that keeps the most warps resident
+        P.nbw = rt::bins_per_chunk(spu, cfg.n_g, P.NBmax);
+        P.direct = cfg.planck_staging == RT_STAGE_DIRECT || cfg.planck_staging == RT_STAGE_INLINE ||
+                   (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g < 4);
+        P.warp_floats = rt::sweep_warp_floats(P.Lmax, P.nbw, P.direct, cfg.layers == RT_ISOTHERMAL);
+        int best = 0;
+        for (int b = 32; b <= rt::kMaxBlock32; b += 32) {
+            const size_t sm = rt::sweep_smem_bytes(b, P.Lmax, P.nbw, P.direct, cfg.layers == RT_ISOTHERMAL);
+            const int occ = rt::occupancy(0, b, sm, 1, 1);
+            if (occ * b > best) {
+                best = occ * b;
+                P.block = b;
+                P.smem = sm;
+                P.grid = occ;
+            }
+        }
+        if (best == 0) return fail(h, RT_EINVAL, "no launch shape of the sweep kernel fits (L=%d)", P.Lmax);
+        int occ = P.grid;
+        if (cfg.ctas_per_sm > 0 && occ > cfg.ctas_per_sm) occ = cfg.ctas_per_sm;
+        const int64_t wpb = P.block / 32;
+        P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
+        P.n_slots = (int64_t)P.grid * P.block;
+    } else if (n > 0) {
         for (;;) {
             int occ;
             if (fp64) {
@@ -233,9 +303,9 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
     P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
     P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256) +
                   align_up(sizeof(double) * (size_t)P.n_bins, 256);
-    P.scr_bytes = (size_t)P.n_slots *
-                  (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
-                        : rt::fp32_scratch_per_slot(P.Lmax));
+    P.scr_bytes = P.sweeps ? 0
+                           : (size_t)P.n_slots * (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
+                                                       : rt::fp32_scratch_per_slot(P.Lmax));
     // inline B: the interfaces' B for the back-substitution, after the elimination scratch
     if (P.inline_b) P.scr_bytes = align_up(P.scr_bytes, 256) + sizeof(float) * (size_t)P.n_slots * P.Lmax;
     // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf [| kt_lay]
@@ -301,9 +371,12 @@ bool wants_kt(const rt_handle *h, const rt_columns *c) {
 
 extern "C" {
 
-int rt_create(const rt_config *cfg, rt_handle **out) {
-    if (!out) return RT_EINVAL;
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// The configuration fields rt_create accepts.
+int check_config(const rt_config *cfg) {
     if (!cfg) return RT_EINVAL;
     if (cfg->n_g < 1 || cfg->n_g > 64 || !cfg->g_weights) return RT_EINVAL;
     if (!(cfg->wn_max > cfg->wn_min) || !(cfg->wn_min >= 0.0)) return RT_EINVAL;
@@ -320,12 +393,25 @@ int rt_create(const rt_config *cfg, rt_handle **out) {
     if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_INLINE) return RT_EINVAL;
     if (cfg->systems_per_lane < 0 || cfg->systems_per_lane > 2) return RT_EINVAL;
     if (cfg->n_edges < 0 || cfg->n_edges == 1 || (cfg->n_edges > 1 && !cfg->wn_edges)) return RT_EINVAL;
+    if (cfg->n_sweeps < 0 || cfg->n_sweeps > (1 << 20)) return RT_EINVAL;
     for (int i = 0; i < cfg->n_edges; ++i) {
         if (!(cfg->wn_edges[i] >= 0.0)) return RT_EINVAL;
         if (i > 0 && !(cfg->wn_edges[i] > cfg->wn_edges[i - 1])) return RT_EINVAL;
     }
     for (int i = 0; i < cfg->n_g; ++i)
         if (!(cfg->g_weights[i] >= 0.0)) return RT_EINVAL;
+    return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rt_create(const rt_config *cfg, rt_handle **out) {
+    if (!out) return RT_EINVAL;
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc) return rc;
 
     rt_handle *h = new rt_handle();
     h->cfg = *cfg;
@@ -386,6 +472,26 @@ int rt_query_bytes(const rt_handle *hc, const rt_columns *cols, size_t *bytes) {
     if (rc) return rc;
     *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes + P.kcube_bytes;
     return RT_OK;
+}
+
+int rt_check_columns(const rt_config *cfg, const rt_columns *cols, char *msg, size_t msg_len) {
+    if (msg && msg_len) msg[0] = '\0';
+    int rc = check_config(cfg);
+    if (rc) {
+        if (msg && msg_len) snprintf(msg, msg_len, "invalid configuration");
+        return rc;
+    }
+    rt_handle tmp;                 // host state only: no device is touched
+    tmp.cfg = *cfg;
+    if (tmp.cfg.block_threads == 0) tmp.cfg.block_threads = cfg->precision == RT_FP64_PLAIN ? 256 : 128;
+    const bool kt = cols && !cols->dtau && !cols->w0 && !cols->g0;
+    tmp.kt_set = kt;               // a state-only descriptor is checked as for rt_solve_ktable
+    tmp.kt_NB = -1;                // (with no table, its bin count is not known)
+    rc = check_columns(&tmp, cols, kt);
+    Plan P;
+    if (!rc && cols->n_cols > 0) rc = validate_plan(&tmp, cols, P, kt);
+    if (rc && msg && msg_len) snprintf(msg, msg_len, "%s", tmp.err.c_str());
+    return rc;
 }
 
 }  // extern "C"
@@ -571,6 +677,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.e_clamp = cfg.e_clamp;
         kp.eps2 = cfg.eps2;
         kp.inv_eps2 = (float)(1.0 / cfg.eps2);
+        kp.n_sweeps = P.sweeps ? cfg.n_sweeps : 0;
         kp.grav = cfg.grav;
         kp.cp = cfg.cp;
         kp.T_int = cfg.T_int;
@@ -632,7 +739,8 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         const bool timing = cfg.kernel_timing && !cap;
         if (timing && cfg.precision == RT_FP64_PLAIN) cudaEventRecord(h->kev[1], s);
         e = cfg.precision == RT_FP64_PLAIN ? rt::launch_fp64(kp, P.grid, P.block, P.smem, s)
-                                           : rt::launch_fp32(kp, P.grid, P.block, P.smem, s, timing ? h->kev : nullptr);
+            : P.sweeps ? rt::launch_sweeps(kp, P.grid, P.block, P.smem, s, timing ? h->kev : nullptr)
+                       : rt::launch_fp32(kp, P.grid, P.block, P.smem, s, timing ? h->kev : nullptr);
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
         if (timing && cfg.precision == RT_FP64_PLAIN) cudaEventRecord(h->kev[2], s);
         h->kev_valid = timing;

@@ -78,6 +78,7 @@ struct KParams {
     int32_t kt_nT, kt_nP;
     float4 *kt_lay;              // [sum L] per layer: (corner offset bits, wT, wP, dp / g)
     float inv_eps2;
+    int32_t n_sweeps;            // 0: Thomas elimination; N > 0: N sweeps of the iterative method
     int32_t Lmax;                // largest L in this batch
     int32_t nb_chunk;            // bins covered by one chunk of systems (smem sizing)
 };
@@ -95,13 +96,17 @@ int bins_per_chunk(int block, int n_g, int max_bins);
 // One-time per-device set-up (dynamic shared-memory limits).
 cudaError_t init_kernels();
 // Resident CTAs per SM for a launch shape (0 if it does not fit).
-int occupancy(int precision_fp64, int block, size_t smem, int ns = 1);
+int occupancy(int precision_fp64, int block, size_t smem, int ns = 1, int sweeps = 0);
 // Launch the fused column kernels.  Return cudaGetLastError().
 // ev (optional): three events recorded before the pre-kernel, between the
 // two kernels and after the solve kernel.
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
                         cudaEvent_t const *ev = nullptr);
 cudaError_t launch_fp64(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s);
+// The iterative method (kp.n_sweeps > 0): the Planck pre-kernel, then the
+// sweep kernel; ev as for launch_fp32.
+cudaError_t launch_sweeps(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
+                          cudaEvent_t const *ev = nullptr);
 // Front end alone: FP32 optics of every (column, layer, bin, g) into packed
 // cubes (cube offsets of the packed layout in pcube_off).
 cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float *dtau, float *w0,
@@ -109,6 +114,12 @@ cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float 
 
 // Largest L the kernels support.
 constexpr int kMaxLayers = 1024;
+// Largest L of the iterative method's kernel (each lane holds its system's
+// per-layer t, r and the level fluxes in registers).
+constexpr int kSweepMaxLayers = 48;
+// Shared memory of the iterative method's kernel: floats per warp, bytes per CTA.
+int sweep_warp_floats(int Lmax, int nbw, int direct, int isothermal);
+size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal);
 // Largest CTA size (launch bounds): FP64 kernel, FP32 kernel.
 constexpr int kMaxBlock = 512;
 constexpr int kMaxBlock32 = 256;

@@ -378,14 +378,24 @@ struct Layer32 {
     V T, R, Su, Sd, omtr, opr, mlay;
 };
 
+// One sub-layer's transmission t and reflection r (both sub-layers of a
+// non-isothermal layer have the same), 1 - t - r, the sources of the upper
+// (top -> centre) and lower (centre -> bottom) sub-layers in departure
+// variables, beam included, and the beam's attenuation m across one
+// sub-layer.  Isothermal layers use the upper fields only.
+template <class V>
+struct Sub32 {
+    V t, r, omtr, suU, sdU, suL, sdL, m;
+};
+
 // Products are grouped by hand: float multiplication is not reassociated by
 // the compiler, and shared factors (1/h and 1/p from one reciprocal of h p,
 // 2q, w0 g0, ...) are formed once per layer.  Multiply-adds are written as
 // vfma so that the scalar and the paired forms round alike.
 template <bool ISO, class V>
-__device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb, float mu, float imu,
-                                              double mu_d, bool beam, V Fb, const KParams &kp, Counters &cn,
-                                              SysCounts<V> &sc, typename VTraits<V>::M on) {
+__device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, float mu, float imu,
+                                          double mu_d, bool beam, V Fb, const KParams &kp, Counters &cn,
+                                          SysCounts<V> &sc, typename VTraits<V>::M on) {
     using M = typename VTraits<V>::M;
     const M valid = (dt >= V(0.f)) & (w0 >= V(0.f)) & (w0 <= V(1.f)) & (vabs(g0) < V(1.f));
     vcount(sc.inv, !valid);
@@ -497,15 +507,37 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
         }
     }
 
+    Sub32<V> o;
+    o.t = t;
+    o.r = r;
+    o.omtr = omtr;
+    o.suU = suU;
+    o.sdU = sdU;
+    o.suL = suL;
+    o.sdL = sdL;
+    o.m = m;
+    return o;
+}
+
+// The layer as one unit for the Thomas elimination: a non-isothermal
+// layer's two sub-layers merged (adding their transmissions, reflections
+// and sources).
+template <bool ISO, class V>
+__device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb, float mu, float imu,
+                                              double mu_d, bool beam, V Fb, const KParams &kp, Counters &cn,
+                                              SysCounts<V> &sc, typename VTraits<V>::M on) {
+    const Sub32<V> s = sub32<ISO, V>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
+    const V t = s.t, r = s.r, omtr = s.omtr;
+    const V omr = omtr + t;                       // 1 - r
     Layer32<V> o;
     if (ISO) {
         o.T = t;
         o.R = r;
-        o.Su = suU;
-        o.Sd = sdU;
+        o.Su = s.suU;
+        o.Sd = s.sdU;
         o.omtr = omtr;
         o.opr = vfma(V(2.f), t, omtr);
-        o.mlay = m;
+        o.mlay = s.m;
     } else {
         // merge upper (top -> centre) and lower (centre -> bottom) sub-layers
         const V opr1 = V(1.f) + r;
@@ -513,11 +545,11 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
         const V tD = t * Dr;
         o.T = t * tD;
         o.R = vfma(r, o.T, r);
-        o.Su = vfma(tD, vfma(r, sdU, suL), suU);
-        o.Sd = vfma(tD, vfma(r, suL, sdU), sdL);
+        o.Su = vfma(tD, vfma(r, s.sdU, s.suL), s.suU);
+        o.Sd = vfma(tD, vfma(r, s.suL, s.sdU), s.sdL);
         o.omtr = (omtr * vfma(V(2.f), t, omtr)) * (opr1 * Dr);   // (1-r-t)(1-r+t)/(1-r)
         o.opr = vfma(omr, o.T, omr);
-        o.mlay = m * m;
+        o.mlay = s.m * s.m;
     }
     return o;
 }
@@ -1529,6 +1561,294 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
 }
 
 // ---------------------------------------------------------------------
+// The iterative method (Sec. 2.2.2) in the FP32 form: the pairwise two-stream
+// relations of every sub-layer applied through the column, repeated N times,
+// instead of the elimination.  One sweep is a downward pass from the TOA
+// condition (each sub-layer gives d at its bottom from d at its top and the
+// previous sweep's u at its bottom), the BOA condition (Eq. 10) and an upward
+// pass (each sub-layer gives u at its top from u at its bottom and d at its
+// top); the sweeps start from zero diffuse flux.  In departure variables
+// (u = F_up - pi B, d = F_dn - pi B at each level, as in the elimination)
+// the relations of a sub-layer with transmission t, reflection r and sources
+// su, sd read
+//   u_top = t u_bot + r d_top + su,   d_bot = t d_top + r u_bot + sd.
+//
+// Layout.  A warp takes work units of 32 systems of a column (one per lane).
+// The coefficient pass streams the cubes once and leaves, per layer, (t, r)
+// and the sub-layer sources in the warp's shared memory, and the warp sums of
+// w F_beam at the interfaces; the lane then moves its t, r into registers
+// next to its level state (u or d at each of the 2L+1 levels), so that a
+// sweep reads only the sources from shared memory: 8 bytes per layer and
+// pass for four FMAs.  Register arrays need compile-time indices, so the
+// passes are unrolled to kSweepMaxLayers layers and stop at the column's L.
+// The last upward pass writes the interface fluxes into the (no longer
+// needed) (t, r) area, swizzled for a conflict-free transposed sum.
+// ---------------------------------------------------------------------
+// (t, r) per layer, then the output rows [2 (Lmax + 1)][32] (XOR-swizzled)
+__host__ __device__ inline int sweep_region_floats(int Lmax) { return 64 * (Lmax + 1); }
+
+// Output row element (row, j) of the swizzled rows: lane j's writes to one
+// row and the lanes' reads of one column each of their own row hit 32
+// different banks.
+__device__ __forceinline__ int out_idx(int row, int j) { return row * 32 + (j ^ (row & 31)); }
+
+int sweep_warp_floats(int Lmax, int nbw, int direct, int isothermal) {
+    const int per = isothermal ? 32 : 64;          // sources per layer and pass (one or two sub-layers)
+    int n = ((direct ? 0 : (2 * Lmax + 1) * nbw) + 3) & ~3;
+    n += (2 * nbw + 3) & ~3;                        // F*, F_BOA
+    n += (Lmax + 1 + 3) & ~3;                       // warp sums of w F_beam per interface
+    n += 2 * per * Lmax;                            // SU, SD
+    n += sweep_region_floats(Lmax);                 // (t, r), then the output rows
+    return n;
+}
+size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal) {
+    return sizeof(float) * (size_t)(block / 32) * sweep_warp_floats(Lmax, nbw, direct, isothermal);
+}
+
+// One upward pass over the lane's system.  X holds d at the levels (u at the
+// BOA); on return it holds u.  EMIT (last sweep): u and u - d at interface
+// i < L go to rows 2i and 2i + 1 of OUT (element of lane j: out_idx).
+// The loop body is kept small, and X is indexed only by the unrolled loop
+// counter (a store at the runtime BOA index would send X to local memory),
+// so that X stays in registers.
+template <bool ISO, bool EMIT, int LR, int NLV>
+__device__ __forceinline__ void sweep_up(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int L, int lane,
+                                         float d0, const float *SU, float *OUT) {
+#pragma unroll
+    for (int k = 0; k < LR; ++k) {
+        const int l = LR - 1 - k;
+        if (l < L) {
+            if constexpr (ISO) {
+                const float dl = l == 0 ? d0 : X[l];
+                X[l] = fmaf(t[l], X[l + 1], fmaf(r[l], dl, SU[l * 32 + lane]));
+                if (EMIT) {
+                    OUT[out_idx(2 * l, lane)] = X[l];
+                    OUT[out_idx(2 * l + 1, lane)] = X[l] - dl;
+                }
+            } else {
+                const float2 su = reinterpret_cast<const float2 *>(SU)[l * 32 + lane];   // (upper, lower)
+                X[2 * l + 1] = fmaf(t[l], X[2 * l + 2], fmaf(r[l], X[2 * l + 1], su.y));
+                const float dl = l == 0 ? d0 : X[2 * l];
+                X[2 * l] = fmaf(t[l], X[2 * l + 1], fmaf(r[l], dl, su.x));
+                if (EMIT) {
+                    OUT[out_idx(2 * l, lane)] = X[2 * l];
+                    OUT[out_idx(2 * l + 1, lane)] = X[2 * l] - dl;
+                }
+            }
+        }
+    }
+}
+
+template <bool ISO, bool DIRECT>
+__device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
+                                           float *fbs, float *SU, float *SD, float *TR, Counters &cn) {
+    constexpr int LR = kSweepMaxLayers;
+    constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
+    const int NG = kp.n_g;
+    const int c = kp.unit_col[unit];
+    const int ku = kp.unit_k[unit];
+    const int L = kp.n_layers[c], NB = kp.n_bins[c];
+    const int S = NB * NG;
+    const long long cube0 = kp.cube_off[c];
+    const float4 cf = kp.colf[c];
+    const float mu = cf.x, imu = cf.y;
+    const double mu_d = kp.mu_star[kp.mu_idx[c]];
+    const bool beam = cf.z != 0.f;
+    const int s0 = ku * 32;
+    const int b_lo = s0 / NG;
+    const int nbc = min(NB - 1, (s0 + 31) / NG) - b_lo + 1;
+
+    // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
+    {
+        const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
+        const int nlev = 2 * L + 1;
+        if constexpr (!DIRECT) {
+            for (int i = lane; i < nlev * nbc; i += 32) {
+                const int lev = i / nbc, bb = i - lev * nbc;
+                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+            }
+        }
+        for (int j = lane; j < nbc; j += 32) {
+            sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
+            sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
+        }
+    }
+    __syncwarp();
+
+    // padding lanes of a column's last unit repeat system s0 with zero weight
+    const bool on = s0 + lane < S;
+    const int sI = on ? s0 + lane : s0;
+    const int bI = sI / NG;
+    const float wg = on ? kp.g_w32[sI - bI * NG] : 0.f;
+    const int bst = DIRECT ? NB : nbc;
+    const float *Bp = DIRECT ? kp.planck32 + kp.planck_off[c] + bI : sB + (bI - b_lo);
+    float Fb = beam ? mu * sFs[bI - b_lo] : 0.f;
+    const float FBOA = sFB[bI - b_lo];
+    SysCounts<float> sc;
+    sc.inv = sc.ecl = sc.etau = 0u;
+
+    // coefficient pass, TOA -> BOA (cubes streamed once, next layer prefetched)
+    float2 *TR2 = reinterpret_cast<float2 *>(TR);
+    const float *pd = kp.dtau + cube0 + sI, *pw = kp.w0 + cube0 + sI, *pg = kp.g0 + cube0 + sI;
+    float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);
+    float Bt = ldB<DIRECT>(Bp);
+    const float d0 = fmaf(-kPiF, Bt, (float)kp.F_toa);   // d at the TOA level
+    for (int l = 0; l < L; ++l) {
+        const float dt = nd, w0 = nw, g0 = ng;
+        if (l + 1 < L) {
+            pd += S;
+            pw += S;
+            pg += S;
+            nd = __ldcs(pd);
+            nw = __ldcs(pw);
+            ng = __ldcs(pg);
+        }
+        const float Bc = ldB<DIRECT>(Bp + (2 * l + 1) * bst), Bb = ldB<DIRECT>(Bp + (2 * l + 2) * bst);
+        float fw = wg * Fb;                                    // interface l: warp sum of w F_beam
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
+        if (lane == 0) fbs[l] = fw;
+        const Sub32<float> sb = sub32<ISO, float>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
+        TR2[l * 32 + lane] = make_float2(sb.t, sb.r);
+        if constexpr (ISO) {
+            SU[l * 32 + lane] = sb.suU;
+            SD[l * 32 + lane] = sb.sdU;
+            Fb *= sb.m;
+        } else {
+            reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(sb.suU, sb.suL);
+            reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(sb.sdU, sb.sdL);
+            Fb *= sb.m * sb.m;
+        }
+        Bt = Bb;
+    }
+    {
+        float fw = wg * Fb;                                    // the BOA interface
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
+        if (lane == 0) fbs[L] = fw;
+    }
+    cn.inv += vmasked(sc.inv, on);
+    cn.eclamp += vmasked(sc.ecl, on);
+    cn.etau += (ISO ? 1u : 2u) * vmasked(sc.etau, on);
+    const float ubc = FBOA + Fb;                               // u - d at the BOA (Eq. 10)
+    __syncwarp();
+
+    // registers: t, r per layer, the state at the levels (zero flux: u = -pi B)
+    float t[LR], r[LR], X[NLV];
+#pragma unroll
+    for (int l = 0; l < LR; ++l) {
+        float2 v = make_float2(0.f, 0.f);
+        if (l < L) v = TR2[l * 32 + lane];
+        t[l] = v.x;
+        r[l] = v.y;
+    }
+#pragma unroll
+    for (int j = 0; j < NLV; ++j) {
+        const int lev = ISO ? 2 * j : j;                       // level in the B table
+        X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldB<DIRECT>(Bp + min(lev, 2 * L) * bst) : 0.f;
+    }
+    __syncwarp();                                              // (t, r) area free for the output rows
+
+    float dB = 0.f;
+    for (int it = 0; it < kp.n_sweeps; ++it) {
+        // downward pass: X takes d at every level below the TOA, then u at the BOA
+        float d = d0;
+#pragma unroll
+        for (int l = 0; l < LR; ++l) {
+            if (l < L) {
+                if constexpr (ISO) {
+                    d = fmaf(t[l], d, fmaf(r[l], X[l + 1], SD[l * 32 + lane]));
+                    X[l + 1] = l == L - 1 ? d + ubc : d;
+                } else {
+                    const float2 sd = reinterpret_cast<const float2 *>(SD)[l * 32 + lane];   // (upper, lower)
+                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 1], sd.x));
+                    X[2 * l + 1] = d;
+                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 2], sd.y));
+                    X[2 * l + 2] = l == L - 1 ? d + ubc : d;
+                }
+            }
+        }
+        dB = d;
+        if (it + 1 < kp.n_sweeps)
+            sweep_up<ISO, false>(X, t, r, L, lane, d0, SU, TR);
+        else
+            sweep_up<ISO, true>(X, t, r, L, lane, d0, SU, TR);
+    }
+    {
+        // the BOA interface: u = d + (F_BOA + F_beam), as the downward pass set it
+        const float uB = dB + ubc;
+        TR[out_idx(2 * L, lane)] = uB;
+        TR[out_idx(2 * L + 1, lane)] = uB - dB;
+    }
+    if (on && !(isfinite(X[0]) && isfinite(dB))) cn.nonfinite++;
+    // weighted fluxes: F_up = pi B + u; F_net + F_beam = u - d
+    for (int i = 0; i <= L; ++i) {
+        const float Bi = ldB<DIRECT>(Bp + 2 * i * bst);
+        TR[out_idx(2 * i, lane)] = wg * fmaf(kPiF, Bi, TR[out_idx(2 * i, lane)]);
+        TR[out_idx(2 * i + 1, lane)] *= wg;
+    }
+    __syncwarp();
+
+    // interface sums: row 2i = sum w F_up, row 2i + 1 = sum w (u - d) - sum w F_beam
+    float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
+    for (int row = lane; row < 2 * (L + 1); row += 32) {
+        float acc = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) acc += TR[out_idx(row, j)];
+        if (row & 1) acc -= fbs[row >> 1];
+        part[row] = acc;
+    }
+    // TOA spectrum: row 0 holds w F_up at the TOA per system
+    if (kp.toa) {
+        for (int jb = lane; jb < nbc; jb += 32) {
+            const int bt = b_lo + jb;
+            const int j0 = max(0, bt * NG - s0);
+            const int j1 = min(min(32, S - s0), (bt + 1) * NG - s0);
+            float acc = 0.f;
+            for (int j = j0; j < j1; ++j) acc += TR[out_idx(0, j)];
+            atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
+        }
+    }
+    __syncwarp();
+
+    // the warp that completes a column's last unit writes the column
+    __threadfence();
+    int done = 0;
+    if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == kp.col_units[c] - 1) {
+        __threadfence();
+        finalize_column(kp, c, lane);
+    }
+    __syncwarp();
+}
+
+template <bool ISO, bool DIRECT>
+__global__ void __launch_bounds__(kMaxBlock32, 1) fp32_sweeps(KParams kp) {
+    extern __shared__ __align__(16) float smem32[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *wsm = smem32 + (size_t)warp * kp.warp_floats;
+    const int Lm = kp.Lmax, nbw = kp.nbw;
+    float *sB = wsm;
+    float *sFs = sB + (((DIRECT ? 0 : (2 * Lm + 1) * nbw) + 3) & ~3);
+    float *sFB = sFs + nbw;
+    float *fbs = sFs + ((2 * nbw + 3) & ~3);
+    float *SU = fbs + ((Lm + 1 + 3) & ~3);
+    float *SD = SU + (ISO ? 32 : 64) * Lm;
+    float *TR = SD + (ISO ? 32 : 64) * Lm;
+    Counters cn = {0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(kp.counter, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= kp.n_units) break;
+        sweep_unit<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR, cn);
+    }
+    flush_counters(cn, kp.stats);
+}
+
+// ---------------------------------------------------------------------
 // FP64 plain path: the paper's formulas as written (App. B), scalar
 // elimination over every level.
 // ---------------------------------------------------------------------
@@ -1794,13 +2114,21 @@ cudaError_t init_kernels() {
         if (e != cudaSuccess) return e;
     }
     if (e != cudaSuccess) return e;
+    for (auto f : {fp32_sweeps<false, false>, fp32_sweeps<true, false>, fp32_sweeps<false, true>,
+                   fp32_sweeps<true, true>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(fp64_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 
-int occupancy(int precision_fp64, int block, size_t smem, int ns) {
+int occupancy(int precision_fp64, int block, size_t smem, int ns, int sweeps) {
     if (smem > (size_t)kMaxDynSmem) return 0;
     int n = 0;
-    cudaError_t e = precision_fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
+    cudaError_t e = sweeps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_sweeps<false, false>, block, smem)
+                    : precision_fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
                     : ns == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 2>,
                                                                             block, smem)
                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 1>,
@@ -1836,6 +2164,26 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     const int st = kp.inline_b ? kStageInline : (kp.direct ? kStageDirect : kStageShared);
     const int sel = (kp.isothermal ? 1 : 0) + 2 * st + (kp.kt_lk ? 6 : 0) + (kp.ns == 2 ? 12 : 0);
     kUnitsLaunch[sel](kp, grid, block, smem, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    return e;
+}
+
+cudaError_t launch_sweeps(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
+                          cudaEvent_t const *ev) {
+    const int pgrid = kp.n_cols < 8 * 148 ? kp.n_cols : 8 * 148;
+    if (ev) cudaEventRecord(ev[0], s);
+    fp32_prep<<<pgrid, 128, sizeof(float) * (2 * kp.Lmax + 2), s>>>(kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    if (kp.isothermal) {
+        if (kp.direct) fp32_sweeps<true, true><<<grid, block, smem, s>>>(kp);
+        else fp32_sweeps<true, false><<<grid, block, smem, s>>>(kp);
+    } else {
+        if (kp.direct) fp32_sweeps<false, true><<<grid, block, smem, s>>>(kp);
+        else fp32_sweeps<false, false><<<grid, block, smem, s>>>(kp);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;

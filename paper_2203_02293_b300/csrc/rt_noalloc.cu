@@ -99,6 +99,9 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     if (cfg->precision != RT_FP32_FORM) return RT_EINVAL;
     if (cfg->n_edges != 0) return RT_EINVAL;                   // uniform bins only
     if (cfg->n_g < 1 || cfg->n_g > kMaxG || !cfg->g_weights) return RT_EINVAL;
+    for (int i = 0; i < cfg->n_g; ++i)
+        if (!(cfg->g_weights[i] >= 0.0)) return RT_EINVAL;     // as rt_create: no negative or NaN weight
+    if (cfg->n_sweeps != 0) return RT_EINVAL;                  // Thomas's algorithm only
     if (!(cfg->wn_max > cfg->wn_min) || !(cfg->wn_min >= 0.0) || !(cfg->eps2 > 0.0) || !(cfg->cp > 0.0) ||
         !(cfg->T_int >= 0.0))
         return RT_EINVAL;

@@ -22,6 +22,7 @@ RT_NONISOTHERMAL, RT_ISOTHERMAL = 0, 1
 RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
 RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
 RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT, RT_STAGE_INLINE = 0, 1, 2, 3
+RT_SWEEP_MAX_LAYERS = 48
 
 _STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
            -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}
@@ -41,6 +42,7 @@ class rt_config(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32), ("planck_staging", ctypes.c_int32),
         ("systems_per_lane", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
         ("n_edges", ctypes.c_int32), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
+        ("n_sweeps", ctypes.c_int32),
     ]
 
 
@@ -55,6 +57,8 @@ class rt_columns(ctypes.Structure):
         ("cube_offset", ctypes.POINTER(ctypes.c_int64)), ("center_offset", ctypes.POINTER(ctypes.c_int64)),
         ("iface_offset", ctypes.POINTER(ctypes.c_int64)), ("bin_offset", ctypes.POINTER(ctypes.c_int64)),
         ("col_index", ctypes.POINTER(ctypes.c_int64)),
+        ("n_cube", ctypes.c_int64), ("n_center", ctypes.c_int64), ("n_iface", ctypes.c_int64),
+        ("n_fstar", ctypes.c_int64), ("n_mu", ctypes.c_int64),
     ]
 
 
@@ -86,6 +90,8 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     H = ctypes.c_void_p
     lib.rt_create.argtypes = [ctypes.POINTER(rt_config), ctypes.POINTER(H)]
     lib.rt_query_bytes.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.POINTER(ctypes.c_size_t)]
+    lib.rt_check_columns.argtypes = [ctypes.POINTER(rt_config), ctypes.POINTER(rt_columns), ctypes.c_char_p,
+                                     ctypes.c_size_t]
     lib.rt_solve_columns.argtypes = [H, ctypes.POINTER(rt_columns), ctypes.c_void_p]
     lib.rt_fluxes.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_heating.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
@@ -106,7 +112,7 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.rt_solve_uniform_noalloc.restype = ctypes.c_int
     for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
               "rt_toa_spectrum", "rt_stats", "rt_set_ktable", "rt_ktable_optics", "rt_solve_ktable",
-              "rt_kernel_times"):
+              "rt_kernel_times", "rt_check_columns"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -175,6 +181,7 @@ class Config:
     systems_per_lane: int = 0            # FP32 form: 1 or 2 (0 = 2)
     kernel_timing: int = 0               # 1: CUDA events around each kernel (rt_kernel_times)
     wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins
+    n_sweeps: int = 0                    # 0: Thomas; N > 0: N sweeps of the iterative method
 
 
 def _config(cfg: Config):
@@ -188,7 +195,7 @@ def _config(cfg: Config):
                   cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
                   cfg.ctas_per_sm, cfg.planck_staging, cfg.systems_per_lane, cfg.kernel_timing,
                   0 if ed is None else ed.size,
-                  None if ed is None else ed.ctypes.data_as(PD))
+                  None if ed is None else ed.ctypes.data_as(PD), cfg.n_sweeps)
     return c, (gw, ed)
 
 
@@ -200,13 +207,23 @@ def rt_create(cfg: Config):
     return h
 
 
+def _count(t) -> int:
+    """Element count of a tensor / array (0 for None)."""
+    if t is None:
+        return 0
+    return int(t.numel()) if hasattr(t, "numel") else int(np.asarray(t).size)
+
+
 def make_columns(n_cols: int, n_layers, n_bins, dtau, w0, g0, T_center, T_iface, p_iface,
-                 mu_star, F_star, L: int = 0, NB: int = 0, gather: dict | None = None):
+                 mu_star, F_star, L: int = 0, NB: int = 0, gather: dict | None = None,
+                 counts: dict | None = None):
     """Build an rt_columns descriptor.  n_layers / n_bins are host int32 arrays
     (or None with uniform L, NB); the rest are device tensors.  ``gather`` may
     give host int64 arrays cube_offset, center_offset, iface_offset,
-    bin_offset, col_index (see include/rt.h).  The returned object keeps the
-    host arrays alive."""
+    bin_offset, col_index (see include/rt.h).  The arrays' element counts,
+    which bound every read, are taken from the tensors unless ``counts``
+    overrides them (keys n_cube, n_center, n_iface, n_fstar, n_mu).  The
+    returned object keeps the host arrays alive."""
     nl = None if n_layers is None else np.ascontiguousarray(n_layers, dtype=np.int32)
     nb = None if n_bins is None else np.ascontiguousarray(n_bins, dtype=np.int32)
     P32 = ctypes.POINTER(ctypes.c_int32)
@@ -219,8 +236,24 @@ def make_columns(n_cols: int, n_layers, n_bins, dtau, w0, g0, T_center, T_iface,
                    _ptr(dtau), _ptr(w0), _ptr(g0), _ptr(T_center), _ptr(T_iface), _ptr(p_iface),
                    _ptr(mu_star), _ptr(F_star), gp["cube_offset"], gp["center_offset"],
                    gp["iface_offset"], gp["bin_offset"], gp["col_index"])
+    n = dict(n_cube=min(_count(dtau), _count(w0), _count(g0)), n_center=_count(T_center),
+             n_iface=min(_count(T_iface), _count(p_iface)), n_fstar=_count(F_star), n_mu=_count(mu_star))
+    n.update(counts or {})
+    for k, v in n.items():
+        setattr(c, k, int(v))
     c._keep = (nl, nb, g)
     return c
+
+
+def rt_check_columns(cfg: Config, cols) -> str:
+    """Host-only validation of ``cols`` for ``cfg`` (no device needed);
+    raises RTError with the library's reason, returns "" when valid."""
+    c, keep = _config(cfg)
+    buf = ctypes.create_string_buffer(512)
+    code = lib().rt_check_columns(ctypes.byref(c), ctypes.byref(cols), buf, len(buf))
+    if code != RT_OK:
+        raise RTError(code, buf.value.decode())
+    return ""
 
 
 def rt_query_bytes(h, cols) -> int:

@@ -104,3 +104,90 @@ def test_missing_library_raises(tmp_path):
     from paper_2203_02293_b300 import rt
     with pytest.raises(RuntimeError):
         rt._load(str(tmp_path / "nope.so"))
+
+
+# ----------------------------------------------------------------------
+# Host-only validation (rt_check_columns): gather offsets against the
+# arrays' element counts.  No device call is made and no array is read.
+# ----------------------------------------------------------------------
+
+def _pool(rt):
+    import numpy as np
+    L = np.array([5, 3, 7], np.int32)
+    NB = np.array([4, 6, 2], np.int32)
+    ng = 3
+    n_cube = int((L * NB).sum()) * ng
+    arrs = dict(dtau=np.zeros(n_cube, np.float32), w0=np.zeros(n_cube, np.float32),
+                g0=np.zeros(n_cube, np.float32), T_center=np.zeros(int(L.sum())),
+                T_iface=np.zeros(int((L + 1).sum())), p_iface=np.zeros(int((L + 1).sum())),
+                mu_star=np.zeros(3), F_star=np.zeros(int(NB.sum())))
+    z = lambda a: np.concatenate([[0], np.cumsum(a)])[:-1].astype(np.int64)
+    off = dict(cube_offset=z(L * NB * ng), center_offset=z(L), iface_offset=z(L + 1), bin_offset=z(NB),
+               col_index=np.arange(3, dtype=np.int64))
+    cfg = rt.Config(g_weights=np.full(ng, 1.0 / ng))
+    return L, NB, arrs, off, cfg
+
+
+def _desc(rt, L, NB, arrs, gather=None, counts=None):
+    a = arrs
+    return rt.make_columns(len(L), L, NB, a["dtau"], a["w0"], a["g0"], a["T_center"], a["T_iface"],
+                           a["p_iface"], a["mu_star"], a["F_star"], gather=gather, counts=counts)
+
+
+def test_check_columns_accepts_packed_and_gathered(librt):
+    rt = librt
+    L, NB, arrs, off, cfg = _pool(rt)
+    assert rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs)) == ""
+    # gathered: the columns in reverse order, each block ending exactly at its column's end
+    rev = {k: v[::-1].copy() for k, v in off.items()}
+    assert rt.rt_check_columns(cfg, _desc(rt, L[::-1].copy(), NB[::-1].copy(), arrs, gather=rev)) == ""
+
+
+@pytest.mark.parametrize("key,count_key,what", [
+    ("cube_offset", "n_cube", "dtau/w0/g0"), ("center_offset", "n_center", "T_center"),
+    ("iface_offset", "n_iface", "T_iface/p_iface"), ("bin_offset", "n_fstar", "F_star"),
+    ("col_index", "n_mu", "mu_star")])
+def test_check_columns_refuses_offset_past_the_end(librt, key, count_key, what):
+    rt = librt
+    L, NB, arrs, off, cfg = _pool(rt)
+    bad = {k: v.copy() for k, v in off.items()}
+    bad[key][2] += 1                      # the last column's block now ends one element past the array
+    with pytest.raises(rt.RTError) as ei:
+        rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs, gather=bad))
+    assert ei.value.code == rt.RT_EINVAL and what in str(ei.value)
+    # a gather offset array without its count is refused too
+    with pytest.raises(rt.RTError) as ei:
+        rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs, gather={key: off[key]}, counts={count_key: 0}))
+    assert ei.value.code == rt.RT_EINVAL and "element count" in str(ei.value)
+
+
+def test_check_columns_packed_count_too_small_and_negative(librt):
+    rt = librt
+    L, NB, arrs, off, cfg = _pool(rt)
+    n = int((L * NB).sum()) * 3
+    with pytest.raises(rt.RTError):
+        rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs, counts={"n_cube": n - 1}))
+    with pytest.raises(rt.RTError):
+        rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs, counts={"n_mu": -1}))
+    # huge offsets do not wrap around
+    bad = {k: v.copy() for k, v in off.items()}
+    bad["cube_offset"][0] = 2 ** 62
+    with pytest.raises(rt.RTError):
+        rt.rt_check_columns(cfg, _desc(rt, L, NB, arrs, gather=bad))
+
+
+def test_check_columns_refuses_bad_config_and_sweep_limits(librt):
+    import numpy as np
+    rt = librt
+    L, NB, arrs, off, cfg = _pool(rt)
+    from dataclasses import replace
+    with pytest.raises(rt.RTError):
+        rt.rt_check_columns(replace(cfg, n_sweeps=-1), _desc(rt, L, NB, arrs))
+    assert rt.rt_check_columns(replace(cfg, n_sweeps=10), _desc(rt, L, NB, arrs)) == ""
+    tall = np.array([rt.RT_SWEEP_MAX_LAYERS + 1], np.int32)
+    big = {k: np.zeros(10000, v.dtype) for k, v in arrs.items()}
+    with pytest.raises(rt.RTError) as ei:
+        rt.rt_check_columns(replace(cfg, n_sweeps=10), _desc(rt, tall, np.array([2], np.int32), big))
+    assert "iterative" in str(ei.value)
+    with pytest.raises(rt.RTError):
+        rt.rt_check_columns(replace(cfg, n_sweeps=10, precision=rt.RT_FP64_PLAIN), _desc(rt, L, NB, arrs))

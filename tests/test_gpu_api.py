@@ -167,6 +167,42 @@ def test_negative_gather_offset_is_rejected():
     s.close()
 
 
+@pytest.mark.parametrize("key", ["cube_offset", "center_offset", "iface_offset", "bin_offset", "col_index"])
+def test_gather_offset_past_the_end_is_refused_before_launch(key):
+    """An offset that puts a column's block one element past its array's end
+    returns RT_EINVAL and enqueues nothing: the handle keeps the previous
+    solve's results, bit for bit."""
+    pool = rt_synth.generate([6, 9, 4], [5, 3, 7], 4, seed=67, optics="uniform")
+    pb = DeviceBatch(pool)
+    o = pool.offsets()
+    idx = np.array([2, 0, 1])
+    good = dict(cube_offset=o["cube"][idx], center_offset=o["lay"][idx], iface_offset=o["iface"][idx],
+                bin_offset=o["bins"][idx], col_index=idx)
+    mk = lambda g: rt.make_columns(len(idx), pool.n_layers[idx], pool.n_bins[idx], pb.dtau, pb.w0, pb.g0,
+                                   pb.T_center, pb.T_iface, pb.p_iface, pb.mu_star, pb.F_star, gather=g)
+    sub = pool.subset(idx)
+    n_if = int((sub.n_layers + 1).sum())
+    for precision in (rt.RT_FP32_FORM, rt.RT_FP64_PLAIN):
+        s = Solver(pool.g_weights, precision=precision)
+        rt.rt_solve_columns(s.h, mk(good))
+        before = torch.empty(n_if, dtype=torch.float64, device="cuda")
+        rt.rt_fluxes(s.h, None, None, before)
+        bad = {k: v.copy() for k, v in good.items()}
+        # the last column of the pool (batch entry 0) ends exactly at each array's end
+        bad[key][0] += 1
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_solve_columns(s.h, mk(bad))
+        assert e.value.code == rt.RT_EINVAL
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_query_bytes(s.h, mk(bad))
+        assert e.value.code == rt.RT_EINVAL
+        after = torch.empty(n_if, dtype=torch.float64, device="cuda")
+        rt.rt_fluxes(s.h, None, None, after)
+        torch.cuda.synchronize()
+        assert torch.equal(before, after)
+        s.close()
+
+
 def test_kernel_times_are_recorded_on_request():
     cols = rt_synth.generate([20, 35], [30, 12], 20, seed=70, optics="ktable")
     b = DeviceBatch(cols)
