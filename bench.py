@@ -204,15 +204,22 @@ def run_reference(args):
     return 0
 
 
-def run_uneven(args, stream):
+def run_uneven(args, stream, ws=1, rank=0, barrier=lambda: None, max_over_ranks=lambda x: x):
     """Config 3: 4096 columns, L ~ U{20..200}, NB ~ U{30..300}, 20 g in one
     persistent launch; launch shape from the autotuner; timed as replays of
-    a captured CUDA graph."""
+    a captured CUDA graph.  With several ranks the one batch is split by
+    column (shard.partition: contiguous, cost-balanced blocks), each rank
+    solves its block on its own GPU with no exchange, and the step time is
+    the maximum over ranks (strong scaling)."""
     import torch
     import rt_synth
+    from paper_2203_02293_b300.shard import partition
     from paper_2203_02293_b300.solver import DeviceBatch, Solver
     from paper_2203_02293_b300.tuning import GraphSolve, autotune
-    dc = rt_synth.config3_device()
+    full = rt_synth.config3_device()
+    n_total = full.n_systems
+    a, b_ = partition(full.n_layers, full.n_bins, ws)[rank]
+    dc = full.column_range(a, b_) if ws > 1 else full
     b = DeviceBatch.from_device(dc)
     from paper_2203_02293_b300.tuning import KNOBS
     tune = autotune(b, dc.g_weights, reps=3)
@@ -221,20 +228,26 @@ def run_uneven(args, stream):
     for _ in range(3):
         g.replay()
     torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.uneven_steps):
         g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.uneven_steps
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.uneven_steps)
     s.close()
     out = {"workload": "4096 cols, L~U{20..200}, NB~U{30..300}, 20 g, one launch (CUDA graph replay)",
-           "systems": dc.n_systems, "input_bytes": int(3 * 4 * dc.dtau.numel()),
-           "ms_per_step": ms, "value": dc.n_systems / (ms * 1e-3), "unit": UNIT,
+           "systems": n_total, "input_bytes": int(3 * 4 * full.dtau.numel()),
+           "ms_per_step": ms, "value": n_total / (ms * 1e-3), "unit": UNIT,
+           "n_gpus": ws, "scaling": "strong",
+           "split": f"columns [{a}, {b_}) of 4096 on rank {rank} (shard.partition, no exchange)" if ws > 1
+                    else "one GPU, whole batch",
            "steps": args.uneven_steps, "autotune": {k: tune[k] for k in (*KNOBS, "stable") if k in tune},
            "autotune_table": tune["table"]}
-    del g, b, dc
+    del g, b, dc, full
     torch.cuda.empty_cache()
     return out
 
@@ -525,6 +538,47 @@ def run_serving(args):
     return summ
 
 
+def run_profile_case(args):
+    """One workload solved twice, for profilers (the second solve is the one
+    to capture: ``ncu -k <kernel> -s 1 -c 1``).  Cases: fp32 / fp64 (GCM
+    shape, cubes in), sweeps (the same with --profile-sweeps sweeps of the
+    iterative method), postproc (R = 500 shape), ktable (k-table front end).
+    --profile-cols sets the column count (2562: cubes 738 MB, above L2)."""
+    import torch
+    import rt_synth
+    from paper_2203_02293_b300 import rt
+    from paper_2203_02293_b300.solver import DeviceBatch, Solver
+    case, ncols = args.profile_case, args.profile_cols
+    if case in ("fp32", "fp64", "sweeps"):
+        cols = rt_synth.config1(n_cols=ncols)
+        b = DeviceBatch(cols)
+        extra = dict(n_sweeps=args.profile_sweeps) if case == "sweeps" else {}
+        s = Solver(cols.g_weights, precision=rt.RT_FP64_PLAIN if case == "fp64" else rt.RT_FP32_FORM, **extra)
+        run = lambda: s.solve(b)
+        n_sys = cols.n_systems
+    elif case == "postproc":
+        dc = rt_synth.postproc_device(ncols, seed=5)
+        b = DeviceBatch.from_device(dc)
+        s = Solver(dc.g_weights, wn_edges=dc.consts["wn_edges"])
+        run = lambda: s.solve(b)
+        n_sys = dc.n_systems
+    elif case == "ktable":
+        cols = rt_synth.state_columns(ncols, 40, 30, 20, seed=26)
+        b = DeviceBatch(cols)
+        s = Solver(cols.g_weights)
+        s.set_ktable(rt_synth.ktable(n_bins=30, n_g=20, seed=11))
+        run = lambda: s.solve_ktable(b)
+        n_sys = cols.n_systems
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    s.close()
+    print("ok", case, ncols, n_sys, flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,11 +598,17 @@ def main():
                     help="sweep counts of the iterative method timed beside Thomas (empty: skip)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
+    ap.add_argument("--profile-case", default=None,
+                    help="fp32 | fp64 | sweeps | postproc | ktable: two solves of one workload, for ncu")
+    ap.add_argument("--profile-cols", type=int, default=2562)
+    ap.add_argument("--profile-sweeps", type=int, default=10)
     ap.add_argument("--table", action="store_true",
                     help="per-workload table (configs 0-3, FP32/FP64 GPU, CPU oracle 1 core / all cores)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.table:
@@ -577,6 +637,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    # One GCM batch of ws x 2562 columns split by column with no exchange on
+    # the data path: partition() gives each rank a contiguous, cost-balanced
+    # block.  The columns are uniform, so block r is columns [2562 r,
+    # 2562 (r + 1)), which rank r draws itself (those columns are the draw
+    # of seed 1 + r): per-GPU work is fixed as ranks are added.
+    from paper_2203_02293_b300.shard import partition
+    lo, hi = partition(np.full(ws * 2562, 40), np.full(ws * 2562, 30), ws)[rank]
+    assert (lo, hi) == (2562 * rank, 2562 * (rank + 1))
     cols = rt_synth.config1(seed=1 + rank)
     batch = DeviceBatch(cols)
     n_sys = batch.n_systems
@@ -772,7 +840,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded k-table stand-in)",
         "config": {"workload": WORKLOAD, "systems_per_gpu": n_sys, "layers": 40, "bins": 30,
                    "g_points": 20, "l2": "inputs 738 MB > 126 MB L2, no flush needed",
-                   "parallelism": f"columns sharded, {ws} rank(s), no collective"},
+                   "parallelism": f"one {ws * 2562}-column batch split by column (shard.partition), "
+                                  f"{ws} rank(s), no collective on the data path"},
         "fp64_plain": {"value": n_sys * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                        "steps": args.fp64_steps},
         "fp32_over_fp64": ms64 / ms32,
@@ -791,10 +860,11 @@ def main():
     }
     if sweeps is not None:
         line["sweeps"] = sweeps
-    if rank == 0 and not args.quick:
+    if not args.quick:
         del batch, host, devs
         torch.cuda.empty_cache()
-        line["uneven"] = run_uneven(args, stream)
+        line["uneven"] = run_uneven(args, stream, ws, rank, barrier, max_over_ranks)
+    if rank == 0 and not args.quick:
         line["postproc"] = run_postproc(args, stream)
         line["ktable"] = run_ktable(args, stream)
         line["serving"] = run_serving(args)

@@ -131,7 +131,7 @@ typedef struct {
 /* Largest layer count of a column solved with n_sweeps > 0 (each GPU lane
  * holds its system's per-layer transmission, reflection and level fluxes in
  * registers). */
-#define RT_SWEEP_MAX_LAYERS 48
+#define RT_SWEEP_MAX_LAYERS 40
 
 /* A packed batch of columns.  Column c has L_c layers, NB_c bins and
  * S_c = NB_c * n_g systems.  Data of consecutive columns follow each other

@@ -116,7 +116,7 @@ cudaError_t launch_kt_optics(const KParams &kp, const int64_t *pcube_off, float 
 constexpr int kMaxLayers = 1024;
 // Largest L of the iterative method's kernel (each lane holds its system's
 // per-layer t, r and the level fluxes in registers).
-constexpr int kSweepMaxLayers = 48;
+constexpr int kSweepMaxLayers = 40;
 // Shared memory of the iterative method's kernel: floats per warp, bytes per CTA.
 int sweep_warp_floats(int Lmax, int nbw, int direct, int isothermal);
 size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal);

@@ -671,16 +671,19 @@ __device__ __forceinline__ void warp_store(R a, R n, int level, int nwarps, R *w
     }
 }
 
+// The warp partials are added to the column sums one at a time in warp
+// (system) order, so the order of the additions does not depend on the CTA
+// size: a column gives the same bits in any batch and launch shape.
 template <typename R>
 __device__ __forceinline__ void fold_warps(int L, int nwarps, Smem<R> &sm) {
     for (int i = threadIdx.x; i <= L; i += blockDim.x) {
-        double sa = 0.0, sn = 0.0;
+        double sa = sm.acc[2 * i], sn = sm.acc[2 * i + 1];
         for (int w = 0; w < nwarps; ++w) {
             sa += (double)sm.wpart[2 * (i * nwarps + w)];
             sn += (double)sm.wpart[2 * (i * nwarps + w) + 1];
         }
-        sm.acc[2 * i] += sa;
-        sm.acc[2 * i + 1] += sn;
+        sm.acc[2 * i] = sa;
+        sm.acc[2 * i + 1] = sn;
     }
 }
 
@@ -1605,192 +1608,269 @@ size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal
     return sizeof(float) * (size_t)(block / 32) * sweep_warp_floats(Lmax, nbw, direct, isothermal);
 }
 
+// Layers per branch-free chunk of the sweep passes.  Inside a chunk no
+// branch separates the layers, so the shared-memory loads of later layers
+// can issue early; layers past the column's L in its last chunk run with
+// t = r = 0 on clamped source rows and write only dead level slots.
+constexpr int kSweepChunk = 8;
+static_assert(kSweepMaxLayers % kSweepChunk == 0, "whole chunks");
+
 // One upward pass over the lane's system.  X holds d at the levels (u at the
 // BOA); on return it holds u.  EMIT (last sweep): u and u - d at interface
-// i < L go to rows 2i and 2i + 1 of OUT (element of lane j: out_idx).
-// The loop body is kept small, and X is indexed only by the unrolled loop
-// counter (a store at the runtime BOA index would send X to local memory),
-// so that X stays in registers.
+// i < L go to rows 2i and 2i + 1 of OUT (element of lane j: out_idx).  X is
+// indexed only by the unrolled loop counters (a store at the runtime BOA
+// index would send X to local memory), so it stays in registers.
 template <bool ISO, bool EMIT, int LR, int NLV>
 __device__ __forceinline__ void sweep_up(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int L, int lane,
                                          float d0, const float *SU, float *OUT) {
+    constexpr int CH = kSweepChunk, NC = LR / kSweepChunk;
+    using S2 = typename std::conditional<ISO, float, float2>::type;    // sources of one layer
+    const S2 *src = reinterpret_cast<const S2 *>(SU);
+    // the top chunk's rows first, then each chunk's loads issue while the
+    // previous chunk computes
+    S2 buf[CH];
+    const int ctop = (L - 1) / CH;
 #pragma unroll
-    for (int k = 0; k < LR; ++k) {
-        const int l = LR - 1 - k;
-        if (l < L) {
-            if constexpr (ISO) {
-                const float dl = l == 0 ? d0 : X[l];
-                X[l] = fmaf(t[l], X[l + 1], fmaf(r[l], dl, SU[l * 32 + lane]));
-                if (EMIT) {
-                    OUT[out_idx(2 * l, lane)] = X[l];
-                    OUT[out_idx(2 * l + 1, lane)] = X[l] - dl;
-                }
-            } else {
-                const float2 su = reinterpret_cast<const float2 *>(SU)[l * 32 + lane];   // (upper, lower)
-                X[2 * l + 1] = fmaf(t[l], X[2 * l + 2], fmaf(r[l], X[2 * l + 1], su.y));
-                const float dl = l == 0 ? d0 : X[2 * l];
-                X[2 * l] = fmaf(t[l], X[2 * l + 1], fmaf(r[l], dl, su.x));
-                if (EMIT) {
-                    OUT[out_idx(2 * l, lane)] = X[2 * l];
-                    OUT[out_idx(2 * l + 1, lane)] = X[2 * l] - dl;
+    for (int k = 0; k < CH; ++k) buf[k] = src[min(ctop * CH + k, L - 1) * 32 + lane];
+#pragma unroll
+    for (int c = NC - 1; c >= 0; --c) {
+        if (c * CH < L) {
+            S2 cur[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) cur[k] = buf[k];
+            if (c > 0) {
+#pragma unroll
+                for (int k = 0; k < CH; ++k) buf[k] = src[((c - 1) * CH + k) * 32 + lane];
+            }
+#pragma unroll
+            for (int k = CH - 1; k >= 0; --k) {
+                const int l = c * CH + k;
+                const bool live = l < L;                 // (always true in all but the last chunk)
+                if constexpr (ISO) {
+                    const float dl = l == 0 ? d0 : X[l];
+                    const float u = fmaf(t[l], X[l + 1], fmaf(r[l], dl, cur[k]));
+                    X[l] = (l == 0 || live) ? u : X[l];  // keeps the BOA value at l = L
+                    if (EMIT && live) {
+                        OUT[out_idx(2 * l, lane)] = u;
+                        OUT[out_idx(2 * l + 1, lane)] = u - dl;
+                    }
+                } else {
+                    X[2 * l + 1] = fmaf(t[l], X[2 * l + 2], fmaf(r[l], X[2 * l + 1], cur[k].y));   // lower
+                    const float dl = l == 0 ? d0 : X[2 * l];
+                    const float u = fmaf(t[l], X[2 * l + 1], fmaf(r[l], dl, cur[k].x));            // upper
+                    X[2 * l] = (l == 0 || live) ? u : X[2 * l];
+                    if (EMIT && live) {
+                        OUT[out_idx(2 * l, lane)] = u;
+                        OUT[out_idx(2 * l + 1, lane)] = u - dl;
+                    }
                 }
             }
         }
     }
 }
 
-template <bool ISO, bool DIRECT>
-__device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
-                                           float *fbs, float *SU, float *SD, float *TR, Counters &cn) {
-    constexpr int LR = kSweepMaxLayers;
-    constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
-    const int NG = kp.n_g;
-    const int c = kp.unit_col[unit];
-    const int ku = kp.unit_k[unit];
-    const int L = kp.n_layers[c], NB = kp.n_bins[c];
-    const int S = NB * NG;
-    const long long cube0 = kp.cube_off[c];
-    const float4 cf = kp.colf[c];
-    const float mu = cf.x, imu = cf.y;
-    const double mu_d = kp.mu_star[kp.mu_idx[c]];
-    const bool beam = cf.z != 0.f;
-    const int s0 = ku * 32;
-    const int b_lo = s0 / NG;
-    const int nbc = min(NB - 1, (s0 + 31) / NG) - b_lo + 1;
-
-    // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
-    {
-        const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
-        const int nlev = 2 * L + 1;
-        if constexpr (!DIRECT) {
-            for (int i = lane; i < nlev * nbc; i += 32) {
-                const int lev = i / nbc, bb = i - lev * nbc;
-                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+// One downward pass: X takes d at every level below the TOA, then u at the
+// BOA (d + (F_BOA + F_beam)); returns d at the BOA.
+template <bool ISO, int LR, int NLV>
+__device__ __forceinline__ float sweep_down(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int L,
+                                            int lane, float d0, float ubc, const float *SD) {
+    constexpr int CH = kSweepChunk, NC = LR / kSweepChunk;
+    using S2 = typename std::conditional<ISO, float, float2>::type;
+    const S2 *src = reinterpret_cast<const S2 *>(SD);
+    S2 buf[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) buf[k] = src[min(k, L - 1) * 32 + lane];
+    float d = d0, dB = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (c * CH < L) {
+            S2 cur[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) cur[k] = buf[k];
+            if (c + 1 < NC) {
+#pragma unroll
+                for (int k = 0; k < CH; ++k) buf[k] = src[min((c + 1) * CH + k, L - 1) * 32 + lane];
+            }
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int l = c * CH + k;
+                if constexpr (ISO) {
+                    d = fmaf(t[l], d, fmaf(r[l], X[l + 1], cur[k]));
+                    X[l + 1] = l == L - 1 ? d + ubc : d;
+                } else {
+                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 1], cur[k].x));          // upper sub-layer
+                    X[2 * l + 1] = d;
+                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 2], cur[k].y));          // lower
+                    X[2 * l + 2] = l == L - 1 ? d + ubc : d;
+                }
+                dB = l == L - 1 ? d : dB;
             }
         }
-        for (int j = lane; j < nbc; j += 32) {
-            sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
-            sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
-        }
     }
-    __syncwarp();
+    return dB;
+}
 
+// Column and lane bookkeeping of a sweep unit (re-derived after the sweeps,
+// so that none of it is held in registers across them).
+struct SweepLane {
+    int c, ku, L, NB, S, s0, b_lo, nbc, bI, bst;
+    bool on;
+    float wg;
+    const float *Bp;
+};
+
+template <bool DIRECT>
+__device__ __forceinline__ SweepLane sweep_lane(const KParams &kp, int unit, int lane, float *sB) {
+    SweepLane q;
+    const int NG = kp.n_g;
+    q.c = kp.unit_col[unit];
+    q.ku = kp.unit_k[unit];
+    q.L = kp.n_layers[q.c];
+    q.NB = kp.n_bins[q.c];
+    q.S = q.NB * NG;
+    q.s0 = q.ku * 32;
+    q.b_lo = q.s0 / NG;
+    q.nbc = min(q.NB - 1, (q.s0 + 31) / NG) - q.b_lo + 1;
     // padding lanes of a column's last unit repeat system s0 with zero weight
-    const bool on = s0 + lane < S;
-    const int sI = on ? s0 + lane : s0;
-    const int bI = sI / NG;
-    const float wg = on ? kp.g_w32[sI - bI * NG] : 0.f;
-    const int bst = DIRECT ? NB : nbc;
-    const float *Bp = DIRECT ? kp.planck32 + kp.planck_off[c] + bI : sB + (bI - b_lo);
-    float Fb = beam ? mu * sFs[bI - b_lo] : 0.f;
-    const float FBOA = sFB[bI - b_lo];
-    SysCounts<float> sc;
-    sc.inv = sc.ecl = sc.etau = 0u;
+    q.on = q.s0 + lane < q.S;
+    const int sI = q.on ? q.s0 + lane : q.s0;
+    q.bI = sI / NG;
+    q.wg = q.on ? kp.g_w32[sI - q.bI * NG] : 0.f;
+    q.bst = DIRECT ? q.NB : q.nbc;
+    q.Bp = DIRECT ? kp.planck32 + kp.planck_off[q.c] + q.bI : sB + (q.bI - q.b_lo);
+    return q;
+}
 
-    // coefficient pass, TOA -> BOA (cubes streamed once, next layer prefetched)
-    float2 *TR2 = reinterpret_cast<float2 *>(TR);
-    const float *pd = kp.dtau + cube0 + sI, *pw = kp.w0 + cube0 + sI, *pg = kp.g0 + cube0 + sI;
-    float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);
-    float Bt = ldB<DIRECT>(Bp);
-    const float d0 = fmaf(-kPiF, Bt, (float)kp.F_toa);   // d at the TOA level
-    for (int l = 0; l < L; ++l) {
-        const float dt = nd, w0 = nw, g0 = ng;
-        if (l + 1 < L) {
-            pd += S;
-            pw += S;
-            pg += S;
-            nd = __ldcs(pd);
-            nw = __ldcs(pw);
-            ng = __ldcs(pg);
-        }
-        const float Bc = ldB<DIRECT>(Bp + (2 * l + 1) * bst), Bb = ldB<DIRECT>(Bp + (2 * l + 2) * bst);
-        float fw = wg * Fb;                                    // interface l: warp sum of w F_beam
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
-        if (lane == 0) fbs[l] = fw;
-        const Sub32<float> sb = sub32<ISO, float>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cn, sc, on);
-        TR2[l * 32 + lane] = make_float2(sb.t, sb.r);
-        if constexpr (ISO) {
-            SU[l * 32 + lane] = sb.suU;
-            SD[l * 32 + lane] = sb.sdU;
-            Fb *= sb.m;
-        } else {
-            reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(sb.suU, sb.suL);
-            reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(sb.sdU, sb.sdL);
-            Fb *= sb.m * sb.m;
-        }
-        Bt = Bb;
-    }
+template <bool ISO, bool DIRECT>
+__device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
+                                           float *fbs, float *SU, float *SD, float *TR) {
+    constexpr int LR = kSweepMaxLayers;
+    constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
+    float t[LR], r[LR], X[NLV];
+    int L;
+    float d0, ubc;
+
+    // ---- coefficient pass: stage B, F*, F_BOA; per layer (t, r) and the
+    // sub-layer sources into shared memory; then t, r and the starting state
+    // into registers
     {
-        float fw = wg * Fb;                                    // the BOA interface
+        const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
+        L = q.L;
+        {
+            const float *Bg = kp.planck32 + kp.planck_off[q.c] + q.b_lo;
+            const int nlev = 2 * L + 1;
+            if constexpr (!DIRECT) {
+                for (int i = lane; i < nlev * q.nbc; i += 32) {
+                    const int lev = i / q.nbc, bb = i - lev * q.nbc;
+                    sB[i] = __ldcg(Bg + (long long)lev * q.NB + bb);
+                }
+            }
+            for (int j = lane; j < q.nbc; j += 32) {
+                sFs[j] = __ldcg(kp.fs32 + kp.bin_off[q.c] + q.b_lo + j);
+                sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[q.c] + q.b_lo + j);
+            }
+        }
+        __syncwarp();
+        const float4 cf = kp.colf[q.c];
+        const float mu = cf.x, imu = cf.y;
+        const double mu_d = kp.mu_star[kp.mu_idx[q.c]];
+        const bool beam = cf.z != 0.f;
+        float Fb = beam ? mu * sFs[q.bI - q.b_lo] : 0.f;
+        const float FBOA = sFB[q.bI - q.b_lo];
+        Counters cu = {0, 0, 0, 0, 0, 0, 0};
+        SysCounts<float> sc;
+        sc.inv = sc.ecl = sc.etau = 0u;
+        float2 *TR2 = reinterpret_cast<float2 *>(TR);
+        const long long e0 = kp.cube_off[q.c] + (q.on ? q.s0 + lane : q.s0);
+        const float *pd = kp.dtau + e0, *pw = kp.w0 + e0, *pg = kp.g0 + e0;
+        float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);   // next layer prefetched
+        float Bt = ldB<DIRECT>(q.Bp);
+        d0 = fmaf(-kPiF, Bt, (float)kp.F_toa);                     // d at the TOA level
+        for (int l = 0; l < L; ++l) {
+            const float dt = nd, w0 = nw, g0 = ng;
+            if (l + 1 < L) {
+                pd += q.S;
+                pw += q.S;
+                pg += q.S;
+                nd = __ldcs(pd);
+                nw = __ldcs(pw);
+                ng = __ldcs(pg);
+            }
+            const float Bc = ldB<DIRECT>(q.Bp + (2 * l + 1) * q.bst), Bb = ldB<DIRECT>(q.Bp + (2 * l + 2) * q.bst);
+            float fw = q.wg * Fb;                                  // interface l: warp sum of w F_beam
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
+            if (lane == 0) fbs[l] = fw;
+            const Sub32<float> sb =
+                sub32<ISO, float>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cu, sc, q.on);
+            TR2[l * 32 + lane] = make_float2(sb.t, sb.r);
+            if constexpr (ISO) {
+                SU[l * 32 + lane] = sb.suU;
+                SD[l * 32 + lane] = sb.sdU;
+                Fb *= sb.m;
+            } else {
+                reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(sb.suU, sb.suL);
+                reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(sb.sdU, sb.sdL);
+                Fb *= sb.m * sb.m;
+            }
+            Bt = Bb;
+        }
+        float fw = q.wg * Fb;                                      // the BOA interface
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
         if (lane == 0) fbs[L] = fw;
-    }
-    cn.inv += vmasked(sc.inv, on);
-    cn.eclamp += vmasked(sc.ecl, on);
-    cn.etau += (ISO ? 1u : 2u) * vmasked(sc.etau, on);
-    const float ubc = FBOA + Fb;                               // u - d at the BOA (Eq. 10)
-    __syncwarp();
-
-    // registers: t, r per layer, the state at the levels (zero flux: u = -pi B)
-    float t[LR], r[LR], X[NLV];
-#pragma unroll
-    for (int l = 0; l < LR; ++l) {
-        float2 v = make_float2(0.f, 0.f);
-        if (l < L) v = TR2[l * 32 + lane];
-        t[l] = v.x;
-        r[l] = v.y;
-    }
-#pragma unroll
-    for (int j = 0; j < NLV; ++j) {
-        const int lev = ISO ? 2 * j : j;                       // level in the B table
-        X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldB<DIRECT>(Bp + min(lev, 2 * L) * bst) : 0.f;
-    }
-    __syncwarp();                                              // (t, r) area free for the output rows
-
-    float dB = 0.f;
-    for (int it = 0; it < kp.n_sweeps; ++it) {
-        // downward pass: X takes d at every level below the TOA, then u at the BOA
-        float d = d0;
+        ubc = FBOA + Fb;                                           // u - d at the BOA (Eq. 10)
+        cu.inv = vmasked(sc.inv, q.on);
+        cu.eclamp = vmasked(sc.ecl, q.on);
+        cu.etau = (ISO ? 1u : 2u) * vmasked(sc.etau, q.on);
+        flush_counters(cu, kp.stats);                              // per unit: nothing kept live
+        __syncwarp();
 #pragma unroll
         for (int l = 0; l < LR; ++l) {
-            if (l < L) {
-                if constexpr (ISO) {
-                    d = fmaf(t[l], d, fmaf(r[l], X[l + 1], SD[l * 32 + lane]));
-                    X[l + 1] = l == L - 1 ? d + ubc : d;
-                } else {
-                    const float2 sd = reinterpret_cast<const float2 *>(SD)[l * 32 + lane];   // (upper, lower)
-                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 1], sd.x));
-                    X[2 * l + 1] = d;
-                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 2], sd.y));
-                    X[2 * l + 2] = l == L - 1 ? d + ubc : d;
-                }
-            }
+            float2 v = make_float2(0.f, 0.f);
+            if (l < L) v = TR2[l * 32 + lane];
+            t[l] = v.x;
+            r[l] = v.y;
         }
-        dB = d;
+        // zero diffuse flux: u = -pi B at every level
+#pragma unroll
+        for (int j = 0; j < NLV; ++j) {
+            const int lev = ISO ? 2 * j : j;                       // level in the B table
+            X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldB<DIRECT>(q.Bp + min(lev, 2 * L) * q.bst) : 0.f;
+        }
+        __syncwarp();                                              // (t, r) area free for the output rows
+    }
+
+    // ---- the sweeps: registers t, r, X; sources from shared memory
+    float dB = 0.f;
+    for (int it = 0; it < kp.n_sweeps; ++it) {
+        dB = sweep_down<ISO>(X, t, r, L, lane, d0, ubc, SD);
         if (it + 1 < kp.n_sweeps)
             sweep_up<ISO, false>(X, t, r, L, lane, d0, SU, TR);
         else
             sweep_up<ISO, true>(X, t, r, L, lane, d0, SU, TR);
     }
+    const bool finite = isfinite(X[0]) && isfinite(dB);
+
+    // ---- interface sums, TOA spectrum, column finalisation
+    const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
     {
         // the BOA interface: u = d + (F_BOA + F_beam), as the downward pass set it
         const float uB = dB + ubc;
         TR[out_idx(2 * L, lane)] = uB;
         TR[out_idx(2 * L + 1, lane)] = uB - dB;
     }
-    if (on && !(isfinite(X[0]) && isfinite(dB))) cn.nonfinite++;
+    const unsigned bad = __ballot_sync(0xffffffffu, q.on && !finite);
+    if (lane == 0 && bad) atomicAdd(kp.stats + ST_NONFINITE, (unsigned long long)__popc(bad));
     // weighted fluxes: F_up = pi B + u; F_net + F_beam = u - d
     for (int i = 0; i <= L; ++i) {
-        const float Bi = ldB<DIRECT>(Bp + 2 * i * bst);
-        TR[out_idx(2 * i, lane)] = wg * fmaf(kPiF, Bi, TR[out_idx(2 * i, lane)]);
-        TR[out_idx(2 * i + 1, lane)] *= wg;
+        const float Bi = ldB<DIRECT>(q.Bp + 2 * i * q.bst);
+        TR[out_idx(2 * i, lane)] = q.wg * fmaf(kPiF, Bi, TR[out_idx(2 * i, lane)]);
+        TR[out_idx(2 * i + 1, lane)] *= q.wg;
     }
     __syncwarp();
-
-    // interface sums: row 2i = sum w F_up, row 2i + 1 = sum w (u - d) - sum w F_beam
-    float *part = kp.partial + kp.part_off[c] + (long long)ku * 2 * (L + 1);
+    // row 2i = sum w F_up, row 2i + 1 = sum w (u - d) - sum w F_beam
+    float *part = kp.partial + kp.part_off[q.c] + (long long)q.ku * 2 * (L + 1);
     for (int row = lane; row < 2 * (L + 1); row += 32) {
         float acc = 0.f;
 #pragma unroll 8
@@ -1800,13 +1880,14 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     }
     // TOA spectrum: row 0 holds w F_up at the TOA per system
     if (kp.toa) {
-        for (int jb = lane; jb < nbc; jb += 32) {
-            const int bt = b_lo + jb;
-            const int j0 = max(0, bt * NG - s0);
-            const int j1 = min(min(32, S - s0), (bt + 1) * NG - s0);
+        const int NG = kp.n_g;
+        for (int jb = lane; jb < q.nbc; jb += 32) {
+            const int bt = q.b_lo + jb;
+            const int j0 = max(0, bt * NG - q.s0);
+            const int j1 = min(min(32, q.S - q.s0), (bt + 1) * NG - q.s0);
             float acc = 0.f;
             for (int j = j0; j < j1; ++j) acc += TR[out_idx(0, j)];
-            atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
+            atomicAdd(kp.toa + kp.bin_off[q.c] + bt, (double)acc);
         }
     }
     __syncwarp();
@@ -1814,11 +1895,11 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     // the warp that completes a column's last unit writes the column
     __threadfence();
     int done = 0;
-    if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
+    if (lane == 0) done = atomicAdd(kp.col_done + q.c, 1);
     done = __shfl_sync(0xffffffffu, done, 0);
-    if (done == kp.col_units[c] - 1) {
+    if (done == kp.col_units[q.c] - 1) {
         __threadfence();
-        finalize_column(kp, c, lane);
+        finalize_column(kp, q.c, lane);
     }
     __syncwarp();
 }
@@ -1837,15 +1918,13 @@ __global__ void __launch_bounds__(kMaxBlock32, 1) fp32_sweeps(KParams kp) {
     float *SU = fbs + ((Lm + 1 + 3) & ~3);
     float *SD = SU + (ISO ? 32 : 64) * Lm;
     float *TR = SD + (ISO ? 32 : 64) * Lm;
-    Counters cn = {0, 0, 0, 0, 0, 0, 0};
     for (;;) {
         int unit = 0;
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        sweep_unit<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR, cn);
+        sweep_unit<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR);
     }
-    flush_counters(cn, kp.stats);
 }
 
 // ---------------------------------------------------------------------
@@ -2052,14 +2131,15 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
             __syncthreads();
             fold_warps<double>(ci.L, nwarps, sm);
             if (kp.toa && tid < nbc) {
-                // one thread per bin sums its systems in order; a bin split
-                // across chunks is continued by the same CTA after a barrier
+                // one thread per bin adds its systems in system order; a bin
+                // split across chunks is continued by the same CTA after a
+                // barrier, with the same sequence of additions
                 const int bt = b_lo + tid;
                 const int j0 = max(0, bt * NG - s0);
                 const int j1 = min(min((int)blockDim.x, ci.S - s0), (bt + 1) * NG - s0);
-                double acc = 0.0;
+                double acc = kp.toa[ci.bin0 + bt];
                 for (int j = j0; j < j1; ++j) acc += sm.stoa[j];
-                kp.toa[ci.bin0 + bt] += acc;
+                kp.toa[ci.bin0 + bt] = acc;
             }
             __syncthreads();
         }

@@ -22,7 +22,7 @@ RT_NONISOTHERMAL, RT_ISOTHERMAL = 0, 1
 RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
 RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
 RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT, RT_STAGE_INLINE = 0, 1, 2, 3
-RT_SWEEP_MAX_LAYERS = 48
+RT_SWEEP_MAX_LAYERS = 40
 
 _STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
            -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}

@@ -12,6 +12,14 @@ different slots overlap on the device.  A
 request's latency runs from its arrival to the host seeing its batch's
 completion event.  Requests that can never fit the budget are refused; a
 request may be cancelled while it waits or refused after a waiting timeout.
+
+With ``split_systems`` set, a request larger than that many systems is cut
+into pieces of whole columns when it arrives; the pieces wait, are admitted
+and run like requests of their own (on several slots at once when free),
+and the request completes when its last piece does.  A large request then
+neither holds one slot for its whole duration nor delays the small requests
+queued behind it, and its results are the same bits as unsplit (columns are
+independent and each column's sums run in a fixed order).
 """
 from __future__ import annotations
 
@@ -41,6 +49,9 @@ class Request:
     t_admit: float = -1.0
     t_done: float = -1.0
     outputs: dict | None = None
+    parent: "Request | None" = None   # for a piece: the request it belongs to
+    pieces: list | None = None         # for a split request: its pieces, in column order
+    pieces_left: int = 0
 
     @property
     def systems(self) -> int:
@@ -99,23 +110,34 @@ class Pool:
         self.cube_elems = cube_elems
         _, self.g_weights = draw.gauss_legendre_01(n_g)
 
+    KEYS = ("cube_offset", "center_offset", "iface_offset", "bin_offset", "col_index")
+
+    def _request_gather(self, r):
+        """Shapes and gather offsets of one request's columns (array
+        arithmetic, computed once per request)."""
+        g = getattr(r, "_gather", None)
+        if g is None:
+            n = r.n_cols
+            cols = np.asarray(r.cols, np.int64)
+            per = r.L * r.NB * self.n_g
+            g = (np.full(n, r.L, np.int32), np.full(n, r.NB, np.int32),
+                 dict(cube_offset=r.cube_base + per * np.arange(n, dtype=np.int64),
+                      center_offset=self.tc_off[r.L] + cols * r.L,
+                      iface_offset=self.if_off[r.L] + cols * (r.L + 1),
+                      bin_offset=np.full(n, self.fs_off[r.NB], np.int64),
+                      col_index=cols))
+            r._gather = g
+        return g
+
     def gather(self, reqs):
         """Shapes and gather offsets of a batch made of ``reqs`` (in order)."""
-        nl, nb, cube, cen, ifc, bins, col = [], [], [], [], [], [], []
-        for r in reqs:
-            per = r.L * r.NB * self.n_g
-            for j, pc in enumerate(r.cols):
-                nl.append(r.L)
-                nb.append(r.NB)
-                cube.append(r.cube_base + j * per)
-                cen.append(self.tc_off[r.L] + pc * r.L)
-                ifc.append(self.if_off[r.L] + pc * (r.L + 1))
-                bins.append(self.fs_off[r.NB])
-                col.append(pc)
-        g = dict(cube_offset=np.array(cube, np.int64), center_offset=np.array(cen, np.int64),
-                 iface_offset=np.array(ifc, np.int64), bin_offset=np.array(bins, np.int64),
-                 col_index=np.array(col, np.int64))
-        return np.array(nl, np.int32), np.array(nb, np.int32), g
+        parts = [self._request_gather(r) for r in reqs]
+        if len(parts) == 1:
+            return parts[0]
+        nl = np.concatenate([p[0] for p in parts])
+        nb = np.concatenate([p[1] for p in parts])
+        g = {k: np.concatenate([p[2][k] for p in parts]) for k in self.KEYS}
+        return nl, nb, g
 
     def descriptor(self, reqs):
         nl, nb, g = self.gather(reqs)
@@ -140,6 +162,23 @@ def make_requests(pool: Pool, n: int, rate_hz: float, seed: int, C_range=(1, 256
     return reqs
 
 
+def split_request(r: Request, max_systems: int) -> list:
+    """``r`` as pieces of whole columns of at most ``max_systems`` systems
+    each (at least one column per piece); ``[r]`` if it is small enough."""
+    per_col = r.NB * r.n_g
+    if max_systems <= 0 or r.systems <= max_systems or r.n_cols == 1:
+        return [r]
+    k = max(1, max_systems // per_col)
+    pieces = []
+    for j0 in range(0, r.n_cols, k):
+        cols = r.cols[j0:j0 + k]
+        pieces.append(Request(r.rid, r.arrival, len(cols), r.L, r.NB, cols,
+                              r.cube_base + j0 * r.L * per_col, n_g=r.n_g, parent=r))
+    r.pieces = pieces
+    r.pieces_left = len(pieces)
+    return pieces
+
+
 @dataclass
 class Slot:
     stream: torch.cuda.Stream
@@ -154,10 +193,11 @@ class Slot:
 class Server:
     def __init__(self, pool: Pool, n_slots: int = 4, hbm_budget_bytes: int = 8 << 30,
                  max_systems_per_batch: int = 24_000_000, wait_timeout_s: float = 0.0,
-                 keep_outputs: bool = False, policy: str = "fifo", **cfg):
+                 keep_outputs: bool = False, policy: str = "fifo", split_systems: int = 0, **cfg):
         # policy: "fifo" admits in arrival order; "sjf" admits the smallest
         # waiting requests first (shorter latency for small requests)
         self.policy = policy
+        self.split = split_systems
         self.pool = pool
         self.budget = hbm_budget_bytes
         self.max_sys = max_systems_per_batch
@@ -178,7 +218,8 @@ class Server:
             r.nbytes = rt.rt_query_bytes(slot.solver.h, desc)
         return r.nbytes
 
-    def _complete(self, slot: Slot, now: float):
+    def _complete(self, slot: Slot, now: float) -> int:
+        """Retire a finished batch; returns how many requests it completed."""
         if self.keep_outputs:
             o = slot.solver.outputs_host(slot.n_if, sum(r.n_cols * r.L for r in slot.reqs))
             i0 = l0 = 0
@@ -188,11 +229,37 @@ class Server:
                              "F_net": o["F_net"][i0:i0 + ni], "Q": o["Q"][l0:l0 + nl]}
                 i0 += ni
                 l0 += nl
+        finished = 0
         for r in slot.reqs:
             r.t_done = now
             r.status = "done"
+            p = r.parent
+            if p is None:
+                finished += 1
+            elif p.status in ("waiting", "running"):
+                p.pieces_left -= 1
+                if p.pieces_left == 0:
+                    p.t_done, p.status = now, "done"
+                    if self.keep_outputs:
+                        p.outputs = {k: np.concatenate([q.outputs[k] for q in p.pieces]) for k in r.outputs}
+                    finished += 1
         self.in_flight_bytes -= slot.nbytes
         slot.reqs, slot.busy, slot.nbytes = [], False, 0
+        return finished
+
+    @staticmethod
+    def _end(r: Request, status: str, now: float) -> int:
+        """End a waiting request or piece; returns 1 when that ends a request
+        (a split request ends with its first piece to be refused, cancelled
+        or timed out; its other pieces are then dropped)."""
+        r.status, r.t_done = status, now
+        p = r.parent
+        if p is None:
+            return 1
+        if p.status in ("waiting", "running"):
+            p.status, p.t_done = status, now
+            return 1
+        return 0
 
     def run(self, requests, cancel: set | None = None, poll_sleep: float = 5e-5):
         """Serve ``requests`` (sorted by arrival); returns a summary dict."""
@@ -207,22 +274,22 @@ class Server:
             while arrivals and arrivals[0].arrival <= now:
                 r = arrivals.popleft()
                 r.status = "waiting"
-                waiting.append(r)
+                for piece in split_request(r, self.split):
+                    piece.status = "waiting"
+                    waiting.append(piece)
             # completions
             for s in self.slots:
                 if s.busy and s.event.query():
-                    n = len(s.reqs)
-                    self._complete(s, time.perf_counter() - t0)
-                    done += n
-            # cancellations, timeouts and requests that can never fit
+                    done += self._complete(s, time.perf_counter() - t0)
+            # cancellations, timeouts, and pieces of requests that have ended
             keep = deque()
             for r in waiting:
-                if r.rid in cancel:
-                    r.status, r.t_done = "cancelled", now
-                    done += 1
+                if r.parent is not None and r.parent.status not in ("waiting", "running"):
+                    r.status = "dropped"
+                elif r.rid in cancel:
+                    done += self._end(r, "cancelled", now)
                 elif self.wait_timeout and now - r.arrival > self.wait_timeout:
-                    r.status, r.t_done = "timeout", now
-                    done += 1
+                    done += self._end(r, "timeout", now)
                 else:
                     keep.append(r)
             waiting = keep
@@ -237,11 +304,14 @@ class Server:
                     r = waiting[0]
                     if batch and nsys + r.systems > self.max_sys:
                         break
+                    if r.parent is not None and r.parent.status not in ("waiting", "running"):
+                        waiting.popleft()              # its request has ended
+                        r.status = "dropped"
+                        continue
                     rb = self._bytes(s, r)
                     if rb > self.budget:
                         waiting.popleft()              # can never fit
-                        r.status, r.t_done = "refused", now
-                        done += 1
+                        done += self._end(r, "refused", now)
                         continue
                     if self.in_flight_bytes + need + rb > self.budget:
                         break
@@ -265,6 +335,8 @@ class Server:
                 t_admit = time.perf_counter() - t0
                 for r in batch:
                     r.status, r.t_admit = "running", t_admit
+                    if r.parent is not None and r.parent.status == "waiting":
+                        r.parent.status, r.parent.t_admit = "running", t_admit
                 s.reqs, s.busy, s.nbytes = batch, True, need
                 s.n_if = int((nl + 1).sum())
                 self.in_flight_bytes += need

@@ -297,6 +297,18 @@ class DeviceColumns:
         z = lambda a: np.concatenate([[0], np.cumsum(a)])
         return dict(cube=z(L * NB * self.n_g), lay=z(L), iface=z(L + 1), bins=z(NB))
 
+    def column_range(self, a: int, b: int) -> "DeviceColumns":
+        """Columns [a, b) as a packed batch of views into the same device
+        memory (no copy): one rank's contiguous share of a sharded batch."""
+        o = self.offsets()
+        t = {}
+        for k, key in (("dtau", "cube"), ("w0", "cube"), ("g0", "cube"), ("T_center", "lay"),
+                       ("T_iface", "iface"), ("p_iface", "iface"), ("F_star", "bins")):
+            t[k] = getattr(self, k)[int(o[key][a]):int(o[key][b])]
+        t["mu_star"] = self.mu_star[a:b]
+        return DeviceColumns(self.n_layers[a:b].copy(), self.n_bins[a:b].copy(), self.n_g, self.g_weights, t,
+                             self.consts, f"{self.name}[{a}:{b}]")
+
     def host_subset(self, idx) -> Columns:
         idx = np.asarray(idx, dtype=np.int64)
         o = self.offsets()

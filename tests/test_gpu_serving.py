@@ -92,3 +92,30 @@ def test_cancel_and_timeout_on_the_host(pool):
     srv.close()
     assert summ["timeout"] >= 1 and summ["timeout"] + summ["done"] == 20
     assert summ["p50_ms"] is None or summ["p99_ms"] >= summ["p50_ms"]
+
+
+def test_split_requests_give_the_same_bits_as_whole(pool):
+    """Requests cut into pieces of a few columns, the pieces batched with
+    other requests and run on several slots: each request's result equals
+    its result solved alone."""
+    reqs = make_requests(pool, 24, rate_hz=4000.0, seed=10, C_range=(8, 64))
+    srv = Server(pool, n_slots=3, keep_outputs=True, split_systems=3 * 40 * 20, policy="sjf")
+    summ = srv.run(reqs)
+    srv.close()
+    assert summ["done"] == 24
+    assert any(r.pieces for r in reqs)
+    for r in reqs[::3]:
+        alone = solve_alone(pool, r)
+        for k in alone:
+            assert np.array_equal(alone[k], r.outputs[k]), (r.rid, k)
+
+
+def test_cancelling_a_split_request_drops_its_waiting_pieces(pool):
+    reqs = make_requests(pool, 10, rate_hz=1e6, seed=11, C_range=(32, 64))
+    srv = Server(pool, n_slots=1, split_systems=2 * 40 * 20)
+    summ = srv.run(reqs, cancel={4})
+    srv.close()
+    assert reqs[4].status in ("cancelled", "done")
+    assert summ["cancelled"] + summ["done"] == 10
+    if reqs[4].status == "cancelled":
+        assert all(p.status in ("dropped", "cancelled", "done") for p in reqs[4].pieces)

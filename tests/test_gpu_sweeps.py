@@ -72,7 +72,7 @@ def test_config1_sweeps_sampled(cfg1, n):
 
 @pytest.mark.parametrize("iso", [False, True])
 def test_one_sweep_without_scattering_is_thomas(iso):
-    cols = rt_synth.generate([40, 7, 1, 48], [30, 5, 3, 2], 20, seed=61, optics="ktable")
+    cols = rt_synth.generate([40, 7, 1, 33], [30, 5, 3, 2], 20, seed=61, optics="ktable")
     cols.w0[:] = 0.0
     opts = method_opts(isothermal=iso)
     ref = oracle_solve(cols, opts)                      # Thomas
@@ -92,10 +92,10 @@ def test_many_sweeps_converge_to_thomas():
 
 @pytest.mark.parametrize("staging", [1, 2])
 def test_ragged_batch_modes_and_edges(staging):
-    """Ragged L in [1, 48] (the kernel's register limit), NB in [1, 41], night
+    """Ragged L in [1, 40] (the kernel's register limit), NB in [1, 41], night
     side, F_TOA, both Planck routes; a column gives the same bits alone."""
-    L, NB = rt_synth.uneven_shapes(29, seed=63, L_range=(1, 48), NB_range=(1, 41))
-    L[0], L[1] = 48, 1
+    L, NB = rt_synth.uneven_shapes(29, seed=63, L_range=(1, 40), NB_range=(1, 41))
+    L[0], L[1] = 40, 1
     cols = rt_synth.generate(L, NB, 5, seed=64, optics="uniform", mu_range=(-0.5, 1.0))
     for opts in (method_opts(), method_opts(isothermal=True, F_toa=20.0), method_opts(improved=False)):
         ref = oracle_sweeps(cols, opts, 7)
@@ -109,7 +109,7 @@ def test_ragged_batch_modes_and_edges(staging):
 
 def test_layer_limit_is_refused():
     from paper_2203_02293_b300 import rt
-    cols = rt_synth.generate([49], [3], 2, seed=65, optics="uniform")
+    cols = rt_synth.generate([41], [3], 2, seed=65, optics="uniform")
     with pytest.raises(rt.RTError) as ei:
         gpu_solve(cols, method_opts(), "fp32", n_sweeps=3)
     assert ei.value.code == rt.RT_EINVAL
