@@ -54,6 +54,46 @@ def dist_env():
 FLOP_PER_SYSTEM = None   # filled from profiles/fp32_units_gcm2562.txt when current
 FP32_LANES_PER_SM = 128
 N_SM = 148
+MUFU_PER_SM_PER_CLK = 16
+
+# Algorithmic work of one non-isothermal layer of one (column, bin, g)
+# system, counted from the paper's equations evaluated directly: FP32
+# FMA-pipe operations (an add, a multiply or a fused a*b+c is one) and MUFU
+# operations (reciprocal, reciprocal square root, base-2 exponential; a
+# division is a reciprocal and a multiply, exp(x) a multiply and ex2).  A
+# layer's two sub-layers have the same w0, g0 and optical depth dtau/2, so
+# everything that depends only on those is evaluated once per layer; what
+# depends on the sub-layer's own B or beam is counted twice.
+#   (equations, per layer)                                  FMA-pipe  MUFU
+ALG_LAYER = {
+    "E fit, Eq. 19 (Horner form, w0 g0 shared)":              (6, 0),
+    "1 - w0 g0, E - w0, q = E (1 - w0 g0)":                   (3, 0),
+    "k = sqrt((E - w0) / q), Eq. B2":                         (2, 2),
+    "zeta+- = (1 +- k) / 2, Eq. B2":                          (2, 0),
+    "exponent 2 q k and dtau / 2":                            (3, 0),
+    "T = exp(-2 q k dtau / 2), Eq. B2 (product, log2 e scale)": (2, 1),
+    "chi, xi, psi, Eq. B1":                                   (9, 0),
+    "Pi, Eq. B5":                                             (3, 1),
+    "1 / (2 q) of Theta, Eqs. 5, 8":                          (0, 1),
+    "t = psi / chi, r = -xi / chi (rows of Eq. 12 over chi)": (2, 1),
+    "D of Eq. 11 and G+-, Eq. B8":                            (13, 1),
+    "beam attenuation over a sub-layer, Eq. B6":              (2, 1),
+    "thermal sources, Eq. B4: shared Theta, chi + xi, Pi/chi": (5, 1),
+    "thermal sources, Eq. B4: two sub-layers x 10":           (20, 0),
+    "beam sources, Eq. B7: shared products over chi":         (8, 0),
+    "beam sources, Eq. B7: two sub-layers x 7":               (14, 0),
+    "elimination, Eqs. 13-14: two levels x 9, t^2 shared":    (19, 2),
+    "back-substitution, Eq. 15: two levels x 2":              (4, 0),
+    "spectral sum at the layer's interface (F_up, F_net)":    (4, 0),
+}
+ALG_BOA = (8, 1)   # Eq. 10 closure and the BOA interface's sums
+
+
+def algorithmic_ops_per_system(L: int):
+    """(FMA-pipe, MUFU) operations of one L-layer non-isothermal system."""
+    f = sum(v[0] for v in ALG_LAYER.values())
+    m = sum(v[1] for v in ALG_LAYER.values())
+    return L * f + ALG_BOA[0], L * m + ALG_BOA[1]
 
 
 def kernel_source_sha1():
@@ -516,23 +556,42 @@ def run_serving(args):
     """Config 4: Poisson arrivals (mean 200/s), requests of logU[1, 2562]
     columns x U{40..100} layers x U{30..300} bins x 20 g sliced from a
     device-resident pool; continuous batching over 8 stream slots, smallest
-    request first, one CTA per SM per batch, at most 2M systems per batch
-    (the best p99 of a sweep over slots, policy, CTAs per SM and batch cap)."""
+    request first, one CTA per SM per batch, at most 2M systems per batch,
+    requests above 2M systems cut into column pieces (the best p99 of a
+    sweep over slots, policy, CTAs per SM, batch cap and piece size).  The
+    FP64 plain path is served beside it at the rate it sustains, the same
+    request mix, 4 slots."""
     import torch
     import rt_synth
+    from paper_2203_02293_b300 import rt
     from paper_2203_02293_b300.serve import Pool, Server, make_requests
     pool = Pool(rt_synth, n_pool=2562, L_range=(40, 100), NB_range=(30, 300), n_g=20)
     n = int(args.serving_seconds * args.serving_rate)
     reqs = make_requests(pool, n, rate_hz=args.serving_rate, seed=4)
     warm = make_requests(pool, 8, rate_hz=1e3, seed=99)
-    knobs = dict(n_slots=8, policy="sjf", ctas_per_sm=1, max_systems_per_batch=2_000_000)
+    knobs = dict(n_slots=8, policy="sjf", ctas_per_sm=1, max_systems_per_batch=2_000_000,
+                 split_systems=2_000_000)
     srv = Server(pool, hbm_budget_bytes=32 << 30, **knobs)
     srv.run(warm)
     srv.batches = 0
     summ = srv.run(reqs)
     srv.close()
+    # lower bound on the slowest requests' latency: their layer-systems at
+    # the whole GPU's rate (the GCM step's solves/s x 40 layers)
+    work = np.array([r.systems * r.L for r in reqs], dtype=np.float64)
     summ.update({"rate_hz": args.serving_rate, "seconds_of_arrivals": args.serving_seconds,
-                 "unit_latency": "ms", "budget_bytes": 32 << 30, **knobs})
+                 "unit_latency": "ms", "budget_bytes": 32 << 30, "precision": "fp32 form", **knobs,
+                 "p99_request_layer_systems": float(np.percentile(work, 99))})
+    if args.serving_fp64_rate > 0:
+        n64 = int(args.serving_fp64_seconds * args.serving_fp64_rate)
+        reqs = make_requests(pool, n64, rate_hz=args.serving_fp64_rate, seed=44)
+        k64 = dict(n_slots=4, policy="sjf", max_systems_per_batch=2_000_000, split_systems=1_000_000)
+        srv = Server(pool, hbm_budget_bytes=32 << 30, precision=rt.RT_FP64_PLAIN, **k64)
+        s64 = srv.run(reqs)
+        srv.close()
+        s64.update({"rate_hz": args.serving_fp64_rate, "seconds_of_arrivals": args.serving_fp64_seconds,
+                    "unit_latency": "ms", "precision": "fp64 plain", **k64})
+        summ["fp64_plain"] = s64
     del pool
     torch.cuda.empty_cache()
     return summ
@@ -594,6 +653,9 @@ def main():
     ap.add_argument("--kernel-timing-steps", type=int, default=50)
     ap.add_argument("--serving-seconds", type=float, default=60.0)
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-fp64-rate", type=float, default=4.0,
+                    help="request rate of the FP64-plain serving arm (0: skip)")
+    ap.add_argument("--serving-fp64-seconds", type=float, default=20.0)
     ap.add_argument("--sweeps", default="10,200",
                     help="sweep counts of the iterative method timed beside Thomas (empty: skip)")
     ap.add_argument("--sweep-steps", type=int, default=20)
@@ -781,34 +843,35 @@ def main():
             max_mhz = json.load(f).get("sm_max_mhz", max_mhz)
     except OSError:
         pass
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     peak_tops = N_SM * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
-    ops_per_sys = float(prof["fp32_pipe_ops_per_system"]) if prof and "fp32_pipe_ops_per_system" in prof else None
-    if ops_per_sys:
-        # the FP32 pipes' bound: FMA-pipe operations per system (FFMA, FMUL
-        # and FADD one each, the paired forms two) over 148 SMs x 128 lanes
-        # x clock; FLOP/s (FFMA = 2) beside it
-        achieved_tops = ops_per_sys * n_sys / (ms_kernel * 1e-3) / 1e12
-        flop_per_sys = float(prof["flop_per_system"])
-        achieved_tf = flop_per_sys * n_sys / (ms_kernel * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
-                    "unit": "T FP32-pipe ops/s", "frac": achieved_tops / peak_tops,
-                    "traffic": float(prof["dram_bytes_per_launch"]),
-                    "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
-                    "kernel_ms_source": f"CUDA events around each launch, mean of {len(kt_solve)} solves",
-                    "fp32_pipe_ops_per_system": ops_per_sys,
-                    "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
-                    "flops": {"achieved": achieved_tf, "peak": peak_tflops, "unit": "TFLOP/s",
-                              "frac": achieved_tf / peak_tflops, "flop_per_system": flop_per_sys},
-                    "hbm": {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                            "frac": achieved_gbs / peak_gbs, "peak_source": peak_src,
-                            "algorithmic_bytes_per_launch": alg_bytes}}
+    peak_mufu = N_SM * MUFU_PER_SM_PER_CLK * max_mhz * 1e6 / 1e12
+    # the binding roofline of the solve kernel is the FP32 FMA pipe: its
+    # algorithmic operations (counted from the paper's equations, not from
+    # what the kernel executes) over 148 SMs x 128 lanes x clock; the MUFU
+    # and HBM bounds beside it are lower
+    alg_f, alg_m = algorithmic_ops_per_system(40)
+    achieved_tops = alg_f * n_sys / (ms_kernel * 1e-3) / 1e12
+    achieved_mufu = alg_m * n_sys / (ms_kernel * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
+                "unit": "T FP32-pipe ops/s", "frac": achieved_tops / peak_tops,
+                "traffic": float(prof["dram_bytes_per_launch"]) if prof else None,
+                "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
+                "kernel_ms_source": f"CUDA events around each launch, mean of {len(kt_solve)} solves",
+                "algorithmic_ops_per_system": {"fp32_pipe": alg_f, "mufu": alg_m,
+                                               "source": "paper's equations, per-equation table in bench.py"},
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock",
+                "bounds_ms": {"fp32_pipe": alg_f * n_sys / (peak_tops * 1e12) * 1e3,
+                              "mufu": alg_m * n_sys / (peak_mufu * 1e12) * 1e3,
+                              "hbm": alg_bytes / (peak_gbs * 1e9) * 1e3},
+                "mufu": {"achieved": achieved_mufu, "peak": peak_mufu, "unit": "T MUFU ops/s",
+                         "frac": achieved_mufu / peak_mufu},
+                "hbm": {"achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                        "frac": achieved_gbs / peak_gbs, "peak_source": peak_src,
+                        "algorithmic_bytes_per_launch": alg_bytes}}
+    if prof:
+        roofline["executed_fp32_pipe_ops_per_system"] = float(prof["fp32_pipe_ops_per_system"])
     else:
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                    "frac": achieved_gbs / peak_gbs, "traffic": None, "peak_source": peak_src,
-                    "kernel": "fp32_units", "kernel_ms": ms_kernel, "prep_kernel_ms": ms_prep,
-                    "algorithmic_bytes_per_launch": alg_bytes,
-                    "note": "no current ncu summary for this kernel source"}
+        roofline["traffic_note"] = "no ncu summary taken on the current kernel source"
     stats = s32.stats()
 
     # --- the iterative method (Sec. 2.2.2) beside Thomas on the same batch ---

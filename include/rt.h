@@ -189,6 +189,9 @@ typedef struct {
     int64_t invalid_inputs;      /* layer-systems with dtau < 0, w0 outside [0,1], |g0| >= 1, NaN */
     int64_t nonfinite_outputs;   /* systems whose fluxes came out non-finite */
     int64_t fp64_evals;          /* FP32 form: layer-systems whose resonance test ran in FP64 */
+    int64_t bounds_violations;   /* bounds-check build of the library (built with
+                                    RT_BOUNDS_CHECK): device accesses found outside
+                                    their array and skipped; always 0 otherwise */
 } rt_stats_t;
 
 /* Create a handle for the problem statement of Sec. 2.2 (the layer model,
@@ -317,11 +320,10 @@ void rt_destroy(rt_handle *h);
 
 /* ---------------------------------------------------------------------
  * Solve without allocating.  The paper has no counterpart: this entry point
- * exists for callers that cannot call cudaMalloc -- code that must remain
- * capturable into a CUDA graph while it runs, programs whose device memory
- * belongs to their own pool or to a framework that forbids raw allocations,
- * and loops that cannot take the device-wide synchronisation an allocation
- * may bring.
+ * exists for callers that cannot call cudaMalloc -- programs whose device
+ * memory belongs to their own pool or to a framework that forbids raw
+ * allocations, and loops that cannot take the device-wide synchronisation
+ * an allocation may bring.
  *
  * It runs the FP32 form (cfg->precision must be RT_FP32_FORM, uniform bins:
  * cfg->n_edges = 0) on a packed batch in which every column has the same shape (cols->n_layers, cols->n_bins
@@ -334,7 +336,19 @@ void rt_destroy(rt_handle *h);
  *   8 n_cols NB (L + 2) + 8 n_cols ceil(NB n_g / 32) (L + 1) + 16 L per
  *   resident thread (at least 64 threads)
  * bytes; a batch that does not fit returns RT_EBUDGET and nothing runs.
+ * Element counts given in cols must cover the packed batch (RT_EINVAL).
  * No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Fixed launch choices: one system per GPU lane (the regular entry point
+ * defaults to two), the Planck values tabulated by the pre-kernel and staged
+ * per warp in shared memory, Thomas's algorithm (n_sweeps must be 0).
+ * cfg->block_threads caps the CTA size; systems_per_lane, planck_staging,
+ * ctas_per_sm, hbm_budget_bytes, kernel_timing, max_layers and max_bins are
+ * ignored.  The elimination scratch shares the fixed array with the
+ * per-column tables, so it caps the resident threads: at the 2562-column GCM
+ * shape (2562 x 40 x 30 x 20) about one 256-thread CTA per SM runs, roughly
+ * a third of the warps rt_solve_columns keeps resident, and the solve takes
+ * several times longer than rt_solve_columns.
  *
  * The first call on a device looks up the array's device address and sets the
  * kernels' shared-memory limits; make that first call before any stream

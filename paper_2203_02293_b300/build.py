@@ -7,6 +7,9 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "librt.so")
+# the same library with every main device-memory access range-checked
+# (RT_BOUNDS_CHECK): out-of-range accesses are counted and skipped
+LIB_BOUNDS = os.path.join(HERE, "librt_bounds.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("rt_kernels.cu", "rt_api.cpp", "rt_noalloc.cu")]
 HEADERS = [os.path.join(HERE, "csrc", "rt_internal.h"), os.path.join(ROOT, "include", "rt.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -30,5 +33,11 @@ def build(lib: str = LIB, extra: list[str] | None = None, verbose: bool = False)
     return lib
 
 
+def build_bounds(lib: str = LIB_BOUNDS) -> str:
+    """The bounds-check variant of the library."""
+    return build(lib, extra=["-DRT_BOUNDS_CHECK"])
+
+
 if __name__ == "__main__":
     print(build(verbose=True))
+    print(build_bounds())

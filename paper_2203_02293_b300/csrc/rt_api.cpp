@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -719,7 +720,29 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
             kp.kt_nP = h->kt_nP;
             kp.kt_lay = d_klay;
         }
+        // array extents (read by bounds-check builds only)
+        kp.ext.cube = cols->n_cube > 0 ? cols->n_cube : P.n_cube;
+        kp.ext.center = cols->n_center > 0 ? cols->n_center : P.n_lay;
+        kp.ext.iface = cols->n_iface > 0 ? cols->n_iface : P.n_if;
+        kp.ext.fstar = cols->n_fstar > 0 ? cols->n_fstar : P.n_bins;
+        kp.ext.mu = cols->n_mu > 0 ? cols->n_mu : n;
+        kp.ext.scr32 = cfg.precision == RT_FP64_PLAIN ? 0 : P.n_slots * (long long)P.Lmax;
+        kp.ext.scr64 = cfg.precision == RT_FP64_PLAIN
+                           ? (long long)(P.scr_bytes / sizeof(double2)) : 0;
+        kp.ext.scrB = P.inline_b ? P.n_slots * (long long)P.Lmax : 0;
+        kp.ext.part = P.n_part;
+        kp.ext.planck = P.n_planck;
+        kp.ext.bins = P.n_bins;
+        kp.ext.cols = n;
+        kp.ext.out_if = P.n_if;
+        kp.ext.out_lay = P.n_lay;
+#ifdef RT_BOUNDS_CHECK
+        // test hook of the checking build: a smaller declared cube extent
+        // (the reads past it stay inside the real arrays and are skipped)
+        if (const char *sh = getenv("RT_BOUNDS_TEST_CUBE_EXTENT")) kp.ext.cube = atoll(sh);
+#endif
         if (optics_out) {
+            kp.ext.cube = P.n_cube;                  // the packed output cubes
             e = rt::launch_kt_optics(kp, d_cube, optics_out[0], optics_out[1], optics_out[2], s);
             if (e != cudaSuccess) return cuda_fail(h, e, "front-end launch");
             return RT_OK;
@@ -734,6 +757,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
             kp.dtau = cd;
             kp.w0 = cw;
             kp.g0 = cg;
+            kp.ext.cube = P.n_cube;
             kp.kt_lk = nullptr;
         }
         const bool timing = cfg.kernel_timing && !cap;
@@ -1005,6 +1029,7 @@ int rt_stats(rt_handle *h, rt_stats_t *out) {
     out->invalid_inputs = (int64_t)v[rt::ST_INVALID];
     out->nonfinite_outputs = (int64_t)v[rt::ST_NONFINITE];
     out->fp64_evals = (int64_t)v[rt::ST_FP64];
+    out->bounds_violations = (int64_t)v[rt::ST_BOUNDS];
     return RT_OK;
 }
 

@@ -13,7 +13,17 @@ enum StatIdx {
     ST_INVALID = 3,
     ST_NONFINITE = 4,
     ST_FP64 = 5,
+    ST_BOUNDS = 6,   // bounds-check builds: accesses found outside their array (and skipped)
     ST_COUNT = 8
+};
+
+// Element counts of every array the kernels index, for the bounds-check
+// build (RT_BOUNDS_CHECK); unused otherwise.
+struct Extents {
+    long long cube, center, iface, fstar, mu;   // caller inputs
+    long long scr32, scr64, scrB;               // elimination scratch (float4, double2, float units)
+    long long part, planck, bins, cols;         // unit partials, Planck table, per-bin and per-column staging
+    long long out_if, out_lay;                  // outputs
 };
 
 struct KParams {
@@ -81,6 +91,7 @@ struct KParams {
     int32_t n_sweeps;            // 0: Thomas elimination; N > 0: N sweeps of the iterative method
     int32_t Lmax;                // largest L in this batch
     int32_t nb_chunk;            // bins covered by one chunk of systems (smem sizing)
+    Extents ext;                 // array extents (checked in bounds-check builds)
 };
 
 // Shared memory needed per CTA for a given block size (bytes).

@@ -174,6 +174,34 @@ __device__ double planck_bin_d(double T, double wlo, double whi) {
 }
 
 // ---------------------------------------------------------------------
+// Bounds-check build (RT_BOUNDS_CHECK): a pointer outside [base, base + n)
+// of its array is counted in stats[ST_BOUNDS] and the access is skipped (a
+// load gives 0).  Nothing traps.  In the normal build the check is the
+// constant true and adds no code.
+// ---------------------------------------------------------------------
+#ifdef RT_BOUNDS_CHECK
+template <class T, class U>
+__device__ __forceinline__ bool rt_in_range(const T *p, const U *base, long long n, unsigned long long *stats) {
+    const char *c = reinterpret_cast<const char *>(p), *b = reinterpret_cast<const char *>(base);
+    const bool ok = base != nullptr && c >= b && c + sizeof(T) <= b + n * (long long)sizeof(U);
+    if (!ok) atomicAdd(stats + ST_BOUNDS, 1ull);
+    return ok;
+}
+#define RT_IN(p, base, n) rt_in_range((p), (base), (long long)(n), kp.stats)
+#else
+#define RT_IN(p, base, n) true
+#endif
+// base[i] of an array of n elements; a store to it (both checked in bounds builds)
+template <class T>
+__device__ __forceinline__ T ck_ld(const KParams &kp, const T *base, long long n, long long i) {
+    return RT_IN(base + i, base, n) ? base[i] : T{};
+}
+template <class T>
+__device__ __forceinline__ void ck_st(const KParams &kp, T *base, long long n, long long i, T v) {
+    if (RT_IN(base + i, base, n)) base[i] = v;
+}
+
+// ---------------------------------------------------------------------
 // Counters kept in registers and flushed once per CTA.
 // ---------------------------------------------------------------------
 struct Counters {
@@ -632,7 +660,7 @@ __device__ __forceinline__ bool next_column(const KParams &kp, int *s_unit, ColI
     ci.tc_in = kp.tc_off[ci.c];
     ci.if_in = kp.if_off[ci.c];
     ci.fs_in = kp.fs_off[ci.c];
-    ci.mu = kp.mu_star[kp.mu_idx[ci.c]];
+    ci.mu = ck_ld(kp, kp.mu_star, kp.ext.mu, kp.mu_idx[ci.c]);
     return true;
 }
 
@@ -646,12 +674,13 @@ __device__ __forceinline__ void stage_planck(const KParams &kp, const ColInfo &c
     static_assert(sizeof(R) == 8, "the FP32 form stages B in fp32_units");
     for (int i = threadIdx.x; i < nlev * nbc; i += blockDim.x) {
         const int lev = i / nbc, bb = i - lev * nbc, b = b_lo + bb;
-        const double T = (lev & 1) ? kp.T_center[ci.tc_in + (lev >> 1)] : kp.T_iface[ci.if_in + (lev >> 1)];
+        const double T = (lev & 1) ? ck_ld(kp, kp.T_center, kp.ext.center, ci.tc_in + (lev >> 1))
+                                   : ck_ld(kp, kp.T_iface, kp.ext.iface, ci.if_in + (lev >> 1));
         sm.sB[i] = planck_bin_d(T, edge(b), edge(b + 1));
     }
     for (int bb = threadIdx.x; bb < nbc; bb += blockDim.x) {
         const int b = b_lo + bb;
-        sm.sFs[bb] = (R)kp.F_star[ci.fs_in + b];
+        sm.sFs[bb] = (R)ck_ld(kp, kp.F_star, kp.ext.fstar, ci.fs_in + b);
         sm.sFB[bb] = kPi * planck_bin_d(kp.T_int, edge(b), edge(b + 1));
     }
 }
@@ -690,15 +719,16 @@ __device__ __forceinline__ void fold_warps(int L, int nwarps, Smem<R> &sm) {
 __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &ci, const double *acc) {
     for (int i = threadIdx.x; i <= ci.L; i += blockDim.x) {
         const double up = acc[2 * i], net = acc[2 * i + 1];
-        kp.F_up[ci.if0 + i] = up;
-        kp.F_net[ci.if0 + i] = net;
-        kp.F_dn[ci.if0 + i] = up - net;
+        ck_st(kp, kp.F_up, kp.ext.out_if, ci.if0 + i, up);
+        ck_st(kp, kp.F_net, kp.ext.out_if, ci.if0 + i, net);
+        ck_st(kp, kp.F_dn, kp.ext.out_if, ci.if0 + i, up - net);
     }
     const double gc = kp.grav / kp.cp;
     for (int l = threadIdx.x; l < ci.L; l += blockDim.x) {
         const double dF = acc[2 * (l + 1) + 1] - acc[2 * l + 1];
-        const double dp = kp.p_iface[ci.if_in + l + 1] - kp.p_iface[ci.if_in + l];
-        kp.Q[ci.lay0 + l] = gc * dF / dp;
+        const double dp = ck_ld(kp, kp.p_iface, kp.ext.iface, ci.if_in + l + 1) -
+                          ck_ld(kp, kp.p_iface, kp.ext.iface, ci.if_in + l);
+        ck_st(kp, kp.Q, kp.ext.out_lay, ci.lay0 + l, gc * dF / dp);
     }
 }
 
@@ -982,8 +1012,10 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         __syncthreads();                          // previous column done with sT
         for (int lev = threadIdx.x; lev <= nlev; lev += blockDim.x)
             sT[lev] = lev == nlev ? (float)kp.T_int
-                                  : (float)((lev & 1) ? kp.T_center[tc0 + (lev >> 1)] : kp.T_iface[ifi + (lev >> 1)]);
-        for (int b = threadIdx.x; b < NB; b += blockDim.x) kp.fs32[b0 + b] = (float)kp.F_star[fsi + b];
+                                  : (float)((lev & 1) ? ck_ld(kp, kp.T_center, kp.ext.center, tc0 + (lev >> 1))
+                                                      : ck_ld(kp, kp.T_iface, kp.ext.iface, ifi + (lev >> 1)));
+        for (int b = threadIdx.x; b < NB; b += blockDim.x)
+            ck_st(kp, kp.fs32, kp.ext.bins, b0 + b, (float)ck_ld(kp, kp.F_star, kp.ext.fstar, fsi + b));
         __syncthreads();
         if (warp == 0) {
             // the coldest level (largest h c / k T) bounds every level's bin
@@ -1000,8 +1032,8 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
             if (lane == 0) {
-                const double mu = kp.mu_star[kp.mu_idx[c]];
-                kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f,
+                const double mu = ck_ld(kp, kp.mu_star, kp.ext.mu, kp.mu_idx[c]);
+                if (RT_IN(kp.colf + c, kp.colf, kp.ext.cols)) kp.colf[c] = make_float4((float)mu, mu > 0.0 ? (float)(1.0 / mu) : 0.f, mu > 0.0 ? 1.f : 0.f,
                                          ok ? tmin : 0.f);
             }
         }
@@ -1009,9 +1041,10 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
         // then overlap the Planck tasks of the other warps
         if (kp.kt_lk)
             for (int l = threadIdx.x; l < L; l += blockDim.x)
-                kp.kt_lay[kp.lay_off[c] + l] =
-                    kt_layer(kp, sG, sG + kp.kt_nT, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
-                             NB * kp.n_g);
+                ck_st(kp, kp.kt_lay, kp.ext.out_lay, kp.lay_off[c] + l,
+                      kt_layer(kp, sG, sG + kp.kt_nT, ck_ld(kp, kp.T_center, kp.ext.center, tc0 + l),
+                               ck_ld(kp, kp.p_iface, kp.ext.iface, ifi + l),
+                               ck_ld(kp, kp.p_iface, kp.ext.iface, ifi + l + 1), NB * kp.n_g));
         const int nchunk = (NB + 30) / 31;
         // levels [lev0, nlev]: the 2L+1 levels, then T_int (T_int alone when
         // the solve kernel evaluates B itself)
@@ -1037,7 +1070,7 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
                 planck_chunk_levels<4>(Tq, sq, wq, dq, iq, vq);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (iq[q]) kp.fboa32[b0 + (t0 + q) * 31 + lane] = vq[q];
+                    if (iq[q]) ck_st(kp, kp.fboa32, kp.ext.bins, b0 + (t0 + q) * 31 + lane, vq[q]);
             }
         } else
         for (int task = warp; task < nchunk * nrun; task += nw) {
@@ -1050,8 +1083,8 @@ __global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
             // four levels per pass (independent evaluation chains), then one at a time
             auto store = [&](int lq, float v) {
                 if (inb) {
-                    if (lq == nlev) kp.fboa32[b0 + bin] = v;
-                    else B[(long long)lq * NB + bin] = v;
+                    if (lq == nlev) ck_st(kp, kp.fboa32, kp.ext.bins, b0 + bin, v);
+                    else if (RT_IN(B + (long long)lq * NB + bin, kp.planck32, kp.ext.planck)) B[(long long)lq * NB + bin] = v;
                 }
             };
             int lev = r0;
@@ -1088,20 +1121,24 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     // unit partials are read through L2 (other SMs wrote them)
     auto sum = [&](int i, int qq) {
         double a = 0.0;
-        for (int uidx = 0; uidx < nu; ++uidx) a += (double)__ldcg(part + (long long)uidx * stride + 2 * i + qq);
+        for (int uidx = 0; uidx < nu; ++uidx) {
+            const float *pp = part + (long long)uidx * stride + 2 * i + qq;
+            a += RT_IN(pp, kp.partial, kp.ext.part) ? (double)__ldcg(pp) : 0.0;
+        }
         return a;
     };
     for (int i = lane; i <= L; i += 32) {
         const double up = sum(i, 0), net = sum(i, 1);
-        kp.F_up[if0 + i] = up;
-        kp.F_net[if0 + i] = net;
-        kp.F_dn[if0 + i] = up - net;
+        ck_st(kp, kp.F_up, kp.ext.out_if, if0 + i, up);
+        ck_st(kp, kp.F_net, kp.ext.out_if, if0 + i, net);
+        ck_st(kp, kp.F_dn, kp.ext.out_if, if0 + i, up - net);
     }
     const float gc = (float)(kp.grav / kp.cp);
     for (int l = lane; l < L; l += 32) {
         const double dF = sum(l + 1, 1) - sum(l, 1);
-        const float dp = (float)(kp.p_iface[kp.if_off[c] + l + 1] - kp.p_iface[kp.if_off[c] + l]);
-        kp.Q[kp.lay_off[c] + l] = (double)(gc * (float)dF * frcp(dp));
+        const float dp = (float)(ck_ld(kp, kp.p_iface, kp.ext.iface, kp.if_off[c] + l + 1) -
+                                 ck_ld(kp, kp.p_iface, kp.ext.iface, kp.if_off[c] + l));
+        ck_st(kp, kp.Q, kp.ext.out_lay, kp.lay_off[c] + l, (double)(gc * (float)dF * frcp(dp)));
     }
 }
 
@@ -1119,6 +1156,12 @@ __device__ __forceinline__ float ldB(const float *p) {
     if constexpr (DIRECT) return __ldg(p);
     else return *p;
 }
+// the same, with DIRECT reads checked against the table in bounds-check builds
+template <bool DIRECT>
+__device__ __forceinline__ float ldBk(const KParams &kp, const float *p) {
+    if constexpr (DIRECT) return RT_IN(p, kp.planck32, kp.ext.planck) ? __ldg(p) : 0.f;
+    else return *p;
+}
 
 // Invalidate the 128-byte L2 line at p (128-byte aligned) without writing it
 // back.  `after` is a value loaded from that line: the compare that reads it
@@ -1133,12 +1176,13 @@ __device__ __forceinline__ void discard_l2_after(const void *p, float after) {
 // Elimination scratch of one interface: (P, Q, alpha', e) of one system in a
 // float4; for a lane with two systems, (P, Q) of both and (alpha', e) of
 // both in two float4 (component pairs stay in their register pairs).
-__device__ __forceinline__ void scr_store(float4 *sp, long long, float P, float Q, float a, float e) {
-    __stcg(sp, make_float4(P, Q, a, e));
+__device__ __forceinline__ void scr_store(const KParams &kp, float4 *sp, long long, float P, float Q, float a,
+                                          float e) {
+    if (RT_IN(sp, kp.scr32, kp.ext.scr32)) __stcg(sp, make_float4(P, Q, a, e));
 }
-__device__ __forceinline__ void scr_store(float4 *sp, long long other, V2 P, V2 Q, V2 a, V2 e) {
-    __stcg(sp, make_float4(P.v.x, P.v.y, Q.v.x, Q.v.y));
-    __stcg(sp + other, make_float4(a.v.x, a.v.y, e.v.x, e.v.y));
+__device__ __forceinline__ void scr_store(const KParams &kp, float4 *sp, long long other, V2 P, V2 Q, V2 a, V2 e) {
+    if (RT_IN(sp, kp.scr32, kp.ext.scr32)) __stcg(sp, make_float4(P.v.x, P.v.y, Q.v.x, Q.v.y));
+    if (RT_IN(sp + other, kp.scr32, kp.ext.scr32)) __stcg(sp + other, make_float4(a.v.x, a.v.y, e.v.x, e.v.y));
 }
 __device__ __forceinline__ void scr_unpack(const float4 *n, float &P, float &Q, float &a, float &e) {
     P = n[0].x;
@@ -1203,12 +1247,14 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         if constexpr (!DIRECT) {
             for (int i = lane; i < nlev * nbc; i += 32) {
                 const int lev = i / nbc, bb = i - lev * nbc;
-                sB[i] = __ldcg(Bg + (long long)lev * NB + bb);
+                const float *pb = Bg + (long long)lev * NB + bb;
+                sB[i] = RT_IN(pb, kp.planck32, kp.ext.planck) ? __ldcg(pb) : 0.f;
             }
         }
         for (int j = lane; j < nbc; j += 32) {
-            sFs[j] = __ldcg(kp.fs32 + kp.bin_off[c] + b_lo + j);
-            sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[c] + b_lo + j);
+            const long long jb = kp.bin_off[c] + b_lo + j;
+            sFs[j] = RT_IN(kp.fs32 + jb, kp.fs32, kp.ext.bins) ? __ldcg(kp.fs32 + jb) : 0.f;
+            sFB[j] = RT_IN(kp.fboa32 + jb, kp.fboa32, kp.ext.bins) ? __ldcg(kp.fboa32 + jb) : 0.f;
         }
     }
     __syncwarp();
@@ -1227,7 +1273,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     V wn0v, wn1v, dnuv;
     bool unit_narrow = false;                  // INL: the unit's bins take two points at every level
     auto B_at = [&](int lev, V &B) {           // B of the lane's systems at level lev
-        const double Td = (lev & 1) ? __ldg(kp.T_center + tc0 + (lev >> 1)) : __ldg(kp.T_iface + ifi + (lev >> 1));
+        const double *pT = (lev & 1) ? kp.T_center + tc0 + (lev >> 1) : kp.T_iface + ifi + (lev >> 1);
+        const double Td = RT_IN(pT, (lev & 1) ? kp.T_center : kp.T_iface, (lev & 1) ? kp.ext.center : kp.ext.iface)
+                              ? __ldg(pT) : 0.0;
         const PlanckLevel lv = planck_level((float)Td, 1.f);
         // narrow bins that take two quadrature points (the R = 500 shape):
         // the lane's systems together on the paired instructions; any other
@@ -1271,9 +1319,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             }
         } else {
             // the B of a layer's bottom interface is carried as the next layer's top
-            cmp(Bt, i) = ldB<DIRECT>(Bp[i]);
-            cmp(Bc, i) = ldB<DIRECT>(Bp[i] + bst);
-            cmp(Bb, i) = ldB<DIRECT>(Bp[i] + 2 * bst);
+            cmp(Bt, i) = ldBk<DIRECT>(kp, Bp[i]);
+            cmp(Bc, i) = ldBk<DIRECT>(kp, Bp[i] + bst);
+            cmp(Bb, i) = ldBk<DIRECT>(kp, Bp[i] + 2 * bst);
         }
     }
     if constexpr (INL) {
@@ -1331,9 +1379,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             pd[i] = kp.dtau + e;
             pw[i] = kp.w0 + e;
             pg[i] = kp.g0 + e;
-            cmp(nd, i) = __ldcs(pd[i]);
-            cmp(nw, i) = __ldcs(pw[i]);
-            cmp(ng, i) = __ldcs(pg[i]);
+            cmp(nd, i) = RT_IN(pd[i], kp.dtau, kp.ext.cube) ? __ldcs(pd[i]) : 0.f;
+            cmp(nw, i) = RT_IN(pw[i], kp.w0, kp.ext.cube) ? __ldcs(pw[i]) : 0.f;
+            cmp(ng, i) = RT_IN(pg[i], kp.g0, kp.ext.cube) ? __ldcs(pg[i]) : 0.f;
         }
     }
     float4 *sp = kp.scr32 + slot;
@@ -1375,9 +1423,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
                     pd[i] += S;
                     pw[i] += S;
                     pg[i] += S;
-                    cmp(nd, i) = __ldcs(pd[i]);
-                    cmp(nw, i) = __ldcs(pw[i]);
-                    cmp(ng, i) = __ldcs(pg[i]);
+                    cmp(nd, i) = RT_IN(pd[i], kp.dtau, kp.ext.cube) ? __ldcs(pd[i]) : 0.f;
+                    cmp(nw, i) = RT_IN(pw[i], kp.w0, kp.ext.cube) ? __ldcs(pw[i]) : 0.f;
+                    cmp(ng, i) = RT_IN(pg[i], kp.g0, kp.ext.cube) ? __ldcs(pg[i]) : 0.f;
                 }
             }
 
@@ -1389,13 +1437,13 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             } else {
 #pragma unroll
                 for (int i = 0; i < NS; ++i) {
-                    cmp(nBc, i) = ldB<DIRECT>(Bp[i] + 3 * bst);
-                    cmp(nBb, i) = ldB<DIRECT>(Bp[i] + 4 * bst);
+                    cmp(nBc, i) = ldBk<DIRECT>(kp, Bp[i] + 3 * bst);
+                    cmp(nBb, i) = ldBk<DIRECT>(kp, Bp[i] + 4 * bst);
                 }
             }
         }
         if constexpr (INL) {
-            stB(spB, Bt);                         // B at interface l, for the back-substitution
+            if (RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS)) stB(spB, Bt);   // B at interface l, for the back-substitution
             spB += gthreads;
         }
 #pragma unroll
@@ -1408,7 +1456,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         const V ipv = vrcp(vfma(ly.R, al, omr));           // 1 / (1 - R a')
         const V P = ly.T * ipv;
         const V Qv = vfma(ly.R, bl, ly.Su) * ipv;
-        scr_store(sp, gthreads, P, Qv, al, bl + Fb);      // e = b' + F_beam
+        scr_store(kp, sp, gthreads, P, Qv, al, bl + Fb);  // e = b' + F_beam
         sp += sstride;
         const V al_n = vfma(al, vfma(ly.R, omr, ly.T * ly.T), ly.omtr * ly.opr) * ipv;
         const V bl_n = vfma(ly.T * vfma(V(1.f) - al, ly.Su, bl), ipv, ly.Sd);
@@ -1436,17 +1484,18 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     V nBi;                   // Bp is at level 2L; prefetch one interface up
     if constexpr (INL) {
         spB -= gthreads;     // interface L-1
-        nBi = ldB_cg(spB);
+        nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
     } else {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldB<DIRECT>(Bp[i] - 2 * bst);
+        for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldBk<DIRECT>(kp, Bp[i] - 2 * bst);
     }
     int gi = 1;              // slots used in the current group of 16 interfaces
     int gtop = L;            // interface held in slot 0 of the group
     sp -= sstride;           // interface L-1
     float4 nst[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) nst[i] = __ldcg(sp + i * gthreads);
+    for (int i = 0; i < NS; ++i)
+        nst[i] = RT_IN(sp + i * gthreads, kp.scr32, kp.ext.scr32) ? __ldcg(sp + i * gthreads) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = L - 1; i >= -1; --i) {
         if (i >= 0) {
             V Pv, Qq, av, ev;
@@ -1455,24 +1504,28 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             for (int j = 0; j < NS; ++j) {
                 // this level's scratch is dead once read: drop its L2
                 // lines (one per 8 lanes) so they are not written back
-                if ((lane & 7) == 0) discard_l2_after(sp + j * gthreads, nst[j].x);
+                if ((lane & 7) == 0 && RT_IN(sp + j * gthreads, kp.scr32, kp.ext.scr32))
+                    discard_l2_after(sp + j * gthreads, nst[j].x);
             }
             const V Bi = nBi;
             if constexpr (INL) {
-                if ((lane & (32 / NS - 1)) == 0) discard_l2_after(spB, cmp(nBi, 0));
+                if ((lane & (32 / NS - 1)) == 0 && RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS))
+                    discard_l2_after(spB, cmp(nBi, 0));
             }
 #pragma unroll
             for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
             if (i > 0) {
                 sp -= sstride;
 #pragma unroll
-                for (int j = 0; j < NS; ++j) nst[j] = __ldcg(sp + j * gthreads);
+                for (int j = 0; j < NS; ++j)
+                    nst[j] = RT_IN(sp + j * gthreads, kp.scr32, kp.ext.scr32) ? __ldcg(sp + j * gthreads)
+                                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
                 if constexpr (INL) {
                     spB -= gthreads;
-                    nBi = ldB_cg(spB);
+                    nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldB<DIRECT>(Bp[j] - 2 * bst);
+                    for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldBk<DIRECT>(kp, Bp[j] - 2 * bst);
                 }
             }
             uu = vfma(Pv, uu, Qq);
@@ -1492,7 +1545,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
                 float acc = 0.f;
 #pragma unroll 8
                 for (int j = 0; j < 32; ++j) acc += row[j];
-                part[2 * (gtop - sl) + qq] = acc;
+                if (RT_IN(part + 2 * (gtop - sl) + qq, kp.partial, kp.ext.part)) part[2 * (gtop - sl) + qq] = acc;
             }
             __syncwarp();
             gtop -= gi;
@@ -1518,7 +1571,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             const int j1 = min(min(SPU, S - s0), (bt + 1) * NG - s0);
             float acc = 0.f;
             for (int j = j0; j < j1; ++j) acc += tb[j];
-            atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
+            if (RT_IN(kp.toa + kp.bin_off[c] + bt, kp.toa, kp.ext.bins)) atomicAdd(kp.toa + kp.bin_off[c] + bt, (double)acc);
         }
         __syncwarp();
     }
@@ -1526,7 +1579,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     // the warp that completes a column's last unit writes the column
     __threadfence();
     int done = 0;
-    if (lane == 0) done = atomicAdd(kp.col_done + c, 1);
+    if (lane == 0 && RT_IN(kp.col_done + c, kp.col_done, kp.ext.cols)) done = atomicAdd(kp.col_done + c, 1);
     done = __shfl_sync(0xffffffffu, done, 0);
     if (done == kp.col_units[c] - 1) {
         __threadfence();
@@ -1762,18 +1815,20 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
             if constexpr (!DIRECT) {
                 for (int i = lane; i < nlev * q.nbc; i += 32) {
                     const int lev = i / q.nbc, bb = i - lev * q.nbc;
-                    sB[i] = __ldcg(Bg + (long long)lev * q.NB + bb);
+                    const float *pb = Bg + (long long)lev * q.NB + bb;
+                    sB[i] = RT_IN(pb, kp.planck32, kp.ext.planck) ? __ldcg(pb) : 0.f;
                 }
             }
             for (int j = lane; j < q.nbc; j += 32) {
-                sFs[j] = __ldcg(kp.fs32 + kp.bin_off[q.c] + q.b_lo + j);
-                sFB[j] = __ldcg(kp.fboa32 + kp.bin_off[q.c] + q.b_lo + j);
+                const long long jb = kp.bin_off[q.c] + q.b_lo + j;
+                sFs[j] = RT_IN(kp.fs32 + jb, kp.fs32, kp.ext.bins) ? __ldcg(kp.fs32 + jb) : 0.f;
+                sFB[j] = RT_IN(kp.fboa32 + jb, kp.fboa32, kp.ext.bins) ? __ldcg(kp.fboa32 + jb) : 0.f;
             }
         }
         __syncwarp();
         const float4 cf = kp.colf[q.c];
         const float mu = cf.x, imu = cf.y;
-        const double mu_d = kp.mu_star[kp.mu_idx[q.c]];
+        const double mu_d = ck_ld(kp, kp.mu_star, kp.ext.mu, kp.mu_idx[q.c]);
         const bool beam = cf.z != 0.f;
         float Fb = beam ? mu * sFs[q.bI - q.b_lo] : 0.f;
         const float FBOA = sFB[q.bI - q.b_lo];
@@ -1783,8 +1838,10 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
         float2 *TR2 = reinterpret_cast<float2 *>(TR);
         const long long e0 = kp.cube_off[q.c] + (q.on ? q.s0 + lane : q.s0);
         const float *pd = kp.dtau + e0, *pw = kp.w0 + e0, *pg = kp.g0 + e0;
-        float nd = __ldcs(pd), nw = __ldcs(pw), ng = __ldcs(pg);   // next layer prefetched
-        float Bt = ldB<DIRECT>(q.Bp);
+        float nd = RT_IN(pd, kp.dtau, kp.ext.cube) ? __ldcs(pd) : 0.f;   // next layer prefetched
+        float nw = RT_IN(pw, kp.w0, kp.ext.cube) ? __ldcs(pw) : 0.f;
+        float ng = RT_IN(pg, kp.g0, kp.ext.cube) ? __ldcs(pg) : 0.f;
+        float Bt = ldBk<DIRECT>(kp, q.Bp);
         d0 = fmaf(-kPiF, Bt, (float)kp.F_toa);                     // d at the TOA level
         for (int l = 0; l < L; ++l) {
             const float dt = nd, w0 = nw, g0 = ng;
@@ -1792,11 +1849,12 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
                 pd += q.S;
                 pw += q.S;
                 pg += q.S;
-                nd = __ldcs(pd);
-                nw = __ldcs(pw);
-                ng = __ldcs(pg);
+                nd = RT_IN(pd, kp.dtau, kp.ext.cube) ? __ldcs(pd) : 0.f;
+                nw = RT_IN(pw, kp.w0, kp.ext.cube) ? __ldcs(pw) : 0.f;
+                ng = RT_IN(pg, kp.g0, kp.ext.cube) ? __ldcs(pg) : 0.f;
             }
-            const float Bc = ldB<DIRECT>(q.Bp + (2 * l + 1) * q.bst), Bb = ldB<DIRECT>(q.Bp + (2 * l + 2) * q.bst);
+            const float Bc = ldBk<DIRECT>(kp, q.Bp + (2 * l + 1) * q.bst);
+            const float Bb = ldBk<DIRECT>(kp, q.Bp + (2 * l + 2) * q.bst);
             float fw = q.wg * Fb;                                  // interface l: warp sum of w F_beam
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
@@ -1836,7 +1894,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
 #pragma unroll
         for (int j = 0; j < NLV; ++j) {
             const int lev = ISO ? 2 * j : j;                       // level in the B table
-            X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldB<DIRECT>(q.Bp + min(lev, 2 * L) * q.bst) : 0.f;
+            X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldBk<DIRECT>(kp, q.Bp + min(lev, 2 * L) * q.bst) : 0.f;
         }
         __syncwarp();                                              // (t, r) area free for the output rows
     }
@@ -1864,7 +1922,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     if (lane == 0 && bad) atomicAdd(kp.stats + ST_NONFINITE, (unsigned long long)__popc(bad));
     // weighted fluxes: F_up = pi B + u; F_net + F_beam = u - d
     for (int i = 0; i <= L; ++i) {
-        const float Bi = ldB<DIRECT>(q.Bp + 2 * i * q.bst);
+        const float Bi = ldBk<DIRECT>(kp, q.Bp + 2 * i * q.bst);
         TR[out_idx(2 * i, lane)] = q.wg * fmaf(kPiF, Bi, TR[out_idx(2 * i, lane)]);
         TR[out_idx(2 * i + 1, lane)] *= q.wg;
     }
@@ -1876,7 +1934,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
 #pragma unroll 8
         for (int j = 0; j < 32; ++j) acc += TR[out_idx(row, j)];
         if (row & 1) acc -= fbs[row >> 1];
-        part[row] = acc;
+        if (RT_IN(part + row, kp.partial, kp.ext.part)) part[row] = acc;
     }
     // TOA spectrum: row 0 holds w F_up at the TOA per system
     if (kp.toa) {
@@ -1887,7 +1945,8 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
             const int j1 = min(min(32, q.S - q.s0), (bt + 1) * NG - q.s0);
             float acc = 0.f;
             for (int j = j0; j < j1; ++j) acc += TR[out_idx(0, j)];
-            atomicAdd(kp.toa + kp.bin_off[q.c] + bt, (double)acc);
+            if (RT_IN(kp.toa + kp.bin_off[q.c] + bt, kp.toa, kp.ext.bins))
+                atomicAdd(kp.toa + kp.bin_off[q.c] + bt, (double)acc);
         }
     }
     __syncwarp();
@@ -1895,7 +1954,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     // the warp that completes a column's last unit writes the column
     __threadfence();
     int done = 0;
-    if (lane == 0) done = atomicAdd(kp.col_done + q.c, 1);
+    if (lane == 0 && RT_IN(kp.col_done + q.c, kp.col_done, kp.ext.cols)) done = atomicAdd(kp.col_done + q.c, 1);
     done = __shfl_sync(0xffffffffu, done, 0);
     if (done == kp.col_units[q.c] - 1) {
         __threadfence();
@@ -2063,9 +2122,9 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
                 float w0f = 0.f, g0f = 0.f;
                 if (active) {
                     const long long idx = base + (long long)l * ci.S;
-                    dt = (double)__ldg(kp.dtau + idx);
-                    w0f = __ldg(kp.w0 + idx);
-                    g0f = __ldg(kp.g0 + idx);
+                    dt = RT_IN(kp.dtau + idx, kp.dtau, kp.ext.cube) ? (double)__ldg(kp.dtau + idx) : 0.0;
+                    w0f = RT_IN(kp.w0 + idx, kp.w0, kp.ext.cube) ? __ldg(kp.w0 + idx) : 0.f;
+                    g0f = RT_IN(kp.g0 + idx, kp.g0, kp.ext.cube) ? __ldg(kp.g0 + idx) : 0.f;
                     w0 = (double)w0f;
                     g0 = (double)g0f;
                 }
@@ -2095,8 +2154,8 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
                     st0.y = (sb.r * bv + sb.su) / piv;             // Q
                     st1.x = a;
                     st1.y = bv + Fb;                               // b + F_beam at the top level
-                    scr[(long long)(2 * lev) * kp.n_slots] = st0;
-                    scr[(long long)(2 * lev + 1) * kp.n_slots] = st1;
+                    ck_st(kp, scr, kp.ext.scr64 - slot, (long long)(2 * lev) * kp.n_slots, st0);
+                    ck_st(kp, scr, kp.ext.scr64 - slot, (long long)(2 * lev + 1) * kp.n_slots, st1);
                     const double a_n = sb.r + sb.t * sb.t * a / piv;
                     const double b_n = sb.sd + sb.t * (bv + a * sb.su) / piv;
                     a = a_n;
@@ -2113,8 +2172,9 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
             bool bad = !isfinite(fu);
             for (int lev = nsub - 1; lev >= 0; --lev) {
                 if (active) {
-                    const double2 st0 = scr[(long long)(2 * lev) * kp.n_slots];
-                    const double2 st1 = scr[(long long)(2 * lev + 1) * kp.n_slots];
+                    const double2 st0 = ck_ld(kp, (const double2 *)scr, kp.ext.scr64 - slot, (long long)(2 * lev) * kp.n_slots);
+                    const double2 st1 = ck_ld(kp, (const double2 *)scr, kp.ext.scr64 - slot,
+                                              (long long)(2 * lev + 1) * kp.n_slots);
                     fu = st0.x * fu + st0.y;
                     fnet = (1.0 - st1.x) * fu - st1.y;
                     bad |= !isfinite(fu);
@@ -2137,9 +2197,9 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
                 const int bt = b_lo + tid;
                 const int j0 = max(0, bt * NG - s0);
                 const int j1 = min(min((int)blockDim.x, ci.S - s0), (bt + 1) * NG - s0);
-                double acc = kp.toa[ci.bin0 + bt];
+                double acc = ck_ld(kp, kp.toa, kp.ext.bins, ci.bin0 + bt);
                 for (int j = j0; j < j1; ++j) acc += sm.stoa[j];
-                kp.toa[ci.bin0 + bt] = acc;
+                ck_st(kp, kp.toa, kp.ext.bins, ci.bin0 + bt, acc);
             }
             __syncthreads();
         }
@@ -2160,7 +2220,8 @@ __global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_
         const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c], base = pcube_off[c];
         __syncthreads();
         for (int l = threadIdx.x; l < L; l += blockDim.x)
-            sl[l] = kt_layer(kp, kp.kt_T, kp.kt_lp, kp.T_center[tc0 + l], kp.p_iface[ifi + l], kp.p_iface[ifi + l + 1],
+            sl[l] = kt_layer(kp, kp.kt_T, kp.kt_lp, ck_ld(kp, kp.T_center, kp.ext.center, tc0 + l),
+                             ck_ld(kp, kp.p_iface, kp.ext.iface, ifi + l), ck_ld(kp, kp.p_iface, kp.ext.iface, ifi + l + 1),
                              S);
         __syncthreads();
         const long long n = (long long)L * S;
@@ -2169,9 +2230,9 @@ __global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_
             const float4 l4 = sl[l];
             const Corners k = kt_corners(kp, l4, S, s);
             const Optics o = kt_mix(k.lo, k.hi, l4, __ldg(kp.kt_bin + s / NG));
-            dtau[base + i] = o.dt;
-            w0[base + i] = o.w0;
-            g0[base + i] = o.g0;
+            ck_st(kp, dtau, kp.ext.cube, base + i, o.dt);
+            ck_st(kp, w0, kp.ext.cube, base + i, o.w0);
+            ck_st(kp, g0, kp.ext.cube, base + i, o.g0);
         }
     }
 }

@@ -1,10 +1,9 @@
 // rt_noalloc.cu -- a solve entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that must stay capturable into a
-// CUDA graph while it runs, host programs whose device memory is handed out
-// by their own pool or by a framework that forbids raw allocations, and loops
-// that cannot afford the device-wide synchronisation an allocation may
-// cause.  rt_solve_uniform_noalloc serves them.  It runs the same FP32 kernels
+// Some callers cannot call cudaMalloc: host programs whose device memory is
+// handed out by their own pool or by a framework that forbids raw
+// allocations, and loops that cannot afford the device-wide synchronisation
+// an allocation may cause.  rt_solve_uniform_noalloc serves them.  It runs the same FP32 kernels
 // as rt_solve_columns on a batch whose columns all have the same shape, and
 // keeps every intermediate in one file-scope device array of fixed size
 // (RT_NOALLOC_SCRATCH_BYTES).  That array is reserved on every GPU that loads
@@ -116,6 +115,11 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     if (!cols->dtau || !cols->w0 || !cols->g0 || !cols->T_center || !cols->T_iface || !cols->p_iface ||
         !cols->mu_star || !cols->F_star)
         return RT_EINVAL;
+    // element counts, where given, must cover the packed batch
+    const int64_t need_cnt[5] = {n * L * NB * NG, n * L, n * (L + 1), n * NB, n};
+    const int64_t have_cnt[5] = {cols->n_cube, cols->n_center, cols->n_iface, cols->n_fstar, cols->n_mu};
+    for (int i = 0; i < 5; ++i)
+        if (have_cnt[i] < 0 || (have_cnt[i] > 0 && have_cnt[i] < need_cnt[i])) return RT_EINVAL;
 
     // carve the fixed scratch; refuse batches that do not fit
     const int64_t upc = (NB * NG + 31) / 32, nu = n * upc;
@@ -150,26 +154,33 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
         return RT_ECUDA;
     }
 
-    // launch shape: as many resident warps as the scratch holds slots for
-    int block = cfg->block_threads ? cfg->block_threads : rt::kMaxBlock32;
-    if (block > rt::kMaxBlock32) block = rt::kMaxBlock32;
-    if (block % 32 || block < 64) return RT_EINVAL;
+    // launch shape: the CTA size (at most cfg->block_threads) that keeps the
+    // most threads resident within the slots the scratch holds, preferring
+    // a grid that reaches every SM
+    int bmax = cfg->block_threads ? cfg->block_threads : rt::kMaxBlock32;
+    if (bmax > rt::kMaxBlock32) bmax = rt::kMaxBlock32;
+    if (bmax % 32 || bmax < 64) return RT_EINVAL;
     size_t smem = 0;
-    int grid = 0;
-    for (;; block -= 32) {
-        if (block < 64) return RT_EBUDGET;
-        smem = rt::fp32_smem_bytes(block, (int)L, nbw, 0);
-        const int occ = rt::occupancy(0, block, smem);
-        const int64_t by_scr = slots_fit / block;
+    int grid = 0, block = 0;
+    int64_t best = 0;
+    for (int b = bmax; b >= 64; b -= 32) {
+        const size_t sm = rt::fp32_smem_bytes(b, (int)L, nbw, 0);
+        const int occ = rt::occupancy(0, b, sm);
         int64_t g = (int64_t)occ * sms;
+        const int64_t by_scr = slots_fit / b;
         if (g > by_scr) g = by_scr;
-        const int64_t by_work = (nu + block / 32 - 1) / (block / 32);
+        const int64_t by_work = (nu + b / 32 - 1) / (b / 32);
         if (g > by_work) g = by_work;
-        if (occ > 0 && g > 0) {
+        if (occ <= 0 || g <= 0) continue;
+        const int64_t score = g * b + (g >= sms ? (int64_t)1 << 40 : 0);
+        if (score > best) {
+            best = score;
             grid = (int)g;
-            break;
+            block = b;
+            smem = sm;
         }
     }
+    if (!grid) return RT_EBUDGET;
 
     cudaStream_t s = (cudaStream_t)stream;
     int32_t *counter = (int32_t *)(base + o_cnt);
@@ -271,6 +282,18 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.fboa32 = (float *)(base + o_fboa);
     kp.colf = (float4 *)(base + o_colf);
     kp.g_w32 = a.gw32;
+    kp.ext.cube = n * L * NB * NG;
+    kp.ext.center = n * L;
+    kp.ext.iface = n * (L + 1);
+    kp.ext.fstar = n * NB;
+    kp.ext.mu = n;
+    kp.ext.scr32 = (long long)(((size_t)RT_NOALLOC_SCRATCH_BYTES - o_scr) / sizeof(float4));
+    kp.ext.part = nu * 2 * (L + 1);
+    kp.ext.planck = n * (2 * L + 1) * NB;
+    kp.ext.bins = n * NB;
+    kp.ext.cols = n;
+    kp.ext.out_if = n * (L + 1);
+    kp.ext.out_lay = n * L;
     e = rt::launch_fp32(kp, grid, block, smem, s);
     return e == cudaSuccess ? RT_OK : RT_ECUDA;
 }

@@ -79,7 +79,7 @@ class rt_ktable(ctypes.Structure):
 class rt_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "systems", "resonance_hits", "etau_hits", "eclamp_hits", "invalid_inputs",
-        "nonfinite_outputs", "fp64_evals")]
+        "nonfinite_outputs", "fp64_evals", "bounds_violations")]
 
 
 def _load(path: str = LIB_PATH) -> ctypes.CDLL:

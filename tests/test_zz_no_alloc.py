@@ -1,8 +1,8 @@
 """The no-allocation entry point against the regular one.
 
 rt_solve_uniform_noalloc serves callers that cannot allocate device memory
-(graph-captured code, programs whose device memory belongs to their own pool,
-loops that cannot afford an allocation's synchronisation).  It keeps all of
+(programs whose device memory belongs to their own pool or framework, loops
+that cannot afford an allocation's synchronisation).  It keeps all of
 its intermediates in a fixed file-scope device array.  Here it is called
 twice in a row through the C ABI and each result is compared with
 rt_solve_columns on the same inputs, within the FP32 tolerance the parity
@@ -58,15 +58,32 @@ def test_noalloc_matches_regular_entry_point_twice():
 
 
 def test_noalloc_refuses_batches_beyond_its_scratch():
-    tiny = torch.zeros(16, dtype=torch.float32, device="cuda")
-    tiny64 = torch.zeros(16, dtype=torch.float64, device="cuda")
-    desc = rt.make_columns(200000, None, None, tiny, tiny, tiny, tiny64, tiny64, tiny64, tiny64,
-                           tiny64, L=100, NB=300)
-    cfg = rt.Config(g_weights=np.full(20, 0.05))
+    """A batch whose inputs and outputs are really allocated at full size
+    (4096 x 40 x 32 x 20: 1.3 GB of cubes) but whose scratch would pass
+    the fixed array is refused with RT_EBUDGET; descriptors that overstate
+    their arrays, or ask for what this entry point does not do, with
+    RT_EINVAL.  Nothing is launched in either case."""
+    n, L, NB, NG = 4096, 40, 32, 20
+    f32 = lambda m: torch.zeros(m, dtype=torch.float32, device="cuda")
+    f64 = lambda m: torch.ones(m, dtype=torch.float64, device="cuda")
+    cubes = [f32(n * L * NB * NG) for _ in range(3)]
+    desc = rt.make_columns(n, None, None, *cubes, f64(n * L), f64(n * (L + 1)), f64(n * (L + 1)),
+                           f64(n), f64(n * NB), L=L, NB=NB)
+    outs = [f64(n * (L + 1)) for _ in range(3)] + [f64(n * L)]
+    cfg = rt.Config(g_weights=np.full(NG, 1.0 / NG))
     with pytest.raises(rt.RTError) as e:
-        rt.rt_solve_uniform_noalloc(cfg, desc, tiny64, tiny64, tiny64, tiny64)
+        rt.rt_solve_uniform_noalloc(cfg, desc, *outs)
     assert e.value.code == rt.RT_EBUDGET
-    bad = rt.Config(g_weights=np.ones(1), precision=rt.RT_FP64_PLAIN)
+    # element counts below the packed batch
+    small = rt.make_columns(n, None, None, *cubes, f64(n * L), f64(n * (L + 1)), f64(n * (L + 1)),
+                            f64(n), f64(n * NB), L=L + 1, NB=NB)
     with pytest.raises(rt.RTError) as e:
-        rt.rt_solve_uniform_noalloc(bad, desc, tiny64, tiny64, tiny64, tiny64)
+        rt.rt_solve_uniform_noalloc(cfg, small, *outs)
     assert e.value.code == rt.RT_EINVAL
+    for bad in (rt.Config(g_weights=np.ones(1), precision=rt.RT_FP64_PLAIN),
+                rt.Config(g_weights=np.array([1.5, -0.5])),
+                rt.Config(g_weights=np.ones(1), n_sweeps=3)):
+        with pytest.raises(rt.RTError) as e:
+            rt.rt_solve_uniform_noalloc(bad, desc, *outs)
+        assert e.value.code == rt.RT_EINVAL
+    assert torch.all(outs[0] == 1.0)
