@@ -660,6 +660,8 @@ def main():
                     help="sweep counts of the iterative method timed beside Thomas (empty: skip)")
     ap.add_argument("--sweep-steps", type=int, default=20)
     ap.add_argument("--quick", action="store_true", help="skip the uneven and serving sections")
+    ap.add_argument("--metrics-log", default=None,
+                    help="append this run's records (one JSON object per section) to a JSONL file")
     ap.add_argument("--profile-case", default=None,
                     help="fp32 | fp64 | sweeps | postproc | ktable: two solves of one workload, for ncu")
     ap.add_argument("--profile-cols", type=int, default=2562)
@@ -937,9 +939,33 @@ def main():
                                 "sample": f"all 2562 columns, {passes} pass(es), {el:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if args.metrics_log:
+            write_metrics_log(args.metrics_log, line)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def write_metrics_log(path: str, line: dict):
+    """Append one JSON object per section of a bench line to a JSONL file:
+    throughput, roofline fractions, latency percentiles, branch-hit counts
+    and the host core count, each with the run's time stamp."""
+    import time
+    stamp = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    recs = [{"section": "gcm_fp32_form", "value": line["value"], "unit": line["unit"],
+             "ms_per_step": line["ms_per_step"], "roofline_frac": line["roofline"]["frac"],
+             "hbm_frac": line["roofline"]["hbm"]["frac"], "mufu_frac": line["roofline"]["mufu"]["frac"],
+             "clocks": line.get("clocks")},
+            {"section": "fp64_plain", **line["fp64_plain"]},
+            {"section": "e2e", **line["e2e"]},
+            {"section": "branch_counts", **line["branch_counts"]},
+            {"section": "host", "cores": cpu_cores()}]
+    for key in ("sweeps", "uneven", "postproc", "ktable", "serving", "cpu_baseline"):
+        if key in line:
+            recs.append({"section": key, **line[key]})
+    with open(path, "a") as f:
+        for r in recs:
+            f.write(json.dumps({"time": stamp, **r}) + "\n")
 
 
 if __name__ == "__main__":

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rt.h"
 #include "rt_internal.h"
 
@@ -26,6 +28,13 @@ namespace {
 struct DevBuf {
     void *p = nullptr;
     size_t cap = 0;
+};
+
+// An NVTX range over a host call (shows the enqueue of each solve in a
+// profiler timeline; a near no-op when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 }  // namespace
@@ -504,6 +513,8 @@ namespace {
 // them; the handle's outputs are left alone.
 int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, float *const *optics_out) {
     if (!h) return RT_EINVAL;
+    NvtxRange range(optics_out ? "rt_ktable_optics" : kt ? "rt_solve_ktable"
+                    : h->cfg.n_sweeps > 0 ? "rt_solve_columns (sweeps)" : "rt_solve_columns");
     h->err.clear();
     int rc = check_columns(h, cols, kt);
     if (rc) return rc;

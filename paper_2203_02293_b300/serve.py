@@ -330,8 +330,10 @@ class Server:
                 if self.in_flight_bytes + need > self.budget:
                     waiting.appendleft(batch.pop())
                     continue
+                torch.cuda.nvtx.range_push(f"serve batch {self.batches}: {len(batch)} requests")
                 rt.rt_solve_columns(s.solver.h, desc, s.stream)
                 s.event.record(s.stream)
+                torch.cuda.nvtx.range_pop()
                 t_admit = time.perf_counter() - t0
                 for r in batch:
                     r.status, r.t_admit = "running", t_admit

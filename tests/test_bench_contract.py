@@ -58,3 +58,28 @@ def test_profile_summary_is_used_only_for_the_current_source(tmp_path, monkeypat
 def test_kernel_source_hash_is_stable():
     assert bench.kernel_source_sha1() == bench.kernel_source_sha1()
     assert len(bench.kernel_source_sha1()) == 40
+
+
+def test_algorithmic_count_is_the_per_equation_table():
+    f, m = bench.algorithmic_ops_per_system(40)
+    per_layer_f = sum(v[0] for v in bench.ALG_LAYER.values())
+    per_layer_m = sum(v[1] for v in bench.ALG_LAYER.values())
+    assert (per_layer_f, per_layer_m) == (121, 11)
+    assert (f, m) == (40 * 121 + bench.ALG_BOA[0], 40 * 11 + bench.ALG_BOA[1]) == (4848, 441)
+
+
+def test_metrics_log_writes_one_record_per_section(tmp_path):
+    line = {"value": 2.0e9, "unit": "solves/s", "ms_per_step": 0.7,
+            "roofline": {"frac": 0.3, "hbm": {"frac": 0.18}, "mufu": {"frac": 0.22}},
+            "fp64_plain": {"value": 1.4e7}, "e2e": {"value": 1.1e8},
+            "branch_counts": {"resonance_hits": 354}, "sweeps": {"runs": []},
+            "serving": {"p50_ms": 2.8, "p99_ms": 31.0}}
+    path = tmp_path / "m.jsonl"
+    bench.write_metrics_log(str(path), line)
+    bench.write_metrics_log(str(path), line)
+    recs = [json.loads(l) for l in path.read_text().splitlines()]
+    sections = [r["section"] for r in recs]
+    assert sections.count("gcm_fp32_form") == 2 and "serving" in sections and "host" in sections
+    first = recs[0]
+    assert first["roofline_frac"] == 0.3 and first["value"] == 2.0e9 and "time" in first
+    assert next(r for r in recs if r["section"] == "serving")["p99_ms"] == 31.0
