@@ -556,11 +556,13 @@ def run_serving(args):
     """Config 4: Poisson arrivals (mean 200/s), requests of logU[1, 2562]
     columns x U{40..100} layers x U{30..300} bins x 20 g sliced from a
     device-resident pool; continuous batching over 8 stream slots, smallest
-    request first, one CTA per SM per batch, at most 2M systems per batch,
-    requests above 2M systems cut into column pieces (the best p99 of a
-    sweep over slots, policy, CTAs per SM, batch cap and piece size).  The
-    FP64 plain path is served beside it at the rate it sustains, the same
-    request mix, 4 slots."""
+    request first except that the remaining pieces of a started request go
+    first, requests above 4M systems cut into column pieces, at most 4M
+    systems per batch, one CTA per SM per batch except batches of 1e8
+    layer-systems or more, which keep every CTA resident (the best p99 of a
+    sweep over slots, policy, CTAs per SM, batch cap, piece size and the
+    wide-batch threshold).  The FP64 plain path is served beside it at the
+    rate it sustains, the same request mix, 4 slots."""
     import torch
     import rt_synth
     from paper_2203_02293_b300 import rt
@@ -569,8 +571,8 @@ def run_serving(args):
     n = int(args.serving_seconds * args.serving_rate)
     reqs = make_requests(pool, n, rate_hz=args.serving_rate, seed=4)
     warm = make_requests(pool, 8, rate_hz=1e3, seed=99)
-    knobs = dict(n_slots=8, policy="sjf", ctas_per_sm=1, max_systems_per_batch=2_000_000,
-                 split_systems=2_000_000)
+    knobs = dict(n_slots=8, policy="gang", ctas_per_sm=1, max_systems_per_batch=4_000_000,
+                 split_systems=4_000_000, wide_layer_systems=100_000_000)
     srv = Server(pool, hbm_budget_bytes=32 << 30, **knobs)
     srv.run(warm)
     srv.batches = 0
@@ -579,9 +581,12 @@ def run_serving(args):
     # lower bound on the slowest requests' latency: their layer-systems at
     # the whole GPU's rate (the GCM step's solves/s x 40 layers)
     work = np.array([r.systems * r.L for r in reqs], dtype=np.float64)
+    p99w = float(np.percentile(work, 99))
     summ.update({"rate_hz": args.serving_rate, "seconds_of_arrivals": args.serving_seconds,
                  "unit_latency": "ms", "budget_bytes": 32 << 30, "precision": "fp32 form", **knobs,
-                 "p99_request_layer_systems": float(np.percentile(work, 99))})
+                 "p99_request_layer_systems": p99w,
+                 "p99_request_whole_gpu_ms": (p99w / args.gcm_layer_systems_per_s * 1e3
+                                              if getattr(args, "gcm_layer_systems_per_s", 0) else None)})
     if args.serving_fp64_rate > 0:
         n64 = int(args.serving_fp64_seconds * args.serving_fp64_rate)
         reqs = make_requests(pool, n64, rate_hz=args.serving_fp64_rate, seed=44)
@@ -930,6 +935,7 @@ def main():
         torch.cuda.empty_cache()
         line["uneven"] = run_uneven(args, stream, ws, rank, barrier, max_over_ranks)
     if rank == 0 and not args.quick:
+        args.gcm_layer_systems_per_s = value / ws * 40      # this GPU's GCM-step rate in layer-systems/s
         line["postproc"] = run_postproc(args, stream)
         line["ktable"] = run_ktable(args, stream)
         line["serving"] = run_serving(args)

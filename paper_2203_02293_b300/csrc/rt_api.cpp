@@ -132,9 +132,24 @@ int check_span(rt_handle *h, int col, const char *what, int64_t off, int64_t spa
     return RT_OK;
 }
 
+// The FP32 work units, largest column first: unit u is unit k of column c.
+void fill_units(Plan &P) {
+    P.unit_col.resize((size_t)P.n_units);
+    P.unit_k.resize((size_t)P.n_units);
+    int64_t u = 0;
+    for (size_t oi = 0; oi < P.order.size(); ++oi) {
+        const int col = P.order[oi];
+        for (int k = 0; k < P.col_units[col]; ++k, ++u) {
+            P.unit_col[u] = col;
+            P.unit_k[u] = k;
+        }
+    }
+}
+
 // The host-side part of a plan: shapes, offsets (gather or packed), their
-// bounds, processing order and work units.  No device call.
-int validate_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
+// bounds, processing order and work units (the per-unit lists only when
+// `units`: sizes need their count alone).  No device call.
+int validate_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units = true) {
     const rt_config &cfg = h->cfg;
     const int n = c->n_cols;
     const bool fp64 = cfg.precision == RT_FP64_PLAIN;
@@ -221,21 +236,17 @@ int validate_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
         return (int64_t)P.nl[a] * P.nb[a] > (int64_t)P.nl[b] * P.nb[b];
     });
     if (!fp64) {
-        for (int oi = 0; oi < n; ++oi) {
-            const int col = P.order[oi];
-            for (int k = 0; k < P.col_units[col]; ++k) {
-                P.unit_col.push_back(col);
-                P.unit_k.push_back(k);
-            }
-        }
-        P.n_units = (int64_t)P.unit_col.size();
-        if (P.n_units > INT32_MAX) return fail(h, RT_EINVAL, "too many work units");
+        int64_t nu = 0;
+        for (int i = 0; i < n; ++i) nu += P.col_units[i];
+        if (nu > INT32_MAX) return fail(h, RT_EINVAL, "too many work units");
+        P.n_units = nu;
+        if (units) fill_units(P);
     }
     return RT_OK;
 }
 
-int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt) {
-    int rc = validate_plan(h, c, P, kt);
+int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units = true) {
+    int rc = validate_plan(h, c, P, kt, units);
     if (rc) return rc;
     const rt_config &cfg = h->cfg;
     const int n = c->n_cols;
@@ -478,7 +489,7 @@ int rt_query_bytes(const rt_handle *hc, const rt_columns *cols, size_t *bytes) {
     int rc = check_columns(h, cols, kt);
     if (rc) return rc;
     Plan P;
-    rc = build_plan(h, cols, P, kt);
+    rc = build_plan(h, cols, P, kt, false);
     if (rc) return rc;
     *bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes + P.kcube_bytes;
     return RT_OK;
@@ -499,7 +510,7 @@ int rt_check_columns(const rt_config *cfg, const rt_columns *cols, char *msg, si
     tmp.kt_NB = -1;                // (with no table, its bin count is not known)
     rc = check_columns(&tmp, cols, kt);
     Plan P;
-    if (!rc && cols->n_cols > 0) rc = validate_plan(&tmp, cols, P, kt);
+    if (!rc && cols->n_cols > 0) rc = validate_plan(&tmp, cols, P, kt, false);
     if (rc && msg && msg_len) snprintf(msg, msg_len, "%s", tmp.err.c_str());
     return rc;
 }
@@ -519,7 +530,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
     int rc = check_columns(h, cols, kt);
     if (rc) return rc;
     Plan P;
-    rc = build_plan(h, cols, P, kt);
+    rc = build_plan(h, cols, P, kt, false);     // unit lists only if the plan is new (below)
     if (rc) return rc;
     const rt_config &cfg = h->cfg;
     const size_t ws_bytes = P.plan_bytes + P.out_bytes + P.scr_bytes + P.aux_bytes + P.kcube_bytes;
@@ -564,6 +575,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
                            h->plan_mu == P.mu_idx;
     if (n > 0 && !same_plan) {
         if (cap) return fail(h, RT_EINVAL, "a new batch shape cannot be planned during stream capture");
+        if (cfg.precision != RT_FP64_PLAIN) fill_units(P);
         const size_t need = P.plan_bytes;
         if (h->stage_pending) {
             cudaError_t e = cudaEventSynchronize(h->stage_ev);

@@ -188,14 +188,22 @@ class Slot:
     nbytes: int = 0
     n_if: int = 0
     busy: bool = False
+    wide: Solver | None = None     # a handle with every CTA resident, for large batches
+    active: Solver | None = None   # the handle of the batch in flight
 
 
 class Server:
     def __init__(self, pool: Pool, n_slots: int = 4, hbm_budget_bytes: int = 8 << 30,
                  max_systems_per_batch: int = 24_000_000, wait_timeout_s: float = 0.0,
-                 keep_outputs: bool = False, policy: str = "fifo", split_systems: int = 0, **cfg):
+                 keep_outputs: bool = False, policy: str = "fifo", split_systems: int = 0,
+                 wide_layer_systems: int = 0, **cfg):
+        # wide_layer_systems > 0: a batch of at least that many layer-systems
+        # (systems x layers) runs on a second handle of the slot that keeps
+        # every CTA resident, so a large request alone on the GPU gets all of
+        # it; smaller batches keep the slot's own launch shape
         # policy: "fifo" admits in arrival order; "sjf" admits the smallest
-        # waiting requests first (shorter latency for small requests)
+        # waiting requests first (shorter latency for small requests);
+        # "gang" is sjf with the pieces of started split requests first
         self.policy = policy
         self.split = split_systems
         self.pool = pool
@@ -203,13 +211,19 @@ class Server:
         self.max_sys = max_systems_per_batch
         self.wait_timeout = wait_timeout_s
         self.keep_outputs = keep_outputs
-        self.slots = [Slot(torch.cuda.Stream(), Solver(pool.g_weights, **cfg)) for _ in range(n_slots)]
+        self.wide_at = wide_layer_systems
+        wide_cfg = {k: v for k, v in cfg.items() if k != "ctas_per_sm"}
+        self.slots = [Slot(torch.cuda.Stream(), Solver(pool.g_weights, **cfg),
+                           wide=Solver(pool.g_weights, **wide_cfg) if wide_layer_systems > 0 else None)
+                      for _ in range(n_slots)]
         self.in_flight_bytes = 0
         self.batches = 0
 
     def close(self):
         for s in self.slots:
             s.solver.close()
+            if s.wide is not None:
+                s.wide.close()
 
     def _bytes(self, slot: Slot, r: Request) -> int:
         # workspace of the request alone (a first estimate for composing a batch)
@@ -221,7 +235,7 @@ class Server:
     def _complete(self, slot: Slot, now: float) -> int:
         """Retire a finished batch; returns how many requests it completed."""
         if self.keep_outputs:
-            o = slot.solver.outputs_host(slot.n_if, sum(r.n_cols * r.L for r in slot.reqs))
+            o = slot.active.outputs_host(slot.n_if, sum(r.n_cols * r.L for r in slot.reqs))
             i0 = l0 = 0
             for r in slot.reqs:
                 ni, nl = r.n_cols * (r.L + 1), r.n_cols * r.L
@@ -293,8 +307,12 @@ class Server:
                 else:
                     keep.append(r)
             waiting = keep
-            if self.policy == "sjf" and len(waiting) > 1:
-                waiting = deque(sorted(waiting, key=lambda r: r.systems * r.L))
+            if self.policy in ("sjf", "gang") and len(waiting) > 1:
+                # "gang": the remaining pieces of a request that has started
+                # go first, so a split request's pieces run together
+                started = lambda r: 0 if (self.policy == "gang" and r.parent is not None
+                                          and r.parent.status == "running") else 1
+                waiting = deque(sorted(waiting, key=lambda r: (started(r), r.systems * r.L)))
             # admission into free slots
             for s in self.slots:
                 if s.busy or not waiting:
@@ -320,18 +338,22 @@ class Server:
                     need += rb
                 if not batch:
                     continue
-                # exact need of the composed batch; hand requests back until it fits
+                # the handle for this batch, then its exact need; hand requests
+                # back until it fits
+                pick = lambda b: s.wide if (s.wide is not None and
+                                            sum(r.systems * r.L for r in b) >= self.wide_at) else s.solver
                 desc, nl = self.pool.descriptor(batch)
-                need = rt.rt_query_bytes(s.solver.h, desc)
+                need = rt.rt_query_bytes(pick(batch).h, desc)
                 while len(batch) > 1 and self.in_flight_bytes + need > self.budget:
                     waiting.appendleft(batch.pop())
                     desc, nl = self.pool.descriptor(batch)
-                    need = rt.rt_query_bytes(s.solver.h, desc)
+                    need = rt.rt_query_bytes(pick(batch).h, desc)
                 if self.in_flight_bytes + need > self.budget:
                     waiting.appendleft(batch.pop())
                     continue
                 torch.cuda.nvtx.range_push(f"serve batch {self.batches}: {len(batch)} requests")
-                rt.rt_solve_columns(s.solver.h, desc, s.stream)
+                s.active = pick(batch)
+                rt.rt_solve_columns(s.active.h, desc, s.stream)
                 s.event.record(s.stream)
                 torch.cuda.nvtx.range_pop()
                 t_admit = time.perf_counter() - t0
