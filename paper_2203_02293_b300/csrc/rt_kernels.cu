@@ -1641,7 +1641,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
 // needed) (t, r) area, swizzled for a conflict-free transposed sum.
 // ---------------------------------------------------------------------
 // (t, r) per layer, then the output rows [2 (Lmax + 1)][32] (XOR-swizzled)
-__host__ __device__ inline int sweep_region_floats(int Lmax) { return 64 * (Lmax + 1); }
+__host__ __device__ inline int sweep_region_floats() { return 64 * (kSweepMaxLayers + 1); }
 
 // Output row element (row, j) of the swizzled rows: lane j's writes to one
 // row and the lanes' reads of one column each of their own row hit 32
@@ -1653,114 +1653,108 @@ int sweep_warp_floats(int Lmax, int nbw, int direct, int isothermal) {
     int n = ((direct ? 0 : (2 * Lmax + 1) * nbw) + 3) & ~3;
     n += (2 * nbw + 3) & ~3;                        // F*, F_BOA
     n += (Lmax + 1 + 3) & ~3;                       // warp sums of w F_beam per interface
-    n += 2 * per * Lmax;                            // SU, SD
-    n += sweep_region_floats(Lmax);                 // (t, r), then the output rows
+    n += 2 * per * kSweepMaxLayers;                 // SU, SD (every system padded to the register limit)
+    n += sweep_region_floats();                     // (t, r), then the output rows
     return n;
 }
 size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal) {
     return sizeof(float) * (size_t)(block / 32) * sweep_warp_floats(Lmax, nbw, direct, isothermal);
 }
 
-// Layers per branch-free chunk of the sweep passes.  Inside a chunk no
-// branch separates the layers, so the shared-memory loads of later layers
-// can issue early; layers past the column's L in its last chunk run with
-// t = r = 0 on clamped source rows and write only dead level slots.
+// Layers per chunk of the sweep passes: each chunk's source rows are loaded
+// while the previous chunk computes.
 constexpr int kSweepChunk = 8;
 static_assert(kSweepMaxLayers % kSweepChunk == 0, "whole chunks");
 
-// One upward pass over the lane's system.  X holds d at the levels (u at the
-// BOA); on return it holds u.  EMIT (last sweep): u and u - d at interface
-// i < L go to rows 2i and 2i + 1 of OUT (element of lane j: out_idx).  X is
-// indexed only by the unrolled loop counters (a store at the runtime BOA
-// index would send X to local memory), so it stays in registers.
+// The passes run over all kSweepMaxLayers layers of every system: a column
+// with fewer layers is padded below its BOA with exact identity layers (t =
+// 1, r = 0, no source, B of the BOA), through which u and d pass unchanged.
+// The BOA condition then sits at a compile-time level and the passes need
+// no per-layer predicate, clamp or select.
+
+// One upward pass.  X holds d at the levels and u at the padded BOA; on
+// return it holds u.  EMIT (last sweep): u and u - d at interface i <= L of
+// the column (level 2i, or i for isothermal layers) go to rows 2i and 2i + 1
+// of OUT (element of lane j: out_idx); interface kSweepMaxLayers is left to
+// the caller.  X is indexed only by the unrolled loop counters, so it stays
+// in registers.
 template <bool ISO, bool EMIT, int LR, int NLV>
 __device__ __forceinline__ void sweep_up(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int L, int lane,
                                          float d0, const float *SU, float *OUT) {
     constexpr int CH = kSweepChunk, NC = LR / kSweepChunk;
     using S2 = typename std::conditional<ISO, float, float2>::type;    // sources of one layer
-    const S2 *src = reinterpret_cast<const S2 *>(SU);
-    // the top chunk's rows first, then each chunk's loads issue while the
-    // previous chunk computes
+    const S2 *src = reinterpret_cast<const S2 *>(SU) + lane;
     S2 buf[CH];
-    const int ctop = (L - 1) / CH;
 #pragma unroll
-    for (int k = 0; k < CH; ++k) buf[k] = src[min(ctop * CH + k, L - 1) * 32 + lane];
+    for (int k = 0; k < CH; ++k) buf[k] = src[((NC - 1) * CH + k) * 32];
 #pragma unroll
     for (int c = NC - 1; c >= 0; --c) {
-        if (c * CH < L) {
-            S2 cur[CH];
+        S2 cur[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) cur[k] = buf[k];
-            if (c > 0) {
+        for (int k = 0; k < CH; ++k) cur[k] = buf[k];
+        if (c > 0) {
 #pragma unroll
-                for (int k = 0; k < CH; ++k) buf[k] = src[((c - 1) * CH + k) * 32 + lane];
+            for (int k = 0; k < CH; ++k) buf[k] = src[((c - 1) * CH + k) * 32];
+        }
+#pragma unroll
+        for (int k = CH - 1; k >= 0; --k) {
+            const int l = c * CH + k;
+            float u, dl;
+            if constexpr (ISO) {
+                dl = l == 0 ? d0 : X[l];
+                u = fmaf(t[l], X[l + 1], fmaf(r[l], dl, cur[k]));
+                X[l] = u;
+            } else {
+                X[2 * l + 1] = fmaf(t[l], X[2 * l + 2], fmaf(r[l], X[2 * l + 1], cur[k].y));   // lower
+                dl = l == 0 ? d0 : X[2 * l];
+                u = fmaf(t[l], X[2 * l + 1], fmaf(r[l], dl, cur[k].x));                       // upper
+                X[2 * l] = u;
             }
-#pragma unroll
-            for (int k = CH - 1; k >= 0; --k) {
-                const int l = c * CH + k;
-                const bool live = l < L;                 // (always true in all but the last chunk)
-                if constexpr (ISO) {
-                    const float dl = l == 0 ? d0 : X[l];
-                    const float u = fmaf(t[l], X[l + 1], fmaf(r[l], dl, cur[k]));
-                    X[l] = (l == 0 || live) ? u : X[l];  // keeps the BOA value at l = L
-                    if (EMIT && live) {
-                        OUT[out_idx(2 * l, lane)] = u;
-                        OUT[out_idx(2 * l + 1, lane)] = u - dl;
-                    }
-                } else {
-                    X[2 * l + 1] = fmaf(t[l], X[2 * l + 2], fmaf(r[l], X[2 * l + 1], cur[k].y));   // lower
-                    const float dl = l == 0 ? d0 : X[2 * l];
-                    const float u = fmaf(t[l], X[2 * l + 1], fmaf(r[l], dl, cur[k].x));            // upper
-                    X[2 * l] = (l == 0 || live) ? u : X[2 * l];
-                    if (EMIT && live) {
-                        OUT[out_idx(2 * l, lane)] = u;
-                        OUT[out_idx(2 * l + 1, lane)] = u - dl;
-                    }
-                }
+            if (EMIT && l <= L) {
+                OUT[out_idx(2 * l, lane)] = u;
+                OUT[out_idx(2 * l + 1, lane)] = u - dl;
             }
         }
     }
 }
 
-// One downward pass: X takes d at every level below the TOA, then u at the
-// BOA (d + (F_BOA + F_beam)); returns d at the BOA.
+// One downward pass: X takes d at every level below the TOA, then u = d +
+// (F_BOA + F_beam) at the padded BOA; returns d there.
 template <bool ISO, int LR, int NLV>
-__device__ __forceinline__ float sweep_down(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int L,
-                                            int lane, float d0, float ubc, const float *SD) {
+__device__ __forceinline__ float sweep_down(float (&X)[NLV], const float (&t)[LR], const float (&r)[LR], int lane,
+                                            float d0, float ubc, const float *SD) {
     constexpr int CH = kSweepChunk, NC = LR / kSweepChunk;
     using S2 = typename std::conditional<ISO, float, float2>::type;
-    const S2 *src = reinterpret_cast<const S2 *>(SD);
+    const S2 *src = reinterpret_cast<const S2 *>(SD) + lane;
     S2 buf[CH];
 #pragma unroll
-    for (int k = 0; k < CH; ++k) buf[k] = src[min(k, L - 1) * 32 + lane];
-    float d = d0, dB = 0.f;
+    for (int k = 0; k < CH; ++k) buf[k] = src[k * 32];
+    float d = d0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        if (c * CH < L) {
-            S2 cur[CH];
+        S2 cur[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) cur[k] = buf[k];
-            if (c + 1 < NC) {
+        for (int k = 0; k < CH; ++k) cur[k] = buf[k];
+        if (c + 1 < NC) {
 #pragma unroll
-                for (int k = 0; k < CH; ++k) buf[k] = src[min((c + 1) * CH + k, L - 1) * 32 + lane];
-            }
+            for (int k = 0; k < CH; ++k) buf[k] = src[((c + 1) * CH + k) * 32];
+        }
 #pragma unroll
-            for (int k = 0; k < CH; ++k) {
-                const int l = c * CH + k;
-                if constexpr (ISO) {
-                    d = fmaf(t[l], d, fmaf(r[l], X[l + 1], cur[k]));
-                    X[l + 1] = l == L - 1 ? d + ubc : d;
-                } else {
-                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 1], cur[k].x));          // upper sub-layer
-                    X[2 * l + 1] = d;
-                    d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 2], cur[k].y));          // lower
-                    X[2 * l + 2] = l == L - 1 ? d + ubc : d;
-                }
-                dB = l == L - 1 ? d : dB;
+        for (int k = 0; k < CH; ++k) {
+            const int l = c * CH + k;
+            if constexpr (ISO) {
+                d = fmaf(t[l], d, fmaf(r[l], X[l + 1], cur[k]));
+                X[l + 1] = d;
+            } else {
+                d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 1], cur[k].x));          // upper sub-layer
+                X[2 * l + 1] = d;
+                d = fmaf(t[l], d, fmaf(r[l], X[2 * l + 2], cur[k].y));          // lower
+                X[2 * l + 2] = d;
             }
         }
     }
-    return dB;
+    X[NLV - 1] = d + ubc;
+    return d;
 }
 
 // Column and lane bookkeeping of a sweep unit (re-derived after the sweeps,
@@ -1873,6 +1867,17 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
             }
             Bt = Bb;
         }
+        // identity layers below the BOA up to the register limit (t = 1, r = 0, no source)
+        for (int l = L; l < LR; ++l) {
+            TR2[l * 32 + lane] = make_float2(1.f, 0.f);
+            if constexpr (ISO) {
+                SU[l * 32 + lane] = 0.f;
+                SD[l * 32 + lane] = 0.f;
+            } else {
+                reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(0.f, 0.f);
+                reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(0.f, 0.f);
+            }
+        }
         float fw = q.wg * Fb;                                      // the BOA interface
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
@@ -1885,16 +1890,15 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
         __syncwarp();
 #pragma unroll
         for (int l = 0; l < LR; ++l) {
-            float2 v = make_float2(0.f, 0.f);
-            if (l < L) v = TR2[l * 32 + lane];
+            const float2 v = TR2[l * 32 + lane];
             t[l] = v.x;
             r[l] = v.y;
         }
-        // zero diffuse flux: u = -pi B at every level
+        // zero diffuse flux: u = -pi B at every level (the BOA's B below it)
 #pragma unroll
         for (int j = 0; j < NLV; ++j) {
             const int lev = ISO ? 2 * j : j;                       // level in the B table
-            X[j] = (j <= (ISO ? L : 2 * L)) ? -kPiF * ldBk<DIRECT>(kp, q.Bp + min(lev, 2 * L) * q.bst) : 0.f;
+            X[j] = -kPiF * ldBk<DIRECT>(kp, q.Bp + min(lev, 2 * L) * q.bst);
         }
         __syncwarp();                                              // (t, r) area free for the output rows
     }
@@ -1902,7 +1906,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     // ---- the sweeps: registers t, r, X; sources from shared memory
     float dB = 0.f;
     for (int it = 0; it < kp.n_sweeps; ++it) {
-        dB = sweep_down<ISO>(X, t, r, L, lane, d0, ubc, SD);
+        dB = sweep_down<ISO>(X, t, r, lane, d0, ubc, SD);
         if (it + 1 < kp.n_sweeps)
             sweep_up<ISO, false>(X, t, r, L, lane, d0, SU, TR);
         else
@@ -1912,9 +1916,10 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
 
     // ---- interface sums, TOA spectrum, column finalisation
     const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
-    {
-        // the BOA interface: u = d + (F_BOA + F_beam), as the downward pass set it
-        const float uB = dB + ubc;
+    if (L == LR) {
+        // the BOA interface of a column with no padding (the last upward
+        // pass emitted it for any other): u = d + (F_BOA + F_beam)
+        const float uB = X[NLV - 1];
         TR[out_idx(2 * L, lane)] = uB;
         TR[out_idx(2 * L + 1, lane)] = uB - dB;
     }
@@ -1975,8 +1980,8 @@ __global__ void __launch_bounds__(kMaxBlock32, 1) fp32_sweeps(KParams kp) {
     float *sFB = sFs + nbw;
     float *fbs = sFs + ((2 * nbw + 3) & ~3);
     float *SU = fbs + ((Lm + 1 + 3) & ~3);
-    float *SD = SU + (ISO ? 32 : 64) * Lm;
-    float *TR = SD + (ISO ? 32 : 64) * Lm;
+    float *SD = SU + (ISO ? 32 : 64) * kSweepMaxLayers;
+    float *TR = SD + (ISO ? 32 : 64) * kSweepMaxLayers;
     for (;;) {
         int unit = 0;
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
