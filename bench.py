@@ -926,7 +926,7 @@ def main():
         "gpu_launches": 2 * args.steps,      # Planck pre-kernel + solve kernel per step
         "roofline": roofline,
         "clocks": clk.summary(),
-        "branch_counts": stats,
+        "branch_counts": {**stats, "resonance_mode": "paper (|D| < 1e-5: D := 2 mu*)"},
     }
     if sweeps is not None:
         line["sweeps"] = sweeps
