@@ -109,6 +109,7 @@ struct Plan {
     int Lmax = 0, NBmax = 0;
     // launch
     int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, inline_b = 0, ns = 1;
+    int group_shift = 4;          // FP32 form: log2 of the interfaces per transposed sum
     bool sweeps = false;          // the iterative method (cfg.n_sweeps > 0) instead of Thomas
     size_t smem = 0;
     int64_t n_slots = 0;
@@ -299,9 +300,23 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                              (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g == 1 && h->narrow_edges);
                 P.direct = P.inline_b || cfg.planck_staging == RT_STAGE_DIRECT ||
                            (cfg.planck_staging == RT_STAGE_AUTO && cfg.n_g < 4);
-                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct);
-                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct);
+                // 16 interfaces per transposed sum of the back-substitution,
+                // unless 8 (half the transpose buffer) keep more CTAs
+                // resident: tall columns' staged B fills shared memory
+                P.group_shift = 4;
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4);
                 occ = rt::occupancy(0, P.block, P.smem, P.ns);
+                {
+                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3);
+                    const int occ8 = rt::occupancy(0, P.block, sm8, P.ns);
+                    const int cap = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 1 << 20;
+                    if (std::min(occ8, cap) > std::min(occ, cap)) {
+                        P.group_shift = 3;
+                        P.smem = sm8;
+                        occ = occ8;
+                    }
+                }
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
@@ -722,6 +737,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.col_done = d_done;
         kp.n_units = (int32_t)P.n_units;
         kp.warp_floats = P.warp_floats;
+        kp.group_shift = P.group_shift;
         kp.nbw = P.nbw;
         kp.direct = P.direct;
         kp.inline_b = P.inline_b;

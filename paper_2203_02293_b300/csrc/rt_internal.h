@@ -60,6 +60,7 @@ struct KParams {
     int32_t *col_done;           // [n_cols] finished units per column (zeroed per solve)
     int32_t n_units;
     int32_t warp_floats;         // shared-memory floats per warp
+    int32_t group_shift;         // FP32 form: log2 of the interfaces per transposed sum (3 or 4)
     // FP32 form: per-column staging written by fp32_prep
     float *planck32;             // B per column [2L+1][NB] (levels: 2i interface, 2i+1 centre)
     const int64_t *planck_off;   // [n_cols]
@@ -95,8 +96,8 @@ struct KParams {
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct);
-int fp32_warp_floats(int Lmax, int nbw, int direct);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift);
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift);
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);

@@ -28,6 +28,7 @@
 //                    column, one thread per system, scalar Thomas on every
 //                    level (sub-layers not merged).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <array>
 #include <type_traits>
 #include <utility>
@@ -602,14 +603,22 @@ __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk
     return b;
 }
 
-int fp32_warp_floats(int Lmax, int nbw, int direct) {
-    // Planck [(2 Lmax + 1) nbw] (staged mode only) + F* [nbw] + F_BOA [nbw]
-    // + transpose [16][2][33]
-    int n = (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw + 16 * 2 * 33;
+// Levels of elimination scratch in flight during the back-substitution, and
+// the shared-memory ring that holds them: kBackDepth + 1 slots of one float4
+// per system, the spare slot being the one read a level earlier.
+constexpr int kBackDepth = 2;
+__host__ __device__ constexpr int back_ring_floats(int ns) { return (kBackDepth + 1) * ns * 32 * 4; }
+
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift) {
+    // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode only)
+    // + F* [nbw] + F_BOA [nbw] + transpose [G][2][33], G = 2^group_shift
+    // interfaces per transposed sum (at least 2 NS 32 floats for the TOA sum)
+    const int tr = std::max((1 << group_shift) * 2 * 33, 64 * ns);
+    int n = back_ring_floats(ns) + (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw + tr;
     return (n + 3) & ~3;
 }
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct) {
-    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift) {
+    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift);
 }
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
@@ -1173,6 +1182,22 @@ __device__ __forceinline__ void discard_l2_after(const void *p, float after) {
         : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only): the
+// copy needs no register while in flight.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Elimination scratch of one interface: (P, Q, alpha', e) of one system in a
 // float4; for a lane with two systems, (P, Q) of both and (alpha', e) of
 // both in two float4 (component pairs stay in their register pairs).
@@ -1218,7 +1243,8 @@ __device__ __forceinline__ bool &cmpm(M2 &m, int i) { return i ? m.y : m.x; }
 // One work unit: SPU = 32 NS consecutive systems of one column, starting at
 // system s0 = ku SPG of the column (SPG: the kernel's unit stride).
 template <bool ISO, int ST, bool KT, int NS, int SPG>
-__device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
+__device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float4 *ring, float *sB, float *sFs,
+                                          float *sFB,
                                           float *tb, long long slot, long long gthreads, long long sstride,
                                           Counters &cn) {
     using V = typename std::conditional<NS == 2, V2, float>::type;
@@ -1240,7 +1266,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     const int b_lo = s0 / NG;
     const int nbc = min(NB - 1, (s0 + SPU - 1) / NG) - b_lo + 1;
 
-    // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA
+    // stage B of the unit's bins at the 2L+1 levels, F* and F_BOA: every
+    // copy issued at once (cp.async), landing while the lanes set up their
+    // systems and the first layer's optics load
     {
         const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
         const int nlev = 2 * L + 1;
@@ -1248,16 +1276,19 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             for (int i = lane; i < nlev * nbc; i += 32) {
                 const int lev = i / nbc, bb = i - lev * nbc;
                 const float *pb = Bg + (long long)lev * NB + bb;
-                sB[i] = RT_IN(pb, kp.planck32, kp.ext.planck) ? __ldcg(pb) : 0.f;
+                if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(sB + i, pb);
+                else sB[i] = 0.f;
             }
         }
         for (int j = lane; j < nbc; j += 32) {
             const long long jb = kp.bin_off[c] + b_lo + j;
-            sFs[j] = RT_IN(kp.fs32 + jb, kp.fs32, kp.ext.bins) ? __ldcg(kp.fs32 + jb) : 0.f;
-            sFB[j] = RT_IN(kp.fboa32 + jb, kp.fboa32, kp.ext.bins) ? __ldcg(kp.fboa32 + jb) : 0.f;
+            if (RT_IN(kp.fs32 + jb, kp.fs32, kp.ext.bins)) cp_async4(sFs + j, kp.fs32 + jb);
+            else sFs[j] = 0.f;
+            if (RT_IN(kp.fboa32 + jb, kp.fboa32, kp.ext.bins)) cp_async4(sFB + j, kp.fboa32 + jb);
+            else sFB[j] = 0.f;
         }
+        cp_async_commit();
     }
-    __syncwarp();
 
     // component i of this lane is system s0 + 32 i + lane; padding
     // systems of a column's last unit repeat system s0 with zero weight,
@@ -1305,7 +1336,6 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         bI[i] = sI[i] / NG;
         cmp(wg, i) = act ? kp.g_w32[sI[i] - bI[i] * NG] : 0.f;
         Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo);
-        cmp(Fb, i) = beam ? mu * sFs[bI[i] - b_lo] : 0.f;
         if constexpr (INL) {
             if (kp.edges32) {
                 wn0[i] = __ldg(kp.edges32 + bI[i]);
@@ -1317,7 +1347,43 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
                 wn1[i] = fmaf((float)(bI[i] + 1), dwn, wmin);
                 dnu[i] = dwn;
             }
-        } else {
+        }
+    }
+    // optics: read from the cubes, or (KT) from the k-table corners of
+    // the layer's grid cell, fetched one layer ahead
+    V nd = V(0.f), nw = V(0.f), ng = V(0.f);
+    const float *pd[NS], *pw[NS], *pg[NS];
+    const float4 *klay = nullptr;
+    float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next;
+    float4 kb[NS];
+    Corners kc[NS];
+    if constexpr (KT) {
+        klay = kp.kt_lay + kp.lay_off[c];
+        kl_next = klay[0];
+        kl_after = L > 1 ? klay[1] : kl_next;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            kb[i] = __ldg(kp.kt_bin + bI[i]);
+            kc[i] = kt_corners(kp, kl_next, S, sI[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const long long e = cube0 + sI[i];
+            pd[i] = kp.dtau + e;
+            pw[i] = kp.w0 + e;
+            pg[i] = kp.g0 + e;
+            cmp(nd, i) = RT_IN(pd[i], kp.dtau, kp.ext.cube) ? __ldcs(pd[i]) : 0.f;
+            cmp(nw, i) = RT_IN(pw[i], kp.w0, kp.ext.cube) ? __ldcs(pw[i]) : 0.f;
+            cmp(ng, i) = RT_IN(pg[i], kp.g0, kp.ext.cube) ? __ldcs(pg[i]) : 0.f;
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();                              // the staged values of every lane
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        cmp(Fb, i) = beam ? mu * sFs[bI[i] - b_lo] : 0.f;
+        if constexpr (!INL) {
             // the B of a layer's bottom interface is carried as the next layer's top
             cmp(Bt, i) = ldBk<DIRECT>(kp, Bp[i]);
             cmp(Bc, i) = ldBk<DIRECT>(kp, Bp[i] + bst);
@@ -1355,35 +1421,6 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     // forward elimination, TOA -> BOA, departure variables
     V al = V(1.f);                                       // alpha' = 1 - a'
     V bl = vfma(V(-kPiF), Bt, V((float)kp.F_toa));       // b' at the TOA
-    // optics: read from the cubes, or (KT) from the k-table corners of
-    // the layer's grid cell, fetched one layer ahead
-    V nd = V(0.f), nw = V(0.f), ng = V(0.f);
-    const float *pd[NS], *pw[NS], *pg[NS];
-    const float4 *klay = nullptr;
-    float4 kl_next = make_float4(0.f, 0.f, 0.f, 0.f), kl_after = kl_next;
-    float4 kb[NS];
-    Corners kc[NS];
-    if constexpr (KT) {
-        klay = kp.kt_lay + kp.lay_off[c];
-        kl_next = klay[0];
-        kl_after = L > 1 ? klay[1] : kl_next;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            kb[i] = __ldg(kp.kt_bin + bI[i]);
-            kc[i] = kt_corners(kp, kl_next, S, sI[i]);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const long long e = cube0 + sI[i];
-            pd[i] = kp.dtau + e;
-            pw[i] = kp.w0 + e;
-            pg[i] = kp.g0 + e;
-            cmp(nd, i) = RT_IN(pd[i], kp.dtau, kp.ext.cube) ? __ldcs(pd[i]) : 0.f;
-            cmp(nw, i) = RT_IN(pw[i], kp.w0, kp.ext.cube) ? __ldcs(pw[i]) : 0.f;
-            cmp(ng, i) = RT_IN(pg[i], kp.g0, kp.ext.cube) ? __ldcs(pg[i]) : 0.f;
-        }
-    }
     float4 *sp = kp.scr32 + slot;
     V *spB = INL ? (V *)kp.scrB + slot : nullptr;
     // two layers per trip: the carried values (B at the levels, the
@@ -1489,69 +1526,90 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
 #pragma unroll
         for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldBk<DIRECT>(kp, Bp[i] - 2 * bst);
     }
-    int gi = 1;              // slots used in the current group of 16 interfaces
-    int gtop = L;            // interface held in slot 0 of the group
-    sp -= sstride;           // interface L-1
-    float4 nst[NS];
+    // The back-substitution does a few operations per level, so each
+    // level's scratch is copied into the shared-memory ring kBackDepth
+    // levels ahead (cp.async, one commit group per level; level i sits in
+    // slot (L - 1 - i) mod (kBackDepth + 1), and the copy of level i - D goes
+    // to the slot read one level earlier).
+    constexpr int D = kBackDepth, NSL = kBackDepth + 1;
+    const float4 *sbase = kp.scr32 + slot;
+    auto issue = [&](int i, int k) {
 #pragma unroll
-    for (int i = 0; i < NS; ++i)
-        nst[i] = RT_IN(sp + i * gthreads, kp.scr32, kp.ext.scr32) ? __ldcg(sp + i * gthreads) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = L - 1; i >= -1; --i) {
-        if (i >= 0) {
-            V Pv, Qq, av, ev;
-            scr_unpack(nst, Pv, Qq, av, ev);
-#pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                // this level's scratch is dead once read: drop its L2
-                // lines (one per 8 lanes) so they are not written back
-                if ((lane & 7) == 0 && RT_IN(sp + j * gthreads, kp.scr32, kp.ext.scr32))
-                    discard_l2_after(sp + j * gthreads, nst[j].x);
-            }
-            const V Bi = nBi;
-            if constexpr (INL) {
-                if ((lane & (32 / NS - 1)) == 0 && RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS))
-                    discard_l2_after(spB, cmp(nBi, 0));
-            }
-#pragma unroll
-            for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
-            if (i > 0) {
-                sp -= sstride;
-#pragma unroll
-                for (int j = 0; j < NS; ++j)
-                    nst[j] = RT_IN(sp + j * gthreads, kp.scr32, kp.ext.scr32) ? __ldcg(sp + j * gthreads)
-                                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-                if constexpr (INL) {
-                    spB -= gthreads;
-                    nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldBk<DIRECT>(kp, Bp[j] - 2 * bst);
-                }
-            }
-            uu = vfma(Pv, uu, Qq);
-            const V fup = vfma(V(kPiF), Bi, uu);
-            Bt = Bi;
-            const V fnet = vfma(av, uu, -ev);
-            tb[(gi * 2) * 33 + lane] = hsum(wg * fup);
-            tb[(gi * 2 + 1) * 33 + lane] = hsum(wg * fnet);
-            ++gi;
+        for (int j = 0; j < NS; ++j) {
+            const float4 *p = sbase + (long long)i * sstride + (long long)j * gthreads;
+            if (RT_IN(p, kp.scr32, kp.ext.scr32)) cp_async16(ring + (k * NS + j) * 32 + lane, p);
         }
-        if (gi == 16 || (i < 0 && gi > 0)) {
-            __syncwarp();
-            // lane j sums row (slot j & 15, quantity j >> 4) over the 32 lanes
-            const int sl = lane & 15, qq = lane >> 4;
-            if (sl < gi) {
-                const float *row = tb + (sl * 2 + qq) * 33;
-                float acc = 0.f;
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) acc += row[j];
-                if (RT_IN(part + 2 * (gtop - sl) + qq, kp.partial, kp.ext.part)) part[2 * (gtop - sl) + qq] = acc;
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (L - 1 - k >= 0) issue(L - 1 - k, k);
+        cp_async_commit();
+    }
+    const int gsh = kp.group_shift, G = 1 << gsh;  // interfaces per transposed sum
+    int gi = 1;              // slots used in the current group of G interfaces
+    int gtop = L;            // interface held in slot 0 of the group
+    for (int i0 = L - 1; i0 >= -1; i0 -= NSL) {
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) {
+            const int i = i0 - k;
+            if (i >= 0) {
+                cp_async_wait<D - 1>();              // level i has landed
+                float4 nst[NS];
+#pragma unroll
+                for (int j = 0; j < NS; ++j) nst[j] = ring[(k * NS + j) * 32 + lane];
+                if (i - D >= 0) issue(i - D, (k + D) % NSL);
+                cp_async_commit();
+                V Pv, Qq, av, ev;
+                scr_unpack(nst, Pv, Qq, av, ev);
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    // this level's scratch is dead once read: drop its L2
+                    // lines (one per 8 lanes) so they are not written back
+                    const float4 *p = sbase + (long long)i * sstride + (long long)j * gthreads;
+                    if ((lane & 7) == 0 && RT_IN(p, kp.scr32, kp.ext.scr32)) discard_l2_after(p, nst[j].x);
+                }
+                const V Bi = nBi;
+                if constexpr (INL) {
+                    if ((lane & (32 / NS - 1)) == 0 && RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS))
+                        discard_l2_after(spB, cmp(nBi, 0));
+                }
+#pragma unroll
+                for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
+                if (i > 0) {
+                    if constexpr (INL) {
+                        spB -= gthreads;
+                        nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldBk<DIRECT>(kp, Bp[j] - 2 * bst);
+                    }
+                }
+                uu = vfma(Pv, uu, Qq);
+                const V fup = vfma(V(kPiF), Bi, uu);
+                Bt = Bi;
+                const V fnet = vfma(av, uu, -ev);
+                tb[(gi * 2) * 33 + lane] = hsum(wg * fup);
+                tb[(gi * 2 + 1) * 33 + lane] = hsum(wg * fnet);
+                ++gi;
             }
-            __syncwarp();
-            gtop -= gi;
-            gi = 0;
+            if (gi == G || (i < 0 && gi > 0)) {
+                __syncwarp();
+                // lane j < 2 G sums row (slot j mod G, quantity j / G) over the 32 lanes
+                const int sl = lane & (G - 1), qq = lane >> gsh;
+                if (qq < 2 && sl < gi) {
+                    const float *row = tb + (sl * 2 + qq) * 33;
+                    float acc = 0.f;
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) acc += row[j];
+                    if (RT_IN(part + 2 * (gtop - sl) + qq, kp.partial, kp.ext.part)) part[2 * (gtop - sl) + qq] = acc;
+                }
+                __syncwarp();
+                gtop -= gi;
+                gi = 0;
+            }
         }
     }
+    cp_async_wait<0>();      // (only empty groups remain)
 #pragma unroll
     for (int i = 0; i < NS; ++i)
         if (cmpm(on, i) && (bad[i] || !isfinite(cmp(uu, i)))) cn.nonfinite++;
@@ -1596,10 +1654,11 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     const int warp = threadIdx.x >> 5;
     float *wsm = smem32 + (size_t)warp * kp.warp_floats;
     const int nbw = kp.nbw;
-    float *sB = wsm;                               // [(2 L + 1) nbc], staged mode
-    float *sFs = wsm + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
+    float4 *ring = reinterpret_cast<float4 *>(wsm);   // [kBackDepth + 1][NS][32], back-substitution
+    float *sB = wsm + back_ring_floats(NS);        // [(2 L + 1) nbc], staged mode
+    float *sFs = sB + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
-    float *tb = sFB + nbw;                         // [16][2][33]
+    float *tb = sFB + nbw;                         // [G][2][33]
     // scratch slots: component i of this thread at slot + i * (threads in the grid)
     const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
@@ -1611,7 +1670,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
+        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, ring, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
     }
     flush_counters(cn, kp.stats);
 }
@@ -2246,14 +2305,16 @@ constexpr int kMaxDynSmem = 200 * 1024;
 
 cudaError_t init_kernels() {
     cudaError_t e = cudaSuccess;
-    for (auto f : {fp32_units<false, false, false, 1>, fp32_units<true, false, false, 1>,
-                   fp32_units<false, true, false, 1>, fp32_units<true, true, false, 1>,
-                   fp32_units<false, false, true, 1>, fp32_units<true, false, true, 1>,
-                   fp32_units<false, true, true, 1>, fp32_units<true, true, true, 1>,
-                   fp32_units<false, false, false, 2>, fp32_units<true, false, false, 2>,
-                   fp32_units<false, true, false, 2>, fp32_units<true, true, false, 2>,
-                   fp32_units<false, false, true, 2>, fp32_units<true, false, true, 2>,
-                   fp32_units<false, true, true, 2>, fp32_units<true, true, true, 2>}) {
+    // every instance of the solve kernel: ISO x staging mode (shared,
+    // direct, inline) x KT x systems per lane
+    for (auto f : {fp32_units<false, 0, false, 1>, fp32_units<true, 0, false, 1>, fp32_units<false, 1, false, 1>,
+                   fp32_units<true, 1, false, 1>, fp32_units<false, 2, false, 1>, fp32_units<true, 2, false, 1>,
+                   fp32_units<false, 0, true, 1>, fp32_units<true, 0, true, 1>, fp32_units<false, 1, true, 1>,
+                   fp32_units<true, 1, true, 1>, fp32_units<false, 2, true, 1>, fp32_units<true, 2, true, 1>,
+                   fp32_units<false, 0, false, 2>, fp32_units<true, 0, false, 2>, fp32_units<false, 1, false, 2>,
+                   fp32_units<true, 1, false, 2>, fp32_units<false, 2, false, 2>, fp32_units<true, 2, false, 2>,
+                   fp32_units<false, 0, true, 2>, fp32_units<true, 0, true, 2>, fp32_units<false, 1, true, 2>,
+                   fp32_units<true, 1, true, 2>, fp32_units<false, 2, true, 2>, fp32_units<true, 2, true, 2>}) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
