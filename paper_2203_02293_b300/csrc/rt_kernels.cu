@@ -415,13 +415,16 @@ struct Layer32 {
 template <class V>
 struct Sub32 {
     V t, r, omtr, suU, sdU, suL, sdL, m;
+    V bu, bd;        // SPLIT: beam source coefficients per unit F_beam at the sub-layer top
 };
 
 // Products are grouped by hand: float multiplication is not reassociated by
 // the compiler, and shared factors (1/h and 1/p from one reciprocal of h p,
 // 2q, w0 g0, ...) are formed once per layer.  Multiply-adds are written as
 // vfma so that the scalar and the paired forms round alike.
-template <bool ISO, class V>
+// SPLIT: the beam terms are left out of the sources and returned as bu, bd
+// (the caller applies F_beam; Fb is not read).
+template <bool ISO, class V, bool SPLIT = false>
 __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, float mu, float imu,
                                           double mu_d, bool beam, V Fb, const KParams &kp, Counters &cn,
                                           SysCounts<V> &sc, typename VTraits<V>::M on) {
@@ -495,7 +498,7 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
         sdU = vfma(V(kPiF), vfma(omr, Bc - Bb, -(t * (Bc - Bt))), base);
     }
 
-    V m = V(1.f);
+    V m = V(1.f), bu_o = V(0.f), bd_o = V(0.f);
     if (beam) {
         const V dl = dts * V(imu);
         m = vexpn(dl);
@@ -527,12 +530,17 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
         if (__any_sync(0xffffffffu, vany(near))) {
             resonance_fix(near, on, w0, g0, mu, imu, mu_d, A, iq, G0h, omtr, r, t, omm, m, kp, cn, bu, bd);
         }
-        suU = vfma(Fb, bu, suU);
-        sdU = vfma(Fb, bd, sdU);
-        if (!ISO) {
-            const V Fc = Fb * m;
-            suL = vfma(Fc, bu, suL);
-            sdL = vfma(Fc, bd, sdL);
+        if (SPLIT) {
+            bu_o = bu;
+            bd_o = bd;
+        } else {
+            suU = vfma(Fb, bu, suU);
+            sdU = vfma(Fb, bd, sdU);
+            if (!ISO) {
+                const V Fc = Fb * m;
+                suL = vfma(Fc, bu, suL);
+                sdL = vfma(Fc, bd, sdL);
+            }
         }
     }
 
@@ -545,6 +553,8 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
     o.suL = suL;
     o.sdL = sdL;
     o.m = m;
+    o.bu = bu_o;
+    o.bd = bd_o;
     return o;
 }
 
@@ -1847,21 +1857,25 @@ __device__ __forceinline__ SweepLane sweep_lane(const KParams &kp, int unit, int
     return q;
 }
 
-template <bool ISO, bool DIRECT>
-__device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
-                                           float *fbs, float *SU, float *SD, float *TR) {
-    constexpr int LR = kSweepMaxLayers;
-    constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
-    float t[LR], r[LR], X[NLV];
+// What the sweeps start from: the column's L, d at the TOA level and u - d
+// at the BOA (Eq. 10).
+struct SweepStart {
     int L;
     float d0, ubc;
+};
 
-    // ---- coefficient pass: stage B, F*, F_BOA; per layer (t, r) and the
-    // sub-layer sources into shared memory; then t, r and the starting state
-    // into registers
+// The coefficient pass of a sweep unit: stage B, F*, F_BOA; per layer (t, r)
+// and the sub-layer sources into shared memory, and the warp sums of w F_beam
+// at the interfaces.  (Inlined: as a call, or with the staging issued as
+// asynchronous copies, the sweeps' register arrays spill.)
+template <bool ISO, bool DIRECT>
+__device__ __forceinline__ SweepStart sweep_coefficients(const KParams &kp, int unit, int lane, float *sB, float *sFs,
+                                                      float *sFB, float *fbs, float *SU, float *SD, float *TR) {
     {
         const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
-        L = q.L;
+        const int L = q.L;
+        constexpr int LR = kSweepMaxLayers;
+        float d0, ubc;
         {
             const float *Bg = kp.planck32 + kp.planck_off[q.c] + q.b_lo;
             const int nlev = 2 * L + 1;
@@ -1878,75 +1892,129 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
                 sFB[j] = RT_IN(kp.fboa32 + jb, kp.fboa32, kp.ext.bins) ? __ldcg(kp.fboa32 + jb) : 0.f;
             }
         }
-        __syncwarp();
+        const long long e0 = kp.cube_off[q.c] + (q.on ? q.s0 + lane : q.s0);
+        const float *pd = kp.dtau + e0, *pw = kp.w0 + e0, *pg = kp.g0 + e0;
+        auto ld_opt = [&](int l, float &d, float &w, float &g) {    // the optics of layer l
+            const long long o = (long long)l * q.S;
+            d = RT_IN(pd + o, kp.dtau, kp.ext.cube) ? __ldcs(pd + o) : 0.f;
+            w = RT_IN(pw + o, kp.w0, kp.ext.cube) ? __ldcs(pw + o) : 0.f;
+            g = RT_IN(pg + o, kp.g0, kp.ext.cube) ? __ldcs(pg + o) : 0.f;
+        };
+        float nd0, nw0, ng0, nd1 = 0.f, nw1 = 0.f, ng1 = 0.f;
+        ld_opt(0, nd0, nw0, ng0);
+        if (L > 1) ld_opt(1, nd1, nw1, ng1);
         const float4 cf = kp.colf[q.c];
         const float mu = cf.x, imu = cf.y;
         const double mu_d = ck_ld(kp, kp.mu_star, kp.ext.mu, kp.mu_idx[q.c]);
         const bool beam = cf.z != 0.f;
+        __syncwarp();                                              // the staged values of every lane
         float Fb = beam ? mu * sFs[q.bI - q.b_lo] : 0.f;
         const float FBOA = sFB[q.bI - q.b_lo];
         Counters cu = {0, 0, 0, 0, 0, 0, 0};
         SysCounts<float> sc;
         sc.inv = sc.ecl = sc.etau = 0u;
+        SysCounts<V2> sc2;
+        sc2.inv = sc2.ecl = sc2.etau = U2{0u, 0u};
+        const M2 on2 = M2{q.on, q.on};
         float2 *TR2 = reinterpret_cast<float2 *>(TR);
-        const long long e0 = kp.cube_off[q.c] + (q.on ? q.s0 + lane : q.s0);
-        const float *pd = kp.dtau + e0, *pw = kp.w0 + e0, *pg = kp.g0 + e0;
-        float nd = RT_IN(pd, kp.dtau, kp.ext.cube) ? __ldcs(pd) : 0.f;   // next layer prefetched
-        float nw = RT_IN(pw, kp.w0, kp.ext.cube) ? __ldcs(pw) : 0.f;
-        float ng = RT_IN(pg, kp.g0, kp.ext.cube) ? __ldcs(pg) : 0.f;
+        auto wsum = [](float v) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        };
+        auto put = [&](int l, float tl, float rl, float uU, float uL, float dU, float dL) {
+            TR2[l * 32 + lane] = make_float2(tl, rl);
+            if constexpr (ISO) {
+                SU[l * 32 + lane] = uU;
+                SD[l * 32 + lane] = dU;
+            } else {
+                reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(uU, uL);
+                reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(dU, dL);
+            }
+        };
+        // layers l and l + 1 side by side on the paired instructions (they
+        // are independent but for F_beam, applied here from the running
+        // product); the next pair's optics prefetched; an odd last layer alone
         float Bt = ldBk<DIRECT>(kp, q.Bp);
         d0 = fmaf(-kPiF, Bt, (float)kp.F_toa);                     // d at the TOA level
-        for (int l = 0; l < L; ++l) {
-            const float dt = nd, w0 = nw, g0 = ng;
-            if (l + 1 < L) {
-                pd += q.S;
-                pw += q.S;
-                pg += q.S;
-                nd = RT_IN(pd, kp.dtau, kp.ext.cube) ? __ldcs(pd) : 0.f;
-                nw = RT_IN(pw, kp.w0, kp.ext.cube) ? __ldcs(pw) : 0.f;
-                ng = RT_IN(pg, kp.g0, kp.ext.cube) ? __ldcs(pg) : 0.f;
+        int l = 0;
+        for (; l + 1 < L; l += 2) {
+            const V2 dt(nd0, nd1), w0(nw0, nw1), g0(ng0, ng1);
+            if (l + 2 < L) ld_opt(l + 2, nd0, nw0, ng0);
+            if (l + 3 < L) ld_opt(l + 3, nd1, nw1, ng1);
+            const float B1 = ldBk<DIRECT>(kp, q.Bp + (2 * l + 1) * q.bst);
+            const float B2 = ldBk<DIRECT>(kp, q.Bp + (2 * l + 2) * q.bst);
+            const float B3 = ldBk<DIRECT>(kp, q.Bp + (2 * l + 3) * q.bst);
+            const float B4 = ldBk<DIRECT>(kp, q.Bp + (2 * l + 4) * q.bst);
+            const Sub32<V2> sb = sub32<ISO, V2, true>(dt, w0, g0, V2(Bt, B2), V2(B1, B3), V2(B2, B4), mu, imu, mu_d,
+                                                      beam, V2(0.f), kp, cu, sc2, on2);
+            const float m0 = sb.m.v.x, m1 = sb.m.v.y;
+            const float Fb0 = Fb, Fb1 = ISO ? Fb0 * m0 : Fb0 * (m0 * m0);
+            const float fw0 = wsum(q.wg * Fb0), fw1 = wsum(q.wg * Fb1);    // interfaces l, l + 1
+            if (lane == 0) {
+                fbs[l] = fw0;
+                fbs[l + 1] = fw1;
             }
+            V2 uU = sb.suU, dU = sb.sdU, uL = sb.suL, dL = sb.sdL;
+            if (beam) {
+                const V2 F(Fb0, Fb1);
+                uU = vfma(F, sb.bu, uU);
+                dU = vfma(F, sb.bd, dU);
+                if constexpr (!ISO) {
+                    const V2 Fc = F * sb.m;
+                    uL = vfma(Fc, sb.bu, uL);
+                    dL = vfma(Fc, sb.bd, dL);
+                }
+            }
+            put(l, sb.t.v.x, sb.r.v.x, uU.v.x, uL.v.x, dU.v.x, dL.v.x);
+            put(l + 1, sb.t.v.y, sb.r.v.y, uU.v.y, uL.v.y, dU.v.y, dL.v.y);
+            Fb = ISO ? Fb1 * m1 : Fb1 * (m1 * m1);
+            Bt = B4;
+        }
+        if (l < L) {
             const float Bc = ldBk<DIRECT>(kp, q.Bp + (2 * l + 1) * q.bst);
             const float Bb = ldBk<DIRECT>(kp, q.Bp + (2 * l + 2) * q.bst);
-            float fw = q.wg * Fb;                                  // interface l: warp sum of w F_beam
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
+            const float fw = wsum(q.wg * Fb);                          // interface l
             if (lane == 0) fbs[l] = fw;
             const Sub32<float> sb =
-                sub32<ISO, float>(dt, w0, g0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cu, sc, q.on);
-            TR2[l * 32 + lane] = make_float2(sb.t, sb.r);
-            if constexpr (ISO) {
-                SU[l * 32 + lane] = sb.suU;
-                SD[l * 32 + lane] = sb.sdU;
-                Fb *= sb.m;
-            } else {
-                reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(sb.suU, sb.suL);
-                reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(sb.sdU, sb.sdL);
-                Fb *= sb.m * sb.m;
-            }
-            Bt = Bb;
+                sub32<ISO, float>(nd0, nw0, ng0, Bt, Bc, Bb, mu, imu, mu_d, beam, Fb, kp, cu, sc, q.on);
+            put(l, sb.t, sb.r, sb.suU, sb.suL, sb.sdU, sb.sdL);
+            Fb *= ISO ? sb.m : sb.m * sb.m;
         }
         // identity layers below the BOA up to the register limit (t = 1, r = 0, no source)
-        for (int l = L; l < LR; ++l) {
-            TR2[l * 32 + lane] = make_float2(1.f, 0.f);
-            if constexpr (ISO) {
-                SU[l * 32 + lane] = 0.f;
-                SD[l * 32 + lane] = 0.f;
-            } else {
-                reinterpret_cast<float2 *>(SU)[l * 32 + lane] = make_float2(0.f, 0.f);
-                reinterpret_cast<float2 *>(SD)[l * 32 + lane] = make_float2(0.f, 0.f);
-            }
+        for (int k = L; k < LR; ++k) put(k, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        {
+            const float fw = wsum(q.wg * Fb);                          // the BOA interface
+            if (lane == 0) fbs[L] = fw;
         }
-        float fw = q.wg * Fb;                                      // the BOA interface
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fw += __shfl_xor_sync(0xffffffffu, fw, o);
-        if (lane == 0) fbs[L] = fw;
         ubc = FBOA + Fb;                                           // u - d at the BOA (Eq. 10)
-        cu.inv = vmasked(sc.inv, q.on);
-        cu.eclamp = vmasked(sc.ecl, q.on);
-        cu.etau = (ISO ? 1u : 2u) * vmasked(sc.etau, q.on);
+        cu.inv = vmasked(sc.inv, q.on) + vmasked(sc2.inv, on2);
+        cu.eclamp = vmasked(sc.ecl, q.on) + vmasked(sc2.ecl, on2);
+        cu.etau = (ISO ? 1u : 2u) * (vmasked(sc.etau, q.on) + vmasked(sc2.etau, on2));
         flush_counters(cu, kp.stats);                              // per unit: nothing kept live
         __syncwarp();
+        return SweepStart{L, d0, ubc};
+    }
+}
+
+template <bool ISO, bool DIRECT>
+__device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
+                                           float *fbs, float *SU, float *SD, float *TR) {
+    constexpr int LR = kSweepMaxLayers;
+    constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
+    float t[LR], r[LR], X[NLV];
+    int L;
+    float d0, ubc;
+
+    // ---- coefficient pass into shared memory; then t, r and the starting
+    // state into registers
+    {
+        const SweepStart st = sweep_coefficients<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR);
+        L = st.L;
+        d0 = st.d0;
+        ubc = st.ubc;
+        const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
+        const float2 *TR2 = reinterpret_cast<const float2 *>(TR);
 #pragma unroll
         for (int l = 0; l < LR; ++l) {
             const float2 v = TR2[l * 32 + lane];
