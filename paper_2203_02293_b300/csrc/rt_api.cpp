@@ -304,10 +304,10 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                 // unless 8 (half the transpose buffer) keep more CTAs
                 // resident: tall columns' staged B fills shared memory
                 P.group_shift = 4;
-                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4);
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4, P.inline_b);
                 occ = rt::occupancy(0, P.block, P.smem, P.ns);
                 {
-                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3);
+                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3, P.inline_b);
                     const int occ8 = rt::occupancy(0, P.block, sm8, P.ns);
                     const int cap = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 1 << 20;
                     if (std::min(occ8, cap) > std::min(occ, cap)) {
@@ -316,7 +316,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                         occ = occ8;
                     }
                 }
-                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift);
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift, P.inline_b);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }

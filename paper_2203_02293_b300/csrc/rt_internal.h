@@ -96,8 +96,8 @@ struct KParams {
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift);
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b);
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b);
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);

@@ -618,17 +618,23 @@ __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk
 // per system, the spare slot being the one read a level earlier.
 constexpr int kBackDepth = 2;
 __host__ __device__ constexpr int back_ring_floats(int ns) { return (kBackDepth + 1) * ns * 32 * 4; }
+// Inline B: B at the interfaces rides along in a second ring ([slot][32] of
+// the lane's ns values).
+__host__ __device__ constexpr int back_ringB_floats(int ns, int inline_b) {
+    return inline_b ? (kBackDepth + 1) * ns * 32 : 0;
+}
 
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift) {
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b) {
     // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode only)
     // + F* [nbw] + F_BOA [nbw] + transpose [G][2][33], G = 2^group_shift
     // interfaces per transposed sum (at least 2 NS 32 floats for the TOA sum)
     const int tr = std::max((1 << group_shift) * 2 * 33, 64 * ns);
-    int n = back_ring_floats(ns) + (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw + tr;
+    int n = back_ring_floats(ns) + back_ringB_floats(ns, inline_b) + (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw +
+            tr;
     return (n + 3) & ~3;
 }
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift) {
-    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b) {
+    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift, inline_b);
 }
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
@@ -1202,6 +1208,10 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -1253,8 +1263,8 @@ __device__ __forceinline__ bool &cmpm(M2 &m, int i) { return i ? m.y : m.x; }
 // One work unit: SPU = 32 NS consecutive systems of one column, starting at
 // system s0 = ku SPG of the column (SPG: the kernel's unit stride).
 template <bool ISO, int ST, bool KT, int NS, int SPG>
-__device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float4 *ring, float *sB, float *sFs,
-                                          float *sFB,
+__device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float4 *ring, float *ringB, float *sB,
+                                          float *sFs, float *sFB,
                                           float *tb, long long slot, long long gthreads, long long sstride,
                                           Counters &cn) {
     using V = typename std::conditional<NS == 2, V2, float>::type;
@@ -1528,11 +1538,8 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     // Bt holds B at level 2L (the BOA interface)
     tb[lane] = hsum(wg * vfma(V(kPiF), Bt, uu));
     tb[33 + lane] = hsum(wg * FBOA);
-    V nBi;                   // Bp is at level 2L; prefetch one interface up
-    if constexpr (INL) {
-        spB -= gthreads;     // interface L-1
-        nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
-    } else {
+    V nBi = V(0.f);          // Bp is at level 2L; prefetch one interface up (inline B: through the ring)
+    if constexpr (!INL) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldBk<DIRECT>(kp, Bp[i] - 2 * bst);
     }
@@ -1543,11 +1550,20 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     // to the slot read one level earlier).
     constexpr int D = kBackDepth, NSL = kBackDepth + 1;
     const float4 *sbase = kp.scr32 + slot;
+    const V *Bbase = INL ? (const V *)kp.scrB + slot : nullptr;      // inline B at interface i: + i gthreads
+    V *rB = reinterpret_cast<V *>(ringB);
     auto issue = [&](int i, int k) {
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
             const float4 *p = sbase + (long long)i * sstride + (long long)j * gthreads;
             if (RT_IN(p, kp.scr32, kp.ext.scr32)) cp_async16(ring + (k * NS + j) * 32 + lane, p);
+        }
+        if constexpr (INL) {
+            const V *pb = Bbase + (long long)i * gthreads;
+            if (RT_IN(pb, (const V *)kp.scrB, kp.ext.scrB / NS)) {
+                if constexpr (NS == 2) cp_async8(rB + k * 32 + lane, pb);
+                else cp_async4(rB + k * 32 + lane, pb);
+            }
         }
     };
 #pragma unroll
@@ -1578,18 +1594,17 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
                     const float4 *p = sbase + (long long)i * sstride + (long long)j * gthreads;
                     if ((lane & 7) == 0 && RT_IN(p, kp.scr32, kp.ext.scr32)) discard_l2_after(p, nst[j].x);
                 }
-                const V Bi = nBi;
+                V Bi = nBi;
                 if constexpr (INL) {
-                    if ((lane & (32 / NS - 1)) == 0 && RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS))
-                        discard_l2_after(spB, cmp(nBi, 0));
+                    Bi = rB[k * 32 + lane];
+                    const V *pb = Bbase + (long long)i * gthreads;
+                    if ((lane & (32 / NS - 1)) == 0 && RT_IN(pb, (const V *)kp.scrB, kp.ext.scrB / NS))
+                        discard_l2_after(pb, cmp(Bi, 0));
                 }
 #pragma unroll
                 for (int j = 0; j < NS; ++j) Bp[j] -= 2 * bst;     // level 2i
-                if (i > 0) {
-                    if constexpr (INL) {
-                        spB -= gthreads;
-                        nBi = RT_IN(spB, (V *)kp.scrB, kp.ext.scrB / NS) ? ldB_cg(spB) : V(0.f);
-                    } else {
+                if constexpr (!INL) {
+                    if (i > 0) {
 #pragma unroll
                         for (int j = 0; j < NS; ++j) cmp(nBi, j) = ldBk<DIRECT>(kp, Bp[j] - 2 * bst);
                     }
@@ -1665,7 +1680,8 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     float *wsm = smem32 + (size_t)warp * kp.warp_floats;
     const int nbw = kp.nbw;
     float4 *ring = reinterpret_cast<float4 *>(wsm);   // [kBackDepth + 1][NS][32], back-substitution
-    float *sB = wsm + back_ring_floats(NS);        // [(2 L + 1) nbc], staged mode
+    float *ringB = wsm + back_ring_floats(NS);     // inline B: [kBackDepth + 1][32] x NS
+    float *sB = ringB + back_ringB_floats(NS, ST == kStageInline);    // [(2 L + 1) nbc], staged mode
     float *sFs = sB + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [G][2][33]
@@ -1680,7 +1696,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, ring, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
+        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, ring, ringB, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
     }
     flush_counters(cn, kp.stats);
 }
