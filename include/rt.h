@@ -126,7 +126,18 @@ typedef struct {
                                     result converges to Thomas's as N grows.  FP32 form,
                                     cube optics, every column L <= RT_SWEEP_MAX_LAYERS;
                                     RT_EINVAL otherwise.  At most 1 << 20 */
+    int32_t staging_depth;       /* FP32 form, Thomas: levels of elimination scratch
+                                    (and, with RT_STAGE_INLINE, of B) that the
+                                    back-substitution (Eq. 15) has in flight ahead of
+                                    their use, copied into a shared-memory ring
+                                    (cp.async): RT_STAGING_DEPTH_MIN ..
+                                    RT_STAGING_DEPTH_MAX, 0 = RT_STAGING_DEPTH_MIN;
+                                    RT_EINVAL otherwise.  More hides more L2 latency
+                                    and costs shared memory (resident CTAs); results
+                                    are the same bits */
 } rt_config;
+#define RT_STAGING_DEPTH_MIN 2
+#define RT_STAGING_DEPTH_MAX 3
 
 /* Largest layer count of a column solved with n_sweeps > 0 (each GPU lane
  * holds its system's per-layer transmission, reflection and level fluxes in

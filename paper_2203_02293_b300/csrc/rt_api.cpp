@@ -22,6 +22,8 @@
 #include "rt_internal.h"
 
 static_assert(rt::kSweepMaxLayers == RT_SWEEP_MAX_LAYERS, "sweep layer limit differs between rt.h and the kernels");
+static_assert(rt::kBackDepthMin == RT_STAGING_DEPTH_MIN && rt::kBackDepthMax == RT_STAGING_DEPTH_MAX,
+              "staging depths differ between rt.h and the kernels");
 
 namespace {
 
@@ -110,6 +112,7 @@ struct Plan {
     // launch
     int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, inline_b = 0, ns = 1;
     int group_shift = 4;          // FP32 form: log2 of the interfaces per transposed sum
+    int depth = 2;                // FP32 form: back-substitution levels in flight (cfg.staging_depth)
     bool sweeps = false;          // the iterative method (cfg.n_sweeps > 0) instead of Thomas
     size_t smem = 0;
     int64_t n_slots = 0;
@@ -176,6 +179,7 @@ int validate_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool unit
     }
     P.kt = kt;
     P.ns = (fp64 || P.sweeps) ? 1 : (cfg.systems_per_lane == 1 ? 1 : 2);
+    P.depth = cfg.staging_depth > 0 ? cfg.staging_depth : 2;
     const int spu = 32 * P.ns;                    // systems per FP32 work unit
     const int64_t *gath[5] = {c->cube_offset, c->center_offset, c->iface_offset, c->bin_offset, c->col_index};
     for (int g = 0; g < 5; ++g)
@@ -304,10 +308,10 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                 // unless 8 (half the transpose buffer) keep more CTAs
                 // resident: tall columns' staged B fills shared memory
                 P.group_shift = 4;
-                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4, P.inline_b);
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4, P.inline_b, P.depth);
                 occ = rt::occupancy(0, P.block, P.smem, P.ns);
                 {
-                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3, P.inline_b);
+                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3, P.inline_b, P.depth);
                     const int occ8 = rt::occupancy(0, P.block, sm8, P.ns);
                     const int cap = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 1 << 20;
                     if (std::min(occ8, cap) > std::min(occ, cap)) {
@@ -316,7 +320,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                         occ = occ8;
                     }
                 }
-                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift, P.inline_b);
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift, P.inline_b, P.depth);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
@@ -428,6 +432,9 @@ int check_config(const rt_config *cfg) {
     if (cfg->ctas_per_sm < 0) return RT_EINVAL;
     if (cfg->planck_staging < RT_STAGE_AUTO || cfg->planck_staging > RT_STAGE_INLINE) return RT_EINVAL;
     if (cfg->systems_per_lane < 0 || cfg->systems_per_lane > 2) return RT_EINVAL;
+    if (cfg->staging_depth != 0 &&
+        (cfg->staging_depth < RT_STAGING_DEPTH_MIN || cfg->staging_depth > RT_STAGING_DEPTH_MAX))
+        return RT_EINVAL;
     if (cfg->n_edges < 0 || cfg->n_edges == 1 || (cfg->n_edges > 1 && !cfg->wn_edges)) return RT_EINVAL;
     if (cfg->n_sweeps < 0 || cfg->n_sweeps > (1 << 20)) return RT_EINVAL;
     for (int i = 0; i < cfg->n_edges; ++i) {
@@ -738,6 +745,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.n_units = (int32_t)P.n_units;
         kp.warp_floats = P.warp_floats;
         kp.group_shift = P.group_shift;
+        kp.back_depth = P.depth;
         kp.nbw = P.nbw;
         kp.direct = P.direct;
         kp.inline_b = P.inline_b;

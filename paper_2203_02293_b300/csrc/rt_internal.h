@@ -61,6 +61,7 @@ struct KParams {
     int32_t n_units;
     int32_t warp_floats;         // shared-memory floats per warp
     int32_t group_shift;         // FP32 form: log2 of the interfaces per transposed sum (3 or 4)
+    int32_t back_depth;          // FP32 form: back-substitution levels in flight (kBackDepthMin..kBackDepthMax)
     // FP32 form: per-column staging written by fp32_prep
     float *planck32;             // B per column [2L+1][NB] (levels: 2i interface, 2i+1 centre)
     const int64_t *planck_off;   // [n_cols]
@@ -96,8 +97,10 @@ struct KParams {
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b);
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth);
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth);
+// Back-substitution prefetch depths with a kernel instance (kp.back_depth).
+constexpr int kBackDepthMin = 2, kBackDepthMax = 3;
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);

@@ -613,28 +613,27 @@ __host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk
     return b;
 }
 
-// Levels of elimination scratch in flight during the back-substitution, and
-// the shared-memory ring that holds them: kBackDepth + 1 slots of one float4
-// per system, the spare slot being the one read a level earlier.
-constexpr int kBackDepth = 2;
-__host__ __device__ constexpr int back_ring_floats(int ns) { return (kBackDepth + 1) * ns * 32 * 4; }
+// The shared-memory ring of the back-substitution: with `depth` levels of
+// elimination scratch in flight, depth + 1 slots of one float4 per system,
+// the spare slot being the one read a level earlier.
+__host__ __device__ constexpr int back_ring_floats(int ns, int depth) { return (depth + 1) * ns * 32 * 4; }
 // Inline B: B at the interfaces rides along in a second ring ([slot][32] of
 // the lane's ns values).
-__host__ __device__ constexpr int back_ringB_floats(int ns, int inline_b) {
-    return inline_b ? (kBackDepth + 1) * ns * 32 : 0;
+__host__ __device__ constexpr int back_ringB_floats(int ns, int inline_b, int depth) {
+    return inline_b ? (depth + 1) * ns * 32 : 0;
 }
 
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b) {
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
     // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode only)
     // + F* [nbw] + F_BOA [nbw] + transpose [G][2][33], G = 2^group_shift
     // interfaces per transposed sum (at least 2 NS 32 floats for the TOA sum)
     const int tr = std::max((1 << group_shift) * 2 * 33, 64 * ns);
-    int n = back_ring_floats(ns) + back_ringB_floats(ns, inline_b) + (direct ? 0 : (2 * Lmax + 1) * nbw) + 2 * nbw +
-            tr;
+    int n = back_ring_floats(ns, depth) + back_ringB_floats(ns, inline_b, depth) + (direct ? 0 : (2 * Lmax + 1) * nbw) +
+            2 * nbw + tr;
     return (n + 3) & ~3;
 }
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b) {
-    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift, inline_b);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
+    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift, inline_b, depth);
 }
 size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
@@ -1218,6 +1217,7 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+
 // Elimination scratch of one interface: (P, Q, alpha', e) of one system in a
 // float4; for a lane with two systems, (P, Q) of both and (alpha', e) of
 // both in two float4 (component pairs stay in their register pairs).
@@ -1262,7 +1262,7 @@ __device__ __forceinline__ bool &cmpm(M2 &m, int i) { return i ? m.y : m.x; }
 
 // One work unit: SPU = 32 NS consecutive systems of one column, starting at
 // system s0 = ku SPG of the column (SPG: the kernel's unit stride).
-template <bool ISO, int ST, bool KT, int NS, int SPG>
+template <bool ISO, int ST, bool KT, int NS, int SPG, int DEP>
 __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane, float4 *ring, float *ringB, float *sB,
                                           float *sFs, float *sFB,
                                           float *tb, long long slot, long long gthreads, long long sstride,
@@ -1544,11 +1544,11 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         for (int i = 0; i < NS; ++i) cmp(nBi, i) = ldBk<DIRECT>(kp, Bp[i] - 2 * bst);
     }
     // The back-substitution does a few operations per level, so each
-    // level's scratch is copied into the shared-memory ring kBackDepth
-    // levels ahead (cp.async, one commit group per level; level i sits in
-    // slot (L - 1 - i) mod (kBackDepth + 1), and the copy of level i - D goes
-    // to the slot read one level earlier).
-    constexpr int D = kBackDepth, NSL = kBackDepth + 1;
+    // level's scratch is copied into the shared-memory ring DEP levels ahead
+    // (cp.async, one commit group per level; level i sits in slot
+    // (L - 1 - i) mod (DEP + 1), and the copy of level i - DEP goes to the
+    // slot read one level earlier).
+    constexpr int D = DEP, NSL = DEP + 1;
     const float4 *sbase = kp.scr32 + slot;
     const V *Bbase = INL ? (const V *)kp.scrB + slot : nullptr;      // inline B at interface i: + i gthreads
     V *rB = reinterpret_cast<V *>(ringB);
@@ -1671,7 +1671,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     __syncwarp();
 }
 
-template <bool ISO, int ST, bool KT, int NS>
+// DEP: levels of elimination scratch in flight in the back-substitution
+// (kp.back_depth; one instance per offered depth).
+template <bool ISO, int ST, bool KT, int NS, int DEP>
 __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KParams kp) {
     constexpr int SPG = 32 * NS;                   // unit stride within a column
     extern __shared__ __align__(16) float smem32[];
@@ -1679,9 +1681,9 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     const int warp = threadIdx.x >> 5;
     float *wsm = smem32 + (size_t)warp * kp.warp_floats;
     const int nbw = kp.nbw;
-    float4 *ring = reinterpret_cast<float4 *>(wsm);   // [kBackDepth + 1][NS][32], back-substitution
-    float *ringB = wsm + back_ring_floats(NS);     // inline B: [kBackDepth + 1][32] x NS
-    float *sB = ringB + back_ringB_floats(NS, ST == kStageInline);    // [(2 L + 1) nbc], staged mode
+    float4 *ring = reinterpret_cast<float4 *>(wsm);   // [DEP + 1][NS][32], back-substitution
+    float *ringB = wsm + back_ring_floats(NS, DEP);   // inline B: [DEP + 1][32] x NS
+    float *sB = ringB + back_ringB_floats(NS, ST == kStageInline, DEP);   // [(2 L + 1) nbc], staged mode
     float *sFs = sB + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [G][2][33]
@@ -1696,7 +1698,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        fp32_unit<ISO, ST, KT, NS, SPG>(kp, unit, lane, ring, ringB, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
+        fp32_unit<ISO, ST, KT, NS, SPG, DEP>(kp, unit, lane, ring, ringB, sB, sFs, sFB, tb, slot, gthreads, sstride, cn);
     }
     flush_counters(cn, kp.stats);
 }
@@ -2387,18 +2389,23 @@ __global__ void __launch_bounds__(256) kt_optics_kernel(KParams kp, const int64_
 
 constexpr int kMaxDynSmem = 200 * 1024;
 
+// Instance SEL: ISO = SEL & 1, staging mode (SEL / 2) % 3, KT = (SEL / 6) & 1,
+// NS = (SEL / 12) % 2 + 1, DEP = kBackDepthMin + SEL / 24.
+template <int SEL>
+constexpr auto units_kernel() {
+    return &fp32_units<(SEL & 1) != 0, (SEL / 2) % 3, (SEL / 6) % 2 != 0, (SEL / 12) % 2 + 1, kBackDepthMin + SEL / 24>;
+}
+constexpr int kUnitsInstances = 24 * (kBackDepthMax - kBackDepthMin + 1);
+template <int... I>
+std::array<const void *, sizeof...(I)> units_kernels(std::integer_sequence<int, I...>) {
+    return {(const void *)units_kernel<I>()...};
+}
+
 cudaError_t init_kernels() {
     cudaError_t e = cudaSuccess;
     // every instance of the solve kernel: ISO x staging mode (shared,
-    // direct, inline) x KT x systems per lane
-    for (auto f : {fp32_units<false, 0, false, 1>, fp32_units<true, 0, false, 1>, fp32_units<false, 1, false, 1>,
-                   fp32_units<true, 1, false, 1>, fp32_units<false, 2, false, 1>, fp32_units<true, 2, false, 1>,
-                   fp32_units<false, 0, true, 1>, fp32_units<true, 0, true, 1>, fp32_units<false, 1, true, 1>,
-                   fp32_units<true, 1, true, 1>, fp32_units<false, 2, true, 1>, fp32_units<true, 2, true, 1>,
-                   fp32_units<false, 0, false, 2>, fp32_units<true, 0, false, 2>, fp32_units<false, 1, false, 2>,
-                   fp32_units<true, 1, false, 2>, fp32_units<false, 2, false, 2>, fp32_units<true, 2, false, 2>,
-                   fp32_units<false, 0, true, 2>, fp32_units<true, 0, true, 2>, fp32_units<false, 1, true, 2>,
-                   fp32_units<true, 1, true, 2>, fp32_units<false, 2, true, 2>, fp32_units<true, 2, true, 2>}) {
+    // direct, inline) x KT x systems per lane x back-substitution depth
+    for (const void *f : units_kernels(std::make_integer_sequence<int, kUnitsInstances>{})) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -2420,9 +2427,9 @@ int occupancy(int precision_fp64, int block, size_t smem, int ns, int sweeps) {
     int n = 0;
     cudaError_t e = sweeps ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_sweeps<false, false>, block, smem)
                     : precision_fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp64_columns, block, smem)
-                    : ns == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 2>,
+                    : ns == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, 0, false, 2, 2>,
                                                                             block, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, false, false, 1>,
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fp32_units<false, 0, false, 1, 2>,
                                                                             block, smem);
     return e == cudaSuccess ? n : 0;
 }
@@ -2430,14 +2437,14 @@ int occupancy(int precision_fp64, int block, size_t smem, int ns, int sweeps) {
 // fp32_units instantiations, indexed by isothermal + 2 stage + 6 k-table + 12 (two systems per lane)
 template <int SEL>
 void units_launch(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
-    fp32_units<(SEL & 1) != 0, (SEL / 2) % 3, (SEL / 6) % 2 != 0, SEL / 12 + 1><<<grid, block, smem, s>>>(kp);
+    units_kernel<SEL>()<<<grid, block, smem, s>>>(kp);
 }
 using UnitsLaunch = void (*)(const KParams &, int, int, size_t, cudaStream_t);
 template <int... I>
 constexpr std::array<UnitsLaunch, sizeof...(I)> units_table(std::integer_sequence<int, I...>) {
     return {&units_launch<I>...};
 }
-constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, 24>{});
+constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, kUnitsInstances>{});
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
                         cudaEvent_t const *ev) {
@@ -2453,7 +2460,8 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     const int st = kp.inline_b ? kStageInline : (kp.direct ? kStageDirect : kStageShared);
-    const int sel = (kp.isothermal ? 1 : 0) + 2 * st + (kp.kt_lk ? 6 : 0) + (kp.ns == 2 ? 12 : 0);
+    const int dep = kp.back_depth < kBackDepthMin ? kBackDepthMin : kp.back_depth > kBackDepthMax ? kBackDepthMax : kp.back_depth;
+    const int sel = (kp.isothermal ? 1 : 0) + 2 * st + (kp.kt_lk ? 6 : 0) + (kp.ns == 2 ? 12 : 0) + 24 * (dep - kBackDepthMin);
     kUnitsLaunch[sel](kp, grid, block, smem, s);
     e = cudaGetLastError();
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);

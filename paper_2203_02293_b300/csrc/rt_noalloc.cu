@@ -164,7 +164,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     int grid = 0, block = 0;
     int64_t best = 0;
     for (int b = bmax; b >= 64; b -= 32) {
-        const size_t sm = rt::fp32_smem_bytes(b, (int)L, nbw, 0, 1, 4, 0);
+        const size_t sm = rt::fp32_smem_bytes(b, (int)L, nbw, 0, 1, 4, 0, 2);
         const int occ = rt::occupancy(0, b, sm);
         int64_t g = (int64_t)occ * sms;
         const int64_t by_scr = slots_fit / b;
@@ -274,8 +274,9 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.partial = (float *)(base + o_part);
     kp.col_done = done;
     kp.n_units = (int32_t)nu;
-    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0, 1, 4, 0);
+    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0, 1, 4, 0, 2);
     kp.group_shift = 4;
+    kp.back_depth = 2;
     kp.nbw = nbw;
     kp.planck32 = (float *)(base + o_planck);
     kp.planck_off = a.pk;

@@ -23,6 +23,8 @@ RT_FP32_FORM, RT_FP64_PLAIN = 0, 1
 RT_RESONANCE_PAPER, RT_RESONANCE_LIMIT = 0, 1
 RT_STAGE_AUTO, RT_STAGE_SHARED, RT_STAGE_DIRECT, RT_STAGE_INLINE = 0, 1, 2, 3
 RT_SWEEP_MAX_LAYERS = 40
+RT_STAGING_DEPTH_MIN = 2
+RT_STAGING_DEPTH_MAX = 3
 
 _STATUS = {0: "RT_OK", -1: "RT_EINVAL", -2: "RT_ENOMEM", -3: "RT_ECUDA", -4: "RT_ENOTSOLVED",
            -5: "RT_EBUDGET", -6: "RT_ETIMEOUT"}
@@ -42,7 +44,7 @@ class rt_config(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32), ("planck_staging", ctypes.c_int32),
         ("systems_per_lane", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
         ("n_edges", ctypes.c_int32), ("wn_edges", ctypes.POINTER(ctypes.c_double)),
-        ("n_sweeps", ctypes.c_int32),
+        ("n_sweeps", ctypes.c_int32), ("staging_depth", ctypes.c_int32),
     ]
 
 
@@ -182,6 +184,7 @@ class Config:
     kernel_timing: int = 0               # 1: CUDA events around each kernel (rt_kernel_times)
     wn_edges: np.ndarray | None = None   # explicit bin edges (cm^-1); None = uniform bins
     n_sweeps: int = 0                    # 0: Thomas; N > 0: N sweeps of the iterative method
+    staging_depth: int = 0               # back-substitution levels in flight, 2 or 3 (0 = 2)
 
 
 def _config(cfg: Config):
@@ -195,7 +198,7 @@ def _config(cfg: Config):
                   cfg.max_layers, cfg.max_bins, cfg.hbm_budget_bytes, cfg.block_threads,
                   cfg.ctas_per_sm, cfg.planck_staging, cfg.systems_per_lane, cfg.kernel_timing,
                   0 if ed is None else ed.size,
-                  None if ed is None else ed.ctypes.data_as(PD), cfg.n_sweeps)
+                  None if ed is None else ed.ctypes.data_as(PD), cfg.n_sweeps, cfg.staging_depth)
     return c, (gw, ed)
 
 

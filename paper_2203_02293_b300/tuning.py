@@ -7,9 +7,12 @@ the batch plan exist before capture.
 
 ``autotune`` times the persistent kernel's variants on the actual batch with
 CUDA events and keeps the fastest: warps per CTA, resident CTAs per SM,
-systems per lane (one, or two on the paired FP32 instructions) and where
+systems per lane (one, or two on the paired FP32 instructions), where
 the Planck values come from (the pre-kernel's table staged in shared memory
-or read directly, or evaluated in the solve kernel).  Work units are 32 x (systems per lane) systems of one column
+or read directly, or evaluated in the solve kernel) and the staging depth
+(levels of elimination scratch the back-substitution has in flight through
+its shared-memory ring: more hides more L2 latency, but costs resident CTAs
+when tall columns already fill shared memory).  Work units are 32 x (systems per lane) systems of one column
 whatever the shape, and each column is summed in unit order, so candidates
 with the same systems per lane must give the same bits; one that does not
 is rejected (stability check).  Across systems per lane only the rounding
@@ -28,14 +31,17 @@ import torch
 from . import rt
 from .solver import DeviceBatch, Solver
 
-KNOBS = ("block_threads", "ctas_per_sm", "systems_per_lane", "planck_staging")
+KNOBS = ("block_threads", "ctas_per_sm", "systems_per_lane", "planck_staging", "staging_depth")
 
 
 def default_candidates(n_g: int) -> list[dict]:
     staging = ((rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE) if n_g < 8
                else (rt.RT_STAGE_SHARED,))
-    return [dict(block_threads=b, ctas_per_sm=c, systems_per_lane=n, planck_staging=st)
-            for n in (1, 2) for st in staging for b in (128, 256) for c in (0, 2)]
+    # staging depths 2 and 3 for the (faster) two systems per lane; one
+    # system per lane at the default depth
+    return [dict(block_threads=b, ctas_per_sm=c, systems_per_lane=n, planck_staging=st, staging_depth=d)
+            for n in (1, 2) for st in staging for b in (128, 256) for c in (0, 2)
+            for d in ((2, 3) if n == 2 else (2,))]
 
 
 class GraphSolve:

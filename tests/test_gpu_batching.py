@@ -80,6 +80,7 @@ def test_autotuner_candidates_agree():
              for n in (1, 2) for bt, c in ((64, 0), (128, 2), (256, 0), (256, 1))]
     cands.append(dict(block_threads=128, ctas_per_sm=0, systems_per_lane=2, planck_staging=rt.RT_STAGE_DIRECT))
     cands.append(dict(block_threads=256, ctas_per_sm=0, systems_per_lane=2, planck_staging=rt.RT_STAGE_INLINE))
+    cands.append(dict(block_threads=128, ctas_per_sm=0, systems_per_lane=2, staging_depth=3))
     res = autotune(b, cols.g_weights, candidates=cands, reps=2)
     assert res["stable"], res["table"]
     assert res["block_threads"] in (64, 128, 256)
@@ -88,3 +89,30 @@ def test_autotuner_candidates_agree():
     s = Solver(cols.g_weights, **{k: res[k] for k in KNOBS if k in res})
     assert_parity(cols, s.solve_numpy(b), ref, "fp32", "autotuned")
     s.close()
+
+
+@pytest.mark.parametrize("staging", [rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE])
+def test_staging_depths_give_the_same_bits(staging):
+    """The back-substitution's prefetch depth (RT_STAGING_DEPTH_MIN to _MAX levels
+    through the shared-memory ring) moves loads, not arithmetic: every depth
+    gives the same bits, for ragged columns (L from 1 to 200, so the ring's
+    slots wrap at every offset), one and two systems per lane; out-of-range
+    depths are refused."""
+    L, NB = rt_synth.uneven_shapes(40, seed=79, L_range=(1, 200), NB_range=(1, 30))
+    L[:4] = [1, 2, 3, 4]
+    cols = rt_synth.generate(L, NB, 3, seed=80, optics="uniform")
+    b = DeviceBatch(cols)
+    for spl in (1, 2):
+        outs = []
+        for d in range(rt.RT_STAGING_DEPTH_MIN, rt.RT_STAGING_DEPTH_MAX + 1):
+            s = Solver(cols.g_weights, systems_per_lane=spl, planck_staging=staging, staging_depth=d)
+            outs.append(s.solve_numpy(b))
+            s.close()
+        for o in outs[1:]:
+            for k in outs[0]:
+                assert np.array_equal(o[k], outs[0][k]), (spl, k)
+    assert_parity(cols, outs[0], oracle_solve(cols, method_opts()), "fp32", f"staging depths {staging}")
+    for bad in (-1, 1, rt.RT_STAGING_DEPTH_MAX + 1):
+        with pytest.raises(rt.RTError) as e:
+            Solver(cols.g_weights, staging_depth=bad)
+        assert e.value.code == rt.RT_EINVAL
