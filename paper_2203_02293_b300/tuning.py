@@ -34,8 +34,15 @@ from .solver import DeviceBatch, Solver
 KNOBS = ("block_threads", "ctas_per_sm", "systems_per_lane", "planck_staging", "staging_depth")
 
 
-def default_candidates(n_g: int) -> list[dict]:
+# Above about this many layers a unit's staged Planck column, not the
+# register file, limits the resident warps: the direct staging mode (B read
+# from the pre-kernel's table, nothing staged) becomes a candidate.
+TALL_COLUMN_LAYERS = 230
+
+
+def default_candidates(n_g: int, max_layers: int = 0) -> list[dict]:
     staging = ((rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT, rt.RT_STAGE_INLINE) if n_g < 8
+               else (rt.RT_STAGE_SHARED, rt.RT_STAGE_DIRECT) if max_layers > TALL_COLUMN_LAYERS
                else (rt.RT_STAGE_SHARED,))
     # staging depths 2 and 3 for the (faster) two systems per lane; one
     # system per lane at the default depth
@@ -90,7 +97,7 @@ def autotune(batch: DeviceBatch, g_weights, candidates=None, reps: int = 5,
     """Return the fastest stable candidate's knobs (``KNOBS``) and 'ms', with
     'table' (every candidate) and 'stable'.  ``candidates`` are dicts of
     ``KNOBS`` (missing ones take the library defaults)."""
-    candidates = candidates or default_candidates(batch.n_g)
+    candidates = candidates or default_candidates(batch.n_g, int(np.max(batch.n_layers)))
     key = signature(batch, dict(cfg, candidates=candidates))
     cache = {}
     if cache_path and os.path.exists(cache_path):
