@@ -352,10 +352,10 @@ void rt_destroy(rt_handle *h);
  *
  * Fixed launch choices: one system per GPU lane (the regular entry point
  * defaults to two), the Planck values tabulated by the pre-kernel and staged
- * per warp in shared memory, Thomas's algorithm (n_sweeps must be 0).
- * cfg->block_threads caps the CTA size; systems_per_lane, planck_staging,
- * ctas_per_sm, hbm_budget_bytes, kernel_timing, max_layers and max_bins are
- * ignored.  The elimination scratch shares the fixed array with the
+ * per warp in shared memory, Thomas's algorithm (n_sweeps must be 0), the
+ * default staging depth.  cfg->block_threads caps the CTA size;
+ * systems_per_lane, planck_staging, staging_depth, ctas_per_sm,
+ * hbm_budget_bytes, kernel_timing, max_layers and max_bins are ignored.  The elimination scratch shares the fixed array with the
  * per-column tables, so it caps the resident threads: at the 2562-column GCM
  * shape (2562 x 40 x 30 x 20) about one 256-thread CTA per SM runs, roughly
  * a third of the warps rt_solve_columns keeps resident, and the solve takes

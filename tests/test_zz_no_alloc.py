@@ -30,11 +30,11 @@ def _uniform_desc(b: DeviceBatch, L: int, NB: int):
                            b.p_iface, b.mu_star, b.F_star, L=L, NB=NB)
 
 
-def _noalloc(cols, b, L, NB, stream=None):
+def _noalloc(cols, b, L, NB, stream=None, **method):
     out = {k: torch.full((b.n_if,), float("nan"), dtype=torch.float64, device="cuda")
            for k in ("F_up", "F_down", "F_net")}
     out["Q"] = torch.full((b.n_lay,), float("nan"), dtype=torch.float64, device="cuda")
-    cfg = rt.Config(g_weights=cols.g_weights)
+    cfg = rt.Config(g_weights=cols.g_weights, **method)
     rt.rt_solve_uniform_noalloc(cfg, _uniform_desc(b, L, NB), out["F_up"], out["F_down"],
                                 out["F_net"], out["Q"], stream)
     torch.cuda.synchronize()
@@ -55,6 +55,22 @@ def test_noalloc_matches_regular_entry_point_twice():
             e = errors(cols, got, ref, "fp32")
             assert all(v <= 1.0 for v in e.values()), e
         assert all(np.isfinite(first[k]).all() for k in first)
+
+
+def test_noalloc_isothermal_and_regular_closures():
+    """The other method switches (isothermal layers; the regular two-stream
+    closure, E = 1) through the no-allocation entry point, against the
+    regular one."""
+    cols = rt_synth.generate([23] * 41, [11] * 41, 20, seed=73, optics="uniform")
+    b = DeviceBatch(cols)
+    for method in (dict(layers=rt.RT_ISOTHERMAL), dict(two_stream=rt.RT_REGULAR),
+                   dict(layers=rt.RT_ISOTHERMAL, two_stream=rt.RT_REGULAR)):
+        s = Solver(cols.g_weights, **method)
+        ref = s.solve_numpy(b)
+        s.close()
+        got = _noalloc(cols, b, 23, 11, **method)
+        e = errors(cols, got, ref, "fp32")
+        assert all(v <= 1.0 for v in e.values()), (method, e)
 
 
 def test_noalloc_refuses_batches_beyond_its_scratch():
