@@ -624,12 +624,14 @@ __host__ __device__ constexpr int back_ringB_floats(int ns, int inline_b, int de
 }
 
 int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
-    // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode only)
-    // + F* [nbw] + F_BOA [nbw] + transpose [G][2][33], G = 2^group_shift
-    // interfaces per transposed sum (at least 2 NS 32 floats for the TOA sum)
+    // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode), or
+    // the column's 2 Lmax + 1 level temperatures in FP64 (inline B), or
+    // nothing (direct) + F* [nbw] + F_BOA [nbw] + transpose [G][2][33],
+    // G = 2^group_shift interfaces per transposed sum (at least 2 NS 32
+    // floats for the TOA sum)
     const int tr = std::max((1 << group_shift) * 2 * 33, 64 * ns);
-    int n = back_ring_floats(ns, depth) + back_ringB_floats(ns, inline_b, depth) + (direct ? 0 : (2 * Lmax + 1) * nbw) +
-            2 * nbw + tr;
+    const int staged = !direct ? (2 * Lmax + 1) * nbw : inline_b ? 2 * (2 * Lmax + 1) : 0;
+    int n = back_ring_floats(ns, depth) + back_ringB_floats(ns, inline_b, depth) + staged + 2 * nbw + tr;
     return (n + 3) & ~3;
 }
 size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
@@ -1300,6 +1302,17 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
                 else sB[i] = 0.f;
             }
         }
+        if constexpr (INL) {
+            // the column's temperatures at its 2L+1 levels (2i: interface i,
+            // 2i + 1: centre of layer i), in FP64 as given
+            double *sT = reinterpret_cast<double *>(sB);
+            for (int lev = lane; lev < nlev; lev += 32) {
+                const double *pT = (lev & 1) ? kp.T_center + kp.tc_off[c] + (lev >> 1) : kp.T_iface + kp.if_off[c] + (lev >> 1);
+                if (RT_IN(pT, (lev & 1) ? kp.T_center : kp.T_iface, (lev & 1) ? kp.ext.center : kp.ext.iface))
+                    cp_async8(sT + lev, pT);
+                else sT[lev] = 0.0;
+            }
+        }
         for (int j = lane; j < nbc; j += 32) {
             const long long jb = kp.bin_off[c] + b_lo + j;
             if (RT_IN(kp.fs32 + jb, kp.fs32, kp.ext.bins)) cp_async4(sFs + j, kp.fs32 + jb);
@@ -1320,14 +1333,11 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     const int bst = DIRECT ? NB : nbc;         // level stride of Bp
     // INL: the bins' edges and FP64-formed widths, and the level temperatures
     float wn0[NS], wn1[NS], dnu[NS];
-    const long long tc0 = kp.tc_off[c], ifi = kp.if_off[c];
     V wn0v, wn1v, dnuv;
     bool unit_narrow = false;                  // INL: the unit's bins take two points at every level
+    const double *sTd = reinterpret_cast<const double *>(sB);   // INL: the level temperatures, staged
     auto B_at = [&](int lev, V &B) {           // B of the lane's systems at level lev
-        const double *pT = (lev & 1) ? kp.T_center + tc0 + (lev >> 1) : kp.T_iface + ifi + (lev >> 1);
-        const double Td = RT_IN(pT, (lev & 1) ? kp.T_center : kp.T_iface, (lev & 1) ? kp.ext.center : kp.ext.iface)
-                              ? __ldg(pT) : 0.0;
-        const PlanckLevel lv = planck_level((float)Td, 1.f);
+        const PlanckLevel lv = planck_level((float)sTd[lev], 1.f);
         // narrow bins that take two quadrature points (the R = 500 shape):
         // the lane's systems together on the paired instructions; any other
         // bin through the per-system rule (the same bits either way)
@@ -1684,7 +1694,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     float4 *ring = reinterpret_cast<float4 *>(wsm);   // [DEP + 1][NS][32], back-substitution
     float *ringB = wsm + back_ring_floats(NS, DEP);   // inline B: [DEP + 1][32] x NS
     float *sB = ringB + back_ringB_floats(NS, ST == kStageInline, DEP);   // [(2 L + 1) nbc], staged mode
-    float *sFs = sB + (ST != kStageShared ? 0 : (2 * kp.Lmax + 1) * nbw);    // [nbc]
+    float *sFs = sB + (ST == kStageShared ? (2 * kp.Lmax + 1) * nbw : ST == kStageInline ? 2 * (2 * kp.Lmax + 1) : 0);   // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [G][2][33]
     // scratch slots: component i of this thread at slot + i * (threads in the grid)
