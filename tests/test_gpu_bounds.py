@@ -47,7 +47,8 @@ def test_config3_sample_under_bounds_checks(checked, precision):
     L, NB = rt_synth.uneven_shapes(4096, seed=3)
     idx = np.array([0, 17, 1024, 2048, 4095, int(np.argmax(L * NB)), int(np.argmin(L * NB))])
     cols = rt_synth.generate(L[idx], NB[idx], 20 if precision == "fp32" else 4, seed=3, optics="uniform")
-    for extra in ({}, dict(systems_per_lane=1), dict(planck_staging=rt.RT_STAGE_DIRECT)):
+    for extra in ({}, dict(systems_per_lane=1), dict(planck_staging=rt.RT_STAGE_DIRECT),
+                  dict(staging_depth=rt.RT_STAGING_DEPTH_MAX)):
         if precision == "fp64" and extra:
             continue
         got = gpu_solve(cols, method_opts(), precision, **extra)
