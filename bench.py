@@ -902,6 +902,21 @@ def main():
                                    "slowdown_vs_thomas": ms / ms32,
                                    "max_rel_dev_from_thomas": dev})
             sw.close()
+        if len(counts) >= 2:
+            # a sweep's roofline: the passes read each sub-layer's source
+            # from shared memory (4 B per sub-layer and pass: 640 B per
+            # 40-layer system and sweep) against 148 SMs x 128 B/clock;
+            # the per-sweep time is the kernel-time difference between the
+            # two sweep counts (the coefficient pass cancels)
+            r0, r1 = sweeps["runs"][0], sweeps["runs"][-1]
+            per_sweep_ms = (r1["kernel_ms"] - r0["kernel_ms"]) / (r1["n_sweeps"] - r0["n_sweeps"])
+            smem_bytes = 2 * 40 * 2 * 4 * n_sys
+            peak_tbs = N_SM * 128 * max_mhz * 1e6 / 1e12
+            sweeps["sweep_roofline"] = {
+                "bound": "shared memory", "per_sweep_us": per_sweep_ms * 1e3,
+                "bytes_per_sweep": smem_bytes, "achieved": smem_bytes / (per_sweep_ms * 1e-3) / 1e12,
+                "peak": peak_tbs, "unit": "TB/s", "frac": smem_bytes / (per_sweep_ms * 1e-3) / 1e12 / peak_tbs,
+                "peak_source": "derived: 148 SMs x 128 B/clock x max SM clock"}
     s32.close()
 
     line = {
