@@ -329,6 +329,14 @@ const char *rt_last_error(const rt_handle *h);
 /* Free the handle and its workspace (synchronises the device). */
 void rt_destroy(rt_handle *h);
 
+/* Failure injection, for tests of the callers' error handling: the next n
+ * device workspace allocations (any handle's, when a solve must grow its
+ * workspace) fail as an out-of-memory device would, and the call that needed
+ * them returns RT_ENOMEM ("injected" in rt_last_error).  The handle stays
+ * usable: its next call allocates again.  n = 0 clears; n < 0 is RT_EINVAL.
+ * Nothing is launched or allocated by this call.  Returns RT_OK. */
+int rt_inject_alloc_failures(int n);
+
 /* ---------------------------------------------------------------------
  * Solve without allocating.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc -- programs whose device

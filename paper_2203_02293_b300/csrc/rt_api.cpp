@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -365,6 +366,9 @@ bool stream_capturing(cudaStream_t s) {
     return st != cudaStreamCaptureStatusNone;
 }
 
+// Pending injected allocation failures (rt_inject_alloc_failures).
+std::atomic<int> g_inject_allocs{0};
+
 int grow(rt_handle *h, DevBuf &b, size_t need, bool capturing, const char *what) {
     if (b.cap >= need) return RT_OK;
     if (capturing)
@@ -377,6 +381,8 @@ int grow(rt_handle *h, DevBuf &b, size_t need, bool capturing, const char *what)
         b.p = nullptr;
         b.cap = 0;
     }
+    if (g_inject_allocs.load() > 0 && g_inject_allocs.fetch_sub(1) > 0)
+        return fail(h, RT_ENOMEM, "cudaMalloc(%zu) for %s: injected failure", need, what);
     cudaError_t e = cudaMalloc(&b.p, need);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1081,6 +1087,12 @@ int rt_stats(rt_handle *h, rt_stats_t *out) {
 }
 
 const char *rt_last_error(const rt_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int rt_inject_alloc_failures(int n) {
+    if (n < 0) return RT_EINVAL;
+    g_inject_allocs.store(n);
+    return RT_OK;
+}
 
 void rt_destroy(rt_handle *h) {
     if (!h) return;

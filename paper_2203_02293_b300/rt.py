@@ -112,6 +112,8 @@ def _load(path: str = LIB_PATH) -> ctypes.CDLL:
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p]
     lib.rt_solve_uniform_noalloc.restype = ctypes.c_int
+    lib.rt_inject_alloc_failures.argtypes = [ctypes.c_int]
+    lib.rt_inject_alloc_failures.restype = ctypes.c_int
     for f in ("rt_create", "rt_query_bytes", "rt_solve_columns", "rt_fluxes", "rt_heating",
               "rt_toa_spectrum", "rt_stats", "rt_set_ktable", "rt_ktable_optics", "rt_solve_ktable",
               "rt_kernel_times", "rt_check_columns"):
@@ -329,6 +331,12 @@ def rt_last_error(h) -> str:
 def rt_destroy(h):
     if h:
         lib().rt_destroy(h)
+
+
+def rt_inject_alloc_failures(n: int):
+    """Make the next ``n`` device workspace allocations fail (RT_ENOMEM);
+    0 clears.  A test hook for callers' error handling."""
+    _check(lib().rt_inject_alloc_failures(n))
 
 
 def rt_solve_uniform_noalloc(cfg: Config, cols, F_up, F_down, F_net, Q, stream=None):

@@ -12,6 +12,9 @@ different slots overlap on the device.  A
 request's latency runs from its arrival to the host seeing its batch's
 completion event.  Requests that can never fit the budget are refused; a
 request may be cancelled while it waits or refused after a waiting timeout.
+A batch whose launch the library refuses (its workspace could not be
+allocated: RT_ENOMEM, or RT_EBUDGET) fails its requests; the slot and its
+handle go on serving.
 
 With ``split_systems`` set, a request larger than that many systems is cut
 into pieces of whole columns when it arrives; the pieces wait, are admitted
@@ -218,6 +221,7 @@ class Server:
                       for _ in range(n_slots)]
         self.in_flight_bytes = 0
         self.batches = 0
+        self.failures: list[str] = []    # messages of launches the library refused
 
     def close(self):
         for s in self.slots:
@@ -264,8 +268,8 @@ class Server:
     @staticmethod
     def _end(r: Request, status: str, now: float) -> int:
         """End a waiting request or piece; returns 1 when that ends a request
-        (a split request ends with its first piece to be refused, cancelled
-        or timed out; its other pieces are then dropped)."""
+        (a split request ends with its first piece to be refused, cancelled,
+        timed out or failed; its other pieces are then dropped)."""
         r.status, r.t_done = status, now
         p = r.parent
         if p is None:
@@ -353,7 +357,19 @@ class Server:
                     continue
                 torch.cuda.nvtx.range_push(f"serve batch {self.batches}: {len(batch)} requests")
                 s.active = pick(batch)
-                rt.rt_solve_columns(s.active.h, desc, s.stream)
+                try:
+                    rt.rt_solve_columns(s.active.h, desc, s.stream)
+                except rt.RTError as e:
+                    # the launch was refused (e.g. its workspace could not be
+                    # allocated): its requests fail, the slot stays free and
+                    # the handle serves the next batch
+                    torch.cuda.nvtx.range_pop()
+                    if e.code not in (rt.RT_ENOMEM, rt.RT_EBUDGET):
+                        raise
+                    for r in batch:
+                        done += self._end(r, "failed", now)
+                    self.failures.append(str(e))
+                    continue
                 s.event.record(s.stream)
                 torch.cuda.nvtx.range_pop()
                 t_admit = time.perf_counter() - t0
@@ -384,6 +400,7 @@ def summarize(requests, wall: float, batches: int) -> dict:
         "refused": sum(r.status == "refused" for r in requests),
         "cancelled": sum(r.status == "cancelled" for r in requests),
         "timeout": sum(r.status == "timeout" for r in requests),
+        "failed": sum(r.status == "failed" for r in requests),
         "batches": batches,
         "p50_ms": float(np.percentile(lat, 50)) if ok else None,
         "p99_ms": float(np.percentile(lat, 99)) if ok else None,

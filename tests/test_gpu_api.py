@@ -219,3 +219,36 @@ def test_kernel_times_are_recorded_on_request():
         assert solve > 0.0 and prep >= 0.0
         assert (prep > 0.0) == (prec == rt.RT_FP32_FORM)
         s.close()
+
+
+def test_injected_allocation_failure_leaves_the_handle_usable():
+    """An allocation failure injected on the host (the next workspace
+    allocation fails as on an out-of-memory device): the solve returns
+    RT_ENOMEM with its message, nothing is left pending, and the same handle's
+    next solve allocates and gives the same results as a fresh handle."""
+    cols = rt_synth.generate([12, 30, 7], [9, 4, 11], 20, seed=91, optics="uniform")
+    b = DeviceBatch(cols)
+    fresh = Solver(cols.g_weights)
+    ref = fresh.solve_numpy(b)
+    fresh.close()
+    s = Solver(cols.g_weights)
+    rt.rt_inject_alloc_failures(1)
+    with pytest.raises(rt.RTError) as e:
+        s.solve(b)
+    assert e.value.code == rt.RT_ENOMEM and "injected" in str(e.value)
+    got = s.solve_numpy(b)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    # a workspace that must grow again after a larger batch
+    big = DeviceBatch(rt_synth.generate([40] * 8, [30] * 8, 20, seed=92, optics="uniform"))
+    rt.rt_inject_alloc_failures(2)
+    for _ in range(2):
+        with pytest.raises(rt.RTError) as e:
+            s.solve(big)
+        assert e.value.code == rt.RT_ENOMEM
+    s.solve(big)
+    torch.cuda.synchronize()
+    rt.rt_inject_alloc_failures(0)
+    with pytest.raises(rt.RTError):
+        rt.rt_inject_alloc_failures(-1)
+    s.close()

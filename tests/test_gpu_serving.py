@@ -119,3 +119,20 @@ def test_cancelling_a_split_request_drops_its_waiting_pieces(pool):
     assert summ["cancelled"] + summ["done"] == 10
     if reqs[4].status == "cancelled":
         assert all(p.status in ("dropped", "cancelled", "done") for p in reqs[4].pieces)
+
+
+def test_a_refused_launch_fails_its_requests_and_serving_goes_on(pool):
+    """An allocation failure injected on the host makes one batch's launch
+    return RT_ENOMEM: that batch's requests fail, the slot and its handle
+    serve the rest, and every other request completes."""
+    reqs = make_requests(pool, 12, rate_hz=3000.0, seed=12, C_range=(1, 16))
+    srv = Server(pool, n_slots=2)
+    rt.rt_inject_alloc_failures(1)
+    try:
+        summ = srv.run(reqs)
+    finally:
+        rt.rt_inject_alloc_failures(0)
+        srv.close()
+    assert summ["failed"] >= 1 and summ["done"] + summ["failed"] == 12, summ
+    assert srv.failures and "injected" in srv.failures[0]
+    assert all(r.status in ("done", "failed") for r in reqs)
