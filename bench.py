@@ -772,6 +772,7 @@ def main():
     # --- FP64 plain path on the same batch ---
     s64 = Solver(cols.g_weights, precision=rt.RT_FP64_PLAIN)
     ms64 = max_over_ranks(timed(s64, batch, args.fp64_steps, 3))
+    accuracy = fp32_errors(cols, s32.outputs(batch, stream), s64.outputs(batch, stream))
     s64.close()
 
     # --- end to end through the public API with pinned host buffers ---
@@ -930,6 +931,7 @@ def main():
         "fp64_plain": {"value": n_sys * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                        "steps": args.fp64_steps},
         "fp32_over_fp64": ms64 / ms32,
+        "fp32_error_vs_fp64": accuracy,
         "two_streams": {"value": n_sys * ws / (ms32_2 * 1e-3), "unit": UNIT, "ms_per_step": ms32_2,
                         "note": "the same resident batch solved on two handles and streams in turn, "
                                 "as independent batches would be (serving): consecutive steps overlap, "
@@ -967,10 +969,40 @@ def main():
     return 0
 
 
+def fp32_errors(cols, o32, o64) -> dict:
+    """Per quantity, the FP32 form's largest relative error against the FP64
+    plain path on the same batch (which matches the FP64 oracle to 1e-10),
+    and its largest error over the FP32 tolerance of the parity tests:
+    max(1e-4 |x|, 1e-6 F*_col) for fluxes, max(1e-3 |Q|, (g / c_P) 1e-6
+    F*_col / dp) for heating (F*_col: the column's stellar flux); beside it
+    the stricter reading with the relative factor on the floor as well,
+    1e-4 max(|x|, 1e-6 F*_col) (1e-3 for Q)."""
+    import torch
+    from paper_2203_02293_b300 import rt
+    torch.cuda.synchronize()
+    o = cols.offsets()
+    L = cols.n_layers.astype(np.int64)
+    fstar = np.add.reduceat(np.asarray(cols.F_star, np.float64), o["bins"][:-1])
+    f_if = np.repeat(1e-6 * fstar, L + 1)
+    dp = np.diff(np.asarray(cols.p_iface, np.float64))
+    dp = np.delete(dp, o["iface"][1:-1] - 1)            # drop the differences across columns
+    c = rt.Config(g_weights=cols.g_weights)
+    f_q = c.grav / c.cp * np.repeat(1e-6 * fstar, L) / dp
+    out = {"reference": "FP64 plain GPU path, same batch and launch"}
+    for k, floor, rtol in (("F_up", f_if, 1e-4), ("F_down", f_if, 1e-4), ("F_net", f_if, 1e-4), ("Q", f_q, 1e-3)):
+        x, y = o32[k].cpu().numpy(), o64[k].cpu().numpy()
+        err = np.abs(x - y)
+        out[k] = {"max_rel": float(np.max(err / np.maximum(np.abs(y), 1e-300))),
+                  "max_err_over_tol": float(np.max(err / np.maximum(rtol * np.abs(y), floor))),
+                  "max_err_over_strict_tol": float(np.max(err / (rtol * np.maximum(np.abs(y), floor))))}
+    return out
+
+
 def write_metrics_log(path: str, line: dict):
     """Append one JSON object per section of a bench line to a JSONL file:
-    throughput, roofline fractions, latency percentiles, branch-hit counts
-    and the host core count, each with the run's time stamp."""
+    throughput, roofline fractions, the FP32 form's per-quantity error,
+    latency percentiles, branch-hit counts and the host core count, each with
+    the run's time stamp."""
     import time
     stamp = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
     recs = [{"section": "gcm_fp32_form", "value": line["value"], "unit": line["unit"],
@@ -981,7 +1013,7 @@ def write_metrics_log(path: str, line: dict):
             {"section": "e2e", **line["e2e"]},
             {"section": "branch_counts", **line["branch_counts"]},
             {"section": "host", "cores": cpu_cores()}]
-    for key in ("sweeps", "uneven", "postproc", "ktable", "serving", "cpu_baseline"):
+    for key in ("fp32_error_vs_fp64", "sweeps", "uneven", "postproc", "ktable", "serving", "cpu_baseline"):
         if key in line:
             recs.append({"section": key, **line[key]})
     with open(path, "a") as f:

@@ -73,7 +73,8 @@ def test_metrics_log_writes_one_record_per_section(tmp_path):
             "roofline": {"frac": 0.3, "hbm": {"frac": 0.18}, "mufu": {"frac": 0.22}},
             "fp64_plain": {"value": 1.4e7}, "e2e": {"value": 1.1e8},
             "branch_counts": {"resonance_hits": 354}, "sweeps": {"runs": []},
-            "serving": {"p50_ms": 2.8, "p99_ms": 31.0}}
+            "serving": {"p50_ms": 2.8, "p99_ms": 31.0},
+            "fp32_error_vs_fp64": {"F_net": {"max_rel": 0.3, "max_err_over_tol": 0.32}}}
     path = tmp_path / "m.jsonl"
     bench.write_metrics_log(str(path), line)
     bench.write_metrics_log(str(path), line)
@@ -83,3 +84,26 @@ def test_metrics_log_writes_one_record_per_section(tmp_path):
     first = recs[0]
     assert first["roofline_frac"] == 0.3 and first["value"] == 2.0e9 and "time" in first
     assert next(r for r in recs if r["section"] == "serving")["p99_ms"] == 31.0
+    assert next(r for r in recs if r["section"] == "fp32_error_vs_fp64")["F_net"]["max_err_over_tol"] == 0.32
+
+
+def test_bench_accuracy_block_matches_the_parity_tolerances(monkeypatch):
+    """The bench line's fp32_error_vs_fp64 uses the parity tests' FP32
+    tolerance (same floors, same formula) on the outputs it is given."""
+    import numpy as np
+    import torch
+    import rt_synth
+    from parity import errors
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    cols = rt_synth.generate([5, 3, 7], [4, 2, 3], 2, seed=1)
+    n_if, n_l = int((cols.n_layers + 1).sum()), int(cols.n_layers.sum())
+    rng = np.random.default_rng(0)
+    ref = {k: rng.uniform(-2, 2, n_if) for k in ("F_up", "F_down", "F_net")}
+    ref["Q"] = rng.uniform(-2, 2, n_l)
+    got = {k: v * (1 + 3e-5) + 1e-3 for k, v in ref.items()}
+    e = bench.fp32_errors(cols, {k: torch.tensor(v) for k, v in got.items()},
+                          {k: torch.tensor(v) for k, v in ref.items()})
+    p = errors(cols, got, ref, "fp32")
+    for k in ("F_up", "F_down", "F_net", "Q"):
+        assert abs(e[k]["max_err_over_tol"] - p[k]) <= 1e-12 * p[k]
+        assert e[k]["max_err_over_strict_tol"] >= e[k]["max_err_over_tol"]
