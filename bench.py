@@ -567,9 +567,11 @@ def run_serving(args):
     import rt_synth
     from paper_2203_02293_b300 import rt
     from paper_2203_02293_b300.serve import Pool, Server, make_requests
-    pool = Pool(rt_synth, n_pool=2562, L_range=(40, 100), NB_range=(30, 300), n_g=20)
+    c4 = rt_synth.CONFIGS["config4"]
+    pool = Pool(rt_synth, n_pool=c4["pool_columns"], L_range=tuple(c4["layers"]), NB_range=tuple(c4["bins"]),
+                n_g=c4["g_points"])
     n = int(args.serving_seconds * args.serving_rate)
-    reqs = make_requests(pool, n, rate_hz=args.serving_rate, seed=4)
+    reqs = make_requests(pool, n, rate_hz=args.serving_rate, seed=c4["seed"], C_range=tuple(c4["columns"]))
     warm = make_requests(pool, 8, rate_hz=1e3, seed=99)
     knobs = dict(n_slots=8, policy="gang", ctas_per_sm=1, max_systems_per_batch=4_000_000,
                  split_systems=4_000_000, wide_layer_systems=100_000_000)

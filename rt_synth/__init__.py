@@ -25,6 +25,8 @@ packed back to back; per-column arrays are float64.
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass, field, replace
 
 import numpy as np
@@ -230,34 +232,55 @@ def generate_fast(n_cols: int, L: int, NB: int, n_g: int, seed: int, optics: str
 # The five workloads.
 # ----------------------------------------------------------------------
 
-def config0(seed: int = 0) -> Columns:
+# The workloads' shapes, distributions and seeds (configs.json); the
+# functions below take their defaults from it.
+with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs.json")) as _f:
+    CONFIGS = json.load(_f)
+
+
+def config0(seed: int | None = None) -> Columns:
     """Plain FP64 case: 64 x 40 layers x 30 bins x 1 g-point, seed 0."""
-    return generate([40] * 64, [30] * 64, 1, seed, "uniform", name="config0 64x40x30x1")
+    c = CONFIGS["config0"]
+    n, L, NB = c["n_cols"], c["layers"], c["bins"]
+    return generate([L] * n, [NB] * n, c["g_points"], c["seed"] if seed is None else seed, c["optics"],
+                    name=f"config0 {n}x{L}x{NB}x{c['g_points']}")
 
 
-def config1(n_cols: int = 2562, seed: int = 1) -> Columns:
+def config1(n_cols: int | None = None, seed: int | None = None) -> Columns:
     """GCM-shaped: 2562 x 40 x 30 x 20 Gauss points, k-table optical depths."""
-    return generate_fast(n_cols, 40, 30, 20, seed, "ktable",
-                         name=f"config1 {n_cols}x40x30x20")
+    c = CONFIGS["config1"]
+    n = c["n_cols"] if n_cols is None else n_cols
+    return generate_fast(n, c["layers"], c["bins"], c["g_points"], c["seed"] if seed is None else seed,
+                         c["optics"], name=f"config1 {n}x{c['layers']}x{c['bins']}x{c['g_points']}")
 
 
-def config2(n_cols: int = 2562, seed: int = 2) -> Columns:
+def config2(n_cols: int | None = None, seed: int | None = None) -> Columns:
     """Precision stress: w0 in [0.99, 1-1e-6], dtau in [1e-8, 1e4], g0 in [0.5, 0.95]."""
-    return generate_fast(n_cols, 40, 30, 20, seed, "stress",
-                         name=f"config2 {n_cols}x40x30x20")
+    c = CONFIGS["config2"]
+    n = c["n_cols"] if n_cols is None else n_cols
+    return generate_fast(n, c["layers"], c["bins"], c["g_points"], c["seed"] if seed is None else seed,
+                         c["optics"], name=f"config2 {n}x{c['layers']}x{c['bins']}x{c['g_points']}")
 
 
-def uneven_shapes(n_cols: int, seed: int, L_range=(20, 200), NB_range=(30, 300)):
-    rng = np.random.default_rng(seed + 1000)
+def uneven_shapes(n_cols: int, seed: int, L_range=None, NB_range=None):
+    """Per-column layer and bin counts, uniform integers over the ranges
+    (config 3's by default)."""
+    c = CONFIGS["config3"]
+    L_range = tuple(c["layers"]) if L_range is None else L_range
+    NB_range = tuple(c["bins"]) if NB_range is None else NB_range
+    rng = np.random.default_rng(seed + c["shape_seed_offset"])
     L = rng.integers(L_range[0], L_range[1] + 1, n_cols).astype(np.int32)
     NB = rng.integers(NB_range[0], NB_range[1] + 1, n_cols).astype(np.int32)
     return L, NB
 
 
-def config3(n_cols: int = 4096, seed: int = 3) -> Columns:
+def config3(n_cols: int | None = None, seed: int | None = None) -> Columns:
     """Uneven batch: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g-points, optics as config 0."""
-    L, NB = uneven_shapes(n_cols, seed)
-    return generate(L, NB, 20, seed, "uniform", name=f"config3 {n_cols} uneven")
+    c = CONFIGS["config3"]
+    n = c["n_cols"] if n_cols is None else n_cols
+    sd = c["seed"] if seed is None else seed
+    L, NB = uneven_shapes(n, sd)
+    return generate(L, NB, c["g_points"], sd, c["optics"], name=f"config3 {n} uneven")
 
 
 # ----------------------------------------------------------------------
@@ -378,10 +401,13 @@ def device_generate(n_layers, n_bins, n_g: int, seed: int, device="cuda", name="
     return DeviceColumns(n_layers, n_bins, n_g, gw, t, _consts(), name)
 
 
-def config3_device(n_cols: int = 4096, seed: int = 3, device="cuda") -> DeviceColumns:
+def config3_device(n_cols: int | None = None, seed: int | None = None, device="cuda") -> DeviceColumns:
     """Uneven batch on the device: L_c ~ U{20..200}, NB_c ~ U{30..300}, 20 g."""
-    L, NB = uneven_shapes(n_cols, seed)
-    return device_generate(L, NB, 20, seed, device, name=f"config3 {n_cols} uneven (device)")
+    c = CONFIGS["config3"]
+    n = c["n_cols"] if n_cols is None else n_cols
+    sd = c["seed"] if seed is None else seed
+    L, NB = uneven_shapes(n, sd)
+    return device_generate(L, NB, c["g_points"], sd, device, name=f"config3 {n} uneven (device)")
 
 
 # ----------------------------------------------------------------------
