@@ -112,6 +112,29 @@ def errors(cols, got, ref, precision):
     return res
 
 
+HIST_EDGES = (1e-4, 1e-3, 1e-2, 1e-1, 0.5, 1.0)
+
+
+def error_histogram(cols, got, ref):
+    """Per quantity, the distribution of FP32 error / tolerance over every
+    interface (layer for Q): the fraction in each bin of HIST_EDGES (below
+    1e-4, [1e-4, 1e-3), ..., [0.5, 1], above 1) and the 50th, 90th, 99th and
+    99.9th percentiles."""
+    f_if, f_q = column_floors(cols)
+    res = {}
+    for k in ("F_up", "F_down", "F_net", "Q"):
+        if k == "Q":
+            tol = np.maximum(1e-3 * np.abs(ref[k]), f_q)
+        else:
+            tol = np.maximum(1e-4 * np.abs(ref[k]), f_if)
+        r = np.abs(got[k] - ref[k]) / tol
+        counts = np.histogram(r, bins=(0.0, *HIST_EDGES, np.inf))[0]
+        res[k] = {"fractions": [float(c) / r.size for c in counts],
+                  "p50": float(np.percentile(r, 50)), "p90": float(np.percentile(r, 90)),
+                  "p99": float(np.percentile(r, 99)), "p99.9": float(np.percentile(r, 99.9))}
+    return res
+
+
 def strict_errors(cols, got, ref):
     """FP32 errors under the stricter reading |e| <= 1e-4 max(|x|, 1e-6 F*)
     (reported, not gated)."""

@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 import rt_synth
-from parity import assert_parity, gpu_solve, method_opts, oracle_solve, strict_errors
+from parity import (HIST_EDGES, assert_parity, error_histogram, gpu_solve, method_opts, oracle_solve,
+                    strict_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -102,6 +103,11 @@ def test_config2_precision_stress_full():
     assert rep["F_net"]["strict_err_over_tol"] < 1e4 and rep["Q"]["strict_err_over_tol"] < 1e4
     print("config2 stats gpu", got["stats"], "oracle", ref["stats"])
     assert got["stats"]["eclamp_hits"] > 0
+    hist = error_histogram(cols, got, ref)
+    print("config2 fp32 error/tol histogram (bins", HIST_EDGES, ")", hist)
+    for k, h in hist.items():
+        assert abs(sum(h["fractions"]) - 1.0) < 1e-9 and h["fractions"][-1] == 0.0, k
+        assert h["p99"] < 0.1, (k, h)       # measured at most 0.013: the bulk sits far inside the tolerance
 
 
 MODES = {
