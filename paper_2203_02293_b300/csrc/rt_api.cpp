@@ -344,7 +344,7 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
     P.plan_bytes = align_up(sizeof(int32_t) * P.i32_count, 256) + align_up(sizeof(int64_t) * 9 * (size_t)n, 256);
     P.out_bytes = align_up(sizeof(double) * 3 * (size_t)P.n_if, 256) + align_up(sizeof(double) * (size_t)P.n_lay, 256) +
                   align_up(sizeof(double) * (size_t)P.n_bins, 256);
-    P.scr_bytes = P.sweeps ? 0
+    P.scr_bytes = P.sweeps ? sizeof(float2) * (size_t)P.n_slots * rt::kSweepMaxLayers   // (t, r) transfer
                            : (size_t)P.n_slots * (fp64 ? rt::fp64_scratch_per_slot(P.Lmax, cfg.layers == RT_ISOTHERMAL)
                                                        : rt::fp32_scratch_per_slot(P.Lmax));
     // inline B: the interfaces' B for the back-substitution, after the elimination scratch
@@ -779,7 +779,9 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.ext.iface = cols->n_iface > 0 ? cols->n_iface : P.n_if;
         kp.ext.fstar = cols->n_fstar > 0 ? cols->n_fstar : P.n_bins;
         kp.ext.mu = cols->n_mu > 0 ? cols->n_mu : n;
-        kp.ext.scr32 = cfg.precision == RT_FP64_PLAIN ? 0 : P.n_slots * (long long)P.Lmax;
+        kp.ext.scr32 = cfg.precision == RT_FP64_PLAIN ? 0
+                       : P.sweeps ? P.n_slots * (long long)rt::kSweepMaxLayers / 2      // float2 (t, r) per layer
+                                  : P.n_slots * (long long)P.Lmax;
         kp.ext.scr64 = cfg.precision == RT_FP64_PLAIN
                            ? (long long)(P.scr_bytes / sizeof(double2)) : 0;
         kp.ext.scrB = P.inline_b ? P.n_slots * (long long)P.Lmax : 0;

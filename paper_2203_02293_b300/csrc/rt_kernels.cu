@@ -1727,17 +1727,20 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
 //   u_top = t u_bot + r d_top + su,   d_bot = t d_top + r u_bot + sd.
 //
 // Layout.  A warp takes work units of 32 systems of a column (one per lane).
-// The coefficient pass streams the cubes once and leaves, per layer, (t, r)
-// and the sub-layer sources in the warp's shared memory, and the warp sums of
-// w F_beam at the interfaces; the lane then moves its t, r into registers
-// next to its level state (u or d at each of the 2L+1 levels), so that a
-// sweep reads only the sources from shared memory: 8 bytes per layer and
-// pass for four FMAs.  Register arrays need compile-time indices, so the
-// passes are unrolled to kSweepMaxLayers layers and stop at the column's L.
-// The last upward pass writes the interface fluxes into the (no longer
-// needed) (t, r) area, swizzled for a conflict-free transposed sum.
+// The coefficient pass streams the cubes once and leaves, per layer, the
+// sub-layer sources in the warp's shared memory, the warp sums of w F_beam at
+// the interfaces there too, and each lane's (t, r) in a global scratch
+// ([layer][thread slot], read back at once, so it stays in L2); the lane
+// then loads its t, r into registers next to its level state (u or d at each
+// of the 2L+1 levels), so that a sweep reads only the sources from shared
+// memory: 8 bytes per layer and pass for four FMAs.  Register arrays need
+// compile-time indices, so the passes are unrolled to kSweepMaxLayers layers.
+// The last upward pass writes the interface fluxes into the downward
+// sources' area (the last downward pass is done by then), swizzled for a
+// conflict-free transposed sum.  Keeping (t, r) out of shared memory is what
+// lets 8 warps (the register limit) rather than 7 reside on an SM.
 // ---------------------------------------------------------------------
-// (t, r) per layer, then the output rows [2 (Lmax + 1)][32] (XOR-swizzled)
+// The output rows [2 (Lmax + 1)][32] (XOR-swizzled)
 __host__ __device__ inline int sweep_region_floats() { return 64 * (kSweepMaxLayers + 1); }
 
 // Output row element (row, j) of the swizzled rows: lane j's writes to one
@@ -1750,8 +1753,8 @@ int sweep_warp_floats(int Lmax, int nbw, int direct, int isothermal) {
     int n = ((direct ? 0 : (2 * Lmax + 1) * nbw) + 3) & ~3;
     n += (2 * nbw + 3) & ~3;                        // F*, F_BOA
     n += (Lmax + 1 + 3) & ~3;                       // warp sums of w F_beam per interface
-    n += 2 * per * kSweepMaxLayers;                 // SU, SD (every system padded to the register limit)
-    n += sweep_region_floats();                     // (t, r), then the output rows
+    n += per * kSweepMaxLayers;                     // SU (every system padded to the register limit)
+    n += std::max(per * kSweepMaxLayers, sweep_region_floats());   // SD, then the output rows
     return n;
 }
 size_t sweep_smem_bytes(int block, int Lmax, int nbw, int direct, int isothermal) {
@@ -1898,7 +1901,8 @@ struct SweepStart {
 // asynchronous copies, the sweeps' register arrays spill.)
 template <bool ISO, bool DIRECT>
 __device__ __forceinline__ SweepStart sweep_coefficients(const KParams &kp, int unit, int lane, float *sB, float *sFs,
-                                                      float *sFB, float *fbs, float *SU, float *SD, float *TR) {
+                                                      float *sFB, float *fbs, float *SU, float *SD, float2 *gtr,
+                                                      long long gst) {
     {
         const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
         const int L = q.L;
@@ -1944,14 +1948,14 @@ __device__ __forceinline__ SweepStart sweep_coefficients(const KParams &kp, int 
         SysCounts<V2> sc2;
         sc2.inv = sc2.ecl = sc2.etau = U2{0u, 0u};
         const M2 on2 = M2{q.on, q.on};
-        float2 *TR2 = reinterpret_cast<float2 *>(TR);
         auto wsum = [](float v) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             return v;
         };
         auto put = [&](int l, float tl, float rl, float uU, float uL, float dU, float dL) {
-            TR2[l * 32 + lane] = make_float2(tl, rl);
+            float2 *pt = gtr + l * gst;
+            if (RT_IN(pt, reinterpret_cast<float2 *>(kp.scr32), 2 * kp.ext.scr32)) __stcg(pt, make_float2(tl, rl));
             if constexpr (ISO) {
                 SU[l * 32 + lane] = uU;
                 SD[l * 32 + lane] = dU;
@@ -2027,7 +2031,7 @@ __device__ __forceinline__ SweepStart sweep_coefficients(const KParams &kp, int 
 
 template <bool ISO, bool DIRECT>
 __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane, float *sB, float *sFs, float *sFB,
-                                           float *fbs, float *SU, float *SD, float *TR) {
+                                           float *fbs, float *SU, float *SD, float *TR, float2 *gtr, long long gst) {
     constexpr int LR = kSweepMaxLayers;
     constexpr int NLV = ISO ? LR + 1 : 2 * LR + 1;    // levels held per lane
     float t[LR], r[LR], X[NLV];
@@ -2037,35 +2041,39 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     // ---- coefficient pass into shared memory; then t, r and the starting
     // state into registers
     {
-        const SweepStart st = sweep_coefficients<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR);
+        const SweepStart st = sweep_coefficients<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, gtr, gst);
         L = st.L;
         d0 = st.d0;
         ubc = st.ubc;
         const SweepLane q = sweep_lane<DIRECT>(kp, unit, lane, sB);
-        const float2 *TR2 = reinterpret_cast<const float2 *>(TR);
 #pragma unroll
         for (int l = 0; l < LR; ++l) {
-            const float2 v = TR2[l * 32 + lane];
+            const float2 *pt = gtr + l * gst;
+            const float2 v = RT_IN(pt, reinterpret_cast<const float2 *>(kp.scr32), 2 * kp.ext.scr32)
+                                 ? __ldcg(pt) : make_float2(1.f, 0.f);
             t[l] = v.x;
             r[l] = v.y;
         }
+
         // zero diffuse flux: u = -pi B at every level (the BOA's B below it)
 #pragma unroll
         for (int j = 0; j < NLV; ++j) {
             const int lev = ISO ? 2 * j : j;                       // level in the B table
             X[j] = -kPiF * ldBk<DIRECT>(kp, q.Bp + min(lev, 2 * L) * q.bst);
         }
-        __syncwarp();                                              // (t, r) area free for the output rows
+        __syncwarp();
     }
 
     // ---- the sweeps: registers t, r, X; sources from shared memory
     float dB = 0.f;
     for (int it = 0; it < kp.n_sweeps; ++it) {
         dB = sweep_down<ISO>(X, t, r, lane, d0, ubc, SD);
-        if (it + 1 < kp.n_sweeps)
+        if (it + 1 < kp.n_sweeps) {
             sweep_up<ISO, false>(X, t, r, L, lane, d0, SU, TR);
-        else
+        } else {
+            __syncwarp();              // every lane's downward pass has read SD: its area takes the output rows
             sweep_up<ISO, true>(X, t, r, L, lane, d0, SU, TR);
+        }
     }
     const bool finite = isfinite(X[0]) && isfinite(dB);
 
@@ -2136,13 +2144,16 @@ __global__ void __launch_bounds__(kMaxBlock32, 1) fp32_sweeps(KParams kp) {
     float *fbs = sFs + ((2 * nbw + 3) & ~3);
     float *SU = fbs + ((Lm + 1 + 3) & ~3);
     float *SD = SU + (ISO ? 32 : 64) * kSweepMaxLayers;
-    float *TR = SD + (ISO ? 32 : 64) * kSweepMaxLayers;
+    float *TR = SD;                                // the output rows, once the last downward pass is done
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gst = (long long)gridDim.x * blockDim.x;
+    float2 *gtr = reinterpret_cast<float2 *>(kp.scr32) + slot;   // (t, r) of layer l at gtr[l gst]
     for (;;) {
         int unit = 0;
         if (lane == 0) unit = atomicAdd(kp.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= kp.n_units) break;
-        sweep_unit<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR);
+        sweep_unit<ISO, DIRECT>(kp, unit, lane, sB, sFs, sFB, fbs, SU, SD, TR, gtr, gst);
     }
 }
 
