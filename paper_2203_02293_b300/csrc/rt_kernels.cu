@@ -445,11 +445,13 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
     const V iq = vrcp(q);
     const M cons = ewm == V(0.f);                 // E = w0 = 1: k = 0, Pi := pi
     const V k = vsel(cons, V(0.f), ewm * vrsqrt(ewm * q));
-    const V piw = V(kPiF) * vrcp(ewm);
-    const V Pi = vsel(cons, V(kPiF), omw * piw);
-    const V dPi = vsel(cons, V(0.f), -em1 * piw);  // Pi - pi
-    const V ip = vrcp(V(1.f) + k);
-    const V eps = (V(1.f) - k) * ip;
+    // Pi and Pi - pi of Eq. B5, both times hs = 1 (isothermal) or 1/2
+    // (non-isothermal, where they meet mean values (B1 + B2)/2)
+    constexpr float hs = ISO ? 1.f : 0.5f;
+    const V piw = V(hs * kPiF) * vrcp(ewm);
+    const V Pi = vsel(cons, V(hs * kPiF), omw * piw);
+    const V dPi = vsel(cons, V(0.f), -em1 * piw);  // hs (Pi - pi)
+    const V opk = V(1.f) + k, omk = V(1.f) - k;
     const V dts = ISO ? dt : V(0.5f) * dt;
 
     const V q2 = q + q;
@@ -458,16 +460,16 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
     const V Tm = vexpn(x);
     const V u = vsel(vabs(x) < V(0.25f), u_series_v(x), (V(1.f) - Tm) * vrcp(x));
     const V qd = q2d * u;                         // (1 - T)/k
-    const V h = vfma(Tm + Tm, ip, qd);
-    const V p = vfma(eps, Tm, V(1.f));
+    // with h = (1 + k) qd + 2T and p = (1 + k) + (1 - k) T (the usual
+    // denominators times 1 + k), one reciprocal of h p gives t, r, 1/h and 1/p
+    const V h = vfma(opk, qd, Tm + Tm);
+    const V p = vfma(omk, Tm, opk);
     const V ihp = vrcp(h * p);
-    const V ih = p * ihp, ipp = h * ihp;          // 1/h, 1/p
-    const V ipihp = ip * ihp;
-    const V t = (V(4.f) * Tm) * (ip * ipihp);
+    const V t = (V(4.f) * Tm) * ihp;
     const V Y = vfma(qd, Tm, qd);                 // (1 - T^2)/k = qd (1 + T)
-    const V r = (eps * ihp) * Y;
+    const V r = ((omk * opk) * Y) * ihp;          // (1 - k^2) Y / (h p)
     const V k2 = k * k;
-    const V omtr = ((k2 + k2) * (qd * ip)) * ipp; // 1 - t - r
+    const V omtr = ((k2 + k2) * qd) * (h * ihp);  // 1 - t - r = 2 k^2 qd / p
     const V omr = omtr + t;                       // 1 - r
 
     V suU, sdU, suL = V(0.f), sdL = V(0.f);
@@ -482,11 +484,12 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
         // The e_tau fallback (isothermal at the mean B, Sec. 2.2.1, written in
         // departures from pi B1 and pi B2) is the same expression with
         // G' = pi (1-r+t)/2, so only G' is selected.
-        const V pig = (Pi * (V(2.f) * u)) * (ip * ih);
-        const V hopr = V(0.5f) * vfma(V(2.f), t, omtr);         // (1 - r + t)/2
-        const V G = vsel(fb, V(kPiF) * hopr, vfma(-dPi, hopr, pig));
+        // (Pi and dPi carry the factor 1/2 here)
+        const V pig = (Pi * (V(4.f) * u)) * (p * ihp);           // Pi 2u / h
+        const V opt = vfma(V(2.f), t, omtr);                    // 1 - r + t
+        const V G = vsel(fb, V(0.5f * kPiF) * opt, vfma(-dPi, opt, pig));
         const V dom = dPi * omtr;
-        const V aU = dom * (V(0.5f) * (Bt + Bc)), aL = dom * (V(0.5f) * (Bc + Bb));
+        const V aU = dom * (Bt + Bc), aL = dom * (Bc + Bb);
         const V gU = G * (Bc - Bt), gL = G * (Bb - Bc);
         suU = aU + gU;
         sdU = aU - gU;
@@ -505,30 +508,29 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
         const V omm = vsel(dl < V(0.25f), dl * u_series_v(dl), V(1.f) - m);   // 1 - m
         const V q2k = q2 * k;
         const V rho = V(mu) * q2k;
-        const V ie2 = V(kp.inv_eps2);
-        const V A = w0 * vfma(g0, ie2, q2);
+        const V Ah = w0 * vfma(g0, V(0.5f * kp.inv_eps2), q);   // A/2
         const V G0h = (wg * V(0.25f * kp.inv_eps2)) * iq;       // G0/2 of Eq. B8
-        const V r2 = r + r;
-        const V tm1r = -vfma(t, omm, omtr + r2);                // (t m - 1) - r
-        const V rmtm = vfma(r, m, (omtr + r) - omm);            // r m - (t - m)
+        const V omt = omtr + r;                                  // 1 - t
+        const V tm1r = -vfma(t, omm, omt + r);                  // (t m - 1) - r
+        const V rmtm = vfma(r, m, omt - omm);                   // r m - (t - m)
         // stable form: the 1/D of G+- divided out (see the block comment)
         const V omrho = V(1.f) - rho;
         const V z = omrho * dl;
         const V lam_s = (m * dl) * u_series_v(-z);
         const V lam_d = (Tm - m) * vrcp(omrho);
         const V Lam = vsel(vabs(z) < V(0.25f), lam_s, lam_d);
-        const V SA2 = ((V(0.5f) * A) * (ip * ipihp)) * (iq * vrcp(V(1.f) + rho));   // 2 SA
+        const V SA2 = (Ah * ihp) * (iq * vrcp(V(1.f) + rho));   // 2 SA
         const V tq = V(mu) * q2;
         const V TL = Tm * Lam;
-        V bu = vfma(SA2, vfma((V(1.f) + k), Y, (TL + TL) * (V(1.f) - tq)), G0h * tm1r);
+        V bu = vfma(SA2, vfma(opk, Y, TL * vfma(tq, V(-2.f), V(2.f))), G0h * tm1r);
         const V cl = vfma(Y, vfma(tq, k2, V(1.f)), (V(1.f) + tq) * vfma(Tm, Tm, V(1.f)));
-        V bd = vfma(SA2, vfma(Lam, cl, -((Tm * (V(1.f) - k)) * Y)), G0h * rmtm);
+        V bd = vfma(SA2, vfma(Lam, cl, -((Tm * omk) * Y)), G0h * rmtm);
         // resonance test of Eq. 11 (rare): the FP64 decision, and the paper's
         // switch to D := 2 mu* when |D| < 1e-5, run only if a lane needs them
         const V D32 = vfma(rho, rho, V(-1.f));
         const M near = vabs(D32) < V(2e-5f);
         if (__any_sync(0xffffffffu, vany(near))) {
-            resonance_fix(near, on, w0, g0, mu, imu, mu_d, A, iq, G0h, omtr, r, t, omm, m, kp, cn, bu, bd);
+            resonance_fix(near, on, w0, g0, mu, imu, mu_d, Ah + Ah, iq, G0h, omtr, r, t, omm, m, kp, cn, bu, bd);
         }
         if (SPLIT) {
             bu_o = bu;
@@ -1298,8 +1300,9 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
             for (int i = lane; i < nlev * nbc; i += 32) {
                 const int lev = i / nbc, bb = i - lev * nbc;
                 const float *pb = Bg + (long long)lev * NB + bb;
-                if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(sB + i, pb);
-                else sB[i] = 0.f;
+                float *dst = sB + bb * nlev + lev;    // [bin][level]: unit level stride
+                if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(dst, pb);
+                else *dst = 0.f;
             }
         }
         if constexpr (INL) {
@@ -1330,7 +1333,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
     int sI[NS], bI[NS];
     V wg, Fb, Bt, Bc, Bb;
     const float *Bp[NS];
-    const int bst = DIRECT ? NB : nbc;         // level stride of Bp
+    const int bst = DIRECT ? NB : 1;           // level stride of Bp (a literal 1 when staged)
     // INL: the bins' edges and FP64-formed widths, and the level temperatures
     float wn0[NS], wn1[NS], dnu[NS];
     V wn0v, wn1v, dnuv;
@@ -1365,7 +1368,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         sI[i] = act ? s0 + 32 * i + lane : s0;
         bI[i] = sI[i] / NG;
         cmp(wg, i) = act ? kp.g_w32[sI[i] - bI[i] * NG] : 0.f;
-        Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo);
+        Bp[i] = DIRECT ? kp.planck32 + kp.planck_off[c] + bI[i] : sB + (bI[i] - b_lo) * (2 * L + 1);
         if constexpr (INL) {
             if (kp.edges32) {
                 wn0[i] = __ldg(kp.edges32 + bI[i]);
@@ -1693,7 +1696,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     const int nbw = kp.nbw;
     float4 *ring = reinterpret_cast<float4 *>(wsm);   // [DEP + 1][NS][32], back-substitution
     float *ringB = wsm + back_ring_floats(NS, DEP);   // inline B: [DEP + 1][32] x NS
-    float *sB = ringB + back_ringB_floats(NS, ST == kStageInline, DEP);   // [(2 L + 1) nbc], staged mode
+    float *sB = ringB + back_ringB_floats(NS, ST == kStageInline, DEP);   // [nbc][2 L + 1] (bin, level), staged mode
     float *sFs = sB + (ST == kStageShared ? (2 * kp.Lmax + 1) * nbw : ST == kStageInline ? 2 * (2 * kp.Lmax + 1) : 0);   // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [G][2][33]
