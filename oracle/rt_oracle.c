@@ -31,7 +31,9 @@
  *   - resonance (Eq. 11): when |D| < 1e-5 the paper mode sets D := 2 mu*;
  *     the limit mode keeps the exact solution (see sub_layer for |D| < 1e-7);
  *   - E := max(E_fit, 1) unless the raw fit is asked for; the fit applies for
- *     w0 > 0.1f, i.e. the threshold is the FP32 value of 0.1;
+ *     w0 > 0.1f, i.e. the threshold is the FP32 value of 0.1; where the raw
+ *     fit gives E < w0, k (Eq. B2) is not real and the system's fluxes are
+ *     NaN (counted as non-finite);
  *   - the e_tau test is dtau_sub < 1e-4f with dtau_sub = dtau / 2; both
  *     sub-layers carry the layer's w0, g0 and half its optical depth;
  *   - F_BOA = pi B(T_int) per bin; no beam when cos(theta*) <= 0;
@@ -256,12 +258,16 @@ static void sub_layer(const oracle_cfg *cfg, const layer_coef *c, double w0,
         chi = zm * zm * T * T - zp * zp;
         xi = zp * zm * (1.0 - T * T);
         psi = (zm * zm - zp * zp) * T;
-    } else {
+    } else if (c->k == 0.0) {
         /* E = w0 = 1.  chi, xi, psi all vanish like k; the relations
          * are homogeneous in them, so use their k -> 0 limits divided by k. */
         chi = -(1.0 + c->q * dtau);
         xi = c->q * dtau;
         psi = -1.0;
+    } else {
+        /* E < w0 (the raw Eq. 19 fit, clamp off): k of Eq. B2 is not real,
+         * the layer has no two-stream solution; NaN marks its fluxes. */
+        chi = xi = psi = NAN;
     }
     double Pi = c->Pi;
     double S_up, S_dn;

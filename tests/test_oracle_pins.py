@@ -398,3 +398,22 @@ def test_resonance_rule_and_limit_mode(orc):
     cols.mu_star[:] = mu
     st = orc.solve_columns(oracle.OracleConfig(), cols)["stats"]
     assert st["resonance_hits"] == 3
+
+
+def test_raw_e_fit_below_w0_has_no_real_solution(orc):
+    """With the clamp off, the raw Eq. 19 fit can fall below w0 (here w0 =
+    0.999, g0 = 0.95 gives E = 0.9972); then k**2 = (E - w0) / (E (1 - w0 g0))
+    of Eq. B2 is negative and the two-stream relations have no real solution.
+    The fluxes of such a system are NaN, never the conservative-limit branch
+    that belongs to k = 0 (E = w0 = 1) alone."""
+    rng = np.random.default_rng(6)
+    dtau, w0, g0, Bc, Bi = random_column(rng, 3)
+    w0[:] = f32([0.5, 0.999, 0.5])
+    g0[:] = f32([0.3, 0.95, 0.3])
+    E = (1.225 - 0.1582 * float(g0[1]) - 0.1777 * float(w0[1]) - 0.07465 * float(g0[1]) ** 2
+         + 0.2351 * float(w0[1]) * float(g0[1]) - 0.05582 * float(w0[1]) ** 2)
+    assert E < float(w0[1])
+    up, dn, _ = orc.solve_system(oracle.OracleConfig(e_clamp=False), dtau, w0, g0, Bc, Bi, 0.7, 1e5, 5.0)
+    assert np.isnan(up).all() and np.isnan(dn).all()
+    up, dn, _ = orc.solve_system(oracle.OracleConfig(e_clamp=True), dtau, w0, g0, Bc, Bi, 0.7, 1e5, 5.0)
+    assert np.isfinite(up).all() and np.isfinite(dn).all()
