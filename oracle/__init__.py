@@ -30,7 +30,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 def build(src: str = SRC, out: str = LIB, extra: tuple = ()) -> str:
     """Compile the oracle into a shared library (gcc, -O2, OpenMP, IEEE math)."""
-    cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", *extra,
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", *extra,
            "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
     return out

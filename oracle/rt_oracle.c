@@ -30,7 +30,8 @@
  *   - mu* enters G+- with the Malik sign, mu* = -cos(theta*) < 0 (App. B);
  *   - resonance (Eq. 11): when |D| < 1e-5 the paper mode sets D := 2 mu*;
  *     the limit mode keeps the exact solution (see sub_layer for |D| < 1e-7);
- *   - E := max(E_fit, 1) unless the raw fit is asked for; the fit applies for
+ *   - E := max(E_fit, 1) unless the raw fit is asked for (its hits are
+ *     counted on E - 1 formed in FP32, see e_fit_m1_f32); the fit applies for
  *     w0 > 0.1f, i.e. the threshold is the FP32 value of 0.1; where the raw
  *     fit gives E < w0, k (Eq. B2) is not real and the system's fluxes are
  *     NaN (counted as non-finite);
@@ -182,6 +183,18 @@ static void g_factors(double w0, double g0, double E, double mus, double eps2,
     *Gm = 0.5 * (lead * (mus - 1.0 / (2.0 * E * one_m_wg)) - tail);
 }
 
+/* E - 1 of Eq. 19 in FP32, the terms grouped as nested fused multiply-adds
+ * (fmaf rounds each once):  0.2351 w0 g0 + (g0 (-0.07465 g0 - 0.1582)
+ * + (w0 (-0.05582 w0 - 0.1777) + 0.225)).  The E clamp's hits are counted on
+ * its sign: the paper states no precision for that decision, so it is taken
+ * in the precision of the FP32 form, on the same expression. */
+static float e_fit_m1_f32(float w0, float g0)
+{
+    float t = fmaf(w0, fmaf(-0.05582f, w0, -0.1777f), 0.225f);
+    t = fmaf(g0, fmaf(-0.07465f, g0, -0.1582f), t);
+    return fmaf(0.2351f, w0 * g0, t);
+}
+
 static void layer_coeffs(const oracle_cfg *cfg, double w0, double g0, double mu,
                          layer_coef *c)
 {
@@ -193,10 +206,10 @@ static void layer_coeffs(const oracle_cfg *cfg, double w0, double g0, double mu,
     if (cfg->improved && w0 > (double)0.1f) {
         E = 1.225 - 0.1582 * g0 - 0.1777 * w0 - 0.07465 * g0 * g0
             + 0.2351 * w0 * g0 - 0.05582 * w0 * w0;
-        if (cfg->e_clamp && E < 1.0) {   /* keep E - w0 >= 1 - w0 > 0 */
+        if (cfg->e_clamp && E < 1.0)     /* keep E - w0 >= 1 - w0 > 0 */
             E = 1.0;
+        if (cfg->e_clamp && e_fit_m1_f32((float)w0, (float)g0) < 0.0f)
             c->eclamp_hit = 1;
-        }
     }
     c->E = E;
     c->q = E * (1.0 - w0 * g0);
