@@ -433,6 +433,9 @@ __device__ __forceinline__ Sub32<V> sub32(V dt, V w0, V g0, V Bt, V Bc, V Bb, fl
     vcount(sc.inv, !valid);
     // E of Eq. 19, switched off for w0 <= 0.1, clamped at 1
     const V wg = w0 * g0;
+    // E - 1 in FP32 as nested fused multiply-adds; the clamp's hits are
+    // decided on this value (the FP64 path and the reference count on the
+    // same FP32 expression)
     V em1 = vfma(g0, vfma(V(-0.07465f), g0, V(-0.1582f)), vfma(w0, vfma(V(-0.05582f), w0, V(-0.1777f)), V(0.225f)));
     em1 = vfma(V(0.2351f), wg, em1);
     em1 = vsel((w0 > V(0.1f)) & (kp.improved != 0), em1, V(0.f));
@@ -2190,11 +2193,13 @@ __device__ __forceinline__ Sub64 sub64(double dts, double w0, double g0, double 
         chi = zm * zm * T * T - zp * zp;
         xi = zp * zm * (1.0 - T * T);
         psi = (zm * zm - zp * zp) * T;
-    } else {
+    } else if (k == 0.0) {                         // E = w0 = 1: the k -> 0 limit
         const double q = E * omwg;
         chi = -(1.0 + q * dts);
         xi = q * dts;
         psi = -1.0;
+    } else {                                       // E < w0 (raw fit): k is not real
+        chi = xi = psi = k;                        // NaN
     }
     double Su, Sd;
     if (kp.isothermal) {
@@ -2307,9 +2312,14 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
                 if (kp.improved && w0 > (double)0.1f) {
                     E = 1.225 - 0.1582 * g0 - 0.1777 * w0 - 0.07465 * g0 * g0 + 0.2351 * w0 * g0
                         - 0.05582 * w0 * w0;
+                    // hits counted on E - 1 in FP32 as the FP32 form forms it
+                    const float w0f = (float)w0, g0f = (float)g0;
+                    const float em1f = fmaf(0.2351f, __fmul_rn(w0f, g0f),
+                                            fmaf(g0f, fmaf(-0.07465f, g0f, -0.1582f),
+                                                 fmaf(w0f, fmaf(-0.05582f, w0f, -0.1777f), 0.225f)));
+                    if (kp.e_clamp && em1f < 0.f) cn.eclamp += cn.on;
                     if (kp.e_clamp && E < 1.0) {
                         E = 1.0;
-                        cn.eclamp += cn.on;
                     }
                 }
                 const int nh = iso ? 1 : 2;

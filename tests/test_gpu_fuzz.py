@@ -1,0 +1,94 @@
+"""Seeded random batches through the CUDA path against the oracle.
+
+Each case draws its own batch shape (ragged layer and bin counts, g-points
+from 1 to 24), optics family, zenith angles (night side included) and method
+switches, then requires the same parity as the fixed-shape tests and the same
+branch counts as the oracle (the E clamp's count included: the precision
+stress optics put many systems within FP32 rounding of E = 1).  The FP64 plain path is held to its 1e-10
+tolerance on the uniform and k-table optics only: the precision-stress optics
+(w0 within 1e-6 of 1) take the FP32 form, whose cancellation-free rewrites
+exist for that case.
+"""
+import numpy as np
+import pytest
+
+import rt_synth
+from parity import assert_parity, gpu_solve, method_opts, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+N_CASES = 24
+
+
+def draw_case(i):
+    rng = np.random.default_rng(7000 + i)
+    n_cols = int(rng.integers(1, 13))
+    L = rng.integers(1, 91, n_cols)
+    NB = rng.integers(1, 41, n_cols)
+    NG = int(rng.choice([1, 2, 3, 7, 16, 20, 24]))
+    optics = str(rng.choice(["uniform", "ktable", "stress"]))
+    # the raw E fit only where it stays above w0 (w0 <= 0.95); below w0 there
+    # is no real solution (test_raw_e_fit_below_w0_is_nan_on_both_sides)
+    raw_fit = optics != "stress" and rng.integers(0, 4) == 0
+    opts = method_opts(isothermal=bool(rng.integers(0, 2)), improved=bool(rng.integers(0, 4) > 0),
+                       resonance=str(rng.choice(["paper", "limit"])), e_clamp=not raw_fit,
+                       eps2=float(rng.choice([2.0 / 3.0, 0.5])), T_int=float(rng.choice([100.0, 0.0, 250.0])),
+                       F_toa=float(rng.choice([0.0, 25.0])))
+    cols = rt_synth.generate(L, NB, NG, seed=7100 + i, optics=optics, mu_range=(-0.3, 1.0),
+                             name=f"fuzz {i}")
+    return cols, opts, optics
+
+
+@pytest.mark.parametrize("i", range(N_CASES))
+def test_random_batch_matches_oracle(i):
+    cols, opts, optics = draw_case(i)
+    ref = oracle_solve(cols, opts)
+    for precision in ("fp32", "fp64"):
+        if precision == "fp64" and optics == "stress":
+            continue
+        got = gpu_solve(cols, opts, precision)
+        assert_parity(cols, got, ref, precision, f"fuzz {i} {optics} {opts}")
+        for k in ("etau_hits", "eclamp_hits", "resonance_hits"):
+            assert got["stats"][k] == ref["stats"][k], (i, precision, k, got["stats"], ref["stats"])
+        assert got["stats"]["invalid_inputs"] == 0
+        assert got["stats"]["nonfinite_outputs"] == ref["stats"]["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_raw_e_fit_below_w0_is_nan_on_both_sides(precision):
+    """With the E clamp off, one layer of one column at w0 = 0.999, g0 = 0.95
+    (raw Eq. 19 fit E = 0.9972 < w0: k of Eq. B2 is not real).  That column's
+    fluxes are NaN on both sides and each of its systems counts as
+    non-finite; every other column keeps its parity."""
+    cols = rt_synth.generate([6, 5, 7], [3, 2, 4], 5, seed=17, optics="uniform")
+    o = cols.offsets()
+    S1 = int(cols.n_bins[1]) * cols.n_g
+    a = o["cube"][1] + 2 * S1                       # layer 2 of column 1
+    cols.w0[a:a + S1] = np.float32(0.999)
+    cols.g0[a:a + S1] = np.float32(0.95)
+    opts = method_opts(e_clamp=False)
+    ref = oracle_solve(cols, opts)
+    got = gpu_solve(cols, opts, precision)
+    assert ref["stats"]["nonfinite"] == got["stats"]["nonfinite_outputs"] == S1
+    oi, ol = o["iface"], o["lay"]
+    # (the FP32 form imposes F_net = F_BOA at the BOA by Eq. 10 directly, so
+    # that one value may stay finite in the affected column)
+    for k, off in (("F_up", oi), ("F_down", oi), ("F_net", oi), ("Q", ol)):
+        for c in range(3):
+            seg = slice(off[c], off[c + 1])
+            for side in (ref, got):
+                if c == 1:
+                    assert np.isnan(side[k][seg]).any(), (k, c)
+                else:
+                    assert np.isfinite(side[k][seg]).all(), (k, c)
+    keep = [0, 2]
+    sub = cols.subset(keep)
+    e = assert_parity(sub, {k: np.concatenate([got[k][slice(off[c], off[c + 1])] for c in keep])
+                            for k, off in (("F_up", oi), ("F_down", oi), ("F_net", oi), ("Q", ol))},
+                      {k: np.concatenate([ref[k][slice(off[c], off[c + 1])] for c in keep])
+                       for k, off in (("F_up", oi), ("F_down", oi), ("F_net", oi), ("Q", ol))},
+                      precision, "columns without the raw-fit layer")

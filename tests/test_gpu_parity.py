@@ -103,6 +103,10 @@ def test_config2_precision_stress_full():
     assert rep["F_net"]["strict_err_over_tol"] < 1e4 and rep["Q"]["strict_err_over_tol"] < 1e4
     print("config2 stats gpu", got["stats"], "oracle", ref["stats"])
     assert got["stats"]["eclamp_hits"] > 0
+    # many systems sit within FP32 rounding of E = 1 here; both sides count the
+    # clamp on the same FP32 expression, so the counts agree exactly
+    for k in ("eclamp_hits", "etau_hits", "resonance_hits"):
+        assert got["stats"][k] == ref["stats"][k], (k, got["stats"], ref["stats"])
     hist = error_histogram(cols, got, ref)
     print("config2 fp32 error/tol histogram (bins", HIST_EDGES, ")", hist)
     for k, h in hist.items():
