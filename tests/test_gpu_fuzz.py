@@ -40,17 +40,21 @@ def draw_case(i):
                        F_toa=float(rng.choice([0.0, 25.0])))
     cols = rt_synth.generate(L, NB, NG, seed=7100 + i, optics=optics, mu_range=(-0.3, 1.0),
                              name=f"fuzz {i}")
-    return cols, opts, optics
+    # launch knobs of the FP32 form: every (systems per lane, Planck route,
+    # staging depth) instance must give the same parity
+    knobs = dict(systems_per_lane=int(rng.integers(1, 3)), planck_staging=int(rng.integers(0, 4)),
+                 staging_depth=int(rng.integers(2, 4)))
+    return cols, opts, optics, knobs
 
 
 @pytest.mark.parametrize("i", range(N_CASES))
 def test_random_batch_matches_oracle(i):
-    cols, opts, optics = draw_case(i)
+    cols, opts, optics, knobs = draw_case(i)
     ref = oracle_solve(cols, opts)
     for precision in ("fp32", "fp64"):
         if precision == "fp64" and optics == "stress":
             continue
-        got = gpu_solve(cols, opts, precision)
+        got = gpu_solve(cols, opts, precision, **(knobs if precision == "fp32" else {}))
         assert_parity(cols, got, ref, precision, f"fuzz {i} {optics} {opts}")
         for k in ("etau_hits", "eclamp_hits", "resonance_hits"):
             assert got["stats"][k] == ref["stats"][k], (i, precision, k, got["stats"], ref["stats"])
