@@ -87,3 +87,23 @@ def test_random_postprocessing_cases_match_oracle(i):
         got = gpu_solve(cols, opts, "fp32", planck_staging=staging)
         assert_parity(cols, got, ref, "fp32", f"post-processing case {i} staging {staging} {opts}")
         check_counts(got, ref)
+
+
+@pytest.mark.parametrize("NG", [32, 33, 50, 64])
+def test_many_g_points_match_oracle(NG):
+    """Up to the 64 g-points the ABI allows: bins then span one, two or (with
+    one system per lane) three work units."""
+    rng = np.random.default_rng(8700 + NG)
+    L = rng.integers(1, 50, 5)
+    NB = rng.integers(1, 12, 5)
+    cols = rt_synth.generate(L, NB, NG, seed=8800 + NG, optics="ktable", mu_range=(-0.3, 1.0))
+    opts = random_opts(rng)
+    ref = oracle_solve(cols, opts)
+    for spl in (1, 2):
+        for staging in (0, 1, 2, 3):
+            got = gpu_solve(cols, opts, "fp32", systems_per_lane=spl, planck_staging=staging)
+            assert_parity(cols, got, ref, "fp32", f"NG={NG} spl={spl} staging={staging} {opts}")
+            check_counts(got, ref)
+    got = gpu_solve(cols, opts, "fp64")
+    assert_parity(cols, got, ref, "fp64", f"NG={NG} fp64 {opts}")
+    check_counts(got, ref)
