@@ -112,6 +112,7 @@ struct Plan {
     int Lmax = 0, NBmax = 0;
     // launch
     int block = 0, grid = 0, nb_chunk = 0, nbw = 0, warp_floats = 0, direct = 0, inline_b = 0, ns = 1;
+    int staged = 0;               // staged Planck values per warp (FP32) / CTA (FP64), see staged_capacity
     int group_shift = 4;          // FP32 form: log2 of the interfaces per transposed sum
     int depth = 2;                // FP32 form: back-substitution levels in flight (cfg.staging_depth)
     bool sweeps = false;          // the iterative method (cfg.n_sweeps > 0) instead of Thomas
@@ -121,6 +122,17 @@ struct Plan {
     size_t i32_count = 0, plan_bytes = 0, out_bytes = 0, scr_bytes = 0, aux_bytes = 0, kcube_bytes = 0;
     bool kt = false;              // optics from the k-table front end
 };
+
+// Shared memory for the staged Planck values: a chunk of systems covers at
+// most `chunk` bins of its column, so column c stages (2 L_c + 1) x
+// min(NB_c, chunk) values; the largest over the batch (not the product of
+// the batch's largest L and NB, which may belong to different columns).
+int staged_capacity(const std::vector<int32_t> &nl, const std::vector<int32_t> &nb, int chunk) {
+    int64_t m = 0;
+    for (size_t i = 0; i < nl.size(); ++i)
+        m = std::max<int64_t>(m, (int64_t)(2 * nl[i] + 1) * std::min<int32_t>(nb[i], chunk));
+    return (int)std::min<int64_t>(m, 1 << 30);
+}
 
 // Element counts of the input arrays: a column's block [off, off + span) of
 // an array must lie inside its count.  Gather offsets need the counts of
@@ -289,7 +301,8 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
             int occ;
             if (fp64) {
                 P.nb_chunk = rt::bins_per_chunk(P.block, cfg.n_g, P.NBmax);
-                P.smem = rt::fp64_smem_bytes(P.block, P.Lmax, P.nb_chunk);
+                P.staged = staged_capacity(P.nl, P.nb, P.nb_chunk);
+                P.smem = rt::fp64_smem_bytes(P.block, P.Lmax, P.nb_chunk, P.staged);
                 occ = rt::occupancy(1, P.block, P.smem);
                 if (occ > 0) P.grid = (int)std::min<int64_t>(n, (int64_t)occ * h->sm_count);
             } else {
@@ -309,10 +322,12 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                 // unless 8 (half the transpose buffer) keep more CTAs
                 // resident: tall columns' staged B fills shared memory
                 P.group_shift = 4;
-                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4, P.inline_b, P.depth);
+                P.staged = P.direct ? 0 : staged_capacity(P.nl, P.nb, P.nbw);
+                P.smem = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 4, P.inline_b, P.depth, P.staged);
                 occ = rt::occupancy(0, P.block, P.smem, P.ns);
                 {
-                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3, P.inline_b, P.depth);
+                    const size_t sm8 = rt::fp32_smem_bytes(P.block, P.Lmax, P.nbw, P.direct, P.ns, 3, P.inline_b, P.depth,
+                                                           P.staged);
                     const int occ8 = rt::occupancy(0, P.block, sm8, P.ns);
                     const int cap = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 1 << 20;
                     if (std::min(occ8, cap) > std::min(occ, cap)) {
@@ -321,7 +336,8 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                         occ = occ8;
                     }
                 }
-                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift, P.inline_b, P.depth);
+                P.warp_floats = rt::fp32_warp_floats(P.Lmax, P.nbw, P.direct, P.ns, P.group_shift, P.inline_b, P.depth,
+                                                     P.staged);
                 const int64_t wpb = P.block / 32;
                 if (occ > 0) P.grid = (int)std::min<int64_t>((P.n_units + wpb - 1) / wpb, (int64_t)occ * h->sm_count);
             }
@@ -742,6 +758,7 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.toa = toa;
         kp.Lmax = P.Lmax;
         kp.nb_chunk = P.nb_chunk;
+        kp.staged = P.staged;
         kp.unit_col = d_ucol;
         kp.unit_k = d_uk;
         kp.col_units = d_cu;

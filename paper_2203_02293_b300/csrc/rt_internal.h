@@ -93,15 +93,19 @@ struct KParams {
     int32_t n_sweeps;            // 0: Thomas elimination; N > 0: N sweeps of the iterative method
     int32_t Lmax;                // largest L in this batch
     int32_t nb_chunk;            // bins covered by one chunk of systems (smem sizing)
+    int32_t staged;              // staged Planck values per warp (FP32) or CTA (FP64): the
+                                 // largest (2 L_c + 1) x (bins a chunk of column c covers)
     Extents ext;                 // array extents (checked in bounds-check builds)
 };
 
 // Shared memory needed per CTA for a given block size (bytes).
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth);
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth);
+// `staged`: the staged Planck values of one warp (shared staging).
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth,
+                       int staged);
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth, int staged);
 // Back-substitution prefetch depths with a kernel instance (kp.back_depth).
 constexpr int kBackDepthMin = 2, kBackDepthMax = 3;
-size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk);
+size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk, int staged);
 // Scratch bytes per thread slot.
 size_t fp32_scratch_per_slot(int Lmax);
 size_t fp64_scratch_per_slot(int Lmax, int isothermal);

@@ -602,17 +602,18 @@ __device__ __forceinline__ Layer32<V> layer32(V dt, V w0, V g0, V Bt, V Bc, V Bb
 // Shared-memory layout (both kernels):
 //   acc   double [2 (Lmax+1)]                  column sums (F_up, F_net)
 //   wpart R      [2 (Lmax+1) nwarps]            warp partial sums
-//   sB    R      [(2 Lmax + 1) nb_chunk]        Planck at levels (2i iface, 2i+1 centre)
+//   sB    R      [staged]                       Planck at levels (2i iface, 2i+1 centre),
+//                                               [(2 L + 1) nbc] of the current chunk
 //   sFs   R      [nb_chunk]                     stellar flux per bin
 //   sFB   R      [nb_chunk]                     F_BOA per bin
 //   stoa  R      [block]                        weighted TOA F_up per system
 // ---------------------------------------------------------------------
 template <typename R>
-__host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk) {
+__host__ __device__ inline size_t smem_bytes_t(int block, int Lmax, int nb_chunk, int staged) {
     const int nw = block / 32;
     size_t b = sizeof(double) * 2 * (size_t)(Lmax + 1);
     b += sizeof(R) * 2 * (size_t)(Lmax + 1) * nw;
-    b += sizeof(R) * (size_t)(2 * Lmax + 1) * nb_chunk;
+    b += sizeof(R) * (size_t)staged;
     b += sizeof(R) * 2 * (size_t)nb_chunk;
     b += sizeof(R) * (size_t)block;
     return b;
@@ -628,21 +629,26 @@ __host__ __device__ constexpr int back_ringB_floats(int ns, int inline_b, int de
     return inline_b ? (depth + 1) * ns * 32 : 0;
 }
 
-int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
-    // back-substitution ring + Planck [(2 Lmax + 1) nbw] (staged mode), or
+int fp32_warp_floats(int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth, int staged) {
+    // back-substitution ring + Planck [staged] (staged mode: the largest
+    // (2 L + 1) x bins-per-unit of the batch's columns), or
     // the column's 2 Lmax + 1 level temperatures in FP64 (inline B), or
     // nothing (direct) + F* [nbw] + F_BOA [nbw] + transpose [G][2][33],
     // G = 2^group_shift interfaces per transposed sum (at least 2 NS 32
     // floats for the TOA sum)
     const int tr = std::max((1 << group_shift) * 2 * 33, 64 * ns);
-    const int staged = !direct ? (2 * Lmax + 1) * nbw : inline_b ? 2 * (2 * Lmax + 1) : 0;
-    int n = back_ring_floats(ns, depth) + back_ringB_floats(ns, inline_b, depth) + staged + 2 * nbw + tr;
+    const int st = !direct ? staged : inline_b ? 2 * (2 * Lmax + 1) : 0;
+    int n = back_ring_floats(ns, depth) + back_ringB_floats(ns, inline_b, depth) + st + 2 * nbw + tr;
     return (n + 3) & ~3;
 }
-size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth) {
-    return sizeof(float) * (size_t)(block / 32) * fp32_warp_floats(Lmax, nbw, direct, ns, group_shift, inline_b, depth);
+size_t fp32_smem_bytes(int block, int Lmax, int nbw, int direct, int ns, int group_shift, int inline_b, int depth,
+                       int staged) {
+    return sizeof(float) * (size_t)(block / 32) *
+           fp32_warp_floats(Lmax, nbw, direct, ns, group_shift, inline_b, depth, staged);
 }
-size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk) { return smem_bytes_t<double>(block, Lmax, nb_chunk); }
+size_t fp64_smem_bytes(int block, int Lmax, int nb_chunk, int staged) {
+    return smem_bytes_t<double>(block, Lmax, nb_chunk, staged);
+}
 size_t fp32_scratch_per_slot(int Lmax) { return sizeof(float4) * (size_t)Lmax; }
 size_t fp64_scratch_per_slot(int Lmax, int isothermal) {
     const int nlev = isothermal ? Lmax : 2 * Lmax;
@@ -657,11 +663,11 @@ template <typename R>
 struct Smem {
     double *acc;
     R *wpart, *sB, *sFs, *sFB, *stoa;
-    __device__ Smem(unsigned char *raw, int Lmax, int nb_chunk, int nwarps) {
+    __device__ Smem(unsigned char *raw, int Lmax, int nb_chunk, int staged, int nwarps) {
         acc = reinterpret_cast<double *>(raw);
         wpart = reinterpret_cast<R *>(acc + 2 * (Lmax + 1));
         sB = wpart + 2 * (Lmax + 1) * nwarps;
-        sFs = sB + (2 * Lmax + 1) * nb_chunk;
+        sFs = sB + staged;
         sFB = sFs + nb_chunk;
         stoa = sFB + nb_chunk;
     }
@@ -1700,7 +1706,7 @@ __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KPara
     float4 *ring = reinterpret_cast<float4 *>(wsm);   // [DEP + 1][NS][32], back-substitution
     float *ringB = wsm + back_ring_floats(NS, DEP);   // inline B: [DEP + 1][32] x NS
     float *sB = ringB + back_ringB_floats(NS, ST == kStageInline, DEP);   // [nbc][2 L + 1] (bin, level), staged mode
-    float *sFs = sB + (ST == kStageShared ? (2 * kp.Lmax + 1) * nbw : ST == kStageInline ? 2 * (2 * kp.Lmax + 1) : 0);   // [nbc]
+    float *sFs = sB + (ST == kStageShared ? kp.staged : ST == kStageInline ? 2 * (2 * kp.Lmax + 1) : 0);   // [nbc]
     float *sFB = sFs + nbw;                        // [nbc]
     float *tb = sFB + nbw;                         // [G][2][33]
     // scratch slots: component i of this thread at slot + i * (threads in the grid)
@@ -2263,7 +2269,7 @@ __global__ void __launch_bounds__(kMaxBlock) fp64_columns(KParams kp) {
     __shared__ int s_unit;
     const int tid = threadIdx.x;
     const int nwarps = blockDim.x >> 5;
-    Smem<double> sm(smem_raw, kp.Lmax, kp.nb_chunk, nwarps);
+    Smem<double> sm(smem_raw, kp.Lmax, kp.nb_chunk, kp.staged, nwarps);
     const int NG = kp.n_g;
     const long long slot = (long long)blockIdx.x * blockDim.x + tid;
     double2 *scr = kp.scr64 + slot;           // element (2 lev + j) n_slots + slot

@@ -125,6 +125,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     const int64_t upc = (NB * NG + 31) / 32, nu = n * upc;
     if (nu > INT32_MAX) return RT_EBUDGET;
     const int nbw = rt::bins_per_chunk(32, (int)NG, (int)NB);
+    const int staged = (2 * (int)L + 1) * nbw;    // staged Planck values per warp (nbw <= NB already)
     size_t off = 0;
     const size_t o_cnt = off;     off += up(sizeof(int32_t));
     const size_t o_stats = off;   off += up(sizeof(unsigned long long) * rt::ST_COUNT);
@@ -164,7 +165,7 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     int grid = 0, block = 0;
     int64_t best = 0;
     for (int b = bmax; b >= 64; b -= 32) {
-        const size_t sm = rt::fp32_smem_bytes(b, (int)L, nbw, 0, 1, 4, 0, 2);
+        const size_t sm = rt::fp32_smem_bytes(b, (int)L, nbw, 0, 1, 4, 0, 2, staged);
         const int occ = rt::occupancy(0, b, sm);
         int64_t g = (int64_t)occ * sms;
         const int64_t by_scr = slots_fit / b;
@@ -274,7 +275,8 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.partial = (float *)(base + o_part);
     kp.col_done = done;
     kp.n_units = (int32_t)nu;
-    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0, 1, 4, 0, 2);
+    kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0, 1, 4, 0, 2, staged);
+    kp.staged = staged;
     kp.group_shift = 4;
     kp.back_depth = 2;
     kp.nbw = nbw;

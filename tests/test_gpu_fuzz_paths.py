@@ -107,3 +107,21 @@ def test_many_g_points_match_oracle(NG):
     got = gpu_solve(cols, opts, "fp64")
     assert_parity(cols, got, ref, "fp64", f"NG={NG} fp64 {opts}")
     check_counts(got, ref)
+
+
+def test_extreme_shapes_match_oracle():
+    """The ABI's limits: columns of 1024 layers (the staged Planck values of a
+    unit no longer fit beside the default launch) and 4096 bins, beside small
+    columns in the same batch."""
+    cols = rt_synth.generate([1024, 700, 3, 2], [2, 5, 4096, 1], 3, seed=8900, optics="uniform",
+                             mu_range=(-0.3, 1.0))
+    opts = method_opts()
+    ref = oracle_solve(cols, opts)
+    for spl in (1, 2):
+        for staging in (0, 1, 2, 3):
+            got = gpu_solve(cols, opts, "fp32", systems_per_lane=spl, planck_staging=staging)
+            assert_parity(cols, got, ref, "fp32", f"extreme shapes spl={spl} staging={staging}")
+            check_counts(got, ref)
+    got = gpu_solve(cols, opts, "fp64")
+    assert_parity(cols, got, ref, "fp64", "extreme shapes fp64")
+    check_counts(got, ref)
