@@ -96,3 +96,28 @@ def test_the_checks_count_and_skip_reads_past_a_declared_extent(checked, monkeyp
     assert got["stats"]["bounds_violations"] > 0
     monkeypatch.delenv("RT_BOUNDS_TEST_CUBE_EXTENT")
     assert gpu_solve(cols, method_opts(), "fp32")["stats"]["bounds_violations"] == 0
+
+
+@pytest.mark.parametrize("i", range(12))
+def test_random_batches_under_bounds_checks(checked, i):
+    """Seeded random batches (ragged shapes up to the ABI's 64 g-points, the
+    three optics families, night side, every launch variant of the FP32 form
+    and the sweep method) read zero violations and keep their parity."""
+    rng = np.random.default_rng(9100 + i)
+    n_cols = int(rng.integers(1, 9))
+    L = rng.integers(1, 41, n_cols)
+    NB = rng.integers(1, 33, n_cols)
+    NG = int(rng.choice([1, 3, 20, 33, 64]))
+    optics = str(rng.choice(["uniform", "ktable", "stress"]))
+    cols = rt_synth.generate(L, NB, NG, seed=9200 + i, optics=optics, mu_range=(-0.3, 1.0))
+    opts = method_opts(isothermal=bool(rng.integers(0, 2)), resonance=str(rng.choice(["paper", "limit"])))
+    ref = oracle_solve(cols, opts)
+    runs = [("fp32", dict(systems_per_lane=spl, planck_staging=st)) for spl in (1, 2) for st in (0, 1, 2, 3)]
+    runs += [("fp32", dict(n_sweeps=int(rng.choice([1, 5])))), ("fp64", {})]
+    for precision, kw in runs:
+        if precision == "fp64" and optics == "stress":
+            continue
+        got = gpu_solve(cols, opts, precision, **kw)
+        _zero(got)
+        if "n_sweeps" not in kw:
+            assert_parity(cols, got, ref, precision, f"checked random {i} {kw}")
