@@ -1306,12 +1306,28 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         const float *Bg = kp.planck32 + kp.planck_off[c] + b_lo;
         const int nlev = 2 * L + 1;
         if constexpr (!DIRECT) {
-            for (int i = lane; i < nlev * nbc; i += 32) {
-                const int lev = i / nbc, bb = i - lev * nbc;
-                const float *pb = Bg + (long long)lev * NB + bb;
-                float *dst = sB + bb * nlev + lev;    // [bin][level]: unit level stride
-                if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(dst, pb);
-                else *dst = 0.f;
+            // [bin][level]: unit level stride.  With at most 32 bins, lane
+            // (lev0, bb) takes bin bb at levels lev0, lev0 + per, ... (one
+            // division per unit instead of one per element)
+            if (nbc <= 32) {
+                const int per = 32 / nbc, lev0 = lane / nbc, bb = lane - lev0 * nbc;
+                if (lev0 < per) {
+                    const float *pb = Bg + (long long)lev0 * NB + bb;
+                    const long long step = (long long)per * NB;
+                    float *dst = sB + bb * nlev;
+                    for (int lev = lev0; lev < nlev; lev += per, pb += step) {
+                        if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(dst + lev, pb);
+                        else dst[lev] = 0.f;
+                    }
+                }
+            } else {
+                for (int i = lane; i < nlev * nbc; i += 32) {
+                    const int lev = i / nbc, bb = i - lev * nbc;
+                    const float *pb = Bg + (long long)lev * NB + bb;
+                    float *dst = sB + bb * nlev + lev;
+                    if (RT_IN(pb, kp.planck32, kp.ext.planck)) cp_async4(dst, pb);
+                    else *dst = 0.f;
+                }
             }
         }
         if constexpr (INL) {
