@@ -71,7 +71,7 @@ struct rt_handle {
     cudaEvent_t stage_ev = nullptr;
     bool stage_pending = false;
     // outputs and scratch
-    DevBuf out, scr, aux;          // aux: FP32 unit partials + per-column completion counters
+    DevBuf out, scr, aux;          // aux: FP32 unit partials, Planck table, per-bin and per-column data
     int32_t *d_counter = nullptr;
     unsigned long long *d_stats = nullptr;
     cudaEvent_t done_ev = nullptr;
@@ -365,9 +365,9 @@ int build_plan(rt_handle *h, const rt_columns *c, Plan &P, bool kt, bool units =
                                                        : rt::fp32_scratch_per_slot(P.Lmax));
     // inline B: the interfaces' B for the back-substitution, after the elimination scratch
     if (P.inline_b) P.scr_bytes = align_up(P.scr_bytes, 256) + sizeof(float) * (size_t)P.n_slots * P.Lmax;
-    // FP32 aux: partial | col_done | planck32 | fs32 | fboa32 | colf [| kt_lay]
+    // FP32 aux: partial | planck32 | fs32 | fboa32 | colf [| kt_lay]
     P.aux_bytes = fp64 ? 0
-                       : align_up(sizeof(float) * (size_t)P.n_part, 256) + align_up(sizeof(int32_t) * (size_t)n, 256) +
+                       : align_up(sizeof(float) * (size_t)P.n_part, 256) +
                              align_up(sizeof(float) * (size_t)P.n_planck, 256) +
                              2 * align_up(sizeof(float) * (size_t)P.n_bins, 256) + align_up(sizeof(float4) * (size_t)n, 256) +
                              (kt ? align_up(sizeof(float4) * (size_t)P.n_lay, 256) : 0);
@@ -685,15 +685,12 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         if (e == cudaSuccess && P.n_bins) e = cudaMemsetAsync(toa, 0, sizeof(double) * (size_t)P.n_bins, s);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_counter, 0, sizeof(int32_t), s);
-    int32_t *d_done = nullptr;
     float *d_part = nullptr, *d_planck = nullptr, *d_fs = nullptr, *d_fboa = nullptr;
     float4 *d_colf = nullptr, *d_klay = nullptr;
     if (P.aux_bytes) {
         char *a = (char *)h->aux.p;
         d_part = (float *)a;
         a += align_up(sizeof(float) * (size_t)P.n_part, 256);
-        d_done = (int32_t *)a;
-        a += align_up(sizeof(int32_t) * (size_t)n, 256);
         d_planck = (float *)a;
         a += align_up(sizeof(float) * (size_t)P.n_planck, 256);
         d_fs = (float *)a;
@@ -703,7 +700,6 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         d_colf = (float4 *)a;
         a += align_up(sizeof(float4) * (size_t)n, 256);
         if (P.kt) d_klay = (float4 *)a;
-        if (e == cudaSuccess && !optics_out) e = cudaMemsetAsync(d_done, 0, sizeof(int32_t) * (size_t)n, s);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
 
@@ -764,7 +760,6 @@ int solve_impl(rt_handle *h, const rt_columns *cols, void *stream, bool kt, floa
         kp.col_units = d_cu;
         kp.part_off = d_poff;
         kp.partial = d_part;
-        kp.col_done = d_done;
         kp.n_units = (int32_t)P.n_units;
         kp.warp_floats = P.warp_floats;
         kp.group_shift = P.group_shift;

@@ -57,7 +57,6 @@ struct KParams {
     const int32_t *col_units;    // [n_cols] units per column
     const int64_t *part_off;     // [n_cols] offset of the column's partial sums
     float *partial;              // per unit and interface: (sum w F_up, sum w F_net)
-    int32_t *col_done;           // [n_cols] finished units per column (zeroed per solve)
     int32_t n_units;
     int32_t warp_floats;         // shared-memory floats per warp
     int32_t group_shift;         // FP32 form: log2 of the interfaces per transposed sum (3 or 4)

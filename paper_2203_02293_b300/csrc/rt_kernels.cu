@@ -20,8 +20,10 @@
 //                    forms, a beam source with the removable singularity at
 //                    mu* alpha = 1 divided out, departure variables u = F - pi
 //                    B, merged sub-layers; FP64 only to decide the paper's
-//                    resonance switch near |D| = 1e-5.  The warp that finishes
-//                    a column's last unit writes the column.
+//                    resonance switch near |D| = 1e-5.  Each unit leaves its
+//                    weighted interface sums as partials.
+//   fp32_finalize    one warp per column: the units' partials summed in unit
+//                    order (FP64) into fluxes, net flux and heating.
 //   kt_optics_kernel the input front end alone (k-table interpolation and
 //                    mixing), writing optics cubes.
 //   fp64_columns     FP64 with the paper's literal formulas, one CTA per
@@ -783,9 +785,9 @@ __device__ __forceinline__ void write_column(const KParams &kp, const ColInfo &c
 // warp stages the B values of the bins its systems touch into its own slice
 // of shared memory, each lane solves one system, and the weighted interface
 // fluxes of the 32 lanes are summed through a padded shared-memory
-// transpose (16 interfaces at a time).  The warp that finishes the last unit
-// of a column sums the column's unit partials in unit order (FP64) and
-// writes fluxes, net flux and heating.
+// transpose (16 interfaces at a time), stored as the unit's partials;
+// fp32_finalize then sums each column's unit partials in unit order (FP64)
+// and writes fluxes, net flux and heating.
 // ---------------------------------------------------------------------
 // One (column, level) per warp: lane e evaluates the Planck integral at bin
 // edge e (whichever of S(x) or P(x) that edge needs), and bin b takes edges b
@@ -1177,6 +1179,18 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
                                  ck_ld(kp, kp.p_iface, kp.ext.iface, kp.if_off[c] + l));
         ck_st(kp, kp.Q, kp.ext.out_lay, kp.lay_off[c] + l, (double)(gc * (float)dF * frcp(dp)));
     }
+}
+
+// The columns' outputs, launched after the unit kernel on the same stream (so
+// every unit's partials are written): each warp takes columns in turn and sums
+// their unit partials in unit order.  Forming them here rather than in the
+// warp that finishes a column's last unit spares every unit a device-wide
+// memory fence and a returning atomic.
+__global__ void __launch_bounds__(128) fp32_finalize(KParams kp) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int c = w; c < kp.n_cols; c += nw) finalize_column(kp, c, lane);
 }
 
 // Where the solve kernel gets a system's B at the levels: staged per unit in
@@ -1697,15 +1711,8 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
         __syncwarp();
     }
 
-    // the warp that completes a column's last unit writes the column
-    __threadfence();
-    int done = 0;
-    if (lane == 0 && RT_IN(kp.col_done + c, kp.col_done, kp.ext.cols)) done = atomicAdd(kp.col_done + c, 1);
-    done = __shfl_sync(0xffffffffu, done, 0);
-    if (done == kp.col_units[c] - 1) {
-        __threadfence();
-        finalize_column(kp, c, lane);
-    }
+    // (the column's outputs are formed from the units' partials by
+    // fp32_finalize, after every unit of the launch)
     __syncwarp();
 }
 
@@ -2147,15 +2154,7 @@ __device__ __forceinline__ void sweep_unit(const KParams &kp, int unit, int lane
     }
     __syncwarp();
 
-    // the warp that completes a column's last unit writes the column
-    __threadfence();
-    int done = 0;
-    if (lane == 0 && RT_IN(kp.col_done + q.c, kp.col_done, kp.ext.cols)) done = atomicAdd(kp.col_done + q.c, 1);
-    done = __shfl_sync(0xffffffffu, done, 0);
-    if (done == kp.col_units[q.c] - 1) {
-        __threadfence();
-        finalize_column(kp, q.c, lane);
-    }
+    // (the column's outputs: fp32_finalize, after every unit of the launch)
     __syncwarp();
 }
 
@@ -2502,6 +2501,14 @@ constexpr std::array<UnitsLaunch, sizeof...(I)> units_table(std::integer_sequenc
 }
 constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, kUnitsInstances>{});
 
+// the columns' outputs after the unit (or sweep) kernel: one warp per column,
+// up to 16 four-warp CTAs per SM
+static cudaError_t launch_finalize(const KParams &kp, cudaStream_t s) {
+    const int g = (kp.n_cols + 3) / 4, cap = 16 * 148;
+    fp32_finalize<<<g < cap ? g : cap, 128, 0, s>>>(kp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
                         cudaEvent_t const *ev) {
     // pre-kernel: 4-warp CTAs when it tabulates B at every level (more columns in flight),
@@ -2520,6 +2527,8 @@ cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cud
     const int sel = (kp.isothermal ? 1 : 0) + 2 * st + (kp.kt_lk ? 6 : 0) + (kp.ns == 2 ? 12 : 0) + 24 * (dep - kBackDepthMin);
     kUnitsLaunch[sel](kp, grid, block, smem, s);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_finalize(kp, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;
 }
@@ -2540,6 +2549,8 @@ cudaError_t launch_sweeps(const KParams &kp, int grid, int block, size_t smem, c
         else fp32_sweeps<false, false><<<grid, block, smem, s>>>(kp);
     }
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_finalize(kp, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     return e;
 }

@@ -129,7 +129,6 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     size_t off = 0;
     const size_t o_cnt = off;     off += up(sizeof(int32_t));
     const size_t o_stats = off;   off += up(sizeof(unsigned long long) * rt::ST_COUNT);
-    const size_t o_done = off;    off += up(sizeof(int32_t) * n);
     const size_t o_part = off;    off += up(sizeof(float) * nu * 2 * (L + 1));
     const size_t o_planck = off;  off += up(sizeof(float) * n * (2 * L + 1) * NB);
     const size_t o_fs = off;      off += up(sizeof(float) * n * NB);
@@ -186,15 +185,13 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     cudaStream_t s = (cudaStream_t)stream;
     int32_t *counter = (int32_t *)(base + o_cnt);
     unsigned long long *stats = (unsigned long long *)(base + o_stats);
-    int32_t *done = (int32_t *)(base + o_done);
     int32_t *i32 = (int32_t *)(base + o_i32);
     int64_t *i64 = (int64_t *)(base + o_i64);
 
-    // everything that must start at zero: work counter, branch counters,
-    // per-column completion counters (the array keeps the last call's data)
+    // everything that must start at zero: work counter and branch counters
+    // (the array keeps the last call's data)
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * rt::ST_COUNT, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, sizeof(int32_t) * n, s);
     if (e != cudaSuccess) return RT_ECUDA;
 
     UniformPlan a{};
@@ -273,7 +270,6 @@ extern "C" int rt_solve_uniform_noalloc(const rt_config *cfg, const rt_columns *
     kp.col_units = a.cu;
     kp.part_off = a.part;
     kp.partial = (float *)(base + o_part);
-    kp.col_done = done;
     kp.n_units = (int32_t)nu;
     kp.warp_floats = rt::fp32_warp_floats((int)L, nbw, 0, 1, 4, 0, 2, staged);
     kp.staged = staged;
