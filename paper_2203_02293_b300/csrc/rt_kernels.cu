@@ -1157,24 +1157,38 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     const long long if0 = kp.lay_off[c] + c;
     const float *part = kp.partial + kp.part_off[c];
     const int stride = 2 * (L + 1);
-    // unit partials are read through L2 (other SMs wrote them)
-    auto sum = [&](int i, int qq) {
-        double a = 0.0;
-        for (int uidx = 0; uidx < nu; ++uidx) {
-            const float *pp = part + (long long)uidx * stride + 2 * i + qq;
-            a += RT_IN(pp, kp.partial, kp.ext.part) ? (double)__ldcg(pp) : 0.0;
-        }
-        return a;
+    // Unit partials, read through L2 (other SMs wrote them), are summed in
+    // unit order as unevaluated FP32 pairs hi + lo: Knuth's TwoSum gives each
+    // addition's rounding error exactly, so hi + lo, formed once in FP64,
+    // carries the sum to about eps_f^2 of the summands' magnitudes (an FP64
+    // accumulation would run on B300's FP64 units, a small fraction of the
+    // FP32 rate, once per unit and interface).
+    auto acc = [](float &hi, float &lo, float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bx = __fadd_rn(s, -hi);
+        const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bx)), __fadd_rn(x, -bx));
+        hi = s;
+        lo = __fadd_rn(lo, e);
     };
     for (int i = lane; i <= L; i += 32) {
-        const double up = sum(i, 0), net = sum(i, 1);
+        float uh = 0.f, ul = 0.f, nh = 0.f, nl = 0.f;
+        for (int uidx = 0; uidx < nu; ++uidx) {
+            const float *pp = part + (long long)uidx * stride + 2 * i;     // (w F_up, w F_net), 8-byte aligned
+            const float2 v = RT_IN(pp + 1, kp.partial, kp.ext.part) ? __ldcg(reinterpret_cast<const float2 *>(pp))
+                                                                     : make_float2(0.f, 0.f);
+            acc(uh, ul, v.x);
+            acc(nh, nl, v.y);
+        }
+        const double up = (double)uh + (double)ul, net = (double)nh + (double)nl;
         ck_st(kp, kp.F_up, kp.ext.out_if, if0 + i, up);
         ck_st(kp, kp.F_net, kp.ext.out_if, if0 + i, net);
         ck_st(kp, kp.F_dn, kp.ext.out_if, if0 + i, up - net);
     }
+    __syncwarp();        // (orders the warp's F_net stores before the loads below)
     const float gc = (float)(kp.grav / kp.cp);
     for (int l = lane; l < L; l += 32) {
-        const double dF = sum(l + 1, 1) - sum(l, 1);
+        const double dF = ck_ld(kp, (const double *)kp.F_net, kp.ext.out_if, if0 + l + 1) -
+                          ck_ld(kp, (const double *)kp.F_net, kp.ext.out_if, if0 + l);
         const float dp = (float)(ck_ld(kp, kp.p_iface, kp.ext.iface, kp.if_off[c] + l + 1) -
                                  ck_ld(kp, kp.p_iface, kp.ext.iface, kp.if_off[c] + l));
         ck_st(kp, kp.Q, kp.ext.out_lay, kp.lay_off[c] + l, (double)(gc * (float)dF * frcp(dp)));
