@@ -77,19 +77,6 @@ __device__ constexpr double kS28 = BC(-23749461029.0, 870, 3.0488834461171386e29
 __device__ constexpr double kS30 = BC(8615841276005.0, 14322, 2.6525285981219105e32, 30);
 #undef BC
 
-// FP32: S(x) for x <= 2 (terms to k = 14, relative error < 1e-7).
-__device__ __forceinline__ float planck_lower_f(float x) {
-    const float x2 = x * x;
-    float s = (float)kS14;
-    s = fmaf(s, x2, (float)kS12);
-    s = fmaf(s, x2, (float)kS10);
-    s = fmaf(s, x2, (float)kS8);
-    s = fmaf(s, x2, (float)kS6);
-    s = fmaf(s, x2, (float)kS4);
-    const float head = fmaf(x, fmaf(x, (float)kS2, (float)kS1), (float)kS0);
-    return fmaf(x2 * x2, s, head) * x2 * x;
-}
-
 // Fast FP32 primitives: MUFU reciprocal, reciprocal square root and
 // exponential (exp(x) = 2^(x log2 e), the PTX ex2 after one multiply).  Each
 // is accurate to a few ulp, far inside the 1e-4 target.  The flush-to-zero
@@ -101,7 +88,6 @@ __device__ __forceinline__ float frcp(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ float fex2(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -113,25 +99,6 @@ __device__ __forceinline__ float frsqrt(float x) {
     return r;
 }
 constexpr float kLog2E = 1.44269504088896340736f;
-
-// FP32: P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
-//   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms,
-// regrouped as e (x^3 A1 + 3 x^2 A2 + 6 x A3 + 6 A4) with
-// A_k = sum_n e^(n-1) / n^k evaluated by Horner in e = e^-x <= e^-2.
-__device__ __forceinline__ float planck_upper_f(float x) {
-    const float e = fexp(-x);
-    float a1 = 1.f / 8.f, a2 = 1.f / 64.f, a3 = 1.f / 512.f, a4 = 1.f / 4096.f;
-#pragma unroll
-    for (int n = 7; n >= 1; --n) {
-        const float y = 1.0f / (float)n;
-        a1 = fmaf(a1, e, y);
-        a2 = fmaf(a2, e, y * y);
-        a3 = fmaf(a3, e, y * y * y);
-        a4 = fmaf(a4, e, y * y * y * y);
-    }
-    const float poly = fmaf(x * x, fmaf(x, a1, 3.f * a2), fmaf(6.f * x, a3, 6.f * a4));
-    return e * poly;
-}
 
 // FP64 versions (terms to k = 30 below x = 2, 20 exponential terms above).
 __device__ __forceinline__ double planck_lower_d(double x) {
@@ -336,6 +303,45 @@ __device__ __forceinline__ unsigned vmasked(unsigned c, bool on) { return on ? c
 __device__ __forceinline__ unsigned vmasked(U2 c, M2 on) { return (on.x ? c.x : 0u) + (on.y ? c.y : 0u); }
 __device__ __forceinline__ unsigned vmasked(bool m, bool on) { return (m && on) ? 1u : 0u; }
 __device__ __forceinline__ unsigned vmasked(M2 m, M2 on) { return (m.x && on.x ? 1u : 0u) + (m.y && on.y ? 1u : 0u); }
+
+// FP32 series for the bin-integrated Planck function, written over V (one
+// value, or two on the paired instructions: every component rounds as the
+// scalar form does, so a pair of levels gives the scalar bits).
+// S(x) for x <= 2 (terms to k = 14, relative error < 1e-7).
+template <class V>
+__device__ __forceinline__ V planck_lower_v(V x) {
+    const V x2 = x * x;
+    V s = V((float)kS14);
+    s = vfma(s, x2, V((float)kS12));
+    s = vfma(s, x2, V((float)kS10));
+    s = vfma(s, x2, V((float)kS8));
+    s = vfma(s, x2, V((float)kS6));
+    s = vfma(s, x2, V((float)kS4));
+    const V head = vfma(x, vfma(x, V((float)kS2), V((float)kS1)), V((float)kS0));
+    return (vfma(x2 * x2, s, head) * x2) * x;
+}
+
+// P(x) = integral_x^inf t^3/(e^t-1) dt for x >= 2 as
+//   sum_n e^(-n x) (x^3/n + 3 x^2/n^2 + 6 x/n^3 + 6/n^4), 8 terms,
+// regrouped as e (x^3 A1 + 3 x^2 A2 + 6 x A3 + 6 A4) with
+// A_k = sum_n e^(n-1) / n^k evaluated by Horner in e = e^-x <= e^-2.
+template <class V>
+__device__ __forceinline__ V planck_upper_v(V x) {
+    const V e = vexpn(x);
+    V a1 = V(1.f / 8.f), a2 = V(1.f / 64.f), a3 = V(1.f / 512.f), a4 = V(1.f / 4096.f);
+#pragma unroll
+    for (int n = 7; n >= 1; --n) {
+        const float y = 1.0f / (float)n;
+        a1 = vfma(a1, e, V(y));
+        a2 = vfma(a2, e, V(y * y));
+        a3 = vfma(a3, e, V(y * y * y));
+        a4 = vfma(a4, e, V(y * y * y * y));
+    }
+    const V poly = vfma(x * x, vfma(x, a1, V(3.f) * a2), vfma(V(6.f) * x, a3, V(6.f) * a4));
+    return e * poly;
+}
+__device__ __forceinline__ float planck_lower_f(float x) { return planck_lower_v(x); }
+__device__ __forceinline__ float planck_upper_f(float x) { return planck_upper_v(x); }
 
 template <class V> struct VTraits;
 template <> struct VTraits<float> {
@@ -924,10 +930,17 @@ __device__ __forceinline__ void planck_chunk_levels(const float (&T)[NQ], const 
     }
     // the edge series only when some bin of this chunk is wide
     if (!__all_sync(0xffffffffu, alln)) {
+        // two levels per paired evaluation (the same bits as one at a time)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float lo = planck_lower_f(x[q]), up = planck_upper_f(x[q]);
-            v[q] = (x[q] < 2.f) ? lo : up;
+        for (int q = 0; q + 1 < NQ; q += 2) {
+            const V2 xq(x[q], x[q + 1]);
+            const V2 lo = planck_lower_v(xq), up = planck_upper_v(xq);
+            v[q] = (x[q] < 2.f) ? lo.v.x : up.v.x;
+            v[q + 1] = (x[q + 1] < 2.f) ? lo.v.y : up.v.y;
+        }
+        if constexpr (NQ & 1) {
+            const float lo = planck_lower_f(x[NQ - 1]), up = planck_upper_f(x[NQ - 1]);
+            v[NQ - 1] = (x[NQ - 1] < 2.f) ? lo : up;
         }
     } else {
 #pragma unroll
@@ -1034,7 +1047,7 @@ __device__ __forceinline__ Corners kt_corners(const KParams &kp, float4 l4, int 
 // from the shared temperatures; the runs are short enough that every warp
 // has work when a column has few bins.  Level 2L+1 stands for T_int (F_BOA =
 // pi B(T_int), Eq. 10).
-__global__ void __launch_bounds__(256) fp32_prep(KParams kp) {
+__global__ void __launch_bounds__(256, 4) fp32_prep(KParams kp) {
     extern __shared__ float sT[];                 // [2 Lmax + 2] temperatures of one column, then T_int
     double *sG = (double *)(sT + 2 * kp.Lmax + 2);  // k-table T and log10 p grids (binary searches)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1172,12 +1185,21 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
     };
     for (int i = lane; i <= L; i += 32) {
         float uh = 0.f, ul = 0.f, nh = 0.f, nl = 0.f;
-        for (int uidx = 0; uidx < nu; ++uidx) {
-            const float *pp = part + (long long)uidx * stride + 2 * i;     // (w F_up, w F_net), 8-byte aligned
-            const float2 v = RT_IN(pp + 1, kp.partial, kp.ext.part) ? __ldcg(reinterpret_cast<const float2 *>(pp))
-                                                                     : make_float2(0.f, 0.f);
-            acc(uh, ul, v.x);
-            acc(nh, nl, v.y);
+        // eight units' loads in flight, then their sums in unit order (a
+        // zero past the last unit leaves hi and lo as they are)
+        for (int u0 = 0; u0 < nu; u0 += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float *pp = part + (long long)(u0 + k) * stride + 2 * i;   // (w F_up, w F_net), 8-byte aligned
+                v[k] = (u0 + k < nu && RT_IN(pp + 1, kp.partial, kp.ext.part))
+                           ? __ldcg(reinterpret_cast<const float2 *>(pp)) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc(uh, ul, v[k].x);
+                acc(nh, nl, v[k].y);
+            }
         }
         const double up = (double)uh + (double)ul, net = (double)nh + (double)nl;
         ck_st(kp, kp.F_up, kp.ext.out_if, if0 + i, up);
