@@ -942,7 +942,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                 "pipelining": "two buffers, handles and streams: step k+1's copy overlaps step k's solve"},
-        "gpu_launches": 2 * args.steps,      # Planck pre-kernel + solve kernel per step
+        "gpu_launches": 3 * args.steps,      # Planck pre-kernel, solve kernel and finalize kernel per step
         "roofline": roofline,
         "clocks": clk.summary(),
         "branch_counts": {**stats, "resonance_mode": "paper (|D| < 1e-5: D := 2 mu*)"},
