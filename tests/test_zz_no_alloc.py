@@ -103,3 +103,40 @@ def test_noalloc_refuses_batches_beyond_its_scratch():
             rt.rt_solve_uniform_noalloc(bad, desc, *outs)
         assert e.value.code == rt.RT_EINVAL
     assert torch.all(outs[0] == 1.0)
+
+
+def test_noalloc_allocates_nothing_and_replays_from_a_cuda_graph():
+    """What the entry point is for: after the first call on the device (which
+    looks up the fixed array's address and sets the kernels' shared-memory
+    limits), repeated calls leave the free device memory as it was (a device
+    allocation reserves at least a 2 MiB page), and the call can be captured
+    into a CUDA graph whose replay writes the direct call's outputs bit for
+    bit."""
+    L, NB = 17, 9
+    cols = rt_synth.generate([L] * 33, [NB] * 33, 20, seed=74, optics="uniform")
+    b = DeviceBatch(cols)
+    desc = _uniform_desc(b, L, NB)
+    cfg = rt.Config(g_weights=cols.g_weights)
+    outs = [torch.zeros(b.n_if, dtype=torch.float64, device="cuda") for _ in range(3)]
+    outs.append(torch.zeros(b.n_lay, dtype=torch.float64, device="cuda"))
+    rt.rt_solve_uniform_noalloc(cfg, desc, *outs)
+    torch.cuda.synchronize()
+    direct = [o.clone() for o in outs]
+    assert all(torch.isfinite(o).all() for o in direct)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rt.rt_solve_uniform_noalloc(cfg, desc, *outs)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (1 << 20)
+    assert all(torch.equal(o, d) for o, d in zip(outs, direct))
+
+    for o in outs:
+        o.fill_(float("nan"))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rt.rt_solve_uniform_noalloc(cfg, desc, *outs, stream=s)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(o, d) for o, d in zip(outs, direct))
