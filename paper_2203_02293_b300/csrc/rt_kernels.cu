@@ -1164,6 +1164,12 @@ __global__ void __launch_bounds__(256, 4) fp32_prep(KParams kp) {
     }
 }
 
+// A kernel launched with programmatic stream serialization may start while
+// the previous kernel on its stream finishes; this waits until that kernel
+// has completed and its memory writes are visible (a no-op for a kernel
+// launched without the attribute).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ void finalize_column(const KParams &kp, int c, int lane) {
     const int L = kp.n_layers[c];
     const int nu = kp.col_units[c];
@@ -1223,6 +1229,7 @@ __device__ void finalize_column(const KParams &kp, int c, int lane) {
 // warp that finishes a column's last unit spares every unit a device-wide
 // memory fence and a returning atomic.
 __global__ void __launch_bounds__(128) fp32_finalize(KParams kp) {
+    grid_dependency_wait();
     const int lane = threadIdx.x & 31;
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -1756,6 +1763,7 @@ __device__ __forceinline__ void fp32_unit(const KParams &kp, int unit, int lane,
 // (kp.back_depth; one instance per offered depth).
 template <bool ISO, int ST, bool KT, int NS, int DEP>
 __global__ void __launch_bounds__(kMaxBlock32, NS == 2 ? 2 : 3) fp32_units(KParams kp) {
+    grid_dependency_wait();                        // the pre-kernel's tables
     constexpr int SPG = 32 * NS;                   // unit stride within a column
     extern __shared__ __align__(16) float smem32[];
     const int lane = threadIdx.x & 31;
@@ -2526,9 +2534,28 @@ int occupancy(int precision_fp64, int block, size_t smem, int ns, int sweeps) {
 }
 
 // fp32_units instantiations, indexed by isothermal + 2 stage + 6 k-table + 12 (two systems per lane)
+// Launch with programmatic stream serialization: the kernel's CTAs may be
+// scheduled while the previous kernel on the stream drains; the kernel
+// waits (grid_dependency_wait) before it reads that kernel's output.
+template <class... A>
+static cudaError_t launch_after_previous(void (*f)(A...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                         const KParams &kp) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, f, kp);
+}
+
 template <int SEL>
 void units_launch(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s) {
-    units_kernel<SEL>()<<<grid, block, smem, s>>>(kp);
+    launch_after_previous(units_kernel<SEL>(), dim3(grid), dim3(block), smem, s, kp);
 }
 using UnitsLaunch = void (*)(const KParams &, int, int, size_t, cudaStream_t);
 template <int... I>
@@ -2541,8 +2568,8 @@ constexpr auto kUnitsLaunch = units_table(std::make_integer_sequence<int, kUnits
 // up to 16 four-warp CTAs per SM
 static cudaError_t launch_finalize(const KParams &kp, cudaStream_t s) {
     const int g = (kp.n_cols + 3) / 4, cap = 16 * 148;
-    fp32_finalize<<<g < cap ? g : cap, 128, 0, s>>>(kp);
-    return cudaGetLastError();
+    const cudaError_t e = launch_after_previous(fp32_finalize, dim3(g < cap ? g : cap), dim3(128), 0, s, kp);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_fp32(const KParams &kp, int grid, int block, size_t smem, cudaStream_t s,
